@@ -1,0 +1,746 @@
+/*
+ * tc_oracle.c -- plain FP64 CPU oracle of the treecode force phase.
+ *
+ * TEST INFRASTRUCTURE ONLY (see tc_oracle.h).  Slow and direct on purpose:
+ * every quantity is computed from its definition, in the order the paper
+ * describes the method (Sec. 3.1): build the oct-tree by recursive
+ * subdivision, give every cell its mass and centre of mass, walk the tree
+ * from the root building an interaction list, loop over the list with the
+ * force law, then move the bodies.
+ *
+ * Readings of what the paper leaves open (it names no bounding box, key,
+ * threshold rule, opening test, softening or integrator):
+ *   R1 root cube: a power-of-two cube on a 2^21 grid, so that every cell
+ *      corner is an exact binary fraction (or_root_cube).
+ *   R2 subdivision: a cube is split while it holds MORE than leaf_max
+ *      bodies and is above level 21; empty sub-cubes are not kept.
+ *   R3 bodies sharing a leaf are ordered by Morton key, then by original
+ *      index (a stable sort).
+ *   R4 groups: contiguous runs of at most gmax bodies that share one walk
+ *      (or_tree_make_groups).
+ *   R5 "distant enough": a cell of side s whose centre of mass lies at
+ *      distance d from the group's bounding box is accepted iff it holds
+ *      none of the group's bodies and s < theta * d.
+ *   R6 force law with Plummer softening eps:
+ *      a_i = G sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2).
+ *   R7 kick-drift-kick leapfrog.
+ */
+#include "tc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* R1: root cube.                                                      */
+/* The cube side is the smallest power of two L with                   */
+/* L >= extent * (1 + 2^-20), extent the largest axis range; the grid  */
+/* step is h = L / 2^21 and the corner c0 = floor(min / h) * h on each */
+/* axis.  With this choice the largest body still falls strictly       */
+/* inside the cube (extent <= L - 2h and c0 > min - h).                */
+/* ------------------------------------------------------------------ */
+static double next_pow2(double t)
+{
+    int e;
+    double m = frexp(t, &e); /* t = m * 2^e, m in [0.5, 1) */
+    if (m == 0.5)
+        return t;
+    return ldexp(1.0, e);
+}
+
+int or_root_cube(const float *pos, int64_t n, double *out5)
+{
+    if (n < 1)
+        return -1;
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        for (int a = 0; a < 3; a++) {
+            double x = (double)pos[3 * i + a];
+            if (!isfinite(x))
+                return -1;
+            if (x < lo[a])
+                lo[a] = x;
+            if (x > hi[a])
+                hi[a] = x;
+        }
+    }
+    double extent = 0.0;
+    for (int a = 0; a < 3; a++)
+        if (hi[a] - lo[a] > extent)
+            extent = hi[a] - lo[a];
+    double target = extent * (1.0 + ldexp(1.0, -20));
+    double L = (target > 0.0) ? next_pow2(target) : 1.0; /* all bodies coincide: unit cube */
+    double h = L / 2097152.0;                             /* 2^21 */
+    for (int a = 0; a < 3; a++)
+        out5[a] = floor(lo[a] / h) * h;
+    out5[3] = L;
+    out5[4] = h;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Morton keys.  Each coordinate is quantised to a 21-bit cell index   */
+/* q = floor((x - c0) / h), clamped to [0, 2^21 - 1]; the key takes    */
+/* one bit of each axis per level, most significant level first, with  */
+/* the x bit highest in each 3-bit digit.  The digit at level l        */
+/* (1..21) is the octant (4*xbit + 2*ybit + zbit) of the level-l cube  */
+/* inside its parent.                                                  */
+/* ------------------------------------------------------------------ */
+static uint64_t quantise(double x, double c0, double h)
+{
+    double q = floor((x - c0) / h);
+    if (q < 0.0)
+        q = 0.0;
+    if (q > 2097151.0)
+        q = 2097151.0;
+    return (uint64_t)q;
+}
+
+void or_keys(const float *pos, int64_t n, const double *cube5, uint64_t *keys)
+{
+    for (int64_t i = 0; i < n; i++) {
+        uint64_t q[3];
+        for (int a = 0; a < 3; a++)
+            q[a] = quantise((double)pos[3 * i + a], cube5[a], cube5[4]);
+        uint64_t k = 0;
+        for (int b = 20; b >= 0; b--) {
+            uint64_t digit = (((q[0] >> b) & 1u) << 2) | (((q[1] >> b) & 1u) << 1) | ((q[2] >> b) & 1u);
+            k = (k << 3) | digit;
+        }
+        keys[i] = k;
+    }
+}
+
+static int digit_at(uint64_t key, int level) /* level 1..21 */
+{
+    return (int)((key >> (3 * (OR_MAX_LEVEL - level))) & 7u);
+}
+
+/* ------------------------------------------------------------------ */
+/* Tree storage.                                                       */
+/* ------------------------------------------------------------------ */
+struct or_tree {
+    int64_t n;
+    int leaf_max;
+    double cube[5];
+    uint64_t *keys; /* sorted */
+    uint32_t *perm; /* sorted position -> original index */
+    double *xs;     /* sorted positions, n x 3 */
+    double *ms;     /* sorted masses */
+
+    int64_t M; /* nodes, breadth-first order */
+    int32_t *level;
+    uint64_t *prefix;
+    int64_t *first, *count, *child_first, *parent;
+    int32_t *nchild;
+    double *mass, *com, *quad;
+
+    int64_t G; /* groups */
+    int64_t *gfirst, *gcount, *gref;
+};
+
+typedef struct {
+    uint64_t key;
+    uint32_t idx;
+} kv_t;
+
+static int cmp_kv(const void *a, const void *b)
+{
+    const kv_t *x = (const kv_t *)a, *y = (const kv_t *)b;
+    if (x->key != y->key)
+        return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+/* Pre-order record produced by the recursive subdivision. */
+typedef struct {
+    int32_t level;
+    uint64_t prefix;
+    int64_t first, count, parent_pre;
+} rec_t;
+
+typedef struct {
+    rec_t *v;
+    int64_t n, cap;
+} recvec_t;
+
+static int64_t push_rec(recvec_t *r, rec_t x)
+{
+    if (r->n == r->cap) {
+        r->cap = r->cap ? 2 * r->cap : 1024;
+        r->v = (rec_t *)realloc(r->v, (size_t)r->cap * sizeof(rec_t));
+    }
+    r->v[r->n] = x;
+    return r->n++;
+}
+
+/* R2: recursive subdivision (Sec. 3.1).  The bodies of the cube
+ * (level, prefix) are the sorted range [first, first + count); its
+ * non-empty octants are consecutive sub-ranges because keys are sorted. */
+static void subdivide(const or_tree *t, recvec_t *out, int level, uint64_t prefix,
+                      int64_t first, int64_t count, int64_t parent_pre)
+{
+    rec_t me = {level, prefix, first, count, parent_pre};
+    int64_t self = push_rec(out, me);
+    if (count <= t->leaf_max || level == OR_MAX_LEVEL)
+        return; /* leaf */
+    int64_t s = first, end = first + count;
+    for (int o = 0; o < 8; o++) {
+        int64_t e = s;
+        while (e < end && digit_at(t->keys[e], level + 1) == o)
+            e++;
+        if (e > s)
+            subdivide(t, out, level + 1, (prefix << 3) | (uint64_t)o, s, e - s, self);
+        s = e;
+    }
+}
+
+static const rec_t *g_sort_recs; /* qsort context (single-threaded oracle) */
+static int cmp_bfs(const void *a, const void *b)
+{
+    const rec_t *x = &g_sort_recs[*(const int64_t *)a];
+    const rec_t *y = &g_sort_recs[*(const int64_t *)b];
+    if (x->level != y->level)
+        return x->level < y->level ? -1 : 1;
+    return x->first < y->first ? -1 : (x->first > y->first);
+}
+
+or_tree *or_tree_build(const float *pos, const float *mass, int64_t n, int leaf_max)
+{
+    if (n < 1 || leaf_max < 1)
+        return NULL;
+    for (int64_t i = 0; i < n; i++)
+        if (!isfinite((double)mass[i]))
+            return NULL;
+    or_tree *t = (or_tree *)calloc(1, sizeof(or_tree));
+    t->n = n;
+    t->leaf_max = leaf_max;
+    if (or_root_cube(pos, n, t->cube) != 0) {
+        free(t);
+        return NULL;
+    }
+
+    /* keys, then the stable (key, index) sort (R3) */
+    uint64_t *k = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    or_keys(pos, n, t->cube, k);
+    kv_t *kv = (kv_t *)malloc((size_t)n * sizeof(kv_t));
+    for (int64_t i = 0; i < n; i++) {
+        kv[i].key = k[i];
+        kv[i].idx = (uint32_t)i;
+    }
+    qsort(kv, (size_t)n, sizeof(kv_t), cmp_kv);
+    free(k);
+    t->keys = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    t->perm = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    t->xs = (double *)malloc((size_t)n * 3 * sizeof(double));
+    t->ms = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t i = 0; i < n; i++) {
+        t->keys[i] = kv[i].key;
+        t->perm[i] = kv[i].idx;
+        for (int a = 0; a < 3; a++)
+            t->xs[3 * i + a] = (double)pos[3 * (int64_t)kv[i].idx + a];
+        t->ms[i] = (double)mass[kv[i].idx];
+    }
+    free(kv);
+
+    /* the oct-tree in pre-order, then re-ordered breadth-first */
+    recvec_t recs = {0};
+    subdivide(t, &recs, 0, 0, 0, n, -1);
+    int64_t M = recs.n;
+    int64_t *order = (int64_t *)malloc((size_t)M * sizeof(int64_t));
+    for (int64_t i = 0; i < M; i++)
+        order[i] = i;
+    g_sort_recs = recs.v;
+    qsort(order, (size_t)M, sizeof(int64_t), cmp_bfs);
+    int64_t *bfs_of_pre = (int64_t *)malloc((size_t)M * sizeof(int64_t));
+    for (int64_t b = 0; b < M; b++)
+        bfs_of_pre[order[b]] = b;
+
+    t->M = M;
+    t->level = (int32_t *)malloc((size_t)M * sizeof(int32_t));
+    t->prefix = (uint64_t *)malloc((size_t)M * sizeof(uint64_t));
+    t->first = (int64_t *)malloc((size_t)M * sizeof(int64_t));
+    t->count = (int64_t *)malloc((size_t)M * sizeof(int64_t));
+    t->child_first = (int64_t *)malloc((size_t)M * sizeof(int64_t));
+    t->parent = (int64_t *)malloc((size_t)M * sizeof(int64_t));
+    t->nchild = (int32_t *)calloc((size_t)M, sizeof(int32_t));
+    for (int64_t b = 0; b < M; b++) {
+        const rec_t *r = &recs.v[order[b]];
+        t->level[b] = r->level;
+        t->prefix[b] = r->prefix;
+        t->first[b] = r->first;
+        t->count[b] = r->count;
+        t->parent[b] = r->parent_pre < 0 ? -1 : bfs_of_pre[r->parent_pre];
+        t->child_first[b] = -1;
+    }
+    for (int64_t b = 0; b < M; b++) {
+        int64_t p = t->parent[b];
+        if (p < 0)
+            continue;
+        t->nchild[p]++;
+        if (t->child_first[p] < 0 || b < t->child_first[p])
+            t->child_first[p] = b;
+    }
+    free(order);
+    free(bfs_of_pre);
+    free(recs.v);
+
+    /* mass, centre of mass and second moments of every cell, each from
+     * the definition over the cell's own bodies (Sec. 3.1: a cell stands
+     * for its bodies by one body of their total mass at their centre of
+     * mass). */
+    t->mass = (double *)malloc((size_t)M * sizeof(double));
+    t->com = (double *)malloc((size_t)M * 3 * sizeof(double));
+    t->quad = (double *)malloc((size_t)M * 6 * sizeof(double));
+    for (int64_t v = 0; v < M; v++) {
+        double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int64_t j = t->first[v]; j < t->first[v] + t->count[v]; j++) {
+            m += t->ms[j];
+            sx += t->ms[j] * t->xs[3 * j + 0];
+            sy += t->ms[j] * t->xs[3 * j + 1];
+            sz += t->ms[j] * t->xs[3 * j + 2];
+        }
+        double c[3] = {sx / m, sy / m, sz / m};
+        double q[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t j = t->first[v]; j < t->first[v] + t->count[v]; j++) {
+            double dx = t->xs[3 * j + 0] - c[0];
+            double dy = t->xs[3 * j + 1] - c[1];
+            double dz = t->xs[3 * j + 2] - c[2];
+            double mj = t->ms[j];
+            q[0] += mj * dx * dx;
+            q[1] += mj * dx * dy;
+            q[2] += mj * dx * dz;
+            q[3] += mj * dy * dy;
+            q[4] += mj * dy * dz;
+            q[5] += mj * dz * dz;
+        }
+        t->mass[v] = m;
+        for (int a = 0; a < 3; a++)
+            t->com[3 * v + a] = c[a];
+        for (int a = 0; a < 6; a++)
+            t->quad[6 * v + a] = q[a];
+    }
+    return t;
+}
+
+void or_tree_free(or_tree *t)
+{
+    if (!t)
+        return;
+    free(t->keys);
+    free(t->perm);
+    free(t->xs);
+    free(t->ms);
+    free(t->level);
+    free(t->prefix);
+    free(t->first);
+    free(t->count);
+    free(t->child_first);
+    free(t->parent);
+    free(t->nchild);
+    free(t->mass);
+    free(t->com);
+    free(t->quad);
+    free(t->gfirst);
+    free(t->gcount);
+    free(t->gref);
+    free(t);
+}
+
+int64_t or_tree_nnodes(const or_tree *t) { return t->M; }
+int64_t or_tree_nbodies(const or_tree *t) { return t->n; }
+void or_tree_get_cube(const or_tree *t, double *out5) { memcpy(out5, t->cube, 5 * sizeof(double)); }
+void or_tree_get_perm(const or_tree *t, uint32_t *perm) { memcpy(perm, t->perm, (size_t)t->n * sizeof(uint32_t)); }
+void or_tree_get_keys(const or_tree *t, uint64_t *k) { memcpy(k, t->keys, (size_t)t->n * sizeof(uint64_t)); }
+
+void or_tree_get_nodes(const or_tree *t, int32_t *level, uint64_t *prefix, int64_t *first,
+                       int64_t *count, int64_t *child_first, int32_t *nchild, int64_t *parent)
+{
+    size_t M = (size_t)t->M;
+    if (level)
+        memcpy(level, t->level, M * sizeof(int32_t));
+    if (prefix)
+        memcpy(prefix, t->prefix, M * sizeof(uint64_t));
+    if (first)
+        memcpy(first, t->first, M * sizeof(int64_t));
+    if (count)
+        memcpy(count, t->count, M * sizeof(int64_t));
+    if (child_first)
+        memcpy(child_first, t->child_first, M * sizeof(int64_t));
+    if (nchild)
+        memcpy(nchild, t->nchild, M * sizeof(int32_t));
+    if (parent)
+        memcpy(parent, t->parent, M * sizeof(int64_t));
+}
+
+void or_tree_get_moments(const or_tree *t, double *mass, double *com, double *quad)
+{
+    size_t M = (size_t)t->M;
+    if (mass)
+        memcpy(mass, t->mass, M * sizeof(double));
+    if (com)
+        memcpy(com, t->com, M * 3 * sizeof(double));
+    if (quad)
+        memcpy(quad, t->quad, M * 6 * sizeof(double));
+}
+
+/* ------------------------------------------------------------------ */
+/* R4: groups.  The paper walks the tree once per body (Sec. 3.2); the */
+/* walk here is shared by a group of at most gmax bodies that are      */
+/* contiguous in Morton order (gmax = 1 is the per-body walk).  Rule,  */
+/* applied from the root down:                                         */
+/*   - a cube holding at most gmax bodies that is the root is a group; */
+/*   - a leaf holding more than gmax bodies is cut into consecutive    */
+/*     chunks of gmax (the last one shorter);                          */
+/*   - the children of an internal cube holding more than gmax bodies  */
+/*     are taken in octant order: a child holding more than gmax is    */
+/*     handled by these rules in turn; runs of consecutive children    */
+/*     holding at most gmax each are packed greedily, left to right,   */
+/*     into groups of at most gmax bodies.                             */
+/* Each group has a reference cube: the cube itself for a single cube  */
+/* or a chunk of a leaf, the common parent for several packed children.*/
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t *first, *count, *ref;
+    int64_t n, cap;
+} grpvec_t;
+
+static void push_group(grpvec_t *g, int64_t first, int64_t count, int64_t ref)
+{
+    if (g->n == g->cap) {
+        g->cap = g->cap ? 2 * g->cap : 1024;
+        g->first = (int64_t *)realloc(g->first, (size_t)g->cap * sizeof(int64_t));
+        g->count = (int64_t *)realloc(g->count, (size_t)g->cap * sizeof(int64_t));
+        g->ref = (int64_t *)realloc(g->ref, (size_t)g->cap * sizeof(int64_t));
+    }
+    g->first[g->n] = first;
+    g->count[g->n] = count;
+    g->ref[g->n] = ref;
+    g->n++;
+}
+
+static void group_cube(const or_tree *t, grpvec_t *out, int64_t v, int gmax)
+{
+    if (t->count[v] <= gmax) { /* only the root gets here */
+        push_group(out, t->first[v], t->count[v], v);
+        return;
+    }
+    if (t->nchild[v] == 0) { /* over-full leaf: chunks */
+        for (int64_t s = 0; s < t->count[v]; s += gmax) {
+            int64_t c = t->count[v] - s < gmax ? t->count[v] - s : gmax;
+            push_group(out, t->first[v] + s, c, v);
+        }
+        return;
+    }
+    int64_t run_first = -1, run_count = 0, run_len = 0, run_only = -1;
+    for (int64_t c = t->child_first[v]; c < t->child_first[v] + t->nchild[v]; c++) {
+        if (t->count[c] > gmax || run_count + t->count[c] > gmax) {
+            if (run_len > 0)
+                push_group(out, run_first, run_count, run_len == 1 ? run_only : v);
+            run_len = 0;
+            run_count = 0;
+        }
+        if (t->count[c] > gmax) {
+            group_cube(t, out, c, gmax);
+            continue;
+        }
+        if (run_len == 0) {
+            run_first = t->first[c];
+            run_only = c;
+        }
+        run_count += t->count[c];
+        run_len++;
+    }
+    if (run_len > 0)
+        push_group(out, run_first, run_count, run_len == 1 ? run_only : v);
+}
+
+int64_t or_tree_make_groups(or_tree *t, int gmax)
+{
+    if (gmax < 1)
+        return -1;
+    grpvec_t g = {0};
+    group_cube(t, &g, 0, gmax);
+    free(t->gfirst);
+    free(t->gcount);
+    free(t->gref);
+    t->gfirst = g.first;
+    t->gcount = g.count;
+    t->gref = g.ref;
+    t->G = g.n;
+    return g.n;
+}
+
+void or_tree_get_groups(const or_tree *t, int64_t *first, int64_t *count, int64_t *ref)
+{
+    size_t G = (size_t)t->G;
+    if (first)
+        memcpy(first, t->gfirst, G * sizeof(int64_t));
+    if (count)
+        memcpy(count, t->gcount, G * sizeof(int64_t));
+    if (ref)
+        memcpy(ref, t->gref, G * sizeof(int64_t));
+}
+
+/* ------------------------------------------------------------------ */
+/* R5: the opening test ("distant enough", Sec. 3.1).                  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t gfirst, gcount;
+    double lo[3], hi[3]; /* tight box of the group's bodies */
+    double theta;
+    int flagged;
+    /* lists */
+    int64_t *cells, ncells, cap_c;
+    int64_t *leaves, nleaves, cap_l;
+    int64_t nbody;
+} walk_t;
+
+static double cube_side(const or_tree *t, int64_t v) { return ldexp(t->cube[3], -t->level[v]); }
+
+static double dist_to_box(const double *p, const double *lo, const double *hi)
+{
+    double s = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double e = 0.0;
+        if (p[a] < lo[a])
+            e = lo[a] - p[a];
+        else if (p[a] > hi[a])
+            e = p[a] - hi[a];
+        s += e * e;
+    }
+    return sqrt(s);
+}
+
+/* 0 = open (holds a body of the group), 1 = open (too close), 2 = accept */
+static int decide(const or_tree *t, walk_t *w, int64_t v)
+{
+    int64_t a0 = t->first[v], a1 = t->first[v] + t->count[v];
+    if (a0 < w->gfirst + w->gcount && w->gfirst < a1)
+        return 0;
+    double s = cube_side(t, v);
+    double d = dist_to_box(&t->com[3 * v], w->lo, w->hi);
+    double td = w->theta * d;
+    if (fabs(s - td) <= 1e-6 * td)
+        w->flagged = 1;
+    return (s < td) ? 2 : 1;
+}
+
+static void push_i64(int64_t **a, int64_t *n, int64_t *cap, int64_t x)
+{
+    if (*n == *cap) {
+        *cap = *cap ? 2 * *cap : 256;
+        *a = (int64_t *)realloc(*a, (size_t)*cap * sizeof(int64_t));
+    }
+    (*a)[(*n)++] = x;
+}
+
+/* v has been opened: a leaf gives its bodies to the list, an internal
+ * cube has each child tested in turn (traversal continues recursively). */
+static void open_cube(const or_tree *t, walk_t *w, int64_t v)
+{
+    if (t->nchild[v] == 0) {
+        push_i64(&w->leaves, &w->nleaves, &w->cap_l, v);
+        w->nbody += t->count[v];
+        return;
+    }
+    for (int64_t c = t->child_first[v]; c < t->child_first[v] + t->nchild[v]; c++) {
+        if (decide(t, w, c) == 2)
+            push_i64(&w->cells, &w->ncells, &w->cap_c, c);
+        else
+            open_cube(t, w, c);
+    }
+}
+
+static uint64_t mix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* R6: softened monopole force of a point mass m at y on a body at x. */
+static void add_force(const double *x, const double *y, double m, double eps2, double G,
+                      double *a, double *phi)
+{
+    double dx = y[0] - x[0], dy = y[1] - x[1], dz = y[2] - x[2];
+    double r2 = dx * dx + dy * dy + dz * dz + eps2;
+    double rinv = 1.0 / sqrt(r2);
+    double f = G * m * rinv * rinv * rinv;
+    a[0] += f * dx;
+    a[1] += f * dy;
+    a[2] += f * dz;
+    *phi -= G * m * rinv;
+}
+
+int or_tree_test(const or_tree *t, int64_t group, int64_t node, double theta)
+{
+    walk_t w;
+    memset(&w, 0, sizeof(w));
+    w.gfirst = t->gfirst[group];
+    w.gcount = t->gcount[group];
+    for (int a = 0; a < 3; a++) {
+        w.lo[a] = INFINITY;
+        w.hi[a] = -INFINITY;
+    }
+    for (int64_t j = w.gfirst; j < w.gfirst + w.gcount; j++)
+        for (int a = 0; a < 3; a++) {
+            if (t->xs[3 * j + a] < w.lo[a])
+                w.lo[a] = t->xs[3 * j + a];
+            if (t->xs[3 * j + a] > w.hi[a])
+                w.hi[a] = t->xs[3 * j + a];
+        }
+    w.theta = theta;
+    return decide(t, &w, node);
+}
+
+int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G, int64_t g_begin,
+                     int64_t g_end, double *acc, double *pot, int64_t *ncell, int64_t *nbody,
+                     uint64_t *hash, int32_t *flag)
+{
+    int64_t inter = 0;
+    double eps2 = eps * eps;
+    walk_t w;
+    memset(&w, 0, sizeof(w));
+    for (int64_t g = g_begin; g < g_end; g++) {
+        w.gfirst = t->gfirst[g];
+        w.gcount = t->gcount[g];
+        w.theta = theta;
+        w.flagged = 0;
+        w.ncells = w.nleaves = w.nbody = 0;
+        for (int a = 0; a < 3; a++) {
+            w.lo[a] = INFINITY;
+            w.hi[a] = -INFINITY;
+        }
+        for (int64_t j = w.gfirst; j < w.gfirst + w.gcount; j++)
+            for (int a = 0; a < 3; a++) {
+                if (t->xs[3 * j + a] < w.lo[a])
+                    w.lo[a] = t->xs[3 * j + a];
+                if (t->xs[3 * j + a] > w.hi[a])
+                    w.hi[a] = t->xs[3 * j + a];
+            }
+        /* the walk starts at the root, which holds every body and so is
+         * always opened */
+        open_cube(t, &w, 0);
+
+        /* loop through the accumulated list for every body of the group */
+        for (int64_t i = w.gfirst; i < w.gfirst + w.gcount; i++) {
+            double a[3] = {0, 0, 0}, phi = 0.0;
+            const double *xi = &t->xs[3 * i];
+            for (int64_t k = 0; k < w.ncells; k++) {
+                int64_t c = w.cells[k];
+                add_force(xi, &t->com[3 * c], t->mass[c], eps2, G, a, &phi);
+            }
+            for (int64_t k = 0; k < w.nleaves; k++) {
+                int64_t v = w.leaves[k];
+                for (int64_t j = t->first[v]; j < t->first[v] + t->count[v]; j++) {
+                    double dummy = 0.0;
+                    add_force(xi, &t->xs[3 * j], t->ms[j], eps2, G, a, j == i ? &dummy : &phi);
+                }
+            }
+            int64_t o = (int64_t)t->perm[i];
+            if (acc) {
+                acc[3 * o + 0] = a[0];
+                acc[3 * o + 1] = a[1];
+                acc[3 * o + 2] = a[2];
+            }
+            if (pot)
+                pot[o] = phi;
+        }
+        inter += w.gcount * (w.ncells + w.nbody);
+        if (ncell)
+            ncell[g] = w.ncells;
+        if (nbody)
+            nbody[g] = w.nbody;
+        if (flag)
+            flag[g] = w.flagged;
+        if (hash) {
+            uint64_t hsum = 0;
+            for (int64_t k = 0; k < w.ncells; k++)
+                hsum += mix64(2 * (uint64_t)w.cells[k] + 1);
+            for (int64_t k = 0; k < w.nleaves; k++)
+                hsum += mix64(2 * (uint64_t)w.leaves[k] + 2);
+            hash[g] = hsum;
+        }
+    }
+    free(w.cells);
+    free(w.leaves);
+    return inter;
+}
+
+/* ------------------------------------------------------------------ */
+/* Direct summation: the exact O(N^2) result the treecode approximates.*/
+/* ------------------------------------------------------------------ */
+void or_direct64(const double *pos, const double *mass, int64_t n, double eps, double G,
+                 const int64_t *idx, int64_t ns, double *acc, double *pot)
+{
+    double eps2 = eps * eps;
+    for (int64_t s = 0; s < ns; s++) {
+        int64_t i = idx[s];
+        double a[3] = {0, 0, 0}, phi = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            double dummy = 0.0;
+            add_force(&pos[3 * i], &pos[3 * j], mass[j], eps2, G, a, j == i ? &dummy : &phi);
+        }
+        acc[3 * s + 0] = a[0];
+        acc[3 * s + 1] = a[1];
+        acc[3 * s + 2] = a[2];
+        if (pot)
+            pot[s] = phi;
+    }
+}
+
+void or_direct(const float *pos, const float *mass, int64_t n, double eps, double G,
+               const int64_t *idx, int64_t ns, double *acc, double *pot)
+{
+    double *p = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *m = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t j = 0; j < n; j++) {
+        for (int a = 0; a < 3; a++)
+            p[3 * j + a] = (double)pos[3 * j + a];
+        m[j] = (double)mass[j];
+    }
+    or_direct64(p, m, n, eps, G, idx, ns, acc, pot);
+    free(p);
+    free(m);
+}
+
+/* ------------------------------------------------------------------ */
+/* R7: kick-drift-kick leapfrog (Sec. 3.1: bodies update position and  */
+/* velocity from the computed forces).                                  */
+/* ------------------------------------------------------------------ */
+void or_kick(double *vel, const double *acc, int64_t n, double h)
+{
+    for (int64_t i = 0; i < 3 * n; i++)
+        vel[i] += acc[i] * h;
+}
+
+void or_drift(double *pos, const double *vel, int64_t n, double dt)
+{
+    for (int64_t i = 0; i < 3 * n; i++)
+        pos[i] += vel[i] * dt;
+}
+
+void or_diag(const double *pos, const double *vel, const double *mass, const double *pot,
+             int64_t n, double *out8)
+{
+    memset(out8, 0, 8 * sizeof(double));
+    for (int64_t i = 0; i < n; i++) {
+        const double *x = &pos[3 * i], *v = &vel[3 * i];
+        double m = mass[i];
+        out8[0] += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (pot)
+            out8[1] += 0.5 * m * pot[i];
+        out8[2] += m * v[0];
+        out8[3] += m * v[1];
+        out8[4] += m * v[2];
+        out8[5] += m * (x[1] * v[2] - x[2] * v[1]);
+        out8[6] += m * (x[2] * v[0] - x[0] * v[2]);
+        out8[7] += m * (x[0] * v[1] - x[1] * v[0]);
+    }
+}

@@ -1,0 +1,101 @@
+/*
+ * tc_oracle.h -- plain, slow FP64 CPU oracle of the treecode force phase.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library
+ * and its Python binding) may include, link or call this code; only the
+ * tests, the smoke check and the CPU-baseline leg of the benchmark do.  It
+ * shares no source, header, table or helper with the GPU path.
+ *
+ * What it computes follows the paper's treecode (Sec. 3.1):
+ *   - the space is divided recursively into 8 sub-cubes until a cube holds
+ *     no more than a threshold of bodies (the oct-tree),
+ *   - each cell carries its total mass and centre of mass,
+ *   - the force on a body is found by walking the tree from the root: a
+ *     cell far enough away joins the interaction list, otherwise the walk
+ *     descends into its children; the list is then summed with the
+ *     gravitational force law F = G m_a m_b / r^2 (Sec. 3.1 equation),
+ *   - bodies then update position and velocity (Sec. 3.1, last paragraph).
+ * Readings of what the paper leaves open (root cube, Morton keys, groups,
+ * opening test, softening, integrator) are stated at each function.
+ *
+ * All arithmetic is IEEE double, compiled with -ffp-contract=off.
+ */
+#ifndef TC_ORACLE_H
+#define TC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAX_LEVEL 21 /* 21 bits per axis, 63-bit keys */
+
+typedef struct or_tree or_tree;
+
+/* Root cube: out[0..2] = corner c0, out[3] = side L, out[4] = grid step
+ * h = L / 2^21.  Returns 0, or -1 for n < 1 or a non-finite coordinate. */
+int or_root_cube(const float *pos, int64_t n, double *out5);
+
+/* Morton keys of n bodies for a given root cube (out of or_root_cube). */
+void or_keys(const float *pos, int64_t n, const double *cube5, uint64_t *keys);
+
+/* Build the oct-tree of n bodies (pos n x 3, mass n) with leaf threshold
+ * leaf_max.  Returns NULL on invalid input (n < 1, leaf_max < 1, NaN/Inf). */
+or_tree *or_tree_build(const float *pos, const float *mass, int64_t n, int leaf_max);
+void or_tree_free(or_tree *t);
+
+int64_t or_tree_nnodes(const or_tree *t);
+int64_t or_tree_nbodies(const or_tree *t);
+void or_tree_get_cube(const or_tree *t, double *out5);
+/* perm[k] = original index of the body at sorted (Morton) position k. */
+void or_tree_get_perm(const or_tree *t, uint32_t *perm);
+void or_tree_get_keys(const or_tree *t, uint64_t *keys_sorted);
+/* Node table in breadth-first order (by level, then by first body). */
+void or_tree_get_nodes(const or_tree *t, int32_t *level, uint64_t *prefix,
+                       int64_t *first, int64_t *count, int64_t *child_first,
+                       int32_t *nchild, int64_t *parent);
+/* mass[M], com[M*3] (absolute), quad[M*6] = Qxx,Qxy,Qxz,Qyy,Qyz,Qzz. */
+void or_tree_get_moments(const or_tree *t, double *mass, double *com, double *quad);
+
+/* Body groups for the group walk; returns the number of groups G. */
+int64_t or_tree_make_groups(or_tree *t, int gmax);
+void or_tree_get_groups(const or_tree *t, int64_t *first, int64_t *count, int64_t *ref);
+
+/* Walk + force for groups [g_begin, g_end).
+ *   acc, pot : n x 3 / n, ORIGINAL body order; only bodies of the walked
+ *              groups are written.  pot may be NULL.
+ *   ncell, nbody : per group (indexed by group id, length G), list lengths.
+ *   hash  : per group order-independent hash of the accepted cells and the
+ *           opened leaves.
+ *   flag  : per group 1 if any opening test it evaluated lay within the
+ *           1e-6 relative tie band, else 0.
+ * Any of ncell, nbody, hash, flag may be NULL.
+ * Returns the number of body-source interactions evaluated. */
+int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G,
+                     int64_t g_begin, int64_t g_end, double *acc, double *pot,
+                     int64_t *ncell, int64_t *nbody, uint64_t *hash, int32_t *flag);
+
+/* For tests: the opening-test decision of one (group, node) pair:
+ * 0 = open (contains a group body), 1 = open (too close), 2 = accept. */
+int or_tree_test(const or_tree *t, int64_t group, int64_t node, double theta);
+
+/* Direct O(N*S) sum for the bodies idx[0..ns) (ORIGINAL indices) over all n
+ * bodies; acc is ns x 3, pot (nullable) ns.  Float and double inputs. */
+void or_direct(const float *pos, const float *mass, int64_t n, double eps, double G,
+               const int64_t *idx, int64_t ns, double *acc, double *pot);
+void or_direct64(const double *pos, const double *mass, int64_t n, double eps, double G,
+                 const int64_t *idx, int64_t ns, double *acc, double *pot);
+
+/* Leapfrog pieces (kick-drift-kick), in place, double precision. */
+void or_kick(double *vel, const double *acc, int64_t n, double h);
+void or_drift(double *pos, const double *vel, int64_t n, double dt);
+
+/* out[0] = kinetic energy, out[1] = potential energy 0.5*sum m*pot,
+ * out[2..4] = linear momentum, out[5..7] = angular momentum. */
+void or_diag(const double *pos, const double *vel, const double *mass,
+             const double *pot, int64_t n, double *out8);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
