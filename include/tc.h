@@ -1,0 +1,166 @@
+/*
+ * tc.h -- C ABI of libtc, a single-GPU (sm_103a) treecode force library.
+ *
+ * The treecode (Barnes-Hut) of the paper, Sec. 3.1: the bodies are put in an
+ * oct-tree by recursively dividing space into 8 sub-cubes until a cube holds
+ * no more than a threshold of bodies; each cell stands for its bodies by
+ * their total mass at their centre of mass; the force on a body is found by
+ * walking the tree from the root, adding a cell to the body's interaction
+ * list when it is distant enough and descending into its children
+ * otherwise, then summing the list with F = G m_a m_b / r^2; finally every
+ * body updates its position and velocity from the force.  The paper spends
+ * upwards of 90% of the cycles in the force summation (Sec. 1, Sec. 3.2).
+ *
+ * Conventions for every function below
+ *   - Return value: TC_OK (0) or a negative TC_E* code; tc_last_error() gives
+ *     a one-line reason.  The library never aborts and never prints.
+ *   - Pointers: any pointer argument may be host or device memory (unified
+ *     addressing); the library copies inputs into its own device buffers and
+ *     the caller keeps ownership of everything it passes.
+ *   - Layouts: positions, velocities and accelerations are n x 3 float32,
+ *     row-major (x, y, z per body), in the caller's (original) body order;
+ *     masses are n float32.
+ *   - Streams: all work is enqueued on the context's stream.  Calls that only
+ *     enqueue return before the GPU work ends; calls that hand data back
+ *     (tc_get_*, tc_diag, tc_direct, tc_sync) synchronise the stream and also
+ *     report device-side errors (TC_EDEVICE) raised by earlier work.
+ *   - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef TC_H
+#define TC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TC_OK 0
+#define TC_EINVAL (-1)  /* invalid argument (n < 1, leaf_max out of range, theta < 0, eps <= 0, NaN/Inf, mass <= 0) */
+#define TC_ENOMEM (-2)  /* device allocation failed (or the TC_ALLOC_CAP_BYTES cap was hit) */
+#define TC_ESTATE (-3)  /* call out of order (forces before build, step before forces) */
+#define TC_EDEVICE (-4) /* a kernel raised its error word (walk stack overflow, ...) */
+#define TC_ECUDA (-5)   /* a CUDA runtime call failed */
+
+typedef struct tc_ctx tc_ctx;
+
+/* Tuning of the force phase (the autotuner's output).
+ *   gmax      bodies per group walk: 32, 64 or 128 (1, 2 or 4 bodies per lane)
+ *   warps     warps per block of the walk kernel, 1..4
+ *   precise   1: cell-relative coordinates for cell sources and compensated
+ *             (TwoSum) accumulation across list tiles; 0: absolute float32
+ *             coordinates and plain accumulation
+ *   want_pot  1: also compute the potential (tc_get_acc's pot, tc_diag's PE)
+ *   verify    1: record per-group list lengths and hashes (tc_get_lists)
+ *   stack     walk stack entries per warp (shared memory), 64..8192
+ *   blocks_per_sm  0 = as many as fit, else a cap                          */
+typedef struct {
+    int32_t gmax;
+    int32_t warps;
+    int32_t precise;
+    int32_t want_pot;
+    int32_t verify;
+    int32_t stack;
+    int32_t blocks_per_sm;
+} tc_config;
+
+/* Create a context on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = the legacy default stream); it must outlive the
+ * context. */
+int tc_create(tc_ctx **ctx, void *cuda_stream);
+void tc_destroy(tc_ctx *ctx);
+int tc_set_config(tc_ctx *ctx, const tc_config *cfg);
+int tc_get_config(tc_ctx *ctx, tc_config *cfg);
+int tc_set_stream(tc_ctx *ctx, void *cuda_stream);
+
+/* Tree construction (Sec. 3.1): copies pos (n x 3) and mass (n), builds the
+ * root cube, Morton keys (stable sort), the oct-tree with leaf threshold
+ * leaf_max (a cube is divided while it holds more than leaf_max bodies,
+ * down to level 21), the cells' masses and centres of mass (FP64 reduction)
+ * and the body groups.  1 <= n < 2^31, 1 <= leaf_max <= 4096, masses > 0.
+ * Velocities are reset to zero when n changes.  Synchronises once (to size
+ * the node table). */
+int tc_ctx_build(tc_ctx *ctx, const float *pos, const float *mass, int64_t n, int leaf_max);
+
+/* Velocities (n x 3) for tc_ctx_step; copied. */
+int tc_ctx_set_velocity(tc_ctx *ctx, const float *vel);
+
+/* Force phase (Sec. 3.1, Sec. 3.2): for every body group, walk the tree from
+ * the root with the opening test "accept a cell of side s whose centre of
+ * mass is at distance d from the group's bounding box iff it holds none of
+ * the group's bodies and s < theta * d", then sum the accepted cells and the
+ * bodies of opened leaves with the Plummer-softened force law
+ *   a_i = G sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2).
+ * theta >= 0 (0 = direct summation through the tree), eps > 0.  Results stay
+ * on the device (tc_get_acc).  Enqueue only. */
+int tc_ctx_forces(tc_ctx *ctx, float theta, float eps, float G);
+
+/* One kick-drift-kick leapfrog step of length dt with the last theta, eps,
+ * G: v += a dt/2; x += v dt; rebuild the tree; forces; v += a dt/2 (the
+ * paper's "each body updates its position and velocity", Sec. 3.1).  Needs
+ * a prior tc_ctx_forces on the current positions.  Synchronises once (the
+ * rebuild). */
+int tc_ctx_step(tc_ctx *ctx, float dt);
+
+/* Accelerations (n x 3) and, if pot != NULL and want_pot was set, the
+ * potential (n) of the last force phase, original body order. */
+int tc_get_acc(tc_ctx *ctx, float *acc, float *pot);
+
+/* Current positions / velocities (n x 3 each; either may be NULL). */
+int tc_get_state(tc_ctx *ctx, float *pos, float *vel);
+/* Replace positions and velocities (n x 3 each, n of the last build) and
+ * rebuild the tree; forces must be recomputed before the next step. */
+int tc_set_state(tc_ctx *ctx, const float *pos, const float *vel);
+
+/* Sizes of the last build: bodies, nodes, groups (any may be NULL). */
+int tc_get_sizes(tc_ctx *ctx, int64_t *n, int64_t *nnodes, int64_t *ngroups);
+
+/* Verification exports of the last build (any pointer may be NULL).
+ *   perm[n]      Morton position -> original index
+ *   keys[n]      sorted 63-bit Morton keys
+ * Node table in breadth-first order (by level, then first body), nnodes long:
+ *   level, prefix (3*level-bit Morton prefix), first, count, child_first
+ *   (-1 for a leaf), nchild, mass, com (3 per node, absolute), quad (6 per
+ *   node: xx, xy, xz, yy, yz, zz second moments about the centre of mass).
+ * Groups, ngroups long: gfirst, gcount, gref (reference cube index). */
+int tc_get_tree(tc_ctx *ctx, uint32_t *perm, uint64_t *keys);
+int tc_get_nodes(tc_ctx *ctx, int32_t *level, uint64_t *prefix, int32_t *first, int32_t *count,
+                 int32_t *child_first, int32_t *nchild, double *mass, double *com, double *quad);
+int tc_get_groups(tc_ctx *ctx, int32_t *gfirst, int32_t *gcount, int32_t *gref);
+/* Root cube of the last build: out5 = {c0x, c0y, c0z, L, h}. */
+int tc_get_cube(tc_ctx *ctx, double *out5);
+
+/* Per-group list lengths of the last force phase (needs verify = 1):
+ * accepted cells, bodies of opened leaves, order-independent hash of the
+ * accepted cells and opened leaves; and totals (interactions = sum over
+ * groups of group size x list length).  Any pointer may be NULL. */
+int tc_get_lists(tc_ctx *ctx, int32_t *ncell, int32_t *nbody, uint64_t *hash,
+                 int64_t *interactions, int64_t *cells, int64_t *bodies);
+
+/* FP64 diagnostics of the current state: out8 = {kinetic energy,
+ * potential energy 1/2 sum m_i pot_i (needs want_pot), momentum x, y, z,
+ * angular momentum x, y, z}. */
+int tc_diag(tc_ctx *ctx, double *out8);
+
+/* Direct O(N * ns) summation for bodies idx[0..ns) (original indices) over
+ * all n bodies of the current state: acc (ns x 3) and pot (ns, nullable),
+ * FP32 terms, FP64 accumulation.  The accuracy judge of the treecode. */
+int tc_direct(tc_ctx *ctx, const int64_t *idx, int64_t ns, float eps, float G, double *acc,
+              double *pot);
+
+/* Wait for the context's stream; report device errors. */
+int tc_sync(tc_ctx *ctx);
+
+/* Reason of the last failure of this context (NULL: the default context). */
+const char *tc_last_error(tc_ctx *ctx);
+
+/* The three calls of the treecode on an implicit default context (created
+ * on first use on the current device and the legacy default stream). */
+int tc_build(const float *pos, const float *mass, int64_t n, int leaf_max);
+int tc_forces(float theta, float eps, float G);
+int tc_step(float dt);
+tc_ctx *tc_default(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -74,7 +74,7 @@ def _load():
     lib.or_tree_make_groups.argtypes = [P, ctypes.c_int]
     lib.or_tree_make_groups.restype = I64
     lib.or_tree_get_groups.argtypes = [P, P, P, P]
-    lib.or_tree_walk.argtypes = [P, D, D, D, I64, I64, P, P, P, P, P, P]
+    lib.or_tree_walk.argtypes = [P, D, D, D, I64, I64, P, P, P, P, P, P, P]
     lib.or_tree_walk.restype = I64
     lib.or_tree_test.argtypes = [P, I64, I64, D]
     lib.or_tree_test.restype = ctypes.c_int
@@ -189,22 +189,24 @@ class Tree:
         """Walk + force for a range of groups (default: all).
 
         Returns dict with acc (n x 3, original order; NaN for bodies outside
-        the walked groups), pot, ncell, nbody, hash, flag (per group, -1 for
-        groups not walked) and the number of interactions."""
+        the walked groups), pot, amag (sum of |term| per body), ncell, nbody,
+        hash, flag (per group, -1 for groups not walked) and the number of
+        interactions."""
         if self.G == 0:
             raise RuntimeError("make_groups first")
         g0, g1 = (0, self.G) if groups is None else groups
         acc = np.full((self.n, 3), np.nan)
         pot = np.full(self.n, np.nan) if want_pot else None
+        amag = np.full(self.n, np.nan)
         ncell = np.full(self.G, -1, dtype=np.int64)
         nbody = np.full(self.G, -1, dtype=np.int64)
         hsh = np.zeros(self.G, dtype=np.uint64)
         flag = np.full(self.G, -1, dtype=np.int32)
         inter = self._lib.or_tree_walk(
             self._h, float(theta), float(eps), float(G), int(g0), int(g1),
-            _ptr(acc), _ptr(pot), _ptr(ncell), _ptr(nbody), _ptr(hsh), _ptr(flag),
+            _ptr(acc), _ptr(pot), _ptr(amag), _ptr(ncell), _ptr(nbody), _ptr(hsh), _ptr(flag),
         )
-        return dict(acc=acc, pot=pot, ncell=ncell, nbody=nbody, hash=hsh, flag=flag,
+        return dict(acc=acc, pot=pot, amag=amag, ncell=ncell, nbody=nbody, hash=hsh, flag=flag,
                     interactions=int(inter))
 
     def test(self, group: int, node: int, theta: float) -> int:

@@ -213,8 +213,8 @@ or_tree *or_tree_build(const float *pos, const float *mass, int64_t n, int leaf_
 {
     if (n < 1 || leaf_max < 1)
         return NULL;
-    for (int64_t i = 0; i < n; i++)
-        if (!isfinite((double)mass[i]))
+    for (int64_t i = 0; i < n; i++) /* masses must be finite and positive */
+        if (!isfinite((double)mass[i]) || !(mass[i] > 0.0f))
             return NULL;
     or_tree *t = (or_tree *)calloc(1, sizeof(or_tree));
     t->n = n;
@@ -566,7 +566,7 @@ static uint64_t mix64(uint64_t z)
 
 /* R6: softened monopole force of a point mass m at y on a body at x. */
 static void add_force(const double *x, const double *y, double m, double eps2, double G,
-                      double *a, double *phi)
+                      double *a, double *phi, double *mag)
 {
     double dx = y[0] - x[0], dy = y[1] - x[1], dz = y[2] - x[2];
     double r2 = dx * dx + dy * dy + dz * dz + eps2;
@@ -576,6 +576,7 @@ static void add_force(const double *x, const double *y, double m, double eps2, d
     a[1] += f * dy;
     a[2] += f * dz;
     *phi -= G * m * rinv;
+    *mag += fabs(f) * sqrt(dx * dx + dy * dy + dz * dz);
 }
 
 int or_tree_test(const or_tree *t, int64_t group, int64_t node, double theta)
@@ -600,8 +601,8 @@ int or_tree_test(const or_tree *t, int64_t group, int64_t node, double theta)
 }
 
 int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G, int64_t g_begin,
-                     int64_t g_end, double *acc, double *pot, int64_t *ncell, int64_t *nbody,
-                     uint64_t *hash, int32_t *flag)
+                     int64_t g_end, double *acc, double *pot, double *amag, int64_t *ncell,
+                     int64_t *nbody, uint64_t *hash, int32_t *flag)
 {
     int64_t inter = 0;
     double eps2 = eps * eps;
@@ -630,17 +631,17 @@ int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G, int64
 
         /* loop through the accumulated list for every body of the group */
         for (int64_t i = w.gfirst; i < w.gfirst + w.gcount; i++) {
-            double a[3] = {0, 0, 0}, phi = 0.0;
+            double a[3] = {0, 0, 0}, phi = 0.0, mag = 0.0;
             const double *xi = &t->xs[3 * i];
             for (int64_t k = 0; k < w.ncells; k++) {
                 int64_t c = w.cells[k];
-                add_force(xi, &t->com[3 * c], t->mass[c], eps2, G, a, &phi);
+                add_force(xi, &t->com[3 * c], t->mass[c], eps2, G, a, &phi, &mag);
             }
             for (int64_t k = 0; k < w.nleaves; k++) {
                 int64_t v = w.leaves[k];
                 for (int64_t j = t->first[v]; j < t->first[v] + t->count[v]; j++) {
                     double dummy = 0.0;
-                    add_force(xi, &t->xs[3 * j], t->ms[j], eps2, G, a, j == i ? &dummy : &phi);
+                    add_force(xi, &t->xs[3 * j], t->ms[j], eps2, G, a, j == i ? &dummy : &phi, &mag);
                 }
             }
             int64_t o = (int64_t)t->perm[i];
@@ -651,6 +652,8 @@ int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G, int64
             }
             if (pot)
                 pot[o] = phi;
+            if (amag)
+                amag[o] = mag;
         }
         inter += w.gcount * (w.ncells + w.nbody);
         if (ncell)
@@ -682,10 +685,10 @@ void or_direct64(const double *pos, const double *mass, int64_t n, double eps, d
     double eps2 = eps * eps;
     for (int64_t s = 0; s < ns; s++) {
         int64_t i = idx[s];
-        double a[3] = {0, 0, 0}, phi = 0.0;
+        double a[3] = {0, 0, 0}, phi = 0.0, mag = 0.0;
         for (int64_t j = 0; j < n; j++) {
             double dummy = 0.0;
-            add_force(&pos[3 * i], &pos[3 * j], mass[j], eps2, G, a, j == i ? &dummy : &phi);
+            add_force(&pos[3 * i], &pos[3 * j], mass[j], eps2, G, a, j == i ? &dummy : &phi, &mag);
         }
         acc[3 * s + 0] = a[0];
         acc[3 * s + 1] = a[1];

@@ -40,7 +40,8 @@ int or_root_cube(const float *pos, int64_t n, double *out5);
 void or_keys(const float *pos, int64_t n, const double *cube5, uint64_t *keys);
 
 /* Build the oct-tree of n bodies (pos n x 3, mass n) with leaf threshold
- * leaf_max.  Returns NULL on invalid input (n < 1, leaf_max < 1, NaN/Inf). */
+ * leaf_max.  Returns NULL on invalid input (n < 1, leaf_max < 1, NaN/Inf,
+ * a mass that is not positive). */
 or_tree *or_tree_build(const float *pos, const float *mass, int64_t n, int leaf_max);
 void or_tree_free(or_tree *t);
 
@@ -64,6 +65,8 @@ void or_tree_get_groups(const or_tree *t, int64_t *first, int64_t *count, int64_
 /* Walk + force for groups [g_begin, g_end).
  *   acc, pot : n x 3 / n, ORIGINAL body order; only bodies of the walked
  *              groups are written.  pot may be NULL.
+ *   amag  : n, ORIGINAL order, sum over the list of |term| (the scale of the
+ *           rounding error of the sum); may be NULL.
  *   ncell, nbody : per group (indexed by group id, length G), list lengths.
  *   hash  : per group order-independent hash of the accepted cells and the
  *           opened leaves.
@@ -72,7 +75,7 @@ void or_tree_get_groups(const or_tree *t, int64_t *first, int64_t *count, int64_
  * Any of ncell, nbody, hash, flag may be NULL.
  * Returns the number of body-source interactions evaluated. */
 int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G,
-                     int64_t g_begin, int64_t g_end, double *acc, double *pot,
+                     int64_t g_begin, int64_t g_end, double *acc, double *pot, double *amag,
                      int64_t *ncell, int64_t *nbody, uint64_t *hash, int32_t *flag);
 
 /* For tests: the opening-test decision of one (group, node) pair:

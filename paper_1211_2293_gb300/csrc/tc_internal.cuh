@@ -1,0 +1,146 @@
+// tc_internal.cuh -- device-side data layout and launchers of the treecode
+// library (CUDA, sm_103a).  Internal to libtc.so; the public C ABI is
+// include/tc.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tc {
+
+constexpr int kMaxLevel = 21;      // 21 bits per axis, 63-bit Morton keys
+constexpr int kLeafMaxLimit = 4096;
+
+// error bits of the device error word
+enum : int32_t {
+    kErrNonFinite = 1,    // NaN/Inf position or mass
+    kErrStack = 2,        // walk stack overflow
+    kErrCapacity = 4,     // a device table outgrew its allocation
+    kErrWorkLoop = 8,     // a persistent loop hit its iteration cap
+};
+
+// Per-context scalars kept in device memory (written by kernels, read by
+// kernels and, at synchronisation points, by the host).
+struct Info {
+    double c0[3];      // root cube corner
+    double L;          // root cube side (power of two)
+    double h;          // grid step L / 2^21
+    double inv_h;      // 1 / h (exact)
+    float Lf;          // L as float (exact)
+    float uf;          // h / 2 as float (exact): unit of the integer centres
+    int32_t err;       // error bits
+    uint32_t ticket;   // last-block-done counter of the bbox reduction
+    int64_t M;         // number of nodes
+    int64_t G;         // number of groups
+    uint32_t work;     // walk work-queue counter
+    uint32_t pad0;
+    unsigned long long interactions;  // body-source interactions of the last walk
+    unsigned long long cells;         // accepted cells summed over groups
+    unsigned long long bodies;        // direct-list bodies summed over groups
+    double diag[8];    // KE, PE, P[3], L[3]
+};
+
+// Node record as the walk reads it (breadth-first order, index v).
+//   a: centre of mass minus cube centre (float), mass (float)
+//   b: first body, body count, first child, level | nchild << 8
+//   c: cube centre in units of u = h/2 (exact integers), 0
+//   d: centre of mass in absolute coordinates (float), mass (plain mode)
+struct NodeTables {
+    float4* a;
+    int4* b;
+    int4* c;
+    float4* d;
+    float* quad;     // 6 per node, second moments about the COM (float)
+    double* mass64;  // FP64 bottom-up reduction results
+    double* com64;   // 3 per node
+    double* quad64;  // 6 per node
+    int32_t* parent;
+    uint32_t* arrive;
+};
+
+// scratch sizes for the radix sort / scans
+struct SortBufs {
+    uint64_t* keys_alt;
+    uint32_t* vals_alt;
+    uint32_t* hist;      // 256 * nblocks
+    uint32_t* blocksum;  // scan partials
+    int64_t cap_items;
+    int64_t cap_hist;
+};
+
+// ---------------------------------------------------------------- launchers
+// all launches go on `s`; none synchronises.
+
+// exclusive scan of n uint32 values into out (out may alias in), total to
+// *total_dev (device pointer, nullable)
+void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
+              uint32_t* blocksum, cudaStream_t s);
+int64_t scan_blocksum_size(int64_t n);
+
+// stable LSD radix sort of (key, val) by bits [0, nbits) of key
+void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b,
+                    cudaStream_t s);
+void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b,
+                    uint32_t* keys_alt32, cudaStream_t s);
+int64_t radix_hist_size(int64_t n);
+
+// build pieces
+void launch_bbox(const float* pos, int64_t n, float* partial, int nblocks, Info* info,
+                 cudaStream_t s);
+int bbox_blocks(int64_t n);
+void launch_keys(const float* pos, const float* mass, int64_t n, const Info* info, uint64_t* keys,
+                 uint32_t* idx, cudaStream_t s);
+void launch_gather(const float* pos, const float* mass, const uint32_t* perm, int64_t n,
+                   float4* body, cudaStream_t s);
+void launch_node_counts(const uint64_t* keys, int64_t n, int leaf_max, int8_t* w, int8_t* delta,
+                        int8_t* top, uint32_t* nstart, cudaStream_t s);
+void launch_emit_preorder(const int8_t* delta, const uint32_t* nstart, const uint32_t* prepos,
+                          int64_t n, uint32_t* pre_level, uint32_t* pre_first, uint32_t* iota,
+                          cudaStream_t s);
+void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n,
+                          const uint32_t* bfs_level, const uint32_t* bfs_pre, const uint32_t* pre_first,
+                          const uint32_t* bfs_of_pre, int64_t M, NodeTables nt, cudaStream_t s);
+void launch_inverse_perm(const uint32_t* perm, int64_t M, uint32_t* inv, cudaStream_t s);
+void launch_moments(const float4* body, int64_t M, const Info* info, NodeTables nt, cudaStream_t s);
+void launch_group_marks(int64_t M, const NodeTables nt, int gmax, int64_t n, uint32_t* gflag,
+                        int32_t* gref_at, cudaStream_t s);
+void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int32_t* gref_at,
+                        int64_t n, const uint32_t* total, int32_t* gfirst, int32_t* gref, Info* info,
+                        cudaStream_t s);
+
+// walk + force
+struct WalkArgs {
+    const float4* body;        // Morton order (x, y, z, m)
+    const uint32_t* perm;      // Morton position -> original index
+    NodeTables nt;
+    const int32_t* gfirst;     // G + 1 entries
+    const int32_t* gref;       // G
+    Info* info;
+    float* acc;                // n x 3, original order
+    float* pot;                // n, original order (nullable)
+    int32_t* ncell;            // per group (nullable)
+    int32_t* nbody;
+    unsigned long long* hash;
+    float theta2, eps2, G;
+    float inv_eps;             // 1/eps for the potential self term
+};
+struct WalkConfig {
+    int gmax;         // 32, 64 or 128
+    int warps;        // warps per block
+    int precise;      // cell-relative sources + compensated accumulation
+    int want_pot;
+    int verify;
+    int blocks_per_sm;
+    int stack;        // walk stack entries per warp
+};
+cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int num_sms, cudaStream_t s);
+
+// dynamics and diagnostics
+void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt,
+                       cudaStream_t s);
+void launch_kick(float* vel, const float* acc, int64_t n, float hkick, cudaStream_t s);
+void launch_diag(const float* pos, const float* vel, const float* mass, const float* pot,
+                 int64_t n, Info* info, cudaStream_t s);
+void launch_direct(const float* pos, const float* mass, int64_t n, const int64_t* idx, int64_t ns,
+                   float eps2, float G, double* acc, double* pot, cudaStream_t s);
+
+}  // namespace tc

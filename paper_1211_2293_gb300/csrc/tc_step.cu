@@ -1,0 +1,141 @@
+// tc_step.cu -- moving the bodies (kick-drift-kick leapfrog), FP64
+// diagnostics and the direct-summation judge.
+//
+// Paper, Sec. 3.1: after the force summation each body updates its position
+// and velocity.  The integrator is not named; the kick-drift-kick leapfrog
+// (velocity Verlet) is used: v += a dt/2; x += v dt; forces; v += a dt/2.
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+
+// v' = v + a*hk, x' = x + v'*dt, each a separately rounded float32 op
+__global__ void k_kick_drift(float* __restrict__ pos, float* __restrict__ vel, const float* __restrict__ acc,
+                             int64_t n3, float hk, float dt)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    float v = __fadd_rn(vel[i], __fmul_rn(acc[i], hk));
+    vel[i] = v;
+    pos[i] = __fadd_rn(pos[i], __fmul_rn(v, dt));
+}
+
+__global__ void k_kick(float* __restrict__ vel, const float* __restrict__ acc, int64_t n3, float hk)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    vel[i] = __fadd_rn(vel[i], __fmul_rn(acc[i], hk));
+}
+
+// KE, PE = 1/2 sum m pot, P, L in FP64; block sums, then FP64 atomics
+__global__ void k_diag(const float* __restrict__ pos, const float* __restrict__ vel, const float* __restrict__ mass,
+                       const float* __restrict__ pot, int64_t n, double* __restrict__ out)
+{
+    __shared__ double sm[8][8];
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double m = mass[i];
+        double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
+        q[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        if (pot) q[1] += 0.5 * m * (double)pot[i];
+        q[2] += m * vx;
+        q[3] += m * vy;
+        q[4] += m * vz;
+        q[5] += m * (y * vz - z * vy);
+        q[6] += m * (z * vx - x * vz);
+        q[7] += m * (x * vy - y * vx);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) q[k] += __shfl_xor_sync(0xffffffffu, q[k], o);
+        if (lane == 0) sm[k][w] = q[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += sm[threadIdx.x][k];
+        atomicAdd(&out[threadIdx.x], s);
+    }
+}
+
+// Direct summation for ns targets over all n sources (original order).
+// FP32 terms; each 256-source tile is summed in FP32 and added in FP64.
+constexpr int kDirTile = 256;
+__global__ void __launch_bounds__(kDirTile) k_direct(const float* __restrict__ pos, const float* __restrict__ mass,
+                                                     int64_t n, const int64_t* __restrict__ idx, int64_t ns,
+                                                     float eps2, float G, double* __restrict__ acc,
+                                                     double* __restrict__ pot)
+{
+    __shared__ float4 tile[kDirTile];
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool act = t < ns;
+    int64_t i = act ? idx[t] : 0;
+    float xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    double ax = 0, ay = 0, az = 0, ph = 0;
+    for (int64_t base = 0; base < n; base += kDirTile) {
+        int64_t j = base + threadIdx.x;
+        __syncthreads();
+        tile[threadIdx.x] = j < n ? make_float4(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], mass[j])
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        int cnt = (int)min((int64_t)kDirTile, n - base);
+        float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < cnt; k++) {
+            float4 s = tile[k];
+            float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+            float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+            float ri = rsqrtf(r2);
+            float mri = s.w * ri;
+            float mri3 = mri * ri * ri;
+            tx = fmaf(dx, mri3, tx);
+            ty = fmaf(dy, mri3, ty);
+            tz = fmaf(dz, mri3, tz);
+            tp -= mri;
+        }
+        ax += tx;
+        ay += ty;
+        az += tz;
+        ph += tp;
+    }
+    if (!act) return;
+    acc[3 * t] = (double)G * ax;
+    acc[3 * t + 1] = (double)G * ay;
+    acc[3 * t + 2] = (double)G * az;
+    if (pot) pot[t] = (double)G * (ph + (double)(mass[i] * rsqrtf(eps2)));
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt, cudaStream_t s)
+{
+    k_kick_drift<<<nblk(3 * n, 256), 256, 0, s>>>(pos, vel, acc, 3 * n, hkick, dt);
+}
+
+void launch_kick(float* vel, const float* acc, int64_t n, float hkick, cudaStream_t s)
+{
+    k_kick<<<nblk(3 * n, 256), 256, 0, s>>>(vel, acc, 3 * n, hkick);
+}
+
+void launch_diag(const float* pos, const float* vel, const float* mass, const float* pot, int64_t n, Info* info,
+                 cudaStream_t s)
+{
+    cudaMemsetAsync(info->diag, 0, 8 * sizeof(double), s);
+    unsigned nb = nblk(n, 256);
+    if (nb > 1024) nb = 1024;
+    k_diag<<<nb, 256, 0, s>>>(pos, vel, mass, pot, n, info->diag);
+}
+
+void launch_direct(const float* pos, const float* mass, int64_t n, const int64_t* idx, int64_t ns, float eps2,
+                   float G, double* acc, double* pot, cudaStream_t s)
+{
+    k_direct<<<nblk(ns, kDirTile), kDirTile, 0, s>>>(pos, mass, n, idx, ns, eps2, G, acc, pot);
+}
+
+}  // namespace tc

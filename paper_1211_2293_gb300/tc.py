@@ -1,0 +1,265 @@
+"""Thin Python binding of libtc (include/tc.h): argument marshalling only.
+
+Every step of the treecode runs in the CUDA library; this module converts
+torch tensors / numpy arrays to pointers, passes the current torch CUDA
+stream, and turns error codes into exceptions.  If the library is missing it
+raises -- there is no fallback.
+
+Same names as the C ABI: ``build``, ``forces``, ``step`` on a ``Context``
+(``tc_ctx_build`` ...) and module-level ``tc_build``/``tc_forces``/``tc_step``
+on the library's implicit default context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtc.so")
+
+TC_OK, TC_EINVAL, TC_ENOMEM, TC_ESTATE, TC_EDEVICE, TC_ECUDA = 0, -1, -2, -3, -4, -5
+_NAMES = {TC_EINVAL: "TC_EINVAL", TC_ENOMEM: "TC_ENOMEM", TC_ESTATE: "TC_ESTATE",
+          TC_EDEVICE: "TC_EDEVICE", TC_ECUDA: "TC_ECUDA"}
+
+# every symbol declared in include/tc.h
+EXPORTS = [
+    "tc_create", "tc_destroy", "tc_set_config", "tc_get_config", "tc_set_stream", "tc_ctx_build",
+    "tc_ctx_set_velocity", "tc_ctx_forces", "tc_ctx_step", "tc_get_acc", "tc_get_state", "tc_set_state",
+    "tc_get_sizes", "tc_get_tree", "tc_get_nodes", "tc_get_groups", "tc_get_cube", "tc_get_lists",
+    "tc_diag", "tc_direct", "tc_sync", "tc_last_error", "tc_build", "tc_forces", "tc_step", "tc_default",
+]
+
+
+class TcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class tc_config(ctypes.Structure):
+    _fields_ = [("gmax", ctypes.c_int32), ("warps", ctypes.c_int32), ("precise", ctypes.c_int32),
+                ("want_pot", ctypes.c_int32), ("verify", ctypes.c_int32), ("stack", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libtc.so (built by ``paper_1211_2293_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libtc.so not found at {p}: run `python -m paper_1211_2293_gb300.build`")
+    lib = ctypes.CDLL(p)
+    P, I32, I64, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    sig = {
+        "tc_create": ([ctypes.POINTER(P), P], I32),
+        "tc_destroy": ([P], None),
+        "tc_set_config": ([P, ctypes.POINTER(tc_config)], I32),
+        "tc_get_config": ([P, ctypes.POINTER(tc_config)], I32),
+        "tc_set_stream": ([P, P], I32),
+        "tc_ctx_build": ([P, P, P, I64, I32], I32),
+        "tc_ctx_set_velocity": ([P, P], I32),
+        "tc_ctx_forces": ([P, F, F, F], I32),
+        "tc_ctx_step": ([P, F], I32),
+        "tc_get_acc": ([P, P, P], I32),
+        "tc_get_state": ([P, P, P], I32),
+        "tc_set_state": ([P, P, P], I32),
+        "tc_get_sizes": ([P, P, P, P], I32),
+        "tc_get_tree": ([P, P, P], I32),
+        "tc_get_nodes": ([P] + [P] * 9, I32),
+        "tc_get_groups": ([P, P, P, P], I32),
+        "tc_get_cube": ([P, P], I32),
+        "tc_get_lists": ([P] + [P] * 6, I32),
+        "tc_diag": ([P, P], I32),
+        "tc_direct": ([P, P, I64, F, F, P, P], I32),
+        "tc_sync": ([P], I32),
+        "tc_last_error": ([P], ctypes.c_char_p),
+        "tc_build": ([P, P, I64, I32], I32),
+        "tc_forces": ([F, F, F], I32),
+        "tc_step": ([F], I32),
+        "tc_default": ([], P),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != TC_OK:
+        msg = _lib.tc_last_error(ctx)
+        raise TcError(rc, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """Pointer of a torch tensor (host or CUDA) or numpy array; None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _current_stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One treecode system on the current CUDA device (a ``tc_ctx``)."""
+
+    def __init__(self, stream=None, **config):
+        lib = load()
+        h = ctypes.c_void_p()
+        s = _current_stream() if stream is None else ctypes.c_void_p(int(stream))
+        _check(lib.tc_create(ctypes.byref(h), s))
+        self._h = h
+        self._lib = lib
+        if config:
+            self.set_config(**config)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        _check(rc, self._h)
+
+    # ------------------------------------------------------------ config
+    def config(self) -> dict:
+        c = tc_config()
+        self._c(self._lib.tc_get_config(self._h, ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in tc_config._fields_}
+
+    def set_config(self, **kw):
+        d = self.config()
+        d.update(kw)
+        c = tc_config(**{k: int(v) for k, v in d.items()})
+        self._c(self._lib.tc_set_config(self._h, ctypes.byref(c)))
+
+    def set_stream(self, stream):
+        self._c(self._lib.tc_set_stream(self._h, ctypes.c_void_p(int(stream))))
+
+    # ------------------------------------------------------------ the path
+    def build(self, pos, mass, leaf_max: int):
+        n = int(mass.shape[0])
+        self._c(self._lib.tc_ctx_build(self._h, _ptr(pos), _ptr(mass), n, int(leaf_max)))
+        self.n = n
+
+    def set_velocity(self, vel):
+        self._c(self._lib.tc_ctx_set_velocity(self._h, _ptr(vel)))
+
+    def forces(self, theta: float, eps: float, G: float = 1.0):
+        self._c(self._lib.tc_ctx_forces(self._h, float(theta), float(eps), float(G)))
+
+    def step(self, dt: float):
+        self._c(self._lib.tc_ctx_step(self._h, float(dt)))
+
+    def sync(self):
+        self._c(self._lib.tc_sync(self._h))
+
+    # ------------------------------------------------------------ outputs
+    def get_acc(self, acc=None, pot=None, with_pot=False):
+        n = self.sizes()[0]
+        if acc is None:
+            acc = np.empty((n, 3), np.float32)
+        if pot is None and with_pot:
+            pot = np.empty(n, np.float32)
+        self._c(self._lib.tc_get_acc(self._h, _ptr(acc), _ptr(pot)))
+        return (acc, pot) if with_pot or pot is not None else acc
+
+    def get_state(self):
+        n = self.sizes()[0]
+        pos = np.empty((n, 3), np.float32)
+        vel = np.empty((n, 3), np.float32)
+        self._c(self._lib.tc_get_state(self._h, _ptr(pos), _ptr(vel)))
+        return pos, vel
+
+    def set_state(self, pos, vel):
+        self._c(self._lib.tc_set_state(self._h, _ptr(pos), _ptr(vel)))
+
+    def sizes(self):
+        n, m, g = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._c(self._lib.tc_get_sizes(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(g)))
+        return n.value, m.value, g.value
+
+    def cube(self):
+        out = np.zeros(5)
+        self._c(self._lib.tc_get_cube(self._h, _ptr(out)))
+        return out
+
+    def tree(self):
+        n, M, G = self.sizes()
+        perm = np.empty(n, np.uint32)
+        keys = np.empty(n, np.uint64)
+        self._c(self._lib.tc_get_tree(self._h, _ptr(perm), _ptr(keys)))
+        a = {k: np.empty(M, np.int32) for k in ("level", "first", "count", "child_first", "nchild")}
+        a["prefix"] = np.empty(M, np.uint64)
+        a["mass"] = np.empty(M)
+        a["com"] = np.empty((M, 3))
+        a["quad"] = np.empty((M, 6))
+        self._c(self._lib.tc_get_nodes(self._h, _ptr(a["level"]), _ptr(a["prefix"]), _ptr(a["first"]),
+                                       _ptr(a["count"]), _ptr(a["child_first"]), _ptr(a["nchild"]),
+                                       _ptr(a["mass"]), _ptr(a["com"]), _ptr(a["quad"])))
+        gf, gc, gr = np.empty(G, np.int32), np.empty(G, np.int32), np.empty(G, np.int32)
+        self._c(self._lib.tc_get_groups(self._h, _ptr(gf), _ptr(gc), _ptr(gr)))
+        a.update(perm=perm, keys=keys, gfirst=gf, gcount=gc, gref=gr)
+        return a
+
+    def lists(self, per_group=True):
+        G = self.sizes()[2]
+        nc = np.empty(G, np.int32) if per_group else None
+        nb = np.empty(G, np.int32) if per_group else None
+        hs = np.empty(G, np.uint64) if per_group else None
+        it, ce, bo = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._c(self._lib.tc_get_lists(self._h, _ptr(nc), _ptr(nb), _ptr(hs), ctypes.byref(it),
+                                       ctypes.byref(ce), ctypes.byref(bo)))
+        return dict(ncell=nc, nbody=nb, hash=hs, interactions=it.value, cells=ce.value, bodies=bo.value)
+
+    def diag(self):
+        out = np.zeros(8)
+        self._c(self._lib.tc_diag(self._h, _ptr(out)))
+        return out
+
+    def direct(self, idx, eps: float, G: float = 1.0):
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        acc = np.empty((idx.shape[0], 3))
+        pot = np.empty(idx.shape[0])
+        self._c(self._lib.tc_direct(self._h, _ptr(idx), idx.shape[0], float(eps), float(G), _ptr(acc), _ptr(pot)))
+        return acc, pot
+
+
+# the three calls on the library's implicit default context
+def tc_build(pos, mass, n: int, leaf_max: int):
+    lib = load()
+    _check(lib.tc_build(_ptr(pos), _ptr(mass), int(n), int(leaf_max)))
+
+
+def tc_forces(theta: float, eps: float, G: float = 1.0):
+    lib = load()
+    _check(lib.tc_forces(float(theta), float(eps), float(G)))
+
+
+def tc_step(dt: float):
+    lib = load()
+    _check(lib.tc_step(float(dt)))

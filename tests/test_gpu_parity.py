@@ -1,0 +1,388 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI (libtc.so).
+
+Bit-exact: Morton permutation and keys, the node table (levels, prefixes,
+body ranges, children), the groups, and the per-group interaction-list
+lengths and hashes, except for groups the oracle flags as holding an
+opening test within 1e-6 (relative) of the threshold.
+
+Floating point: forces within 2e-5 relative of the oracle's FP64 forces on
+the same tree and lists, for every body whose force is not dominated by
+cancellation; every body within the float32 rounding bound of its list sum,
+err <= 2e-5 |a| + 32 u sum_j |a_ij| (u = 2^-24).  Cell masses and centres of
+mass within FP64 rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1211_2293_gb300 import inputs
+from tests.helpers import rel_err_rms
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def _dev(x):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _bodies(kind, n, seed):
+    if kind == "plummer":
+        p, v, m = inputs.plummer(n, seed)
+    elif kind == "uniform":
+        p, v, m = inputs.uniform_cube(n, seed)
+    elif kind == "random":
+        rng = np.random.default_rng(seed)
+        p = rng.standard_normal((n, 3)).astype(np.float32)
+        v = np.zeros((n, 3), np.float32)
+        m = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    elif kind == "coincident":
+        p = np.zeros((n, 3), np.float32)
+        p[: n // 2] = [0.5, 0.5, 0.5]
+        p[n // 2:] = [-0.25, 0.75, 0.125]
+        v = np.zeros((n, 3), np.float32)
+        m = np.full(n, 1.0 / n, np.float32)
+    else:
+        raise ValueError(kind)
+    return p, v, m
+
+
+def _ctx(tc, **cfg):
+    base = dict(gmax=64, verify=1, want_pot=1, precise=1)
+    base.update(cfg)
+    return tc.Context(**base)
+
+
+def _compare_tree(ctx, t, gmax):
+    tr = ctx.tree()
+    n, M, G = ctx.sizes()
+    assert n == t.n and M == t.M, (M, t.M)
+    assert np.array_equal(tr["perm"], t.perm)
+    assert np.array_equal(tr["keys"], t.keys)
+    assert np.array_equal(ctx.cube(), t.cube5)
+    for k in ("level", "first", "count", "nchild", "child_first"):
+        assert np.array_equal(tr[k].astype(np.int64), getattr(t, k).astype(np.int64)), k
+    assert np.array_equal(tr["prefix"], t.prefix)
+    side = t.side()
+    assert np.allclose(tr["mass"], t.node_mass, rtol=1e-12, atol=0)
+    scale = np.abs(t.com).max(1) + side
+    assert np.all(np.abs(tr["com"] - t.com).max(1) <= 1e-12 * scale)
+    qs = t.node_mass * side ** 2
+    assert np.all(np.abs(tr["quad"] - t.quad).max(1) <= 1e-9 * qs)
+    t.make_groups(gmax)
+    assert G == t.G
+    assert np.array_equal(tr["gfirst"], t.gfirst)
+    assert np.array_equal(tr["gcount"], t.gcount)
+    assert np.array_equal(tr["gref"], t.gref)
+
+
+@pytest.mark.parametrize("kind,n,leaf,gmax", [
+    ("plummer", 4096, 8, 64), ("random", 1, 1, 32), ("random", 2, 1, 32), ("random", 9, 8, 32),
+    ("random", 17, 4, 64), ("random", 100, 3, 128), ("uniform", 5000, 16, 64), ("coincident", 40, 4, 32),
+    ("random", 3000, 1, 32), ("plummer", 20000, 64, 128)])
+def test_tree_bit_exact(tc, kind, n, leaf, gmax):
+    p, _, m = _bodies(kind, n, 7)
+    ctx = _ctx(tc, gmax=gmax)
+    ctx.build(_dev(p), _dev(m), leaf)
+    t = oracle.Tree(p, m, leaf)
+    _compare_tree(ctx, t, gmax)
+
+
+def _check_forces(acc, pot, w, t, mask_bodies, tol=2e-5, kappa_max=50.0):
+    a_or = w["acc"][mask_bodies]
+    a_gpu = acc[mask_bodies].astype(np.float64)
+    err = np.linalg.norm(a_gpu - a_or, axis=1)
+    amp = np.linalg.norm(a_or, axis=1)
+    amag = w["amag"][mask_bodies]
+    kappa = amag / np.maximum(amp, 1e-300)
+    assert np.all(err <= tol * amp + 32 * U32 * amag), (err / amp).max()
+    well = kappa <= kappa_max
+    rel = err[well] / amp[well]
+    assert rel.max() <= tol, rel.max()
+    if pot is not None:
+        p_or = w["pot"][mask_bodies]
+        perr = np.abs(pot[mask_bodies] - p_or)
+        assert np.all(perr <= tol * np.abs(p_or)), (perr / np.abs(p_or)).max()
+    return float(rel.max()), int((~well).sum())
+
+
+def _walk_case(tc, kind, n, leaf, gmax, theta, eps, G=1.0, precise=1, stack=1024, seed=3):
+    p, _, m = _bodies(kind, n, seed)
+    ctx = _ctx(tc, gmax=gmax, precise=precise, stack=stack)
+    ctx.build(_dev(p), _dev(m), leaf)
+    ctx.forces(theta, eps, G)
+    acc, pot = ctx.get_acc(with_pot=True)
+    L = ctx.lists()
+    t = oracle.Tree(p, m, leaf, gmax)
+    w = t.walk(theta, eps, G)
+    return ctx, t, w, acc, pot, L
+
+
+@pytest.mark.parametrize("kind,n,leaf,gmax,theta,eps", [
+    ("plummer", 4096, 8, 64, 0.5, 0.01),
+    ("plummer", 4096, 8, 32, 0.75, 0.01),
+    ("plummer", 4096, 8, 128, 0.9, 0.01),
+    ("uniform", 20000, 16, 64, 0.7, 1e-3),
+    ("random", 777, 1, 32, 0.6, 0.05),
+    ("coincident", 100, 4, 32, 0.5, 0.01),
+    ("random", 2, 1, 32, 0.5, 0.1),
+    ("random", 1, 1, 32, 0.5, 0.1),
+])
+def test_lists_and_forces_match_oracle(tc, kind, n, leaf, gmax, theta, eps):
+    ctx, t, w, acc, pot, L = _walk_case(tc, kind, n, leaf, gmax, theta, eps, G=0.75)
+    ok = w["flag"] == 0
+    assert ok.mean() > 0.9
+    assert np.array_equal(L["ncell"][ok], w["ncell"][ok])
+    assert np.array_equal(L["nbody"][ok], w["nbody"][ok])
+    assert np.array_equal(L["hash"][ok], w["hash"][ok])
+    assert L["interactions"] == int(np.sum(t.gcount * (L["ncell"] + L["nbody"])))
+    body_ok = np.zeros(n, bool)
+    for g in np.where(ok)[0]:
+        body_ok[t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]] = True
+    if n == 1:
+        assert np.all(acc == 0)
+        return
+    _check_forces(acc, pot, w, t, body_ok)
+
+
+def test_theta_zero_is_direct_summation(tc):
+    n = 3000
+    ctx, t, w, acc, pot, L = _walk_case(tc, "plummer", n, 8, 64, 0.0, 0.01, stack=4096)
+    assert np.all(L["ncell"] == 0) and np.all(L["nbody"] == n)
+    ad, pd = oracle.direct(*_bodies("plummer", n, 3)[::2], 0.01)
+    _check_forces(acc, pot, dict(acc=ad, pot=pd, amag=w["amag"]), t, np.ones(n, bool))
+
+
+def test_plain_mode_matches_oracle(tc):
+    ctx, t, w, acc, pot, L = _walk_case(tc, "plummer", 4096, 8, 64, 0.5, 0.01, precise=0)
+    ok = w["flag"] == 0
+    assert np.array_equal(L["ncell"][ok], w["ncell"][ok])
+    body_ok = np.zeros(t.n, bool)
+    for g in np.where(ok)[0]:
+        body_ok[t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]] = True
+    _check_forces(acc, pot, w, t, body_ok, tol=1e-4)
+
+
+def test_full_size_uniform_1m_sampled(tc):
+    """The bench workload (uniform cube, N = 2^20, leaf 16, eps 1e-3,
+    theta 0.5 and 0.7, default launch configuration): whole tree bit-exact,
+    lists and forces of sampled groups against the oracle, RMS error against
+    direct summation on 4096 sampled bodies at or below 1e-3 at theta 0.5."""
+    n = 1 << 20
+    p, _, m = _bodies("uniform", n, 0)
+    ctx = tc.Context(verify=1, want_pot=0)
+    gmax = ctx.config()["gmax"]
+    ctx.build(_dev(p), _dev(m), 16)
+    t = oracle.Tree(p, m, 16)
+    _compare_tree(ctx, t, gmax)
+    for theta in (0.5, 0.7):
+        ctx.forces(theta, 1e-3)
+        acc = ctx.get_acc()
+        L = ctx.lists()
+        groups = []
+        for g0 in np.linspace(0, t.G - 200, 6).astype(int):
+            groups.append((g0, g0 + 200))
+        body_ok = np.zeros(n, bool)
+        w_all = dict(acc=np.full((n, 3), np.nan), amag=np.full(n, np.nan))
+        for g0, g1 in groups:
+            w = t.walk(theta, 1e-3, groups=(g0, g1), want_pot=False)
+            sl = slice(g0, g1)
+            ok = w["flag"][sl] == 0
+            assert np.array_equal(L["ncell"][sl][ok], w["ncell"][sl][ok])
+            assert np.array_equal(L["nbody"][sl][ok], w["nbody"][sl][ok])
+            assert np.array_equal(L["hash"][sl][ok], w["hash"][sl][ok])
+            for g in np.arange(g0, g1)[ok]:
+                idx = t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]
+                body_ok[idx] = True
+                w_all["acc"][idx] = w["acc"][idx]
+                w_all["amag"][idx] = w["amag"][idx]
+        _check_forces(acc, None, w_all, t, body_ok)
+        if theta == 0.5:
+            idx = inputs.sample_indices(n, 4096, seed=1)
+            ad, _ = ctx.direct(idx, 1e-3)
+            assert rel_err_rms(acc[idx].astype(np.float64), ad) <= 1e-3
+
+
+def test_direct_kernel_matches_oracle(tc):
+    p, _, m = _bodies("plummer", 20000, 5)
+    ctx = _ctx(tc)
+    ctx.build(_dev(p), _dev(m), 8)
+    idx = inputs.sample_indices(20000, 300, seed=2)
+    a, ph = ctx.direct(idx, 0.01, 2.0)
+    ao, po = oracle.direct(p, m, 0.01, 2.0, idx=idx)
+    assert np.all(np.linalg.norm(a - ao, axis=1) <= 1e-5 * np.linalg.norm(ao, axis=1))
+    assert np.all(np.abs(ph - po) <= 1e-6 * np.abs(po))
+
+
+def test_step_matches_oracle(tc):
+    """One kick-drift-kick step: the drift from the GPU's own state to
+    within float32 rounding, the rebuilt tree bit-exact, the closing kick
+    within the force tolerance."""
+    n, dt, eps = 4096, 1e-3, 0.01
+    p, v, m = _bodies("plummer", n, 0)
+    ctx = _ctx(tc)
+    ctx.build(_dev(p), _dev(m), 8)
+    ctx.set_velocity(_dev(v))
+    ctx.forces(0.5, eps)
+    a0 = ctx.get_acc().astype(np.float64)
+    x0, v0 = ctx.get_state()
+    ctx.step(dt)
+    x1, v1 = ctx.get_state()
+    vh = v0.astype(np.float64) + a0 * (dt / 2)
+    x1o = x0.astype(np.float64) + vh * dt
+    assert np.all(np.abs(x1 - x1o) <= 4 * np.spacing(np.abs(x1o).astype(np.float32)))
+    t = oracle.Tree(x1, m, 8)
+    _compare_tree(ctx, t, 64)
+    w = t.walk(0.5, eps)
+    v1o = vh + w["acc"] * (dt / 2)
+    tol = 2e-5 * np.abs(w["acc"]).max() * dt + 4 * np.spacing(np.abs(v1o).astype(np.float32))
+    assert np.all(np.abs(v1 - v1o) <= tol)
+
+
+def test_diag_matches_oracle(tc):
+    p, v, m = _bodies("plummer", 4096, 0)
+    ctx = _ctx(tc)
+    ctx.build(_dev(p), _dev(m), 8)
+    ctx.set_velocity(_dev(v))
+    ctx.forces(0.5, 0.01)
+    d = ctx.diag()
+    _, pot = ctx.get_acc(with_pot=True)
+    do = oracle.diag(p, v, m, pot)
+    assert np.allclose(d, do, rtol=1e-10, atol=1e-12)
+    t = oracle.Tree(p, m, 8, 64)
+    w = t.walk(0.5, 0.01)
+    assert abs(d[1] - oracle.diag(p, v, m, w["pot"])[1]) <= 1e-5 * abs(d[1])
+
+
+def test_energy_and_momentum_over_steps(tc):
+    """20 KDK steps of a Plummer sphere: momentum stays ~0 and the energy
+    change is small (treecode force error + O(dt^2))."""
+    p, v, m = _bodies("plummer", 8192, 4)
+    ctx = _ctx(tc)
+    ctx.build(_dev(p), _dev(m), 8)
+    ctx.set_velocity(_dev(v))
+    ctx.forces(0.5, 0.01)
+    d0 = ctx.diag()
+    for _ in range(20):
+        ctx.step(1e-3)
+    d1 = ctx.diag()
+    E0, E1 = d0[0] + d0[1], d1[0] + d1[1]
+    assert abs(E1 - E0) <= 2e-4 * abs(E0)
+    assert np.abs(d1[2:5] - d0[2:5]).max() <= 1e-5
+
+
+def test_checkpoint_resume_bit_identical(tc):
+    p, v, m = _bodies("plummer", 4096, 6)
+    ctx = _ctx(tc)
+    ctx.build(_dev(p), _dev(m), 8)
+    ctx.set_velocity(_dev(v))
+    ctx.forces(0.6, 0.01)
+    for _ in range(2):
+        ctx.step(1e-3)
+    xs, vs = ctx.get_state()
+    for _ in range(3):
+        ctx.step(1e-3)
+    xa, va = ctx.get_state()
+    ctx.set_state(xs, vs)
+    ctx.forces(0.6, 0.01)
+    for _ in range(3):
+        ctx.step(1e-3)
+    xb, vb = ctx.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_host_buffers_give_the_same_result(tc):
+    p, _, m = _bodies("plummer", 4096, 9)
+    c1 = _ctx(tc)
+    c1.build(_dev(p), _dev(m), 8)
+    c1.forces(0.5, 0.01)
+    c2 = _ctx(tc)
+    c2.build(p, m, 8)
+    c2.forces(0.5, 0.01)
+    assert np.array_equal(c1.get_acc(), c2.get_acc())
+
+
+def test_default_context_calls(tc):
+    p, _, m = _bodies("plummer", 2048, 1)
+    tc.tc_build(_dev(p), _dev(m), 2048, 8)
+    tc.tc_forces(0.5, 0.01, 1.0)
+    tc.tc_step(1e-3)
+    lib = tc.load()
+    assert lib.tc_default()
+
+
+# ---------------------------------------------------------------- errors
+def test_invalid_arguments(tc):
+    p, _, m = _bodies("random", 100, 1)
+    ctx = _ctx(tc)
+    with pytest.raises(tc.TcError) as e:
+        ctx.forces(0.5, 0.01)
+    assert e.value.code == tc.TC_ESTATE
+    with pytest.raises(tc.TcError) as e:
+        ctx.build(_dev(p[:0]), _dev(m[:0]), 8)
+    assert e.value.code == tc.TC_EINVAL
+    with pytest.raises(tc.TcError) as e:
+        ctx.build(_dev(p), _dev(m), 0)
+    assert e.value.code == tc.TC_EINVAL
+    ctx.build(_dev(p), _dev(m), 8)
+    with pytest.raises(tc.TcError) as e:
+        ctx.step(1e-3)
+    assert e.value.code == tc.TC_ESTATE
+    for th, ep in ((-0.1, 0.01), (0.5, 0.0), (float("nan"), 0.01), (0.5, float("inf"))):
+        with pytest.raises(tc.TcError) as e:
+            ctx.forces(th, ep)
+        assert e.value.code == tc.TC_EINVAL
+    with pytest.raises(tc.TcError):
+        ctx.set_config(gmax=48)
+    ctx.forces(0.5, 0.01)  # still usable
+
+
+@pytest.mark.parametrize("bad", ["nan_pos", "inf_pos", "zero_mass", "neg_mass"])
+def test_bad_inputs_rejected(tc, bad):
+    p, _, m = _bodies("random", 100, 2)
+    if bad == "nan_pos":
+        p[17, 1] = np.nan
+    elif bad == "inf_pos":
+        p[3, 0] = np.inf
+    elif bad == "zero_mass":
+        m[5] = 0.0
+    else:
+        m[9] = -1.0
+    ctx = _ctx(tc)
+    with pytest.raises(tc.TcError) as e:
+        ctx.build(_dev(p), _dev(m), 8)
+    assert e.value.code == tc.TC_EINVAL
+    p2, _, m2 = _bodies("random", 100, 3)
+    ctx.build(_dev(p2), _dev(m2), 8)  # the context recovers
+    ctx.forces(0.5, 0.01)
+    ctx.get_acc()
+
+
+def test_walk_stack_overflow_is_reported(tc):
+    """A stack too small for theta = 0 sets the kernel's error word (the
+    kernel checks before every push) and the next sync reports it."""
+    p, _, m = _bodies("plummer", 4096, 1)
+    ctx = _ctx(tc, stack=64)
+    ctx.build(_dev(p), _dev(m), 4)
+    ctx.forces(0.0, 0.01)
+    with pytest.raises(tc.TcError) as e:
+        ctx.get_acc()
+    assert e.value.code == tc.TC_EDEVICE
+    ctx.set_config(stack=4096)
+    ctx.forces(0.0, 0.01)
+    ctx.get_acc()
+
+
+def test_allocation_cap_is_reported(tc, monkeypatch):
+    p, _, m = _bodies("random", 10000, 4)
+    monkeypatch.setenv("TC_ALLOC_CAP_BYTES", "100000")
+    ctx = _ctx(tc)
+    with pytest.raises(tc.TcError) as e:
+        ctx.build(_dev(p), _dev(m), 8)
+    assert e.value.code == tc.TC_ENOMEM
+    monkeypatch.delenv("TC_ALLOC_CAP_BYTES")
+    ctx2 = _ctx(tc)
+    ctx2.build(_dev(p), _dev(m), 8)
