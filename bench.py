@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the treecode force phase on one GB300 (or N replicas).
+
+Workload (default): uniform random cube [-1, 1]^3, N = 2^20 equal masses,
+leaf threshold 16, Plummer softening eps = 1e-3, opening angle theta = 0.5,
+kick-drift-kick leapfrog with dt = 1e-4.  One timed step is one pass of the
+whole hot path: kick + drift, tree build (bounding box, Morton keys, radix
+sort, node table, FP64 moments, groups), the walk + force kernel, kick.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  ``value`` is bodies/s summed over ranks
+(each rank runs an independent replica: the force phase needs no exchange
+on one GPU), timed with CUDA events around each step, L2 flushed (a 256 MiB
+write) between steps.  ``roofline`` is the walk + force kernel against the
+FP32 CUDA-core peak (20 flops per body-source interaction), timed with the
+library's CUDA events on its own stream.  ``--impl reference`` times the CPU
+oracle (plain FP64 C, one core) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "force evals (bodies/s) at RMS force err 1e-3: plain vs learned; % FP32 peak"
+N_DEFAULT = 1 << 20
+LEAF, EPS, DT, THETA, SEED = 16, 1e-3, 1e-4, 0.5, 0
+FLOPS_PER_INTERACTION = 20
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "walk_uniform_1m.txt")
+WALK_SRC = os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", "tc_walk.cu")
+
+
+def workload_config(n, theta):
+    return {
+        "workload": f"uniform cube [-1,1]^3, N={n}, equal masses 1/N, leaf 16, eps 1e-3, theta {theta}, "
+                    f"KDK leapfrog dt 1e-4 (build + walk/force + update per step)",
+        "n_bodies": n, "theta": theta, "leaf": LEAF, "eps": EPS, "dt": DT, "seed": SEED,
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    return 2.0 * FP32_LANES * SMS * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.dev is not None:
+                cmd += ["-i", str(self.dev)]
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile():
+    """dram bytes per walk launch from the committed ncu summary, or None if
+    the walk kernel's source changed since it was captured."""
+    try:
+        txt = open(PROFILE_TRAFFIC).read()
+        cur = hashlib.sha256(open(WALK_SRC, "rb").read()).hexdigest()[:16]
+        kv = {}
+        for line in txt.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("walk_source_sha256_16") != cur:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(p, m, v, theta, frac_groups=8, gmax=64):
+    """One sampled oracle step: full tree build, the walk for 1/frac_groups of
+    the groups (evenly spread), the leapfrog update; returns the extrapolated
+    seconds of a whole step and what was sampled."""
+    import oracle
+
+    n = p.shape[0]
+    t0 = time.perf_counter()
+    t = oracle.Tree(p, m, LEAF, gmax)
+    t1 = time.perf_counter()
+    nchunks = 16
+    per = max(1, t.G // (frac_groups * nchunks))
+    walked = 0
+    for g0 in np.linspace(0, t.G - per, nchunks).astype(int):
+        t.walk(theta, EPS, groups=(int(g0), int(g0) + per), want_pot=False)
+        walked += per
+    t2 = time.perf_counter()
+    acc = np.zeros((n, 3))
+    vv = oracle.kick(v.astype(np.float64), acc, DT / 2)
+    oracle.drift(p.astype(np.float64), vv, DT)
+    oracle.kick(vv, acc, DT / 2)
+    t3 = time.perf_counter()
+    scale = t.G / walked
+    est = (t1 - t0) + (t2 - t1) * scale + (t3 - t2)
+    sample = (f"oracle tree build of all {n} bodies + walk/force of {walked} of {t.G} groups "
+              f"(x{scale:.1f} extrapolated) + leapfrog update")
+    return est, sample, (t3 - t0)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1211_2293_gb300 import inputs
+
+    n = args.n
+    p, v, m = inputs.uniform_cube(n, SEED)
+    times = []
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        est, sample, _ = oracle_sample(p, m, v, args.theta, frac_groups=args.ref_frac)
+        if k >= args.warmup:
+            times.append(est)
+    sec = statistics.mean(times)
+    value = n / sec
+    line = {
+        "metric": METRIC, "value": value, "unit": "bodies/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": workload_config(n, args.theta),
+        "cpu_baseline": {"value": value, "unit": "bodies/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "bodies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1211_2293_gb300 import inputs, tc
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    tc.load()
+    n = args.n
+    p, v, m = inputs.uniform_cube(n, SEED + rank)
+    P = torch.from_numpy(p).to(dev)
+    V = torch.from_numpy(v).to(dev)
+    Mm = torch.from_numpy(m).to(dev)
+    ctx = tc.Context(want_pot=0, verify=0)
+    ctx.build(P, Mm, LEAF)
+    ctx.set_velocity(V)
+    ctx.forces(args.theta, EPS)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.step(DT)
+    ctx.sync()
+
+    clocks = ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else None)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    step_ms, inter = [], []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(DT)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        inter.append(ctx.lists(per_group=False)["interactions"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    tim = ctx.timings()
+    ctx.set_timing(False)
+
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms / 1e3)
+
+    walk_ms = tim["walk_ms"] / args.steps
+    inter_avg = statistics.mean(inter)
+    achieved = inter_avg * FLOPS_PER_INTERACTION / (walk_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    traffic = _traffic_from_profile()
+
+    # accuracy against direct summation (4096 sampled bodies), current state
+    ctx.forces(args.theta, EPS)
+    acc = ctx.get_acc()
+    idx = inputs.sample_indices(n, 4096, seed=1)
+    ad, _ = ctx.direct(idx, EPS)
+    a = acc[idx].astype(np.float64)
+    rms = float(np.sqrt(np.mean(np.sum((a - ad) ** 2, 1) / np.sum(ad ** 2, 1))))
+
+    # end to end through the C ABI with host buffers: upload, build, forces,
+    # download of the accelerations
+    hp = torch.from_numpy(p).pin_memory()
+    hm = torch.from_numpy(m).pin_memory()
+    hacc = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    e2e_ctx = tc.Context(want_pot=0, verify=0)
+    for _ in range(2):
+        e2e_ctx.build(hp, hm, LEAF)
+        e2e_ctx.forces(args.theta, EPS)
+        e2e_ctx.get_acc(hacc)
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_ctx.build(hp, hm, LEAF)
+        e2e_ctx.forces(args.theta, EPS)
+        e2e_ctx.get_acc(hacc)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = n * world / (statistics.mean(e2e_ms) / 1e3)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            est, sample, _ = oracle_sample(p, m, v, args.theta, frac_groups=args.cpu_frac)
+            cpu = {"value": n / est, "unit": "bodies/s", "cores": 1, "kind": "oracle", "sample": sample}
+        line = {
+            "metric": METRIC, "value": value, "unit": "bodies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(n, args.theta),
+            "rms_force_err": rms,
+            "interactions_per_step": inter_avg,
+            "phase_ms_per_step": {"build": tim["build_ms"] / args.steps, "walk_force": walk_ms,
+                                  "update": tim["update_ms"] / args.steps},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_walk (walk + force)",
+                         "peak_basis": "2 flops x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)",
+                         "frac_at_measured_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])
+                                                    if clk.get("sm_mhz") else None)},
+            "e2e": {"value": e2e_val, "unit": "bodies/s", "h2d_bytes_per_step": int(16 * n),
+                    "d2h_bytes_per_step": int(12 * n),
+                    "what": "force evaluation from pinned host pos/mass: upload, build, walk/force, "
+                            "download of accelerations"},
+            "gpu_launches": tim["launches"],
+            "clocks": clk,
+            "wall_s_timed": wall,
+            "cpu_baseline": cpu,
+        }
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--theta", type=float, default=THETA)
+    ap.add_argument("--cpu-frac", type=int, default=8, help="oracle walks 1/cpu_frac of the groups")
+    ap.add_argument("--ref-frac", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -147,6 +147,16 @@ int tc_diag(tc_ctx *ctx, double *out8);
 int tc_direct(tc_ctx *ctx, const int64_t *idx, int64_t ns, float eps, float G, double *acc,
               double *pot);
 
+/* Phase timers.  tc_set_timing(ctx, 1) starts recording CUDA events on the
+ * context's stream around the build, the walk + force kernel and the
+ * leapfrog updates (and clears earlier records).  tc_get_timings
+ * synchronises and returns out6 = {build ms, walk ms, update ms (sums over
+ * the calls since the last tc_set_timing / tc_get_timings), kernels launched
+ * by this process's libtc since then, kernels launched in total, 0}, then
+ * clears the records. */
+int tc_set_timing(tc_ctx *ctx, int on);
+int tc_get_timings(tc_ctx *ctx, double *out6);
+
 /* Wait for the context's stream; report device errors. */
 int tc_sync(tc_ctx *ctx);
 

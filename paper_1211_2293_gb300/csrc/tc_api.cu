@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "../../include/tc.h"
 #include "tc_internal.cuh"
@@ -55,7 +56,22 @@ struct tc_ctx {
     Info* info_h = nullptr;  // pinned mirror
     size_t allocated = 0;
     std::unordered_map<void*, size_t> sizes;
+
+    // phase timers (CUDA events on the context stream), when enabled
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_phase[3];  // build, walk, update
+    long long launches_mark = 0;
 };
+
+namespace tc {
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace tc
 
 namespace {
 
@@ -206,11 +222,40 @@ int check_device(tc_ctx* c)
 
 bool finite(float x) { return std::isfinite(x); }
 
+cudaEvent_t take_event(tc_ctx* c)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// records the start of a timed phase; returns the event (or null)
+cudaEvent_t phase_begin(tc_ctx* c)
+{
+    if (!c->timing) return nullptr;
+    cudaEvent_t e = take_event(c);
+    if (e) cudaEventRecord(e, c->stream);
+    return e;
+}
+
+void phase_end(tc_ctx* c, int phase, cudaEvent_t start)
+{
+    if (!start) return;
+    cudaEvent_t e = take_event(c);
+    if (!e) return;
+    cudaEventRecord(e, c->stream);
+    c->ev_phase[phase].push_back({start, e});
+}
+
 // The whole build from c->pos / c->mass (already on the device).
 int build_tree(tc_ctx* c)
 {
     cudaStream_t s = c->stream;
     const int64_t n = c->n;
+    cudaEvent_t t0 = phase_begin(c);
     TC_CUDA(c, cudaMemsetAsync(&c->info->err, 0, sizeof(int32_t), s));
     int nb = bbox_blocks(n);
     launch_bbox(c->pos, n, c->bbox_partial, nb, c->info, s);
@@ -240,6 +285,7 @@ int build_tree(tc_ctx* c)
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);
     launch_group_table(c->gflag, c->gscan, c->gref_at, n, &c->totals[1], c->gfirst, c->gref, c->info, s);
     TC_CUDA(c, cudaGetLastError());
+    phase_end(c, 0, t0);
     c->built = true;
     c->have_forces = false;
     return TC_OK;
@@ -274,8 +320,10 @@ int run_forces(tc_ctx* c, float theta, float eps, float G)
     if (c->M < st) st = c->M < 32 ? 32 : c->M;  // a stack of M entries cannot overflow
     st = (st + 3) & ~(int64_t)3;                // keeps every warp's tiles 16-byte aligned
     wc.stack = (int)st;
+    cudaEvent_t t0 = phase_begin(c);
     cudaError_t e = launch_walk(a, wc, c->num_sms, c->stream);
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk launch: %s", cudaGetErrorString(e));
+    phase_end(c, 1, t0);
     c->have_forces = true;
     c->forces_pot = c->cfg.want_pot != 0;
     c->theta = theta;
@@ -331,6 +379,7 @@ void tc_destroy(tc_ctx* c)
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->info_h) cudaFreeHost(c->info_h);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -407,12 +456,16 @@ int tc_ctx_step(tc_ctx* c, float dt)
     if (!c) return fail(c, TC_EINVAL, "tc_step: null context");
     if (!finite(dt)) return fail(c, TC_EINVAL, "tc_step: dt must be finite");
     if (!c->have_forces) return fail(c, TC_ESTATE, "tc_step: compute forces on the current positions first");
+    cudaEvent_t t0 = phase_begin(c);
     launch_kick_drift(c->pos, c->vel, c->acc, c->n, 0.5f * dt, dt, c->stream);
+    phase_end(c, 2, t0);
     int r = build_tree(c);
     if (r) return r;
     r = run_forces(c, c->theta, c->eps, c->Gc);
     if (r) return r;
+    t0 = phase_begin(c);
     launch_kick(c->vel, c->acc, c->n, 0.5f * dt, c->stream);
+    phase_end(c, 2, t0);
     TC_CUDA(c, cudaGetLastError());
     return TC_OK;
 }
@@ -613,6 +666,41 @@ int tc_direct(tc_ctx* c, const int64_t* idx, int64_t ns, float eps, float G, dou
     TC_CUDA(c, cudaMemcpyAsync(acc, c->dir_out, 3 * ns * sizeof(double), cudaMemcpyDefault, c->stream));
     if (pot) TC_CUDA(c, cudaMemcpyAsync(pot, c->dir_out + 3 * ns, ns * sizeof(double), cudaMemcpyDefault, c->stream));
     return check_device(c);
+}
+
+int tc_set_timing(tc_ctx* c, int on)
+{
+    if (!c) return fail(c, TC_EINVAL, "tc_set_timing: null context");
+    TC_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->timing = on != 0;
+    for (auto& v : c->ev_phase) v.clear();
+    c->ev_used = 0;
+    c->launches_mark = launches_total();
+    return TC_OK;
+}
+
+int tc_get_timings(tc_ctx* c, double* out6)
+{
+    if (!c || !out6) return fail(c, TC_EINVAL, "tc_get_timings: null argument");
+    int r = check_device(c);
+    if (r) return r;
+    for (int p = 0; p < 3; p++) {
+        double ms = 0.0;
+        for (auto& pr : c->ev_phase[p]) {
+            float t = 0.f;
+            TC_CUDA(c, cudaEventElapsedTime(&t, pr.first, pr.second));
+            ms += t;
+        }
+        out6[p] = ms;
+        c->ev_phase[p].clear();
+    }
+    long long now = launches_total();
+    out6[3] = (double)(now - c->launches_mark);
+    c->launches_mark = now;
+    c->ev_used = 0;
+    out6[4] = (double)launches_total();
+    out6[5] = 0.0;
+    return TC_OK;
 }
 
 const char* tc_last_error(tc_ctx* c)

@@ -460,6 +460,7 @@ int bbox_blocks(int64_t n)
 void launch_bbox(const float* pos, int64_t n, float* partial, int nblocks, Info* info, cudaStream_t s)
 {
     k_bbox<<<nblocks, kBboxThreads, 0, s>>>(pos, n, partial, info);
+    count_launches(1);
 }
 
 void launch_keys(const float* pos, const float* mass, int64_t n, const Info* info, uint64_t* keys,
@@ -467,12 +468,14 @@ void launch_keys(const float* pos, const float* mass, int64_t n, const Info* inf
 {
     k_keys<<<nblk(n, 256), 256, 0, s>>>(pos, mass, n, info, keys, idx,
                                          const_cast<int32_t*>(&info->err));
+    count_launches(1);
 }
 
 void launch_gather(const float* pos, const float* mass, const uint32_t* perm, int64_t n, float4* body,
                    cudaStream_t s)
 {
     k_gather<<<nblk(n, 256), 256, 0, s>>>(pos, mass, perm, n, body);
+    count_launches(1);
 }
 
 void launch_node_counts(const uint64_t* keys, int64_t n, int leaf_max, int8_t* w, int8_t* delta, int8_t* top,
@@ -480,17 +483,20 @@ void launch_node_counts(const uint64_t* keys, int64_t n, int leaf_max, int8_t* w
 {
     k_window<<<nblk(n, 256), 256, 0, s>>>(keys, n, leaf_max, w);
     k_node_counts<<<nblk(n, 256), 256, 0, s>>>(keys, w, n, leaf_max, delta, top, nstart);
+    count_launches(2);
 }
 
 void launch_emit_preorder(const int8_t* delta, const uint32_t* nstart, const uint32_t* prepos, int64_t n,
                           uint32_t* pre_level, uint32_t* pre_first, uint32_t* iota, cudaStream_t s)
 {
     k_emit_preorder<<<nblk(n, 256), 256, 0, s>>>(delta, nstart, prepos, n, pre_level, pre_first, iota);
+    count_launches(1);
 }
 
 void launch_inverse_perm(const uint32_t* perm, int64_t M, uint32_t* inv, cudaStream_t s)
 {
     k_inverse_perm<<<nblk(M, 256), 256, 0, s>>>(perm, M, inv);
+    count_launches(1);
 }
 
 void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n, const uint32_t* bfs_level,
@@ -498,11 +504,13 @@ void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n, co
                           int64_t M, NodeTables nt, cudaStream_t s)
 {
     k_node_finalize<<<nblk(M, 128), 128, 0, s>>>(keys, top, n, bfs_level, bfs_pre, pre_first, bfs_of_pre, M, nt);
+    count_launches(1);
 }
 
 void launch_moments(const float4* body, int64_t M, const Info* info, NodeTables nt, cudaStream_t s)
 {
     k_moments<<<nblk(M, 128), 128, 0, s>>>(body, M, info, nt);
+    count_launches(1);
 }
 
 void launch_group_marks(int64_t M, const NodeTables nt, int gmax, int64_t n, uint32_t* gflag, int32_t* gref_at,
@@ -510,12 +518,14 @@ void launch_group_marks(int64_t M, const NodeTables nt, int gmax, int64_t n, uin
 {
     cudaMemsetAsync(gflag, 0, n * sizeof(uint32_t), s);
     k_group_marks<<<nblk(M, 128), 128, 0, s>>>(M, nt, gmax, gflag, gref_at);
+    count_launches(1);
 }
 
 void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int32_t* gref_at, int64_t n,
                         const uint32_t* total, int32_t* gfirst, int32_t* gref, Info* info, cudaStream_t s)
 {
     k_group_table<<<nblk(n, 256), 256, 0, s>>>(gflag, gscan, gref_at, n, total, gfirst, gref, info);
+    count_launches(1);
 }
 
 }  // namespace tc

@@ -68,7 +68,10 @@ struct SortBufs {
 };
 
 // ---------------------------------------------------------------- launchers
-// all launches go on `s`; none synchronises.
+// all launches go on `s`; none synchronises.  Every launcher adds the number
+// of kernels it launched to a process-wide counter (count_launches).
+void count_launches(int k);
+long long launches_total();
 
 // exclusive scan of n uint32 values into out (out may alias in), total to
 // *total_dev (device pointer, nullable)

@@ -202,6 +202,7 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, blocksum);
     k_scan_top<<<1, 1024, 0, s>>>(blocksum, nb, total_dev);
     k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, blocksum);
+    count_launches(3);
 }
 
 int64_t radix_hist_size(int64_t n) { return 256 * ((n + kSortTile - 1) / kSortTile); }
@@ -222,6 +223,7 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, int nbits, SortB
         k_radix_hist<K><<<nb, kSortThreads, 0, s>>>(ka, n, shift, b.hist, nb);
         scan_u32(b.hist, b.hist, nh, nullptr, b.blocksum, s);
         k_radix_scatter<K><<<nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, b.hist, nb);
+        count_launches(2);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
         passes++;

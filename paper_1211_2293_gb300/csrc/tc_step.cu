@@ -116,11 +116,13 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt, cudaStream_t s)
 {
     k_kick_drift<<<nblk(3 * n, 256), 256, 0, s>>>(pos, vel, acc, 3 * n, hkick, dt);
+    count_launches(1);
 }
 
 void launch_kick(float* vel, const float* acc, int64_t n, float hkick, cudaStream_t s)
 {
     k_kick<<<nblk(3 * n, 256), 256, 0, s>>>(vel, acc, 3 * n, hkick);
+    count_launches(1);
 }
 
 void launch_diag(const float* pos, const float* vel, const float* mass, const float* pot, int64_t n, Info* info,
@@ -130,12 +132,14 @@ void launch_diag(const float* pos, const float* vel, const float* mass, const fl
     unsigned nb = nblk(n, 256);
     if (nb > 1024) nb = 1024;
     k_diag<<<nb, 256, 0, s>>>(pos, vel, mass, pot, n, info->diag);
+    count_launches(1);
 }
 
 void launch_direct(const float* pos, const float* mass, int64_t n, const int64_t* idx, int64_t ns, float eps2,
                    float G, double* acc, double* pot, cudaStream_t s)
 {
     k_direct<<<nblk(ns, kDirTile), kDirTile, 0, s>>>(pos, mass, n, idx, ns, eps2, G, acc, pot);
+    count_launches(1);
 }
 
 }  // namespace tc

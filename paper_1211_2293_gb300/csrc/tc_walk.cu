@@ -370,6 +370,7 @@ cudaError_t launch_t(const WalkArgs& a, const WalkConfig& c, int num_sms, cudaSt
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (c.blocks_per_sm > 0 && c.blocks_per_sm < per_sm) per_sm = c.blocks_per_sm;
     kern<<<num_sms * per_sm, warps * 32, smem, s>>>(a, c.stack);
+    count_launches(1);
     return cudaGetLastError();
 }
 

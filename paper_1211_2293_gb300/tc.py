@@ -29,6 +29,7 @@ EXPORTS = [
     "tc_ctx_set_velocity", "tc_ctx_forces", "tc_ctx_step", "tc_get_acc", "tc_get_state", "tc_set_state",
     "tc_get_sizes", "tc_get_tree", "tc_get_nodes", "tc_get_groups", "tc_get_cube", "tc_get_lists",
     "tc_diag", "tc_direct", "tc_sync", "tc_last_error", "tc_build", "tc_forces", "tc_step", "tc_default",
+    "tc_set_timing", "tc_get_timings",
 ]
 
 
@@ -84,6 +85,8 @@ def load(path: str | None = None):
         "tc_forces": ([F, F, F], I32),
         "tc_step": ([F], I32),
         "tc_default": ([], P),
+        "tc_set_timing": ([P, I32], I32),
+        "tc_get_timings": ([P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -177,6 +180,16 @@ class Context:
 
     def sync(self):
         self._c(self._lib.tc_sync(self._h))
+
+    def set_timing(self, on: bool = True):
+        self._c(self._lib.tc_set_timing(self._h, int(bool(on))))
+
+    def timings(self) -> dict:
+        """Phase times (ms, summed since the last call) and kernel launches."""
+        out = np.zeros(6)
+        self._c(self._lib.tc_get_timings(self._h, _ptr(out)))
+        return dict(build_ms=out[0], walk_ms=out[1], update_ms=out[2], launches=int(out[3]),
+                    launches_total=int(out[4]))
 
     # ------------------------------------------------------------ outputs
     def get_acc(self, acc=None, pot=None, with_pot=False):

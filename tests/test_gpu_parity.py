@@ -231,15 +231,20 @@ def test_step_matches_oracle(tc):
     x0, v0 = ctx.get_state()
     ctx.step(dt)
     x1, v1 = ctx.get_state()
-    vh = v0.astype(np.float64) + a0 * (dt / 2)
+    h = dt / 2
+    vh = v0.astype(np.float64) + a0 * h
     x1o = x0.astype(np.float64) + vh * dt
-    assert np.all(np.abs(x1 - x1o) <= 4 * np.spacing(np.abs(x1o).astype(np.float32)))
+    # float32 rounding of vh = fl(v + fl(a h)) and x1 = fl(x + fl(vh dt)),
+    # each op within u = 2^-24 relative
+    err_vh = U32 * (np.abs(a0 * h) + np.abs(vh))
+    tol_x = 2 * (U32 * (np.abs(x1o) + np.abs(vh * dt)) + dt * err_vh)
+    assert np.all(np.abs(x1 - x1o) <= tol_x)
     t = oracle.Tree(x1, m, 8)
     _compare_tree(ctx, t, 64)
     w = t.walk(0.5, eps)
-    v1o = vh + w["acc"] * (dt / 2)
-    tol = 2e-5 * np.abs(w["acc"]).max() * dt + 4 * np.spacing(np.abs(v1o).astype(np.float32))
-    assert np.all(np.abs(v1 - v1o) <= tol)
+    v1o = vh + w["acc"] * h
+    tol_v = 2 * (err_vh + U32 * (np.abs(w["acc"] * h) + np.abs(v1o))) + 2e-5 * np.abs(w["acc"]) * h
+    assert np.all(np.abs(v1 - v1o) <= tol_v)
 
 
 def test_diag_matches_oracle(tc):
