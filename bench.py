@@ -50,6 +50,7 @@ def workload_config(n, theta):
                     f"KDK leapfrog dt 1e-4 (build + walk/force + update per step)",
         "n_bodies": n, "theta": theta, "leaf": LEAF, "eps": EPS, "dt": DT, "seed": SEED,
         "l2": "flushed between timed steps (256 MiB write)",
+        "clock_window": "1 s of back-to-back steps before the timed steps, then the timed steps",
     }
 
 
@@ -71,7 +72,7 @@ class ClockSampler:
     def start(self):
         try:
             self.f = open(self.path, "w")
-            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
             if self.dev is not None:
                 cmd += ["-i", str(self.dev)]
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
@@ -212,8 +213,14 @@ def run_ours(args, rank, world, local_rank):
         ctx.step(DT)
     ctx.sync()
 
+    # clocks are sampled (every 50 ms) over a 1 s window of the same step run
+    # back to back just before the timed steps, and through the timed steps
     clocks = ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else None)
     clocks.start()
+    t_load = time.perf_counter()
+    while time.perf_counter() - t_load < 1.0:
+        ctx.step(DT)
+        ctx.sync()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
