@@ -41,7 +41,60 @@ namespace tc {
 namespace {
 
 constexpr int kTile = 128;              // list entries per tile flush
-constexpr int kTileCap = kTile + 32;    // a step adds at most 32 before a flush check
+constexpr int kTileCap = kTile + 34;    // + up to 32 added by a step, + 1 pad, kept even
+
+// ---------------------------------------------------------------- packed FP32
+// Blackwell's paired FP32 instructions (add/sub/mul/fma .f32x2) work on a
+// 64-bit register holding two floats.  A list tile is stored pair-interleaved
+// -- {x_j, x_j+1}, {y_j, y_j+1}, {z_j, z_j+1}, {m_j, m_j+1} per pair of
+// entries -- so one pair of 16-byte shared loads yields two sources already
+// packed, and every FP32 operation of the force loop serves two sources.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2pack(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(f2 r, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2 f2sub(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float f2sum(f2 a)
+{
+    float x, y;
+    f2unpack(a, x, y);
+    return x + y;
+}
+
+// entry k of a pair-interleaved tile
+__device__ __forceinline__ void put_entry(float* tile, int k, float4 q)
+{
+    float* t = tile + 8 * (k >> 1) + (k & 1);
+    t[0] = q.x;
+    t[2] = q.y;
+    t[4] = q.z;
+    t[6] = q.w;
+}
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 {
@@ -72,60 +125,96 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x)
     c = __fadd_rn(c, e);
 }
 
+// The force loop: npairs pairs of sources against the lane's B bodies.
+// Body coordinates are held duplicated ({x, x}); the two halves of each
+// accumulator collect the even and the odd sources of the tile.
+//   r2 = |d|^2 + eps^2, ri = rsqrt(r2), a += d * m * ri^3, pot -= m * ri
 template <int B, bool POT>
-__device__ __forceinline__ void sum_tile(const float4* __restrict__ tile, int n, const float3 (&x)[B],
-                                         float eps2, float (&ax)[B], float (&ay)[B], float (&az)[B],
-                                         float (&ph)[B])
+__device__ __forceinline__ void sum_tile(const float* __restrict__ tile, int npairs, const f2 (&X)[B],
+                                         const f2 (&Y)[B], const f2 (&Z)[B], f2 E2, f2 (&ax)[B],
+                                         f2 (&ay)[B], f2 (&az)[B], f2 (&ph)[B])
 {
-#pragma unroll 4
-    for (int j = 0; j < n; j++) {
-        const float4 s = tile[j];
+    const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
+#pragma unroll 2
+    for (int p = 0; p < npairs; p++) {
+        const ulonglong2 xy = t2[2 * p];
+        const ulonglong2 zm = t2[2 * p + 1];
 #pragma unroll
         for (int b = 0; b < B; b++) {
-            float dx = s.x - x[b].x;
-            float dy = s.y - x[b].y;
-            float dz = s.z - x[b].z;
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-            float ri = rsqrtf(r2);
-            float mri = s.w * ri;
-            float mri3 = mri * (ri * ri);
-            ax[b] = fmaf(dx, mri3, ax[b]);
-            ay[b] = fmaf(dy, mri3, ay[b]);
-            az[b] = fmaf(dz, mri3, az[b]);
-            if (POT) ph[b] -= mri;
+            const f2 dx = f2sub(xy.x, X[b]);
+            const f2 dy = f2sub(xy.y, Y[b]);
+            const f2 dz = f2sub(zm.x, Z[b]);
+            const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2fma(dx, dx, E2)));
+            float r2a, r2b;
+            f2unpack(r2, r2a, r2b);
+            const f2 ri = f2pack(rsqrtf(r2a), rsqrtf(r2b));
+            const f2 mri = f2mul(zm.y, ri);
+            const f2 mri3 = f2mul(mri, f2mul(ri, ri));
+            ax[b] = f2fma(dx, mri3, ax[b]);
+            ay[b] = f2fma(dy, mri3, ay[b]);
+            az[b] = f2fma(dz, mri3, az[b]);
+            if (POT) ph[b] = f2sub(ph[b], mri);
         }
     }
 }
 
 template <int B, bool PRECISE, bool POT>
 struct Accum {
-    float ax[B], ay[B], az[B], ph[B];     // running sums
-    float cx[B], cy[B], cz[B], cp[B];     // compensations (precise)
+    f2 ax[B], ay[B], az[B], ph[B];        // packed running sums (plain mode)
+    float sx[B], sy[B], sz[B], sp[B];     // running sums (precise mode)
+    float cx[B], cy[B], cz[B], cp[B];     // their compensations
     __device__ void init()
     {
 #pragma unroll
-        for (int b = 0; b < B; b++) ax[b] = ay[b] = az[b] = ph[b] = cx[b] = cy[b] = cz[b] = cp[b] = 0.f;
+        for (int b = 0; b < B; b++) {
+            ax[b] = ay[b] = az[b] = ph[b] = 0ull;
+            sx[b] = sy[b] = sz[b] = sp[b] = cx[b] = cy[b] = cz[b] = cp[b] = 0.f;
+        }
     }
-    __device__ void flush(const float4* tile, int n, const float3 (&x)[B], float eps2)
+    // sums tile[0, n) (pads an odd count with a massless entry)
+    __device__ void flush(float* tile, int n, const f2 (&X)[B], const f2 (&Y)[B], const f2 (&Z)[B], f2 E2)
     {
         if (n <= 0) return;
+        if ((n & 1) && (threadIdx.x & 31) == 0) put_entry(tile, n, make_float4(0.f, 0.f, 0.f, 0.f));
         __syncwarp();
+        const int np = (n + 1) >> 1;
         if (PRECISE) {
-            float tx[B], ty[B], tz[B], tp[B];
+            f2 tx[B], ty[B], tz[B], tp[B];
 #pragma unroll
-            for (int b = 0; b < B; b++) tx[b] = ty[b] = tz[b] = tp[b] = 0.f;
-            sum_tile<B, POT>(tile, n, x, eps2, tx, ty, tz, tp);
+            for (int b = 0; b < B; b++) tx[b] = ty[b] = tz[b] = tp[b] = 0ull;
+            sum_tile<B, POT>(tile, np, X, Y, Z, E2, tx, ty, tz, tp);
 #pragma unroll
             for (int b = 0; b < B; b++) {
-                two_sum_acc(ax[b], cx[b], tx[b]);
-                two_sum_acc(ay[b], cy[b], ty[b]);
-                two_sum_acc(az[b], cz[b], tz[b]);
-                if (POT) two_sum_acc(ph[b], cp[b], tp[b]);
+                two_sum_acc(sx[b], cx[b], f2sum(tx[b]));
+                two_sum_acc(sy[b], cy[b], f2sum(ty[b]));
+                two_sum_acc(sz[b], cz[b], f2sum(tz[b]));
+                if (POT) two_sum_acc(sp[b], cp[b], f2sum(tp[b]));
             }
         } else {
-            sum_tile<B, POT>(tile, n, x, eps2, ax, ay, az, ph);
+            sum_tile<B, POT>(tile, np, X, Y, Z, E2, ax, ay, az, ph);
         }
         __syncwarp();
+    }
+    __device__ void result(int b, float& fx, float& fy, float& fz, float& fp) const
+    {
+        if (PRECISE) {
+            fx = sx[b];
+            fy = sy[b];
+            fz = sz[b];
+            fp = sp[b];
+        } else {
+            fx = f2sum(ax[b]);
+            fy = f2sum(ay[b]);
+            fz = f2sum(az[b]);
+            fp = f2sum(ph[b]);
+        }
+    }
+    __device__ void comp(int b, float& fx, float& fy, float& fz, float& fp) const
+    {
+        fx = PRECISE ? cx[b] : 0.f;
+        fy = PRECISE ? cy[b] : 0.f;
+        fz = PRECISE ? cz[b] : 0.f;
+        fp = PRECISE ? cp[b] : 0.f;
     }
 };
 
@@ -136,9 +225,10 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const size_t per_warp = (size_t)2 * kTileCap * sizeof(float4) + (size_t)stack_cap * sizeof(uint32_t);
-    float4* ctile = reinterpret_cast<float4*>(smem + wib * per_warp);
-    float4* btile = ctile + kTileCap;
-    uint32_t* stk = reinterpret_cast<uint32_t*>(btile + kTileCap);
+    float* ctile = reinterpret_cast<float*>(smem + wib * per_warp);
+    float* btile = ctile + 4 * kTileCap;
+    uint32_t* stk = reinterpret_cast<uint32_t*>(btile + 4 * kTileCap);
+    const f2 E2 = f2pack(a.eps2, a.eps2);
     const uint32_t lt = (1u << lane) - 1u;
 
     const Info* info = a.info;
@@ -159,8 +249,9 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
         const int4 rc = nt.c[a.gref[g]];
         const double gx = c0x + (double)rc.x * ud, gy = c0y + (double)rc.y * ud, gz = c0z + (double)rc.z * ud;
 
-        // the group's bodies: absolute and reference-relative positions
-        float3 xa[B], xr[B];
+        // the group's bodies: absolute and reference-relative positions,
+        // each coordinate duplicated into a packed pair
+        f2 XA[B], YA[B], ZA[B], XR[B], YR[B], ZR[B];
         bool act[B];
         float mi[B];
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -169,10 +260,17 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             int i = gfirst + lane + 32 * b;
             act[b] = i < gend;
             float4 q = a.body[act[b] ? i : gfirst];
-            xa[b] = make_float3(q.x, q.y, q.z);
+            XA[b] = f2pack(q.x, q.x);
+            YA[b] = f2pack(q.y, q.y);
+            ZA[b] = f2pack(q.z, q.z);
             mi[b] = q.w;
-            if (PRECISE)
-                xr[b] = make_float3((float)((double)q.x - gx), (float)((double)q.y - gy), (float)((double)q.z - gz));
+            if (PRECISE) {
+                const float rx = (float)((double)q.x - gx), ry = (float)((double)q.y - gy),
+                            rz = (float)((double)q.z - gz);
+                XR[b] = f2pack(rx, rx);
+                YR[b] = f2pack(ry, ry);
+                ZR[b] = f2pack(rz, rz);
+            }
             lo[0] = fminf(lo[0], q.x); hi[0] = fmaxf(hi[0], q.x);
             lo[1] = fminf(lo[1], q.y); hi[1] = fmaxf(hi[1], q.y);
             lo[2] = fminf(lo[2], q.z); hi[2] = fmaxf(hi[2], q.z);
@@ -227,12 +325,13 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             bool acc = false, oleaf = false, oint = false;
             float4 src = make_float4(0.f, 0.f, 0.f, 0.f);
             if (v >= 0) {
-                nb = nt.b[v];
+                // the three node records are independent loads: issue together
+                nb = __ldg(&nt.b[v]);
+                const float4 na = __ldg(&nt.a[v]);
+                const int4 cc = __ldg(&nt.c[v]);
                 const int nch = nb.w >> 8;
                 const bool overlap = (nb.x < gend) && (gfirst < nb.x + nb.y);
                 if (!overlap) {
-                    const float4 na = nt.a[v];
-                    const int4 cc = nt.c[v];
                     const int D[3] = {cc.x - rc.x, cc.y - rc.y, cc.z - rc.z};
                     const float off[3] = {na.x, na.y, na.z};
                     float e2 = 0.f;
@@ -272,33 +371,45 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             // accepted cells -> cell tile
             const unsigned am = __ballot_sync(0xffffffffu, acc);
             if (acc) {
-                ctile[cn + __popc(am & lt)] = src;
+                put_entry(ctile, cn + __popc(am & lt), src);
                 hsh += mix64(2ull * (unsigned)v + 1ull);
             }
             cn += __popc(am);
             Lc += __popc(am);
-            // opened leaves -> body tile
-            unsigned lm = __ballot_sync(0xffffffffu, oleaf);
-            if (oleaf) hsh += mix64(2ull * (unsigned)v + 2ull);
-            while (lm) {
-                const int srcl = __ffs(lm) - 1;
-                lm &= lm - 1;
-                const int f = __shfl_sync(0xffffffffu, nb.x, srcl);
-                const int c = __shfl_sync(0xffffffffu, nb.y, srcl);
-                Lb += c;
-                for (int o = 0; o < c; o += 32) {
-                    if (o + lane < c) btile[bn + lane] = a.body[f + o + lane];
-                    bn += min(32, c - o);
+            // opened leaves -> body tile.  The bodies of all leaves opened in
+            // this step are gathered 32 at a time: lane j takes body t of the
+            // concatenated ranges, finding its leaf by a binary search over
+            // the lanes' exclusive offsets.
+            const unsigned lm = __ballot_sync(0xffffffffu, oleaf);
+            if (lm) {
+                if (oleaf) hsh += mix64(2ull * (unsigned)v + 2ull);
+                const int cnt = oleaf ? nb.y : 0;
+                const int incl_c = warp_incl_scan_i(cnt);
+                const int excl_c = incl_c - cnt;
+                const int T = __shfl_sync(0xffffffffu, incl_c, 31);
+                Lb += T;
+                for (int o = 0; o < T; o += 32) {
+                    const int t = min(o + lane, T - 1);
+                    int pos = 0;
+#pragma unroll
+                    for (int step = 16; step; step >>= 1) {
+                        const int e = __shfl_sync(0xffffffffu, excl_c, pos + step);
+                        if (e <= t) pos += step;
+                    }
+                    const int f = __shfl_sync(0xffffffffu, nb.x, pos);
+                    const int e0 = __shfl_sync(0xffffffffu, excl_c, pos);
+                    if (o + lane < T) put_entry(btile, bn + lane, __ldg(&a.body[f + (t - e0)]));
+                    bn += min(32, T - o);
                     if (bn >= kTile) {
-                        bacc.flush(btile, bn, xa, a.eps2);
+                        bacc.flush(btile, bn, XA, YA, ZA, E2);
                         bn = 0;
                     }
                 }
             }
             __syncwarp();
             if (cn >= kTile) {
-                if (PRECISE) cacc.flush(ctile, cn, xr, a.eps2);
-                else cacc.flush(ctile, cn, xa, a.eps2);
+                if (PRECISE) cacc.flush(ctile, cn, XR, YR, ZR, E2);
+                else cacc.flush(ctile, cn, XA, YA, ZA, E2);
                 cn = 0;
             }
         }
@@ -307,9 +418,9 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             __syncwarp();
             continue;
         }
-        if (PRECISE) cacc.flush(ctile, cn, xr, a.eps2);
-        else cacc.flush(ctile, cn, xa, a.eps2);
-        bacc.flush(btile, bn, xa, a.eps2);
+        if (PRECISE) cacc.flush(ctile, cn, XR, YR, ZR, E2);
+        else cacc.flush(ctile, cn, XA, YA, ZA, E2);
+        bacc.flush(btile, bn, XA, YA, ZA, E2);
 
         // results, scattered back to the original body order
 #pragma unroll
@@ -317,19 +428,16 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             if (!act[b]) continue;
             const int i = gfirst + lane + 32 * b;
             const int64_t o = a.perm[i];
-            float fx, fy, fz, fp;
-            if (PRECISE) {
-                // (cell sum) + (body sum), each carried with its compensation
-                fx = (cacc.ax[b] + bacc.ax[b]) + (cacc.cx[b] + bacc.cx[b]);
-                fy = (cacc.ay[b] + bacc.ay[b]) + (cacc.cy[b] + bacc.cy[b]);
-                fz = (cacc.az[b] + bacc.az[b]) + (cacc.cz[b] + bacc.cz[b]);
-                fp = (cacc.ph[b] + bacc.ph[b]) + (cacc.cp[b] + bacc.cp[b]);
-            } else {
-                fx = cacc.ax[b] + bacc.ax[b];
-                fy = cacc.ay[b] + bacc.ay[b];
-                fz = cacc.az[b] + bacc.az[b];
-                fp = cacc.ph[b] + bacc.ph[b];
-            }
+            float cx_, cy_, cz_, cp_, bx_, by_, bz_, bp_, kx, ky, kz, kp, qx, qy, qz, qp;
+            cacc.result(b, cx_, cy_, cz_, cp_);
+            bacc.result(b, bx_, by_, bz_, bp_);
+            cacc.comp(b, kx, ky, kz, kp);
+            bacc.comp(b, qx, qy, qz, qp);
+            // (cell sum) + (body sum), each carried with its compensation
+            const float fx = (cx_ + bx_) + (kx + qx);
+            const float fy = (cy_ + by_) + (ky + qy);
+            const float fz = (cz_ + bz_) + (kz + qz);
+            const float fp = (cp_ + bp_) + (kp + qp);
             a.acc[3 * o + 0] = a.G * fx;
             a.acc[3 * o + 1] = a.G * fy;
             a.acc[3 * o + 2] = a.G * fz;
