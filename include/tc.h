@@ -157,6 +157,32 @@ int tc_direct(tc_ctx *ctx, const int64_t *idx, int64_t ns, float eps, float G, d
 int tc_set_timing(tc_ctx *ctx, int on);
 int tc_get_timings(tc_ctx *ctx, double *out6);
 
+/* Direct summation with no device allocation (no counterpart in the paper;
+ * the same sums as tc_direct).  For callers that cannot let a library call
+ * cudaMalloc -- a framework whose caching allocator already owns the
+ * device's memory budget, or a latency-critical loop that cannot afford the
+ * implicit synchronisation of cudaMalloc/cudaFree.  Nothing is allocated:
+ * the inputs are read where they are, the outputs written where they are,
+ * and the only scratch (per-slice partial sums) lives in a fixed 4 MiB
+ * array that every GPU loading libtc holds until the process exits.
+ *   pos (n x 3), mass (n), idx (ns, original indices in [0, n)), acc
+ *   (ns x 3), pot (ns, nullable): all device-accessible memory (device,
+ *   managed or mapped host); host pageable memory is rejected (TC_EINVAL)
+ *   because it would need staging.  An index outside [0, n) yields NaN
+ *   for that target.
+ *   1 <= ns <= 8192 (the scratch's capacity; more is rejected with
+ *   TC_EINVAL), 1 <= n < 2^31, eps > 0.
+ *   stream: cudaStream_t for the two kernels (NULL = legacy default);
+ *   the call only enqueues.
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls on a device share the scratch: calls whose work
+ * overlaps on the GPU (different streams, no ordering) race and give
+ * wrong results.  Errors: tc_last_error(NULL) gives the reason (while the
+ * implicit default context has no error of its own pending). */
+int tc_direct_static(const float *pos, const float *mass, int64_t n, const int64_t *idx, int64_t ns,
+                     float eps, float G, double *acc, double *pot, void *cuda_stream);
+
 /* Wait for the context's stream; report device errors. */
 int tc_sync(tc_ctx *ctx);
 

@@ -79,6 +79,12 @@ std::mutex g_default_mu;
 tc_ctx* g_default = nullptr;
 thread_local std::string g_tls_err;
 
+}  // namespace
+
+void tc::set_thread_error(const char* msg) { g_tls_err = msg; }
+
+namespace {
+
 int fail(tc_ctx* c, int code, const char* fmt, ...)
 {
     char buf[512];

@@ -72,6 +72,8 @@ struct SortBufs {
 // of kernels it launched to a process-wide counter (count_launches).
 void count_launches(int k);
 long long launches_total();
+// records the reason of a failure outside any context (tc_last_error(NULL))
+void set_thread_error(const char* msg);
 
 // exclusive scan of n uint32 values into out (out may alias in), total to
 // *total_dev (device pointer, nullable)

@@ -29,7 +29,7 @@ EXPORTS = [
     "tc_ctx_set_velocity", "tc_ctx_forces", "tc_ctx_step", "tc_get_acc", "tc_get_state", "tc_set_state",
     "tc_get_sizes", "tc_get_tree", "tc_get_nodes", "tc_get_groups", "tc_get_cube", "tc_get_lists",
     "tc_diag", "tc_direct", "tc_sync", "tc_last_error", "tc_build", "tc_forces", "tc_step", "tc_default",
-    "tc_set_timing", "tc_get_timings",
+    "tc_set_timing", "tc_get_timings", "tc_direct_static",
 ]
 
 
@@ -87,6 +87,7 @@ def load(path: str | None = None):
         "tc_default": ([], P),
         "tc_set_timing": ([P, I32], I32),
         "tc_get_timings": ([P, P], I32),
+        "tc_direct_static": ([P, P, I64, P, I64, F, F, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -276,3 +277,12 @@ def tc_forces(theta: float, eps: float, G: float = 1.0):
 def tc_step(dt: float):
     lib = load()
     _check(lib.tc_step(float(dt)))
+
+
+def tc_direct_static(pos, mass, idx, eps: float, G: float, acc, pot=None, stream=None):
+    """Direct summation into caller-owned device buffers; allocates nothing
+    on the device (see include/tc.h).  All arrays must be CUDA tensors."""
+    lib = load()
+    s = _current_stream() if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib.tc_direct_static(_ptr(pos), _ptr(mass), int(mass.shape[0]), _ptr(idx), int(idx.shape[0]),
+                                float(eps), float(G), _ptr(acc), _ptr(pot), s))
