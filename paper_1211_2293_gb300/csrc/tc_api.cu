@@ -198,8 +198,6 @@ int ensure_nodes(tc_ctx* c, int64_t M)
     TC_GROW(c, c->nt.mass64, cap);
     TC_GROW(c, c->nt.com64, 3 * cap);
     TC_GROW(c, c->nt.quad64, 6 * cap);
-    TC_GROW(c, c->nt.parent, cap);
-    TC_GROW(c, c->nt.arrive, cap);
     // the level sort reuses the body sort's value ping-pong buffer
     if (cap > c->cap_n) TC_GROW(c, c->sb.vals_alt, cap);
     int64_t nh = radix_hist_size(cap);
@@ -268,7 +266,8 @@ int build_tree(tc_ctx* c)
     launch_keys(c->pos, c->mass, n, c->info, c->keys, c->perm, s);
     radix_sort_u64(c->keys, c->perm, n, 63, c->sb, s);
     launch_gather(c->pos, c->mass, c->perm, n, c->body, s);
-    launch_node_counts(c->keys, n, c->leaf_max, c->w, c->delta, c->top, c->nstart, s);
+    TC_CUDA(c, cudaMemsetAsync(&c->info->depth, 0, sizeof(int32_t), s));
+    launch_node_counts(c->keys, n, c->leaf_max, c->w, c->delta, c->top, c->nstart, &c->info->depth, s);
     scan_u32(c->nstart, c->prepos, n, &c->totals[0], c->sb.blocksum, s);
     TC_CUDA(c, cudaGetLastError());
     uint32_t M32 = 0;
@@ -286,7 +285,7 @@ int build_tree(tc_ctx* c)
     radix_sort_u32(c->pre_level, c->iota, M, 8, lb, c->lvl_alt, s);
     launch_inverse_perm(c->iota, M, c->bfs_of_pre, s);
     launch_node_finalize(c->keys, c->top, n, c->pre_level, c->iota, c->pre_first, c->bfs_of_pre, M, c->nt, s);
-    launch_moments(c->body, M, c->info, c->nt, s);
+    launch_moments(c->body, M, c->info_h->depth, c->sb.hist, M, c->info, c->nt, s);
     launch_group_marks(M, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);
     launch_group_table(c->gflag, c->gscan, c->gref_at, n, &c->totals[1], c->gfirst, c->gref, c->info, s);
@@ -381,7 +380,7 @@ void tc_destroy(tc_ctx* c)
                     c->gflag, c->gscan, c->gref_at, c->gfirst, c->gref, c->ncell, c->nbody, c->hash,
                     c->bbox_partial, c->totals, c->idx_dev, c->dir_out, c->pre_level, c->pre_first, c->iota,
                     c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c, c->nt.d, c->nt.quad, c->nt.mass64,
-                    c->nt.com64, c->nt.quad64, c->nt.parent, c->nt.arrive, c->info};
+                    c->nt.com64, c->nt.quad64, c->info};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->info_h) cudaFreeHost(c->info_h);

@@ -13,8 +13,9 @@
 //                  sorted body (a sliding-window test, below)
 //   6. scan + k_emit_preorder      node table in pre-order
 //   7. one stable radix pass by level  -> breadth-first order
-//   8. k_node_finalize  counts, children, integer centres, parents
-//   9. k_moments   FP64 mass / centre of mass / second moments, bottom-up
+//   8. k_node_finalize  counts, children, integer centres
+//   9. k_leaf_moments, then k_level_moments level by level from the deepest
+//                  FP64 mass / centre of mass / second moments, bottom-up
 //  10. k_group_marks + scan + k_group_table   body groups for the walk
 //
 // Which cubes exist.  Let cd(a, b) be the number of leading octal digits two
@@ -203,18 +204,25 @@ __global__ void k_window(const uint64_t* __restrict__ keys, int64_t n, int leaf_
 
 __global__ void k_node_counts(const uint64_t* __restrict__ keys, const int8_t* __restrict__ w, int64_t n,
                               int leaf_max, int8_t* __restrict__ delta, int8_t* __restrict__ top,
-                              uint32_t* __restrict__ nstart)
+                              uint32_t* __restrict__ nstart, int32_t* __restrict__ depth)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int d = (s == 0) ? -1 : common_digits(keys[s - 1], keys[s]);
-    int W = -1;
-    int64_t j0 = s - leaf_max < 0 ? 0 : s - leaf_max;
-    for (int64_t j = j0; j <= s; j++) W = max(W, (int)w[j]);
-    int t = min(W + 1, kMaxLevel);
-    delta[s] = (int8_t)d;
-    top[s] = (int8_t)t;
-    nstart[s] = (uint32_t)max(0, t - d);
+    int t = 0;
+    if (s < n) {
+        int d = (s == 0) ? -1 : common_digits(keys[s - 1], keys[s]);
+        int W = -1;
+        int64_t j0 = s - leaf_max < 0 ? 0 : s - leaf_max;
+        for (int64_t j = j0; j <= s; j++) W = max(W, (int)w[j]);
+        t = min(W + 1, kMaxLevel);
+        delta[s] = (int8_t)d;
+        top[s] = (int8_t)t;
+        nstart[s] = (uint32_t)max(0, t - d);
+    }
+    // deepest level of the tree: a warp maximum (every lane of the launch's
+    // full warps takes part), then one atomic per warp
+#pragma unroll
+    for (int o = 16; o; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(depth, t);
 }
 
 __global__ void k_emit_preorder(const int8_t* __restrict__ delta, const uint32_t* __restrict__ nstart,
@@ -275,22 +283,21 @@ __global__ void k_node_finalize(const uint64_t* __restrict__ keys, const int8_t*
             c = run_end(keys, c + 1, e, shc, cp);
             nch++;
         }
-        for (int k = 0; k < nch; k++) nt.parent[cf + k] = (int32_t)b;
     }
-    if (b == 0) nt.parent[0] = -1;
     nt.b[b] = make_int4((int)s, (int)(e - s), cf, l | (nch << 8));
     uint32_t ix = compact3(pfx >> 2), iy = compact3(pfx >> 1), iz = compact3(pfx);
     int c1 = 1 << (kMaxLevel - l);
     nt.c[b] = make_int4((int)(2 * ix + 1) * c1, (int)(2 * iy + 1) * c1, (int)(2 * iz + 1) * c1, 0);
-    nt.arrive[b] = 0;
 }
 
 // ------------------------------------------------------------------ moments
 // Mass, centre of mass and second moments about the centre of mass, FP64.
-// Leaves sum their bodies; an internal cell combines its children
-// (M = sum M_c, com = sum M_c com_c / M, Q = sum Q_c + M_c dc dc^T with
-// dc = com_c - com).  The thread finishing the last child of a cell goes on
-// with the cell (arrival counter), so one launch climbs to the root.
+// Leaves sum their bodies (positions taken relative to the cube centre);
+// an internal cell combines its children: M = sum M_c,
+// com = sum M_c com_c / M, Q = sum Q_c + M_c dc dc^T with dc = com_c - com.
+// Leaves are done in one launch; internal cells level by level from the
+// deepest, one thread per cell of the level (cells of a level are contiguous
+// in breadth-first order), so every lane of a warp has a cell to do.
 __device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const double* Q,
                            const Info* info, int4 c)
 {
@@ -304,75 +311,80 @@ __device__ void store_node(NodeTables& nt, int64_t v, double M, const double* co
     for (int a = 0; a < 6; a++) nt.quad[6 * v + a] = (float)Q[a];
 }
 
-__global__ void k_moments(const float4* __restrict__ body, int64_t M, const Info* __restrict__ info,
-                          NodeTables nt)
+__global__ void k_leaf_moments(const float4* __restrict__ body, int64_t M, const Info* __restrict__ info,
+                               NodeTables nt)
 {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= M) return;
-    int4 b = nt.b[v];
-    if ((b.w >> 8) != 0) return;  // internal: reached by the climb
-    {
-        int4 c = nt.c[v];
-        const double u = 0.5 * info->h;
-        double C[3] = {info->c0[0] + (double)c.x * u, info->c0[1] + (double)c.y * u, info->c0[2] + (double)c.z * u};
-        double m = 0.0, S[3] = {0, 0, 0};
-        for (int j = b.x; j < b.x + b.y; j++) {
-            float4 q = body[j];
-            m += (double)q.w;
-            S[0] += (double)q.w * ((double)q.x - C[0]);
-            S[1] += (double)q.w * ((double)q.y - C[1]);
-            S[2] += (double)q.w * ((double)q.z - C[2]);
-        }
-        double off[3] = {S[0] / m, S[1] / m, S[2] / m};
-        double Q[6] = {0, 0, 0, 0, 0, 0};
-        for (int j = b.x; j < b.x + b.y; j++) {
-            float4 q = body[j];
-            double dx = ((double)q.x - C[0]) - off[0];
-            double dy = ((double)q.y - C[1]) - off[1];
-            double dz = ((double)q.z - C[2]) - off[2];
-            double mj = (double)q.w;
-            Q[0] += mj * dx * dx;
-            Q[1] += mj * dx * dy;
-            Q[2] += mj * dx * dz;
-            Q[3] += mj * dy * dy;
-            Q[4] += mj * dy * dz;
-            Q[5] += mj * dz * dz;
-        }
-        double com[3] = {C[0] + off[0], C[1] + off[1], C[2] + off[2]};
-        store_node(nt, v, m, com, Q, info, c);
+    const int4 b = nt.b[v];
+    if ((b.w >> 8) != 0) return;  // internal
+    const int4 c = nt.c[v];
+    const double u = 0.5 * info->h;
+    const double C[3] = {info->c0[0] + (double)c.x * u, info->c0[1] + (double)c.y * u,
+                         info->c0[2] + (double)c.z * u};
+    double m = 0.0, S[3] = {0, 0, 0};
+    for (int j = b.x; j < b.x + b.y; j++) {
+        const float4 q = body[j];
+        m += (double)q.w;
+        S[0] += (double)q.w * ((double)q.x - C[0]);
+        S[1] += (double)q.w * ((double)q.y - C[1]);
+        S[2] += (double)q.w * ((double)q.z - C[2]);
     }
-    __threadfence();
-    int64_t p = nt.parent[v];
-    while (p >= 0) {
-        int4 pb = nt.b[p];
-        int nch = pb.w >> 8;
-        unsigned old = atomicAdd(&nt.arrive[p], 1u);
-        if ((int)old != nch - 1) return;
-        __threadfence();
+    const double inv = 1.0 / m;
+    const double off[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = b.x; j < b.x + b.y; j++) {
+        const float4 q = body[j];
+        const double dx = ((double)q.x - C[0]) - off[0];
+        const double dy = ((double)q.y - C[1]) - off[1];
+        const double dz = ((double)q.z - C[2]) - off[2];
+        const double mj = (double)q.w;
+        Q[0] += mj * dx * dx;
+        Q[1] += mj * dx * dy;
+        Q[2] += mj * dx * dz;
+        Q[3] += mj * dy * dy;
+        Q[4] += mj * dy * dz;
+        Q[5] += mj * dz * dz;
+    }
+    const double com[3] = {C[0] + off[0], C[1] + off[1], C[2] + off[2]};
+    store_node(nt, v, m, com, Q, info, c);
+}
+
+// internal cells of level `lev`: [start, end) read from the level sort's
+// scanned histogram (digit-major, nb blocks: start of level l = hist[l * nb])
+__global__ void k_level_moments(int lev, const uint32_t* __restrict__ lvl_hist, int nb, int64_t M,
+                                const Info* __restrict__ info, NodeTables nt)
+{
+    const int64_t start = lvl_hist[(int64_t)lev * nb];
+    const int64_t end = lev + 1 < 256 ? (int64_t)lvl_hist[(int64_t)(lev + 1) * nb] : M;
+    for (int64_t v = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < end;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int4 pb = nt.b[v];
+        const int nch = pb.w >> 8;
+        if (nch == 0) continue;  // leaf: done by k_leaf_moments
         double m = 0.0, S[3] = {0, 0, 0};
         for (int k = 0; k < nch; k++) {
-            int64_t c = pb.z + k;
-            double mc = __ldcg(&nt.mass64[c]);
+            const int64_t c = pb.z + k;
+            const double mc = nt.mass64[c];
             m += mc;
-            for (int a = 0; a < 3; a++) S[a] += mc * __ldcg(&nt.com64[3 * c + a]);
+            for (int a = 0; a < 3; a++) S[a] += mc * nt.com64[3 * c + a];
         }
-        double com[3] = {S[0] / m, S[1] / m, S[2] / m};
+        const double inv = 1.0 / m;
+        const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
         double Q[6] = {0, 0, 0, 0, 0, 0};
         for (int k = 0; k < nch; k++) {
-            int64_t c = pb.z + k;
-            double mc = __ldcg(&nt.mass64[c]);
+            const int64_t c = pb.z + k;
+            const double mc = nt.mass64[c];
             double d[3];
-            for (int a = 0; a < 3; a++) d[a] = __ldcg(&nt.com64[3 * c + a]) - com[a];
-            Q[0] += __ldcg(&nt.quad64[6 * c + 0]) + mc * d[0] * d[0];
-            Q[1] += __ldcg(&nt.quad64[6 * c + 1]) + mc * d[0] * d[1];
-            Q[2] += __ldcg(&nt.quad64[6 * c + 2]) + mc * d[0] * d[2];
-            Q[3] += __ldcg(&nt.quad64[6 * c + 3]) + mc * d[1] * d[1];
-            Q[4] += __ldcg(&nt.quad64[6 * c + 4]) + mc * d[1] * d[2];
-            Q[5] += __ldcg(&nt.quad64[6 * c + 5]) + mc * d[2] * d[2];
+            for (int a = 0; a < 3; a++) d[a] = nt.com64[3 * c + a] - com[a];
+            Q[0] += nt.quad64[6 * c + 0] + mc * d[0] * d[0];
+            Q[1] += nt.quad64[6 * c + 1] + mc * d[0] * d[1];
+            Q[2] += nt.quad64[6 * c + 2] + mc * d[0] * d[2];
+            Q[3] += nt.quad64[6 * c + 3] + mc * d[1] * d[1];
+            Q[4] += nt.quad64[6 * c + 4] + mc * d[1] * d[2];
+            Q[5] += nt.quad64[6 * c + 5] + mc * d[2] * d[2];
         }
-        store_node(nt, p, m, com, Q, info, nt.c[p]);
-        __threadfence();
-        p = nt.parent[p];
+        store_node(nt, v, m, com, Q, info, nt.c[v]);
     }
 }
 
@@ -479,10 +491,10 @@ void launch_gather(const float* pos, const float* mass, const uint32_t* perm, in
 }
 
 void launch_node_counts(const uint64_t* keys, int64_t n, int leaf_max, int8_t* w, int8_t* delta, int8_t* top,
-                        uint32_t* nstart, cudaStream_t s)
+                        uint32_t* nstart, int32_t* depth, cudaStream_t s)
 {
     k_window<<<nblk(n, 256), 256, 0, s>>>(keys, n, leaf_max, w);
-    k_node_counts<<<nblk(n, 256), 256, 0, s>>>(keys, w, n, leaf_max, delta, top, nstart);
+    k_node_counts<<<nblk(n, 256), 256, 0, s>>>(keys, w, n, leaf_max, delta, top, nstart, depth);
     count_launches(2);
 }
 
@@ -507,10 +519,18 @@ void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n, co
     count_launches(1);
 }
 
-void launch_moments(const float4* body, int64_t M, const Info* info, NodeTables nt, cudaStream_t s)
+void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* lvl_hist, int64_t M_sorted,
+                    const Info* info, NodeTables nt, cudaStream_t s)
 {
-    k_moments<<<nblk(M, 128), 128, 0, s>>>(body, M, info, nt);
+    k_leaf_moments<<<nblk(M, 128), 128, 0, s>>>(body, M, info, nt);
     count_launches(1);
+    const int nb = (int)((M_sorted + 4095) / 4096);  // blocks of the level sort
+    int64_t g = nblk(M, 128);
+    if (g > 8 * 152) g = 8 * 152;
+    for (int lev = depth - 1; lev >= 0; lev--) {
+        k_level_moments<<<(unsigned)g, 128, 0, s>>>(lev, lvl_hist, nb, M, info, nt);
+        count_launches(1);
+    }
 }
 
 void launch_group_marks(int64_t M, const NodeTables nt, int gmax, int64_t n, uint32_t* gflag, int32_t* gref_at,

@@ -32,7 +32,7 @@ struct Info {
     int64_t M;         // number of nodes
     int64_t G;         // number of groups
     uint32_t work;     // walk work-queue counter
-    uint32_t pad0;
+    int32_t depth;     // deepest level of the tree
     unsigned long long interactions;  // body-source interactions of the last walk
     unsigned long long cells;         // accepted cells summed over groups
     unsigned long long bodies;        // direct-list bodies summed over groups
@@ -53,8 +53,6 @@ struct NodeTables {
     double* mass64;  // FP64 bottom-up reduction results
     double* com64;   // 3 per node
     double* quad64;  // 6 per node
-    int32_t* parent;
-    uint32_t* arrive;
 };
 
 // scratch sizes for the radix sort / scans
@@ -97,7 +95,7 @@ void launch_keys(const float* pos, const float* mass, int64_t n, const Info* inf
 void launch_gather(const float* pos, const float* mass, const uint32_t* perm, int64_t n,
                    float4* body, cudaStream_t s);
 void launch_node_counts(const uint64_t* keys, int64_t n, int leaf_max, int8_t* w, int8_t* delta,
-                        int8_t* top, uint32_t* nstart, cudaStream_t s);
+                        int8_t* top, uint32_t* nstart, int32_t* depth, cudaStream_t s);
 void launch_emit_preorder(const int8_t* delta, const uint32_t* nstart, const uint32_t* prepos,
                           int64_t n, uint32_t* pre_level, uint32_t* pre_first, uint32_t* iota,
                           cudaStream_t s);
@@ -105,7 +103,10 @@ void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n,
                           const uint32_t* bfs_level, const uint32_t* bfs_pre, const uint32_t* pre_first,
                           const uint32_t* bfs_of_pre, int64_t M, NodeTables nt, cudaStream_t s);
 void launch_inverse_perm(const uint32_t* perm, int64_t M, uint32_t* inv, cudaStream_t s);
-void launch_moments(const float4* body, int64_t M, const Info* info, NodeTables nt, cudaStream_t s);
+// moments: leaves, then internal levels depth-1 .. 0; lvl_hist is the level
+// sort's scanned histogram (sort block size 4096)
+void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* lvl_hist, int64_t M_sorted,
+                    const Info* info, NodeTables nt, cudaStream_t s);
 void launch_group_marks(int64_t M, const NodeTables nt, int gmax, int64_t n, uint32_t* gflag,
                         int32_t* gref_at, cudaStream_t s);
 void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int32_t* gref_at,
