@@ -156,11 +156,11 @@ int ensure_bodies(tc_ctx* c, int64_t n)
     TC_GROW(c, c->body, cap);
     TC_GROW(c, c->sb.keys_alt, cap);
     TC_GROW(c, c->sb.vals_alt, cap);
-    int64_t nh = radix_hist_size(cap);
-    TC_GROW(c, c->sb.hist, nh);
-    int64_t nbs = scan_blocksum_size(nh > cap ? nh : cap);
-    nbs = nbs > scan_blocksum_size(32 * cap) ? nbs : scan_blocksum_size(32 * cap);
-    TC_GROW(c, c->sb.blocksum, nbs);
+    TC_GROW(c, c->sb.ghist, 8 * 256);
+    TC_GROW(c, c->sb.status, 8 * radix_tiles(cap) * 256);  // look-back words of the 8 key passes
+    TC_GROW(c, c->sb.tiles, 8);
+    c->sb.err = &c->info->err;
+    TC_GROW(c, c->sb.blocksum, scan_blocksum_size(cap));
     TC_GROW(c, c->w, cap);
     TC_GROW(c, c->delta, cap);
     TC_GROW(c, c->top, cap);
@@ -200,8 +200,8 @@ int ensure_nodes(tc_ctx* c, int64_t M)
     TC_GROW(c, c->nt.quad64, 6 * cap);
     // the level sort reuses the body sort's value ping-pong buffer
     if (cap > c->cap_n) TC_GROW(c, c->sb.vals_alt, cap);
-    int64_t nh = radix_hist_size(cap);
-    if (nh > radix_hist_size(c->cap_n)) TC_GROW(c, c->sb.hist, nh);
+    if (radix_tiles(cap) > 8 * radix_tiles(c->cap_n))  // the level sort's single pass
+        TC_GROW(c, c->sb.status, radix_tiles(cap) * 256);
     c->cap_m = cap;
     return TC_OK;
 }
@@ -285,7 +285,8 @@ int build_tree(tc_ctx* c)
     radix_sort_u32(c->pre_level, c->iota, M, 8, lb, c->lvl_alt, s);
     launch_inverse_perm(c->iota, M, c->bfs_of_pre, s);
     launch_node_finalize(c->keys, c->top, n, c->pre_level, c->iota, c->pre_first, c->bfs_of_pre, M, c->nt, s);
-    launch_moments(c->body, M, c->info_h->depth, c->sb.hist, M, c->info, c->nt, s);
+    // after the level sort, ghist[l] is the first breadth-first index of level l
+    launch_moments(c->body, M, c->info_h->depth, c->sb.ghist, c->info, c->nt, s);
     launch_group_marks(M, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);
     launch_group_table(c->gflag, c->gscan, c->gref_at, n, &c->totals[1], c->gfirst, c->gref, c->info, s);
@@ -376,7 +377,7 @@ void tc_destroy(tc_ctx* c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     void* bufs[] = {c->pos, c->vel, c->acc, c->pot, c->mass, c->keys, c->perm, c->body, c->sb.keys_alt,
-                    c->sb.vals_alt, c->sb.hist, c->sb.blocksum, c->w, c->delta, c->top, c->nstart, c->prepos,
+                    c->sb.vals_alt, c->sb.ghist, c->sb.status, c->sb.tiles, c->sb.blocksum, c->w, c->delta, c->top, c->nstart, c->prepos,
                     c->gflag, c->gscan, c->gref_at, c->gfirst, c->gref, c->ncell, c->nbody, c->hash,
                     c->bbox_partial, c->totals, c->idx_dev, c->dir_out, c->pre_level, c->pre_first, c->iota,
                     c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c, c->nt.d, c->nt.quad, c->nt.mass64,

@@ -350,13 +350,12 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, int64_t M, const
     store_node(nt, v, m, com, Q, info, c);
 }
 
-// internal cells of level `lev`: [start, end) read from the level sort's
-// scanned histogram (digit-major, nb blocks: start of level l = hist[l * nb])
-__global__ void k_level_moments(int lev, const uint32_t* __restrict__ lvl_hist, int nb, int64_t M,
-                                const Info* __restrict__ info, NodeTables nt)
+// internal cells of level `lev`: [level_start[lev], level_start[lev + 1])
+__global__ void k_level_moments(int lev, const uint32_t* __restrict__ level_start, const Info* __restrict__ info,
+                                NodeTables nt)
 {
-    const int64_t start = lvl_hist[(int64_t)lev * nb];
-    const int64_t end = lev + 1 < 256 ? (int64_t)lvl_hist[(int64_t)(lev + 1) * nb] : M;
+    const int64_t start = level_start[lev];
+    const int64_t end = level_start[lev + 1];
     for (int64_t v = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < end;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int4 pb = nt.b[v];
@@ -519,16 +518,15 @@ void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n, co
     count_launches(1);
 }
 
-void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* lvl_hist, int64_t M_sorted,
-                    const Info* info, NodeTables nt, cudaStream_t s)
+void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* level_start, const Info* info,
+                    NodeTables nt, cudaStream_t s)
 {
     k_leaf_moments<<<nblk(M, 128), 128, 0, s>>>(body, M, info, nt);
     count_launches(1);
-    const int nb = (int)((M_sorted + 4095) / 4096);  // blocks of the level sort
     int64_t g = nblk(M, 128);
     if (g > 8 * 152) g = 8 * 152;
     for (int lev = depth - 1; lev >= 0; lev--) {
-        k_level_moments<<<(unsigned)g, 128, 0, s>>>(lev, lvl_hist, nb, M, info, nt);
+        k_level_moments<<<(unsigned)g, 128, 0, s>>>(lev, level_start, info, nt);
         count_launches(1);
     }
 }

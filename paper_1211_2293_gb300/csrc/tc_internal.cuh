@@ -59,10 +59,11 @@ struct NodeTables {
 struct SortBufs {
     uint64_t* keys_alt;
     uint32_t* vals_alt;
-    uint32_t* hist;      // 256 * nblocks
-    uint32_t* blocksum;  // scan partials
-    int64_t cap_items;
-    int64_t cap_hist;
+    uint32_t* ghist;                 // 8 passes x 256 digit counts -> exclusive offsets
+    unsigned long long* status;      // look-back words, passes x tiles x 256
+    uint32_t* tiles;                 // tile counters, one per pass
+    int32_t* err;                    // device error word (bounded look-back)
+    uint32_t* blocksum;              // scan partials
 };
 
 // ---------------------------------------------------------------- launchers
@@ -79,12 +80,13 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
               uint32_t* blocksum, cudaStream_t s);
 int64_t scan_blocksum_size(int64_t n);
 
-// stable LSD radix sort of (key, val) by bits [0, nbits) of key
+// stable LSD radix sort of (key, val) by bits [0, nbits) of key; afterwards
+// b.ghist[p * 256 + d] is the number of keys whose pass-p digit is below d
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b,
                     cudaStream_t s);
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b,
                     uint32_t* keys_alt32, cudaStream_t s);
-int64_t radix_hist_size(int64_t n);
+int64_t radix_tiles(int64_t n);  // tiles of one pass (status words: 256 per tile per pass)
 
 // build pieces
 void launch_bbox(const float* pos, int64_t n, float* partial, int nblocks, Info* info,
@@ -103,10 +105,11 @@ void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n,
                           const uint32_t* bfs_level, const uint32_t* bfs_pre, const uint32_t* pre_first,
                           const uint32_t* bfs_of_pre, int64_t M, NodeTables nt, cudaStream_t s);
 void launch_inverse_perm(const uint32_t* perm, int64_t M, uint32_t* inv, cudaStream_t s);
-// moments: leaves, then internal levels depth-1 .. 0; lvl_hist is the level
-// sort's scanned histogram (sort block size 4096)
-void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* lvl_hist, int64_t M_sorted,
-                    const Info* info, NodeTables nt, cudaStream_t s);
+// moments: leaves, then internal levels depth-1 .. 0; level_start[l] is the
+// first node of level l (the level sort's digit offsets; level_start[l+1]
+// ends it)
+void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* level_start, const Info* info,
+                    NodeTables nt, cudaStream_t s);
 void launch_group_marks(int64_t M, const NodeTables nt, int gmax, int64_t n, uint32_t* gflag,
                         int32_t* gref_at, cudaStream_t s);
 void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int32_t* gref_at,

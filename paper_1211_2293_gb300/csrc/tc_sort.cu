@@ -106,54 +106,87 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restric
     }
 }
 
+// ------------------------------------------------------------------ radix sort
+// Onesweep LSD radix sort (8-bit digits): one kernel computes the global
+// digit histograms of every pass, one kernel turns them into exclusive
+// offsets, then each pass is a single kernel whose tiles find their place by
+// decoupled look-back (Merrill & Garland's single-pass prefix scan): a tile
+// publishes its per-digit count ("aggregate"), then adds up its
+// predecessors' counts walking back until it meets an inclusive prefix, and
+// publishes its own inclusive prefix.  Tiles take their index from an atomic
+// counter in launch order, so a tile only ever waits for tiles that have
+// already started and publish before they look back themselves.  Every wait
+// is bounded; a tile that gives up sets the error word and writes nothing.
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned kLookbackMaxPolls = 1u << 24;
+
 template <typename K>
-__global__ void k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
-                             int nb)
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(const K* __restrict__ keys, int64_t n, int npass,
+                                                                uint32_t* __restrict__ ghist)
 {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[8][256];
+    for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int i = 0; i < kSortItems; i++) {
-        int64_t k = base + (int64_t)i * kSortThreads + threadIdx.x;
-        if (k < n) atomicAdd(&h[(uint32_t)(keys[k] >> shift) & 255u], 1u);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const K key = keys[k];
+        for (int p = 0; p < npass; p++) atomicAdd(&h[p][(uint32_t)(key >> (8 * p)) & 255u], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+    for (int p = 0; p < npass; p++) {
+        const uint32_t c = h[p][threadIdx.x];
+        if (c) atomicAdd(&ghist[p * 256 + threadIdx.x], c);
+    }
 }
 
-// Stable scatter: warp w of block b owns items [b*T + w*512, +512), taken in
-// 16 rounds of 32 in index order.  Within a round, lanes holding equal digits
-// find each other with __match_any_sync; the lowest such lane reserves their
-// slots in the warp's per-digit counter.  Warp counters are then offset by
-// the counts of the earlier warps and by the digit's global offset.
+// exclusive scan of each pass's 256 digit counts, in place
+__global__ void __launch_bounds__(256) k_sort_offsets(uint32_t* __restrict__ ghist, int npass)
+{
+    __shared__ uint32_t sm[33];
+    for (int p = 0; p < npass; p++) {
+        uint32_t tot;
+        const uint32_t e = block_excl_scan<256>(ghist[p * 256 + threadIdx.x], tot, sm);
+        ghist[p * 256 + threadIdx.x] = e;
+    }
+}
+
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
-    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
-    uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offs, int nb)
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                           K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                                           int shift, const uint32_t* __restrict__ goff,
+                                                           unsigned long long* status, uint32_t* tile_counter,
+                                                           int32_t* err)
 {
     __shared__ uint32_t wh[kSortWarps][256];
-    __shared__ uint32_t gb[256];
+    __shared__ uint32_t base[256];
+    __shared__ int tile_sh;
+    __shared__ int fail_sh;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&wh[0][0])[i] = 0;
-    gb[threadIdx.x] = offs[(int64_t)threadIdx.x * nb + blockIdx.x];
+    if (threadIdx.x == 0) {
+        tile_sh = (int)atomicAdd(tile_counter, 1u);
+        fail_sh = 0;
+    }
     __syncthreads();
+    const int tile = tile_sh;
 
-    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)w * kWarpItems;
+    // stable ranks within the tile (warp w owns items [tile*T + w*512, +512),
+    // in 16 rounds of 32; equal digits of a round find each other with
+    // __match_any_sync and the lowest lane reserves their slots)
+    const int64_t wbase = (int64_t)tile * kSortTile + (int64_t)w * kWarpItems;
     const uint32_t lt = (1u << lane) - 1u;
     K key[kSortItems];
     uint32_t val[kSortItems];
     uint32_t rank[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; r++) {
-        int64_t k = wbase + r * 32 + lane;
-        bool ok = k < n;
+        const int64_t k = wbase + r * 32 + lane;
+        const bool ok = k < n;
         key[r] = ok ? kin[k] : K(0);
         val[r] = ok ? vin[k] : 0u;
-        uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        int leader = __ffs(peers) - 1;
+        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (ok && lane == leader) {
             old = wh[w][d];
@@ -164,23 +197,59 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         __syncwarp();
     }
     __syncthreads();
+
+    // per digit: offsets of the warps inside the tile, the tile's count,
+    // then the decoupled look-back over the preceding tiles
     {
-        uint32_t run = 0;
         const int d = threadIdx.x;
+        uint32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < kSortWarps; ww++) {
-            uint32_t c = wh[ww][d];
-            wh[ww][d] = run + gb[d];
+            const uint32_t c = wh[ww][d];
+            wh[ww][d] = run;
             run += c;
+        }
+        volatile unsigned long long* st = status;
+        if (tile == 0) {
+            st[d] = kFlagPrefix | run;
+            base[d] = goff[d];
+        } else {
+            st[(int64_t)tile * 256 + d] = kFlagAgg | run;
+            uint32_t excl = 0;
+            int64_t k = tile - 1;
+            unsigned polls = 0;
+            bool fail = false;
+            while (k >= 0) {
+                const unsigned long long v = st[k * 256 + d];
+                const unsigned long long f = v & (3ull << 62);
+                if (f == 0) {
+                    if (++polls > kLookbackMaxPolls) {
+                        fail = true;
+                        break;
+                    }
+                    if (polls > 64) __nanosleep(32);
+                    continue;
+                }
+                excl += (uint32_t)v;
+                if (f == kFlagPrefix) break;
+                k--;
+            }
+            st[(int64_t)tile * 256 + d] = kFlagPrefix | (uint32_t)(excl + run);
+            base[d] = goff[d] + excl;
+            if (fail) {
+                fail_sh = 1;
+                atomicOr(err, kErrWorkLoop);
+            }
         }
     }
     __syncthreads();
+    if (fail_sh) return;  // positions unknown: write nothing
 #pragma unroll
     for (int r = 0; r < kSortItems; r++) {
-        int64_t k = wbase + r * 32 + lane;
+        const int64_t k = wbase + r * 32 + lane;
         if (k < n) {
-            uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
-            uint32_t p = wh[w][d] + rank[r];
+            const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+            const uint32_t p = base[d] + wh[w][d] + rank[r];
             kout[p] = key[r];
             vout[p] = val[r];
         }
@@ -205,30 +274,39 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
     count_launches(3);
 }
 
-int64_t radix_hist_size(int64_t n) { return 256 * ((n + kSortTile - 1) / kSortTile); }
+int64_t radix_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 
 template <typename K>
 static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b, K* keys_alt,
                             cudaStream_t s)
 {
-    if (n <= 1) return;
-    int nb = (int)((n + kSortTile - 1) / kSortTile);
-    int64_t nh = (int64_t)256 * nb;
+    if (n <= 1) {
+        cudaMemsetAsync(b.ghist, 0, 8 * 256 * sizeof(uint32_t), s);  // offsets of an empty or single list
+        return;
+    }
+    const int npass = (nbits + 7) / 8;
+    const int64_t nt = radix_tiles(n);
+    // zero the histograms, the look-back words of every pass and the tile counters
+    cudaMemsetAsync(b.ghist, 0, 8 * 256 * sizeof(uint32_t), s);
+    cudaMemsetAsync(b.status, 0, (size_t)npass * nt * 256 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(b.tiles, 0, 8 * sizeof(uint32_t), s);
+    int hb = (int)((n + kSortThreads * 16 - 1) / (kSortThreads * 16));
+    if (hb > 4 * 152) hb = 4 * 152;
+    k_sort_hist_all<K><<<hb, kSortThreads, 0, s>>>(keys, n, npass, b.ghist);
+    k_sort_offsets<<<1, 256, 0, s>>>(b.ghist, npass);
+    count_launches(2);
     K* ka = keys;
     uint32_t* va = vals;
     K* kb = keys_alt;
     uint32_t* vb = b.vals_alt;
-    int passes = 0;
-    for (int shift = 0; shift < nbits; shift += 8) {
-        k_radix_hist<K><<<nb, kSortThreads, 0, s>>>(ka, n, shift, b.hist, nb);
-        scan_u32(b.hist, b.hist, nh, nullptr, b.blocksum, s);
-        k_radix_scatter<K><<<nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, b.hist, nb);
-        count_launches(2);
+    for (int p = 0; p < npass; p++) {
+        k_onesweep<K><<<(unsigned)nt, kSortThreads, 0, s>>>(ka, va, kb, vb, n, 8 * p, b.ghist + 256 * p,
+                                                            b.status + (size_t)p * nt * 256, b.tiles + p, b.err);
+        count_launches(1);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
-        passes++;
     }
-    if (passes & 1) {
+    if (npass & 1) {
         cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     }
