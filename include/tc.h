@@ -52,7 +52,10 @@ typedef struct tc_ctx tc_ctx;
  *   want_pot  1: also compute the potential (tc_get_acc's pot, tc_diag's PE)
  *   verify    1: record per-group list lengths and hashes (tc_get_lists)
  *   stack     walk stack entries per warp (shared memory), 64..8192
- *   blocks_per_sm  0 = as many as fit, else a cap                          */
+ *   blocks_per_sm  0 = as many as fit, else a cap
+ *   quad      1: also reduce the cells' second moments about the centre of
+ *             mass (FP64; the learned correction's features, tc_get_nodes'
+ *             quad); 0: mass and centre of mass only                     */
 typedef struct {
     int32_t gmax;
     int32_t warps;
@@ -61,6 +64,7 @@ typedef struct {
     int32_t verify;
     int32_t stack;
     int32_t blocks_per_sm;
+    int32_t quad;
 } tc_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a
@@ -120,7 +124,8 @@ int tc_get_sizes(tc_ctx *ctx, int64_t *n, int64_t *nnodes, int64_t *ngroups);
  * Node table in breadth-first order (by level, then first body), nnodes long:
  *   level, prefix (3*level-bit Morton prefix), first, count, child_first
  *   (-1 for a leaf), nchild, mass, com (3 per node, absolute), quad (6 per
- *   node: xx, xy, xz, yy, yz, zz second moments about the centre of mass).
+ *   node: xx, xy, xz, yy, yz, zz second moments about the centre of mass;
+ *   needs quad = 1 in the configuration, else TC_ESTATE).
  * Groups, ngroups long: gfirst, gcount, gref (reference cube index). */
 int tc_get_tree(tc_ctx *ctx, uint32_t *perm, uint64_t *keys);
 int tc_get_nodes(tc_ctx *ctx, int32_t *level, uint64_t *prefix, int32_t *first, int32_t *count,

@@ -92,7 +92,10 @@ int or_root_cube(const float *pos, int64_t n, double *out5)
 /* ------------------------------------------------------------------ */
 static uint64_t quantise(double x, double c0, double h)
 {
-    double q = floor((x - c0) / h);
+    /* (x - c0) / h evaluated exactly: h is a power of two and c0 an integer
+     * multiple of h, so x / h and c0 / h are exact and so is the difference
+     * of their integer parts */
+    double q = floor(x / h) - c0 / h;
     if (q < 0.0)
         q = 0.0;
     if (q > 2097151.0)

@@ -286,7 +286,7 @@ int build_tree(tc_ctx* c)
     launch_inverse_perm(c->iota, M, c->bfs_of_pre, s);
     launch_node_finalize(c->keys, c->top, n, c->pre_level, c->iota, c->pre_first, c->bfs_of_pre, M, c->nt, s);
     // after the level sort, ghist[l] is the first breadth-first index of level l
-    launch_moments(c->body, M, c->info_h->depth, c->sb.ghist, c->info, c->nt, s);
+    launch_moments(c->body, M, c->info_h->depth, c->sb.ghist, c->info, c->nt, c->cfg.quad != 0, s);
     launch_group_marks(M, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);
     launch_group_table(c->gflag, c->gscan, c->gref_at, n, &c->totals[1], c->gfirst, c->gref, c->info, s);
@@ -367,6 +367,7 @@ int tc_create(tc_ctx** out, void* stream)
     c->cfg.verify = 0;
     c->cfg.stack = 1024;
     c->cfg.blocks_per_sm = 0;
+    c->cfg.quad = 0;
     *out = c;
     return TC_OK;
 }
@@ -397,11 +398,12 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
     if (cfg->warps < 1 || cfg->warps > 4) return fail(c, TC_EINVAL, "warps must be 1..4 (got %d)", cfg->warps);
     if (cfg->stack < 64 || cfg->stack > 8192) return fail(c, TC_EINVAL, "stack must be 64..8192 (got %d)", cfg->stack);
     if (cfg->blocks_per_sm < 0) return fail(c, TC_EINVAL, "blocks_per_sm must be >= 0");
-    bool regroup = c->built && cfg->gmax != c->cfg.gmax;
+    bool regroup = c->built && (cfg->gmax != c->cfg.gmax || (cfg->quad != 0) != (c->cfg.quad != 0));
     c->cfg = *cfg;
     c->cfg.precise = cfg->precise ? 1 : 0;
     c->cfg.want_pot = cfg->want_pot ? 1 : 0;
     c->cfg.verify = cfg->verify ? 1 : 0;
+    c->cfg.quad = cfg->quad ? 1 : 0;
     if (regroup) return build_tree(c);  // groups depend on gmax
     return TC_OK;
 }
@@ -551,6 +553,7 @@ int tc_get_nodes(tc_ctx* c, int32_t* level, uint64_t* prefix, int32_t* first, in
 {
     if (!c) return fail(c, TC_EINVAL, "tc_get_nodes: null context");
     if (!c->built) return fail(c, TC_ESTATE, "tc_get_nodes: build first");
+    if (quad && !c->cfg.quad) return fail(c, TC_ESTATE, "tc_get_nodes: second moments not computed (quad = 0)");
     int r = check_device(c);
     if (r) return r;
     const int64_t M = c->M;

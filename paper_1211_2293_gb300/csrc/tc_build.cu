@@ -127,14 +127,31 @@ __global__ void __launch_bounds__(kBboxThreads) k_bbox(const float* __restrict__
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
+    // the last block reduces the partials with all its threads
+    float r[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        for (int a = 0; a < 3; a++) {
+            r[a] = fminf(r[a], __ldcg(&partial[6 * b + a]));
+            r[3 + a] = fmaxf(r[3 + a], __ldcg(&partial[6 * b + 3 + a]));
+        }
+    }
+    for (int a = 0; a < 3; a++) {
+        r[a] = warp_min(r[a]);
+        r[3 + a] = warp_max(r[3 + a]);
+    }
+    __syncthreads();
+    if (lane == 0)
+        for (int a = 0; a < 6; a++) sm[a][w] = r[a];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double dlo[3], dhi[3];
     for (int a = 0; a < 3; a++) {
         float l = INFINITY, h = -INFINITY;
-        for (unsigned b = 0; b < gridDim.x; b++) {
-            l = fminf(l, __ldcg(&partial[6 * b + a]));
-            h = fmaxf(h, __ldcg(&partial[6 * b + 3 + a]));
+        for (int k = 0; k < kBboxThreads / 32; k++) {
+            l = fminf(l, sm[a][k]);
+            h = fmaxf(h, sm[3 + a][k]);
         }
         dlo[a] = (double)l;
         dhi[a] = (double)h;
@@ -152,7 +169,14 @@ __global__ void __launch_bounds__(kBboxThreads) k_bbox(const float* __restrict__
         L = (m == 0.5) ? target : ldexp(1.0, e);
     }
     double h = L / 2097152.0;
-    for (int a = 0; a < 3; a++) info->c0[a] = floor(dlo[a] / h) * h;
+    int eh;
+    frexp(h, &eh);  // h = 2^(eh - 1)
+    info->qexp = 1 - eh;  // 1/h = 2^qexp
+    for (int a = 0; a < 3; a++) {
+        const double K0 = floor(dlo[a] / h);
+        info->c0[a] = K0 * h;
+        info->qoff[a] = (long long)K0;
+    }
     info->L = L;
     info->h = h;
     info->inv_h = 1.0 / h;
@@ -162,24 +186,30 @@ __global__ void __launch_bounds__(kBboxThreads) k_bbox(const float* __restrict__
 }
 
 // ------------------------------------------------------------------ keys
-// q = floor((x - c0) / h) clamped to [0, 2^21 - 1]; the multiply by the
-// exact power of two 1/h equals the division.  key digit l holds the level-l
-// bits of (qx, qy, qz) with x highest.
+// q = floor((x - c0) / h) clamped to [0, 2^21 - 1], evaluated exactly: h is
+// a power of two and c0 = K0 h with K0 an integer, so q = floor(x * 2^k) - K0
+// with 2^k = 1/h -- an exact float scaling, an exact floor and an integer
+// subtraction.  Key digit l holds the level-l bits of (qx, qy, qz), x highest.
+__device__ __forceinline__ uint64_t quantise(float x, int k, long long K0)
+{
+    float t = floorf(scalbnf(x, k));
+    if (x < 0.0f && t == 0.0f) t = -1.0f;  // a negative value scaled below the float range
+    long long q = __float2ll_rz(t) - K0;    // the conversion saturates out-of-range values
+    q = q < 0 ? 0 : (q > 2097151 ? 2097151 : q);
+    return (uint64_t)q;
+}
+
 __global__ void k_keys(const float* __restrict__ pos, const float* __restrict__ mass, int64_t n,
                        const Info* __restrict__ info, uint64_t* __restrict__ keys,
                        uint32_t* __restrict__ idx, int32_t* err)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double inv_h = info->inv_h;
-    uint64_t q[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        double t = floor(((double)pos[3 * i + a] - info->c0[a]) * inv_h);
-        t = fmin(fmax(t, 0.0), 2097151.0);
-        q[a] = (uint64_t)t;
-    }
-    keys[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+    const int k = info->qexp;
+    const uint64_t qx = quantise(pos[3 * i], k, info->qoff[0]);
+    const uint64_t qy = quantise(pos[3 * i + 1], k, info->qoff[1]);
+    const uint64_t qz = quantise(pos[3 * i + 2], k, info->qoff[2]);
+    keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     idx[i] = (uint32_t)i;
     float m = mass[i];
     if (!(isfinite(m) && m > 0.0f)) atomicOr(err, kErrNonFinite);
@@ -298,19 +328,23 @@ __global__ void k_node_finalize(const uint64_t* __restrict__ keys, const int8_t*
 // Leaves are done in one launch; internal cells level by level from the
 // deepest, one thread per cell of the level (cells of a level are contiguous
 // in breadth-first order), so every lane of a warp has a cell to do.
+template <bool QUAD>
 __device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const double* Q,
                            const Info* info, int4 c)
 {
     nt.mass64[v] = M;
     for (int a = 0; a < 3; a++) nt.com64[3 * v + a] = com[a];
-    for (int a = 0; a < 6; a++) nt.quad64[6 * v + a] = Q[a];
     const double u = 0.5 * info->h;
     double C[3] = {info->c0[0] + (double)c.x * u, info->c0[1] + (double)c.y * u, info->c0[2] + (double)c.z * u};
     nt.a[v] = make_float4((float)(com[0] - C[0]), (float)(com[1] - C[1]), (float)(com[2] - C[2]), (float)M);
     nt.d[v] = make_float4((float)com[0], (float)com[1], (float)com[2], (float)M);
-    for (int a = 0; a < 6; a++) nt.quad[6 * v + a] = (float)Q[a];
+    if (QUAD) {
+        for (int a = 0; a < 6; a++) nt.quad64[6 * v + a] = Q[a];
+        for (int a = 0; a < 6; a++) nt.quad[6 * v + a] = (float)Q[a];
+    }
 }
 
+template <bool QUAD>
 __global__ void k_leaf_moments(const float4* __restrict__ body, int64_t M, const Info* __restrict__ info,
                                NodeTables nt)
 {
@@ -333,7 +367,7 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, int64_t M, const
     const double inv = 1.0 / m;
     const double off[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
     double Q[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = b.x; j < b.x + b.y; j++) {
+    for (int j = b.x; QUAD && j < b.x + b.y; j++) {
         const float4 q = body[j];
         const double dx = ((double)q.x - C[0]) - off[0];
         const double dy = ((double)q.y - C[1]) - off[1];
@@ -347,10 +381,11 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, int64_t M, const
         Q[5] += mj * dz * dz;
     }
     const double com[3] = {C[0] + off[0], C[1] + off[1], C[2] + off[2]};
-    store_node(nt, v, m, com, Q, info, c);
+    store_node<QUAD>(nt, v, m, com, Q, info, c);
 }
 
 // internal cells of level `lev`: [level_start[lev], level_start[lev + 1])
+template <bool QUAD>
 __global__ void k_level_moments(int lev, const uint32_t* __restrict__ level_start, const Info* __restrict__ info,
                                 NodeTables nt)
 {
@@ -371,7 +406,7 @@ __global__ void k_level_moments(int lev, const uint32_t* __restrict__ level_star
         const double inv = 1.0 / m;
         const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
         double Q[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = 0; k < nch; k++) {
+        for (int k = 0; QUAD && k < nch; k++) {
             const int64_t c = pb.z + k;
             const double mc = nt.mass64[c];
             double d[3];
@@ -383,7 +418,7 @@ __global__ void k_level_moments(int lev, const uint32_t* __restrict__ level_star
             Q[4] += nt.quad64[6 * c + 4] + mc * d[1] * d[2];
             Q[5] += nt.quad64[6 * c + 5] + mc * d[2] * d[2];
         }
-        store_node(nt, v, m, com, Q, info, nt.c[v]);
+        store_node<QUAD>(nt, v, m, com, Q, info, nt.c[v]);
     }
 }
 
@@ -519,14 +554,16 @@ void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n, co
 }
 
 void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* level_start, const Info* info,
-                    NodeTables nt, cudaStream_t s)
+                    NodeTables nt, bool quad, cudaStream_t s)
 {
-    k_leaf_moments<<<nblk(M, 128), 128, 0, s>>>(body, M, info, nt);
+    if (quad) k_leaf_moments<true><<<nblk(M, 128), 128, 0, s>>>(body, M, info, nt);
+    else k_leaf_moments<false><<<nblk(M, 128), 128, 0, s>>>(body, M, info, nt);
     count_launches(1);
     int64_t g = nblk(M, 128);
     if (g > 8 * 152) g = 8 * 152;
     for (int lev = depth - 1; lev >= 0; lev--) {
-        k_level_moments<<<(unsigned)g, 128, 0, s>>>(lev, level_start, info, nt);
+        if (quad) k_level_moments<true><<<(unsigned)g, 128, 0, s>>>(lev, level_start, info, nt);
+        else k_level_moments<false><<<(unsigned)g, 128, 0, s>>>(lev, level_start, info, nt);
         count_launches(1);
     }
 }

@@ -25,6 +25,9 @@ struct Info {
     double L;          // root cube side (power of two)
     double h;          // grid step L / 2^21
     double inv_h;      // 1 / h (exact)
+    long long qoff[3]; // c0 / h (integers): q = floor(x / h) - qoff
+    int32_t qexp;      // 1 / h = 2^qexp
+    int32_t pad1;
     float Lf;          // L as float (exact)
     float uf;          // h / 2 as float (exact): unit of the integer centres
     int32_t err;       // error bits
@@ -109,7 +112,7 @@ void launch_inverse_perm(const uint32_t* perm, int64_t M, uint32_t* inv, cudaStr
 // first node of level l (the level sort's digit offsets; level_start[l+1]
 // ends it)
 void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* level_start, const Info* info,
-                    NodeTables nt, cudaStream_t s);
+                    NodeTables nt, bool quad, cudaStream_t s);
 void launch_group_marks(int64_t M, const NodeTables nt, int gmax, int64_t n, uint32_t* gflag,
                         int32_t* gref_at, cudaStream_t s);
 void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int32_t* gref_at,

@@ -42,7 +42,7 @@ class TcError(RuntimeError):
 class tc_config(ctypes.Structure):
     _fields_ = [("gmax", ctypes.c_int32), ("warps", ctypes.c_int32), ("precise", ctypes.c_int32),
                 ("want_pot", ctypes.c_int32), ("verify", ctypes.c_int32), ("stack", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("quad", ctypes.c_int32)]
 
 
 _lib = None
@@ -231,7 +231,7 @@ class Context:
         a["prefix"] = np.empty(M, np.uint64)
         a["mass"] = np.empty(M)
         a["com"] = np.empty((M, 3))
-        a["quad"] = np.empty((M, 6))
+        a["quad"] = np.empty((M, 6)) if self.config()["quad"] else None
         self._c(self._lib.tc_get_nodes(self._h, _ptr(a["level"]), _ptr(a["prefix"]), _ptr(a["first"]),
                                        _ptr(a["count"]), _ptr(a["child_first"]), _ptr(a["nchild"]),
                                        _ptr(a["mass"]), _ptr(a["com"]), _ptr(a["quad"])))
