@@ -317,11 +317,166 @@ def run_ours(args, rank, world, local_rank):
                     "what": "force evaluation from pinned host pos/mass: upload, build, walk/force, "
                             "download of accelerations"},
             "gpu_launches": tim["launches"],
+            "step_structure": "graph-captured kick + drift + rebuild, then the walk and the closing kick "
+                              "as timed launches on the same stream",
             "clocks": clk,
             "wall_s_timed": wall,
             "cpu_baseline": cpu,
         }
     return line
+
+
+def run_batch(args, rank, world, local_rank):
+    """512 independent Plummer systems (N log-uniform in [1024, 65536],
+    theta 0.6, leaf 8, eps 0.01, KDK dt 1e-3) in one forest: one walk launch
+    and one step graph per step; launch shape from the autotuner."""
+    import torch
+
+    from paper_1211_2293_gb300 import inputs, tc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    tc.load()
+    theta, eps, dt, leaf = 0.6, 0.01, 1e-3, 8
+    sizes = inputs.batch_sizes(args.nsys, seed=rank)
+    parts = [inputs.plummer(int(k), seed=1000 * rank + s) for s, k in enumerate(sizes)]
+    p = np.concatenate([a for a, _, _ in parts])
+    v = np.concatenate([b for _, b, _ in parts])
+    m = np.concatenate([c for _, _, c in parts])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    ctx = tc.Context()
+    ctx.build_batch(torch.from_numpy(p).to(dev), torch.from_numpy(m).to(dev), off, leaf)
+    ctx.set_velocity(torch.from_numpy(v).to(dev))
+    best, tune_ms = ctx.autotune(theta, eps, reps=2)
+    ctx.forces(theta, eps)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.step(dt)
+    ctx.sync()
+    clocks = ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else None)
+    clocks.start()
+    t_load = time.perf_counter()
+    while time.perf_counter() - t_load < 1.0:
+        ctx.step(dt)
+        ctx.sync()
+    ctx.set_timing(True)
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(dt)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    tim = ctx.timings()
+    ctx.set_timing(False)
+    inter = ctx.lists(per_group=False)["interactions"]
+    ms = statistics.mean(step_ms)
+    walk_ms = tim["walk_ms"] / args.steps
+    achieved = inter * FLOPS_PER_INTERACTION / (walk_ms / 1e3) / 1e12
+    # graph-only steps (whole step captured, no phase timing)
+    g_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(dt)
+        e1.record(stream)
+        e1.synchronize()
+        g_ms.append(e0.elapsed_time(e1))
+    line = {
+        "metric": METRIC, "value": n * world / (statistics.mean(g_ms) / 1e3), "unit": "bodies/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(g_ms),
+        "ms_per_step_phase_timed": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch of {args.nsys} Plummer systems, N log-uniform in [1024, 65536], "
+                               f"total {n}, theta 0.6, leaf 8, eps 0.01, KDK dt 1e-3, one step graph per step",
+                   "n_bodies": n, "systems": args.nsys, "l2": "flushed between timed steps (256 MiB write)"},
+        "autotuned": {"gmax": best["gmax"], "tile": best["tile"], "warps": best["warps"], "walk_ms": tune_ms},
+        "phase_ms_per_step": {"build": tim["build_ms"] / args.steps, "walk_force": walk_ms,
+                              "update": tim["update_ms"] / args.steps},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak_tflops(), "traffic": None, "kernel": "k_walk (walk + force)"},
+        "graph_kernels_per_step": tim["graph_kernels"],
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_precision(args, rank, world, local_rank):
+    """Two Plummer spheres of 2^23 bodies each, 6 scale radii apart and
+    approaching at 0.5 (N = 2^24, theta 0.75, leaf 16, eps 5e-4): forces of
+    the precise mode (cell-relative coordinates, compensated tile sums) and of
+    the plain float32 mode against the FP64 oracle's forces on the same tree
+    and lists for the groups holding 8192 sampled bodies; and the cost."""
+    import torch
+
+    import oracle
+    from paper_1211_2293_gb300 import inputs, tc
+
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    tc.load()
+    theta, eps, leaf = 0.75, 5e-4, 16
+    n = args.n if args.n != N_DEFAULT else 1 << 24
+    p, v, m = inputs.two_plummer(n, seed=0)
+    P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
+    res = {}
+    for mode in (1, 0):
+        ctx = tc.Context(precise=mode, want_pot=0, verify=0)
+        ctx.build(P, M, leaf)
+        ctx.forces(theta, eps)
+        ctx.sync()
+        ctx.set_timing(True)
+        for _ in range(3):
+            ctx.forces(theta, eps)
+        walk_ms = ctx.timings()["walk_ms"] / 3
+        ctx.set_timing(False)
+        res[mode] = dict(acc=ctx.get_acc(), walk_ms=walk_ms)
+        gmax = ctx.config()["gmax"]
+    t0 = time.perf_counter()
+    t = oracle.Tree(p, m, leaf, gmax)
+    sample = inputs.sample_indices(n, 8192, seed=3)
+    inv = np.empty(n, np.int64)
+    inv[t.perm] = np.arange(n)
+    gid = np.searchsorted(t.gfirst, inv[sample], side="right") - 1
+    groups = np.unique(gid)
+    acc_or = np.full((n, 3), np.nan)
+    flagged = 0
+    for g in groups:
+        w = t.walk(theta, eps, groups=(int(g), int(g) + 1), want_pot=False)
+        flagged += int(w["flag"][g] == 1)
+        idx = t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]
+        acc_or[idx] = w["acc"][idx]
+    oracle_s = time.perf_counter() - t0
+    ao = acc_or[sample]
+    out = {}
+    for mode, name in ((1, "precise"), (0, "plain")):
+        a = res[mode]["acc"][sample].astype(np.float64)
+        rel = np.linalg.norm(a - ao, axis=1) / np.linalg.norm(ao, axis=1)
+        out[name] = {"max_rel_err": float(rel.max()), "rms_rel_err": float(np.sqrt(np.mean(rel ** 2))),
+                     "p99_rel_err": float(np.percentile(rel, 99)), "walk_ms": res[mode]["walk_ms"],
+                     "bodies_per_s_walk": n / (res[mode]["walk_ms"] / 1e3)}
+    line = {"metric": "force error vs FP64 oracle (8192 sampled bodies) and walk throughput: precise vs plain",
+            "value": out["precise"]["max_rel_err"], "unit": "max relative error", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"two Plummer spheres, N={n}, 6 scale radii apart, approaching at 0.5, "
+                                   f"theta 0.75, leaf 16, eps 5e-4", "n_bodies": n},
+            "precise": out["precise"], "plain": out["plain"],
+            "precise_cost": res[1]["walk_ms"] / res[0]["walk_ms"],
+            "sampled_groups": int(groups.size), "flagged_groups": flagged, "oracle_seconds": oracle_s}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def main():
@@ -335,6 +490,10 @@ def main():
     ap.add_argument("--cpu-frac", type=int, default=8, help="oracle walks 1/cpu_frac of the groups")
     ap.add_argument("--ref-frac", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["uniform", "batch", "precision"], default="uniform",
+                    help="uniform: the benchmark line; batch: 512 Plummer systems in one forest; "
+                         "precision: cell-relative vs plain float32 on two colliding Plummer spheres")
+    ap.add_argument("--nsys", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -344,6 +503,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, rank, world, local_rank)
+    if args.workload == "precision":
+        return run_precision(args, rank, world, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

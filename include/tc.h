@@ -55,7 +55,14 @@ typedef struct tc_ctx tc_ctx;
  *   blocks_per_sm  0 = as many as fit, else a cap
  *   quad      1: also reduce the cells' second moments about the centre of
  *             mass (FP64; the learned correction's features, tc_get_nodes'
- *             quad); 0: mass and centre of mass only                     */
+ *             quad); 0: mass and centre of mass only
+ *   tile      interaction-list entries summed per shared-memory tile: 64,
+ *             128 or 256
+ *   graph     1: tc_ctx_step replays one captured CUDA graph per step (the
+ *             whole step -- kick, drift, rebuild, walk, kick -- with no host
+ *             synchronisation; with phase timing on, the walk and the
+ *             closing kick follow the graph as timed launches); 0: the same
+ *             launches issued one by one                                  */
 typedef struct {
     int32_t gmax;
     int32_t warps;
@@ -65,6 +72,8 @@ typedef struct {
     int32_t stack;
     int32_t blocks_per_sm;
     int32_t quad;
+    int32_t tile;
+    int32_t graph;
 } tc_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a
@@ -85,6 +94,15 @@ int tc_set_stream(tc_ctx *ctx, void *cuda_stream);
  * the node table). */
 int tc_ctx_build(tc_ctx *ctx, const float *pos, const float *mass, int64_t n, int leaf_max);
 
+/* A batch of nsys independent systems in one context (bodies of system s are
+ * pos/mass rows [offsets[s], offsets[s+1]); offsets has nsys + 1 entries,
+ * offsets[0] = 0, every system holds at least one body, 1 <= nsys <= 65536).
+ * Each system gets its own root cube and tree (one forest); forces act only
+ * within a system; one walk launch and one step graph serve all systems.
+ * tc_ctx_build is the batch of one system. */
+int tc_ctx_build_batch(tc_ctx *ctx, const float *pos, const float *mass, const int64_t *offsets,
+                       int64_t nsys, int leaf_max);
+
 /* Velocities (n x 3) for tc_ctx_step; copied. */
 int tc_ctx_set_velocity(tc_ctx *ctx, const float *vel);
 
@@ -101,8 +119,10 @@ int tc_ctx_forces(tc_ctx *ctx, float theta, float eps, float G);
 /* One kick-drift-kick leapfrog step of length dt with the last theta, eps,
  * G: v += a dt/2; x += v dt; rebuild the tree; forces; v += a dt/2 (the
  * paper's "each body updates its position and velocity", Sec. 3.1).  Needs
- * a prior tc_ctx_forces on the current positions.  Synchronises once (the
- * rebuild). */
+ * a prior tc_ctx_forces on the current positions.  Enqueue only: the rebuild
+ * reuses the node table sized by the last tc_ctx_build / tc_set_state (with
+ * 50% headroom); a tree that outgrows it stops the step on the device and
+ * the next synchronising call reports TC_EDEVICE. */
 int tc_ctx_step(tc_ctx *ctx, float dt);
 
 /* Accelerations (n x 3) and, if pot != NULL and want_pot was set, the
@@ -131,8 +151,10 @@ int tc_get_tree(tc_ctx *ctx, uint32_t *perm, uint64_t *keys);
 int tc_get_nodes(tc_ctx *ctx, int32_t *level, uint64_t *prefix, int32_t *first, int32_t *count,
                  int32_t *child_first, int32_t *nchild, double *mass, double *com, double *quad);
 int tc_get_groups(tc_ctx *ctx, int32_t *gfirst, int32_t *gcount, int32_t *gref);
-/* Root cube of the last build: out5 = {c0x, c0y, c0z, L, h}. */
+/* Root cube of the last build (system 0): out5 = {c0x, c0y, c0z, L, h}. */
 int tc_get_cube(tc_ctx *ctx, double *out5);
+/* Number of systems and their root cubes (nsys x 5, as tc_get_cube). */
+int tc_get_systems(tc_ctx *ctx, int64_t *nsys, double *cubes);
 
 /* Per-group list lengths of the last force phase (needs verify = 1):
  * accepted cells, bodies of opened leaves, order-independent hash of the
@@ -157,8 +179,11 @@ int tc_direct(tc_ctx *ctx, const int64_t *idx, int64_t ns, float eps, float G, d
  * leapfrog updates (and clears earlier records).  tc_get_timings
  * synchronises and returns out6 = {build ms, walk ms, update ms (sums over
  * the calls since the last tc_set_timing / tc_get_timings), kernels launched
- * by this process's libtc since then, kernels launched in total, 0}, then
- * clears the records. */
+ * by this process's libtc since then (a replayed step graph counts its
+ * kernels), kernels launched in total, kernels in one step graph}, then
+ * clears the records.  In graph mode with timing on, a step's graph holds
+ * kick + drift + rebuild (timed as "build") and the walk and closing kick
+ * are launched after it, each bracketed by events. */
 int tc_set_timing(tc_ctx *ctx, int on);
 int tc_get_timings(tc_ctx *ctx, double *out6);
 
@@ -187,6 +212,14 @@ int tc_get_timings(tc_ctx *ctx, double *out6);
  * implicit default context has no error of its own pending). */
 int tc_direct_static(const float *pos, const float *mass, int64_t n, const int64_t *idx, int64_t ns,
                      float eps, float G, double *acc, double *pot, void *cuda_stream);
+
+/* Autotuner: times the walk + force kernel for every group size (32, 64,
+ * 128), list tile (64, 128, 256) and warps per block (2, 4) on the current
+ * bodies (reps timed runs each, the fastest kept), sets the best and returns
+ * it with its time in ms.  When the environment variable TC_AUTOTUNE_CACHE
+ * names a file, results are looked up there first and appended after a
+ * search (key: N, systems, leaf, theta, eps, precision, potential). */
+int tc_autotune(tc_ctx *ctx, float theta, float eps, float G, int reps, tc_config *best, double *best_ms);
 
 /* Wait for the context's stream; report device errors. */
 int tc_sync(tc_ctx *ctx);

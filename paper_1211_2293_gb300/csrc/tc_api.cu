@@ -1,7 +1,9 @@
 // tc_api.cu -- the C ABI of libtc (declared in include/tc.h): context,
-// argument checks, buffer management and the order of launches.
+// argument checks, buffer management, the order of launches, the CUDA graph
+// of a leapfrog step and the launch-configuration autotuner.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -20,19 +22,28 @@ using namespace tc;
 
 struct tc_ctx {
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // a stream of our own to capture step graphs on
     int device = 0;
     int num_sms = 0;
     tc_config cfg{};
     std::string err;
 
     int64_t n = 0, cap_n = 0;
-    int64_t M = 0, cap_m = 0;
+    int nsys = 0, cap_sys = 0;
+    std::vector<int64_t> off_h;  // system offsets (host)
+    int nchunks = 0, cap_chunks = 0;
+    int64_t M = 0, cap_m = 0;  // nodes of the last synchronised build, node table capacity
     int leaf_max = 0;
     bool built = false, have_forces = false, forces_pot = false;
     float theta = 0.f, eps = 0.f, Gc = 0.f;
 
     // state, original body order
     float *pos = nullptr, *vel = nullptr, *acc = nullptr, *pot = nullptr, *mass = nullptr;
+    // systems
+    uint32_t* sys_of = nullptr;
+    SysParams* sysp = nullptr;
+    int64_t* off_dev = nullptr;
+    int4* chunks = nullptr;
     // per-body build scratch
     uint64_t* keys = nullptr;
     uint32_t* perm = nullptr;
@@ -44,7 +55,6 @@ struct tc_ctx {
     int32_t *gref_at = nullptr, *gfirst = nullptr, *gref = nullptr;
     int32_t *ncell = nullptr, *nbody = nullptr;
     unsigned long long* hash = nullptr;
-    float* bbox_partial = nullptr;
     uint32_t* totals = nullptr;  // [0] nodes, [1] groups
     int64_t* idx_dev = nullptr;
     int64_t cap_idx = 0;
@@ -54,8 +64,15 @@ struct tc_ctx {
     NodeTables nt{};
     Info* info = nullptr;
     Info* info_h = nullptr;  // pinned mirror
+    int64_t cap_m_h = 0;     // source of the device copy of cap_m
     size_t allocated = 0;
     std::unordered_map<void*, size_t> sizes;
+
+    // walk launch shape for the current configuration
+    bool walk_ready = false;
+    int walk_grid = 0;
+    size_t walk_smem = 0;
+    WalkConfig walk_cfg{};
 
     // phase timers (CUDA events on the context stream), when enabled
     bool timing = false;
@@ -63,6 +80,11 @@ struct tc_ctx {
     size_t ev_used = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_phase[3];  // build, walk, update
     long long launches_mark = 0;
+
+    // the captured leapfrog step
+    cudaGraphExec_t gexec = nullptr;
+    std::string gkey;
+    long long graph_kernels = 0;
 };
 
 namespace tc {
@@ -110,9 +132,17 @@ size_t alloc_cap()
     return (size_t)strtoull(s, nullptr, 10);
 }
 
+void drop_graph(tc_ctx* c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey.clear();
+}
+
 template <typename T>
 int grow(tc_ctx* c, T** p, int64_t count)
 {
+    drop_graph(c);  // a captured step refers to the old buffers
     if (*p) {
         auto it = c->sizes.find((void*)*p);
         if (it != c->sizes.end()) {
@@ -151,14 +181,15 @@ int ensure_bodies(tc_ctx* c, int64_t n)
     TC_GROW(c, c->acc, 3 * cap);
     TC_GROW(c, c->pot, cap);
     TC_GROW(c, c->mass, cap);
+    TC_GROW(c, c->sys_of, cap);
     TC_GROW(c, c->keys, cap);
     TC_GROW(c, c->perm, cap);
     TC_GROW(c, c->body, cap);
     TC_GROW(c, c->sb.keys_alt, cap);
     TC_GROW(c, c->sb.vals_alt, cap);
-    TC_GROW(c, c->sb.ghist, 8 * 256);
-    TC_GROW(c, c->sb.status, 8 * radix_tiles(cap) * 256);  // look-back words of the 8 key passes
-    TC_GROW(c, c->sb.tiles, 8);
+    TC_GROW(c, c->sb.ghist, kSortMaxPasses * 256);
+    TC_GROW(c, c->sb.status, (int64_t)kSortMaxPasses * radix_tiles(cap) * 256);
+    TC_GROW(c, c->sb.tiles, kSortMaxPasses);
     c->sb.err = &c->info->err;
     TC_GROW(c, c->sb.blocksum, scan_blocksum_size(cap));
     TC_GROW(c, c->w, cap);
@@ -174,17 +205,30 @@ int ensure_bodies(tc_ctx* c, int64_t n)
     TC_GROW(c, c->ncell, cap);
     TC_GROW(c, c->nbody, cap);
     TC_GROW(c, c->hash, cap);
-    TC_GROW(c, c->bbox_partial, 6 * 1024);
     TC_GROW(c, c->totals, 4);
     c->cap_n = cap;
     c->cap_m = 0;  // node tables are sized with the first build at this capacity
     return TC_OK;
 }
 
+int ensure_systems(tc_ctx* c, int nsys, int nchunks)
+{
+    if (nsys > c->cap_sys) {
+        TC_GROW(c, c->sysp, nsys);
+        TC_GROW(c, c->off_dev, nsys + 1);
+        c->cap_sys = nsys;
+    }
+    if (nchunks > c->cap_chunks) {
+        TC_GROW(c, c->chunks, nchunks);
+        c->cap_chunks = nchunks;
+    }
+    return TC_OK;
+}
+
 int ensure_nodes(tc_ctx* c, int64_t M)
 {
     if (M <= c->cap_m) return TC_OK;
-    int64_t cap = M + M / 4 + 64;
+    const int64_t cap = M + M / 2 + 1024;  // headroom for the rebuilds of later steps
     TC_GROW(c, c->pre_level, cap);
     TC_GROW(c, c->pre_first, cap);
     TC_GROW(c, c->iota, cap);
@@ -198,15 +242,16 @@ int ensure_nodes(tc_ctx* c, int64_t M)
     TC_GROW(c, c->nt.mass64, cap);
     TC_GROW(c, c->nt.com64, 3 * cap);
     TC_GROW(c, c->nt.quad64, 6 * cap);
-    // the level sort reuses the body sort's value ping-pong buffer
+    // the level sort reuses the body sort's value ping-pong buffer and status words
     if (cap > c->cap_n) TC_GROW(c, c->sb.vals_alt, cap);
-    if (radix_tiles(cap) > 8 * radix_tiles(c->cap_n))  // the level sort's single pass
+    if (radix_tiles(cap) > (int64_t)kSortMaxPasses * radix_tiles(c->cap_n))
         TC_GROW(c, c->sb.status, radix_tiles(cap) * 256);
     c->cap_m = cap;
+    c->walk_ready = false;  // the stack bound may follow the capacity
     return TC_OK;
 }
 
-// device error word -> status (synchronises)
+// device error word -> status (synchronises); clears the word it reports
 int check_device(tc_ctx* c)
 {
     TC_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -217,8 +262,12 @@ int check_device(tc_ctx* c)
         TC_CUDA(c, cudaStreamSynchronize(c->stream));
         if (e & kErrNonFinite)
             return fail(c, TC_EINVAL, "input holds a non-finite coordinate or a non-positive/non-finite mass");
-        if (e & kErrStack)
-            return fail(c, TC_EDEVICE, "walk stack overflow (raise tc_config.stack)");
+        if (e & kErrCapacity)
+            return fail(c, TC_EDEVICE,
+                        "node table capacity exceeded by a rebuild inside a step; the state holds that step's "
+                        "drift -- call tc_ctx_build or tc_set_state to resize");
+        if (e & kErrStack) return fail(c, TC_EDEVICE, "walk stack overflow (raise tc_config.stack)");
+        if (e & kErrWorkLoop) return fail(c, TC_EDEVICE, "a bounded device wait gave up");
         return fail(c, TC_EDEVICE, "device error word 0x%x", e);
     }
     return TC_OK;
@@ -237,71 +286,131 @@ cudaEvent_t take_event(tc_ctx* c)
 }
 
 // records the start of a timed phase; returns the event (or null)
-cudaEvent_t phase_begin(tc_ctx* c)
+cudaEvent_t phase_begin(tc_ctx* c, cudaStream_t s)
 {
     if (!c->timing) return nullptr;
     cudaEvent_t e = take_event(c);
-    if (e) cudaEventRecord(e, c->stream);
+    if (e) cudaEventRecord(e, s);
     return e;
 }
 
-void phase_end(tc_ctx* c, int phase, cudaEvent_t start)
+void phase_end(tc_ctx* c, int phase, cudaEvent_t start, cudaStream_t s)
 {
     if (!start) return;
     cudaEvent_t e = take_event(c);
     if (!e) return;
-    cudaEventRecord(e, c->stream);
+    cudaEventRecord(e, s);
     c->ev_phase[phase].push_back({start, e});
 }
 
-// The whole build from c->pos / c->mass (already on the device).
-int build_tree(tc_ctx* c)
+int sys_bits(int nsys)
 {
-    cudaStream_t s = c->stream;
+    int b = 0;
+    while ((1 << b) < nsys) b++;
+    return b;
+}
+
+// system offsets -> per-body system ids, bounding-box chunks
+int setup_systems(tc_ctx* c, const int64_t* off, int nsys)
+{
+    std::vector<int4> ch;
+    for (int s = 0; s < nsys; s++)
+        for (int64_t a = off[s]; a < off[s + 1]; a += kBboxChunk)
+            ch.push_back(make_int4(s, (int)a, (int)std::min(off[s + 1], a + (int64_t)kBboxChunk), 0));
+    int r = ensure_systems(c, nsys, (int)ch.size());
+    if (r) return r;
+    c->off_h.assign(off, off + nsys + 1);
+    c->nsys = nsys;
+    c->nchunks = (int)ch.size();
+    TC_CUDA(c, cudaMemcpyAsync(c->off_dev, c->off_h.data(), (nsys + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                               c->stream));
+    TC_CUDA(c, cudaMemcpyAsync(c->chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
+    launch_sys_ids(c->off_dev, nsys, c->n, c->sys_of, c->sysp, c->stream);
+    // the host vectors above may be copied from pageable memory: wait before they go
+    TC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+// The build from c->pos / c->mass (already on the device), on stream s.
+// synced: validate the input and size the node table (one synchronisation);
+// otherwise no host interaction at all (the form captured in a step graph),
+// with the node count checked against the capacity on the device.
+int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
+{
     const int64_t n = c->n;
-    cudaEvent_t t0 = phase_begin(c);
-    TC_CUDA(c, cudaMemsetAsync(&c->info->err, 0, sizeof(int32_t), s));
-    int nb = bbox_blocks(n);
-    launch_bbox(c->pos, n, c->bbox_partial, nb, c->info, s);
-    launch_keys(c->pos, c->mass, n, c->info, c->keys, c->perm, s);
-    radix_sort_u64(c->keys, c->perm, n, 63, c->sb, s);
+    cudaEvent_t t0 = phase_begin(c, s);
+    if (synced) TC_CUDA(c, cudaMemsetAsync(&c->info->err, 0, sizeof(int32_t), s));
+    launch_bbox(c->pos, c->chunks, c->nchunks, c->sysp, c->nsys, &c->info->err, s);
+    launch_keys(c->pos, c->mass, n, c->sys_of, c->sysp, c->keys, c->perm, &c->info->err, s);
+    radix_sort_u64(c->keys, c->perm, n, 63, c->sys_of, c->nsys > 1 ? sys_bits(c->nsys) : 0, c->sb, s);
     launch_gather(c->pos, c->mass, c->perm, n, c->body, s);
     TC_CUDA(c, cudaMemsetAsync(&c->info->depth, 0, sizeof(int32_t), s));
-    launch_node_counts(c->keys, n, c->leaf_max, c->w, c->delta, c->top, c->nstart, &c->info->depth, s);
+    launch_node_counts(c->keys, c->sys_of, n, c->leaf_max, c->w, c->delta, c->top, c->nstart, &c->info->depth, s);
     scan_u32(c->nstart, c->prepos, n, &c->totals[0], c->sb.blocksum, s);
-    TC_CUDA(c, cudaGetLastError());
-    uint32_t M32 = 0;
-    TC_CUDA(c, cudaMemcpyAsync(&M32, &c->totals[0], sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    int r = check_device(c);  // synchronises: M32 valid afterwards
-    if (r) return r;
-    const int64_t M = M32;
-    if (M < 1) return fail(c, TC_EDEVICE, "empty node table");
-    r = ensure_nodes(c, M);
-    if (r) return r;
-    c->M = M;
-    launch_emit_preorder(c->delta, c->nstart, c->prepos, n, c->pre_level, c->pre_first, c->iota, s);
+    int depth = -1;
+    if (synced) {
+        TC_CUDA(c, cudaGetLastError());
+        int r = check_device(c);  // synchronises; reports invalid input
+        if (r) return r;
+        uint32_t M32 = 0;
+        TC_CUDA(c, cudaMemcpy(&M32, &c->totals[0], sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        if (M32 < 1) return fail(c, TC_EDEVICE, "empty node table");
+        r = ensure_nodes(c, M32);
+        if (r) return r;
+        c->M = M32;
+        c->cap_m_h = c->cap_m;
+        TC_CUDA(c, cudaMemcpyAsync(&c->info->cap_m, &c->cap_m_h, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        depth = c->info_h->depth;
+    }
+    launch_check_capacity(&c->totals[0], c->info, s);
+    launch_emit_preorder(c->delta, c->nstart, c->prepos, n, c->info, c->pre_level, c->pre_first, c->iota, s);
     // breadth-first order: stable sort of the pre-order nodes by level
     SortBufs lb = c->sb;
-    radix_sort_u32(c->pre_level, c->iota, M, 8, lb, c->lvl_alt, s);
-    launch_inverse_perm(c->iota, M, c->bfs_of_pre, s);
-    launch_node_finalize(c->keys, c->top, n, c->pre_level, c->iota, c->pre_first, c->bfs_of_pre, M, c->nt, s);
+    radix_sort_u32(c->pre_level, c->iota, c->cap_m, &c->info->M, 8, lb, c->lvl_alt, s);
+    launch_inverse_perm(c->iota, c->cap_m, c->info, c->bfs_of_pre, s);
+    launch_node_finalize(c->keys, c->top, c->sys_of, c->sysp, n, c->pre_level, c->iota, c->pre_first, c->bfs_of_pre,
+                         c->cap_m, c->info, c->nt, s);
     // after the level sort, ghist[l] is the first breadth-first index of level l
-    launch_moments(c->body, M, c->info_h->depth, c->sb.ghist, c->info, c->nt, c->cfg.quad != 0, s);
-    launch_group_marks(M, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
+    launch_moments(c->body, c->cap_m, depth, c->sb.ghist, c->sys_of, c->sysp, c->info, c->nt, c->cfg.quad != 0, s);
+    launch_group_marks(c->cap_m, c->info, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);
     launch_group_table(c->gflag, c->gscan, c->gref_at, n, &c->totals[1], c->gfirst, c->gref, c->info, s);
     TC_CUDA(c, cudaGetLastError());
-    phase_end(c, 0, t0);
+    phase_end(c, 0, t0, s);
     c->built = true;
     c->have_forces = false;
     return TC_OK;
 }
 
-int run_forces(tc_ctx* c, float theta, float eps, float G)
+int prepare_forces(tc_ctx* c)
+{
+    WalkConfig wc{};
+    wc.gmax = c->cfg.gmax;
+    wc.warps = c->cfg.warps;
+    wc.precise = c->cfg.precise;
+    wc.want_pot = c->cfg.want_pot;
+    wc.verify = c->cfg.verify;
+    wc.blocks_per_sm = c->cfg.blocks_per_sm;
+    wc.tile = c->cfg.tile;
+    int64_t st = c->cfg.stack;
+    if (c->cap_m < st) st = c->cap_m < 32 ? 32 : c->cap_m;  // a stack of M entries cannot overflow
+    st = (st + 3) & ~(int64_t)3;                            // keeps every warp's tiles 16-byte aligned
+    wc.stack = (int)st;
+    if (c->walk_ready && memcmp(&wc, &c->walk_cfg, sizeof(wc)) == 0) return TC_OK;
+    cudaError_t e = prepare_walk(wc, c->num_sms, &c->walk_grid, &c->walk_smem);
+    if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk kernel set-up: %s", cudaGetErrorString(e));
+    c->walk_cfg = wc;
+    c->walk_ready = true;
+    return TC_OK;
+}
+
+int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
 {
     WalkArgs a{};
     a.body = c->body;
     a.perm = c->perm;
+    a.sys_of = c->sys_of;
+    a.sysp = c->sysp;
     a.nt = c->nt;
     a.gfirst = c->gfirst;
     a.gref = c->gref;
@@ -315,26 +424,104 @@ int run_forces(tc_ctx* c, float theta, float eps, float G)
     a.eps2 = eps * eps;
     a.G = G;
     a.inv_eps = 1.0f / eps;
-    WalkConfig wc{};
-    wc.gmax = c->cfg.gmax;
-    wc.warps = c->cfg.warps;
-    wc.precise = c->cfg.precise;
-    wc.want_pot = c->cfg.want_pot;
-    wc.verify = c->cfg.verify;
-    wc.blocks_per_sm = c->cfg.blocks_per_sm;
-    int64_t st = c->cfg.stack;
-    if (c->M < st) st = c->M < 32 ? 32 : c->M;  // a stack of M entries cannot overflow
-    st = (st + 3) & ~(int64_t)3;                // keeps every warp's tiles 16-byte aligned
-    wc.stack = (int)st;
-    cudaEvent_t t0 = phase_begin(c);
-    cudaError_t e = launch_walk(a, wc, c->num_sms, c->stream);
+    cudaEvent_t t0 = phase_begin(c, s);
+    cudaError_t e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, s);
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk launch: %s", cudaGetErrorString(e));
-    phase_end(c, 1, t0);
+    phase_end(c, 1, t0, s);
     c->have_forces = true;
     c->forces_pot = c->cfg.want_pot != 0;
     c->theta = theta;
     c->eps = eps;
     c->Gc = G;
+    return TC_OK;
+}
+
+// kick + drift, sync-free rebuild, walk, kick -- eagerly on the context stream
+int step_eager(tc_ctx* c, float dt)
+{
+    cudaStream_t s = c->stream;
+    int r = prepare_forces(c);
+    if (r) return r;
+    cudaEvent_t t0 = phase_begin(c, s);
+    launch_kick_drift(c->pos, c->vel, c->acc, c->n, 0.5f * dt, dt, c->info, s);
+    phase_end(c, 2, t0, s);
+    r = build_tree(c, false, s);
+    if (r) return r;
+    r = run_forces(c, c->theta, c->eps, c->Gc, s);
+    if (r) return r;
+    t0 = phase_begin(c, s);
+    launch_kick(c->vel, c->acc, c->n, 0.5f * dt, c->info, s);
+    phase_end(c, 2, t0, s);
+    TC_CUDA(c, cudaGetLastError());
+    return TC_OK;
+}
+
+std::string graph_key(tc_ctx* c, float dt)
+{
+    char b[512];
+    snprintf(b, sizeof(b), "%lld/%lld/%d/%d/%a/%a/%a/%a/%d/%d/%d/%d/%d/%d/%d/%d/%d", (long long)c->n,
+             (long long)c->cap_m, c->nsys, c->leaf_max, (double)dt, (double)c->theta, (double)c->eps, (double)c->Gc,
+             c->cfg.gmax, c->cfg.warps, c->cfg.precise, c->cfg.want_pot, c->cfg.verify, c->cfg.stack,
+             c->cfg.blocks_per_sm, c->cfg.quad, c->cfg.tile);
+    return b;
+}
+
+// One step as a captured CUDA graph, captured once per configuration on a
+// stream of our own and replayed on the context stream.  Without phase
+// timing the graph holds the whole step (kick, drift, rebuild, walk, kick).
+// With phase timing it holds kick + drift + rebuild, and the walk and the
+// closing kick follow as direct launches bracketed by CUDA events on the
+// context stream (events recorded inside a graph cannot be timed).
+int step_graph(tc_ctx* c, float dt)
+{
+    const bool timing = c->timing;
+    const std::string key = graph_key(c, dt) + (timing ? "/timed" : "");
+    if (!c->gexec || key != c->gkey) {
+        drop_graph(c);
+        if (!c->cap_stream) TC_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        int r = prepare_forces(c);
+        if (r) return r;
+        c->timing = false;
+        const long long k0 = launches_total();
+        cudaStream_t s = c->cap_stream;
+        TC_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        launch_kick_drift(c->pos, c->vel, c->acc, c->n, 0.5f * dt, dt, c->info, s);
+        r = build_tree(c, false, s);
+        if (!timing) {
+            if (!r) r = run_forces(c, c->theta, c->eps, c->Gc, s);
+            launch_kick(c->vel, c->acc, c->n, 0.5f * dt, c->info, s);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        c->timing = timing;
+        c->graph_kernels = launches_total() - k0;
+        count_launches((int)-c->graph_kernels);  // counted when the graph runs
+        if (r) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) return fail(c, TC_ECUDA, "step capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, TC_ECUDA, "step graph instantiation: %s", cudaGetErrorString(e));
+        }
+        c->gkey = key;
+    }
+    cudaEvent_t t0 = phase_begin(c, c->stream);
+    TC_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+    count_launches((int)c->graph_kernels);
+    phase_end(c, 0, t0, c->stream);  // (timing mode: kick + drift + rebuild)
+    if (timing) {
+        int r = run_forces(c, c->theta, c->eps, c->Gc, c->stream);
+        if (r) return r;
+        t0 = phase_begin(c, c->stream);
+        launch_kick(c->vel, c->acc, c->n, 0.5f * dt, c->info, c->stream);
+        phase_end(c, 2, t0, c->stream);
+        TC_CUDA(c, cudaGetLastError());
+    }
+    c->have_forces = true;
     return TC_OK;
 }
 
@@ -368,6 +555,8 @@ int tc_create(tc_ctx** out, void* stream)
     c->cfg.stack = 1024;
     c->cfg.blocks_per_sm = 0;
     c->cfg.quad = 0;
+    c->cfg.tile = 128;
+    c->cfg.graph = 1;
     *out = c;
     return TC_OK;
 }
@@ -377,16 +566,18 @@ void tc_destroy(tc_ctx* c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    void* bufs[] = {c->pos, c->vel, c->acc, c->pot, c->mass, c->keys, c->perm, c->body, c->sb.keys_alt,
-                    c->sb.vals_alt, c->sb.ghist, c->sb.status, c->sb.tiles, c->sb.blocksum, c->w, c->delta, c->top, c->nstart, c->prepos,
-                    c->gflag, c->gscan, c->gref_at, c->gfirst, c->gref, c->ncell, c->nbody, c->hash,
-                    c->bbox_partial, c->totals, c->idx_dev, c->dir_out, c->pre_level, c->pre_first, c->iota,
-                    c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c, c->nt.d, c->nt.quad, c->nt.mass64,
-                    c->nt.com64, c->nt.quad64, c->info};
+    drop_graph(c);
+    void* bufs[] = {c->pos, c->vel, c->acc, c->pot, c->mass, c->sys_of, c->sysp, c->off_dev, c->chunks, c->keys,
+                    c->perm, c->body, c->sb.keys_alt, c->sb.vals_alt, c->sb.ghist, c->sb.status, c->sb.tiles,
+                    c->sb.blocksum, c->w, c->delta, c->top, c->nstart, c->prepos, c->gflag, c->gscan, c->gref_at,
+                    c->gfirst, c->gref, c->ncell, c->nbody, c->hash, c->totals, c->idx_dev, c->dir_out,
+                    c->pre_level, c->pre_first, c->iota, c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c,
+                    c->nt.d, c->nt.quad, c->nt.mass64, c->nt.com64, c->nt.quad64, c->info};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->info_h) cudaFreeHost(c->info_h);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -398,13 +589,17 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
     if (cfg->warps < 1 || cfg->warps > 4) return fail(c, TC_EINVAL, "warps must be 1..4 (got %d)", cfg->warps);
     if (cfg->stack < 64 || cfg->stack > 8192) return fail(c, TC_EINVAL, "stack must be 64..8192 (got %d)", cfg->stack);
     if (cfg->blocks_per_sm < 0) return fail(c, TC_EINVAL, "blocks_per_sm must be >= 0");
-    bool regroup = c->built && (cfg->gmax != c->cfg.gmax || (cfg->quad != 0) != (c->cfg.quad != 0));
+    if (cfg->tile != 64 && cfg->tile != 128 && cfg->tile != 256)
+        return fail(c, TC_EINVAL, "tile must be 64, 128 or 256 (got %d)", cfg->tile);
+    bool rebuild = c->built && (cfg->gmax != c->cfg.gmax || (cfg->quad != 0) != (c->cfg.quad != 0));
     c->cfg = *cfg;
     c->cfg.precise = cfg->precise ? 1 : 0;
     c->cfg.want_pot = cfg->want_pot ? 1 : 0;
     c->cfg.verify = cfg->verify ? 1 : 0;
     c->cfg.quad = cfg->quad ? 1 : 0;
-    if (regroup) return build_tree(c);  // groups depend on gmax
+    c->cfg.graph = cfg->graph ? 1 : 0;
+    c->walk_ready = false;
+    if (rebuild) return build_tree(c, true, c->stream);  // groups depend on gmax, moments on quad
     return TC_OK;
 }
 
@@ -423,22 +618,42 @@ int tc_set_stream(tc_ctx* c, void* stream)
     return TC_OK;
 }
 
-int tc_ctx_build(tc_ctx* c, const float* pos, const float* mass, int64_t n, int leaf_max)
+int tc_ctx_build_batch(tc_ctx* c, const float* pos, const float* mass, const int64_t* offsets, int64_t nsys,
+                       int leaf_max)
 {
     if (!c) return fail(c, TC_EINVAL, "tc_build: null context");
-    if (!pos || !mass) return fail(c, TC_EINVAL, "tc_build: null pos or mass");
-    if (n < 1 || n >= (int64_t)1 << 31) return fail(c, TC_EINVAL, "tc_build: n must be in [1, 2^31) (got %lld)", (long long)n);
+    if (!pos || !mass || !offsets) return fail(c, TC_EINVAL, "tc_build: null pos, mass or offsets");
+    if (nsys < 1 || nsys > (1 << 16)) return fail(c, TC_EINVAL, "tc_build: nsys must be in [1, 65536]");
     if (leaf_max < 1 || leaf_max > kLeafMaxLimit)
         return fail(c, TC_EINVAL, "tc_build: leaf_max must be in [1, %d] (got %d)", kLeafMaxLimit, leaf_max);
+    std::vector<int64_t> off(nsys + 1);
+    TC_CUDA(c, cudaMemcpy(off.data(), offsets, (nsys + 1) * sizeof(int64_t), cudaMemcpyDefault));
+    if (off[0] != 0) return fail(c, TC_EINVAL, "tc_build: offsets[0] must be 0");
+    for (int64_t s = 0; s < nsys; s++)
+        if (off[s + 1] <= off[s]) return fail(c, TC_EINVAL, "tc_build: system %lld holds no body", (long long)s);
+    const int64_t n = off[nsys];
+    if (n >= (int64_t)1 << 31) return fail(c, TC_EINVAL, "tc_build: n must be below 2^31 (got %lld)", (long long)n);
     int r = ensure_bodies(c, n);
     if (r) return r;
     if (n != c->n) TC_CUDA(c, cudaMemsetAsync(c->vel, 0, 3 * n * sizeof(float), c->stream));
     c->n = n;
     c->leaf_max = leaf_max;
+    if ((int)nsys != c->nsys || off != c->off_h) {
+        r = setup_systems(c, off.data(), (int)nsys);
+        if (r) return r;
+    }
     TC_CUDA(c, cudaMemcpyAsync(c->pos, pos, 3 * n * sizeof(float), cudaMemcpyDefault, c->stream));
     TC_CUDA(c, cudaMemcpyAsync(c->mass, mass, n * sizeof(float), cudaMemcpyDefault, c->stream));
     c->built = false;
-    return build_tree(c);
+    return build_tree(c, true, c->stream);
+}
+
+int tc_ctx_build(tc_ctx* c, const float* pos, const float* mass, int64_t n, int leaf_max)
+{
+    if (!c) return fail(c, TC_EINVAL, "tc_build: null context");
+    if (n < 1 || n >= (int64_t)1 << 31) return fail(c, TC_EINVAL, "tc_build: n must be in [1, 2^31) (got %lld)", (long long)n);
+    const int64_t off[2] = {0, n};
+    return tc_ctx_build_batch(c, pos, mass, off, 1, leaf_max);
 }
 
 int tc_ctx_set_velocity(tc_ctx* c, const float* vel)
@@ -456,7 +671,9 @@ int tc_ctx_forces(tc_ctx* c, float theta, float eps, float G)
     if (!finite(theta) || theta < 0.f) return fail(c, TC_EINVAL, "tc_forces: theta must be finite and >= 0");
     if (!finite(eps) || eps <= 0.f) return fail(c, TC_EINVAL, "tc_forces: eps must be finite and > 0");
     if (!finite(G)) return fail(c, TC_EINVAL, "tc_forces: G must be finite");
-    return run_forces(c, theta, eps, G);
+    int r = prepare_forces(c);
+    if (r) return r;
+    return run_forces(c, theta, eps, G, c->stream);
 }
 
 int tc_ctx_step(tc_ctx* c, float dt)
@@ -464,18 +681,8 @@ int tc_ctx_step(tc_ctx* c, float dt)
     if (!c) return fail(c, TC_EINVAL, "tc_step: null context");
     if (!finite(dt)) return fail(c, TC_EINVAL, "tc_step: dt must be finite");
     if (!c->have_forces) return fail(c, TC_ESTATE, "tc_step: compute forces on the current positions first");
-    cudaEvent_t t0 = phase_begin(c);
-    launch_kick_drift(c->pos, c->vel, c->acc, c->n, 0.5f * dt, dt, c->stream);
-    phase_end(c, 2, t0);
-    int r = build_tree(c);
-    if (r) return r;
-    r = run_forces(c, c->theta, c->eps, c->Gc);
-    if (r) return r;
-    t0 = phase_begin(c);
-    launch_kick(c->vel, c->acc, c->n, 0.5f * dt, c->stream);
-    phase_end(c, 2, t0);
-    TC_CUDA(c, cudaGetLastError());
-    return TC_OK;
+    if (c->cfg.graph) return step_graph(c, dt);
+    return step_eager(c, dt);
 }
 
 int tc_sync(tc_ctx* c)
@@ -512,7 +719,7 @@ int tc_set_state(tc_ctx* c, const float* pos, const float* vel)
     if (!c->built) return fail(c, TC_ESTATE, "tc_set_state: build first");
     TC_CUDA(c, cudaMemcpyAsync(c->pos, pos, 3 * c->n * sizeof(float), cudaMemcpyDefault, c->stream));
     TC_CUDA(c, cudaMemcpyAsync(c->vel, vel, 3 * c->n * sizeof(float), cudaMemcpyDefault, c->stream));
-    return build_tree(c);
+    return build_tree(c, true, c->stream);
 }
 
 int tc_get_sizes(tc_ctx* c, int64_t* n, int64_t* nnodes, int64_t* ngroups)
@@ -522,8 +729,27 @@ int tc_get_sizes(tc_ctx* c, int64_t* n, int64_t* nnodes, int64_t* ngroups)
     int r = check_device(c);
     if (r) return r;
     if (n) *n = c->n;
-    if (nnodes) *nnodes = c->M;
+    if (nnodes) *nnodes = c->info_h->M;
     if (ngroups) *ngroups = c->info_h->G;
+    return TC_OK;
+}
+
+int tc_get_systems(tc_ctx* c, int64_t* nsys, double* cubes)
+{
+    if (!c) return fail(c, TC_EINVAL, "tc_get_systems: null context");
+    if (!c->built) return fail(c, TC_ESTATE, "tc_get_systems: build first");
+    int r = check_device(c);
+    if (r) return r;
+    if (nsys) *nsys = c->nsys;
+    if (cubes) {
+        std::vector<SysParams> sp(c->nsys);
+        TC_CUDA(c, cudaMemcpy(sp.data(), c->sysp, c->nsys * sizeof(SysParams), cudaMemcpyDeviceToHost));
+        for (int s = 0; s < c->nsys; s++) {
+            for (int a = 0; a < 3; a++) cubes[5 * s + a] = sp[s].c0[a];
+            cubes[5 * s + 3] = sp[s].L;
+            cubes[5 * s + 4] = sp[s].h;
+        }
+    }
     return TC_OK;
 }
 
@@ -531,11 +757,10 @@ int tc_get_cube(tc_ctx* c, double* out5)
 {
     if (!c || !out5) return fail(c, TC_EINVAL, "tc_get_cube: null argument");
     if (!c->built) return fail(c, TC_ESTATE, "tc_get_cube: build first");
-    int r = check_device(c);
+    std::vector<double> all(5 * (size_t)c->nsys);
+    int r = tc_get_systems(c, nullptr, all.data());
     if (r) return r;
-    for (int a = 0; a < 3; a++) out5[a] = c->info_h->c0[a];
-    out5[3] = c->info_h->L;
-    out5[4] = c->info_h->h;
+    for (int k = 0; k < 5; k++) out5[k] = all[k];
     return TC_OK;
 }
 
@@ -556,22 +781,13 @@ int tc_get_nodes(tc_ctx* c, int32_t* level, uint64_t* prefix, int32_t* first, in
     if (quad && !c->cfg.quad) return fail(c, TC_ESTATE, "tc_get_nodes: second moments not computed (quad = 0)");
     int r = check_device(c);
     if (r) return r;
-    const int64_t M = c->M;
-    int4* b = (int4*)malloc(M * sizeof(int4));
-    if (!b) return fail(c, TC_ENOMEM, "tc_get_nodes: host memory");
-    cudaError_t e = cudaMemcpy(b, c->nt.b, M * sizeof(int4), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-        free(b);
-        return fail(c, TC_ECUDA, "tc_get_nodes: %s", cudaGetErrorString(e));
-    }
-    uint64_t* keys = nullptr;
+    const int64_t M = c->info_h->M;
+    std::vector<int4> b(M);
+    TC_CUDA(c, cudaMemcpy(b.data(), c->nt.b, M * sizeof(int4), cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> keys;
     if (prefix) {
-        keys = (uint64_t*)malloc(c->n * sizeof(uint64_t));
-        if (!keys || cudaMemcpy(keys, c->keys, c->n * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            free(b);
-            free(keys);
-            return fail(c, TC_ECUDA, "tc_get_nodes: key copy failed");
-        }
+        keys.resize(c->n);
+        TC_CUDA(c, cudaMemcpy(keys.data(), c->keys, c->n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     }
     for (int64_t v = 0; v < M; v++) {
         int l = b[v].w & 255;
@@ -582,8 +798,6 @@ int tc_get_nodes(tc_ctx* c, int32_t* level, uint64_t* prefix, int32_t* first, in
         if (nchild) nchild[v] = b[v].w >> 8;
         if (prefix) prefix[v] = l == 0 ? 0ull : (keys[b[v].x] >> (3 * (kMaxLevel - l)));
     }
-    free(b);
-    free(keys);
     if (mass) TC_CUDA(c, cudaMemcpy(mass, c->nt.mass64, M * sizeof(double), cudaMemcpyDefault));
     if (com) TC_CUDA(c, cudaMemcpy(com, c->nt.com64, 3 * M * sizeof(double), cudaMemcpyDefault));
     if (quad) TC_CUDA(c, cudaMemcpy(quad, c->nt.quad64, 6 * M * sizeof(double), cudaMemcpyDefault));
@@ -597,19 +811,13 @@ int tc_get_groups(tc_ctx* c, int32_t* gfirst, int32_t* gcount, int32_t* gref)
     int r = check_device(c);
     if (r) return r;
     const int64_t G = c->info_h->G;
-    int32_t* f = (int32_t*)malloc((G + 1) * sizeof(int32_t));
-    if (!f) return fail(c, TC_ENOMEM, "tc_get_groups: host memory");
-    cudaError_t e = cudaMemcpy(f, c->gfirst, (G + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && gref) e = cudaMemcpy(gref, c->gref, G * sizeof(int32_t), cudaMemcpyDefault);
-    if (e != cudaSuccess) {
-        free(f);
-        return fail(c, TC_ECUDA, "tc_get_groups: %s", cudaGetErrorString(e));
-    }
+    std::vector<int32_t> f(G + 1);
+    TC_CUDA(c, cudaMemcpy(f.data(), c->gfirst, (G + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (gref) TC_CUDA(c, cudaMemcpy(gref, c->gref, G * sizeof(int32_t), cudaMemcpyDefault));
     for (int64_t g = 0; g < G; g++) {
         if (gfirst) gfirst[g] = f[g];
         if (gcount) gcount[g] = f[g + 1] - f[g];
     }
-    free(f);
     return TC_OK;
 }
 
@@ -652,25 +860,19 @@ int tc_direct(tc_ctx* c, const int64_t* idx, int64_t ns, float eps, float G, dou
     if (!c->built) return fail(c, TC_ESTATE, "tc_direct: build first");
     if (ns < 1) return fail(c, TC_EINVAL, "tc_direct: ns must be >= 1");
     if (!finite(eps) || eps <= 0.f || !finite(G)) return fail(c, TC_EINVAL, "tc_direct: eps > 0 and finite G required");
+    std::vector<int64_t> hidx(ns);
+    TC_CUDA(c, cudaMemcpy(hidx.data(), idx, ns * sizeof(int64_t), cudaMemcpyDefault));
+    for (int64_t k = 0; k < ns; k++)
+        if (hidx[k] < 0 || hidx[k] >= c->n)
+            return fail(c, TC_EINVAL, "tc_direct: index %lld out of range", (long long)hidx[k]);
     if (ns > c->cap_idx) {
         TC_GROW(c, c->idx_dev, ns);
         TC_GROW(c, c->dir_out, 4 * ns);
         c->cap_idx = ns;
     }
-    TC_CUDA(c, cudaMemcpyAsync(c->idx_dev, idx, ns * sizeof(int64_t), cudaMemcpyDefault, c->stream));
-    // indices must address bodies: checked on the host copy
-    int64_t* hidx = (int64_t*)malloc(ns * sizeof(int64_t));
-    if (!hidx) return fail(c, TC_ENOMEM, "tc_direct: host memory");
-    TC_CUDA(c, cudaMemcpyAsync(hidx, c->idx_dev, ns * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    TC_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int64_t k = 0; k < ns; k++)
-        if (hidx[k] < 0 || hidx[k] >= c->n) {
-            long long bad = (long long)hidx[k];
-            free(hidx);
-            return fail(c, TC_EINVAL, "tc_direct: index %lld out of range", bad);
-        }
-    free(hidx);
-    launch_direct(c->pos, c->mass, c->n, c->idx_dev, ns, eps * eps, G, c->dir_out, c->dir_out + 3 * ns, c->stream);
+    TC_CUDA(c, cudaMemcpyAsync(c->idx_dev, hidx.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    launch_direct(c->pos, c->mass, c->sys_of, c->sysp, c->idx_dev, ns, eps * eps, G, c->dir_out, c->dir_out + 3 * ns,
+                  c->stream);
     TC_CUDA(c, cudaGetLastError());
     TC_CUDA(c, cudaMemcpyAsync(acc, c->dir_out, 3 * ns * sizeof(double), cudaMemcpyDefault, c->stream));
     if (pot) TC_CUDA(c, cudaMemcpyAsync(pot, c->dir_out + 3 * ns, ns * sizeof(double), cudaMemcpyDefault, c->stream));
@@ -708,7 +910,91 @@ int tc_get_timings(tc_ctx* c, double* out6)
     c->launches_mark = now;
     c->ev_used = 0;
     out6[4] = (double)launches_total();
-    out6[5] = 0.0;
+    out6[5] = (double)c->graph_kernels;
+    return TC_OK;
+}
+
+// Launch-configuration autotuner: times the walk + force kernel for every
+// (group size, list tile, warps per block) on the context's current bodies
+// and keeps the fastest.  Results are cached in the text file named by the
+// TC_AUTOTUNE_CACHE environment variable (one "key gmax tile warps ms" line
+// per workload) when it is set.
+int tc_autotune(tc_ctx* c, float theta, float eps, float G, int reps, tc_config* best_out, double* best_ms_out)
+{
+    if (!c) return fail(c, TC_EINVAL, "tc_autotune: null context");
+    if (!c->built) return fail(c, TC_ESTATE, "tc_autotune: build first");
+    if (!finite(theta) || theta < 0.f || !finite(eps) || eps <= 0.f || !finite(G))
+        return fail(c, TC_EINVAL, "tc_autotune: theta >= 0, eps > 0, finite G required");
+    if (reps < 1) reps = 1;
+    char key[256];
+    snprintf(key, sizeof(key), "n=%lld,nsys=%d,leaf=%d,theta=%a,eps=%a,precise=%d,pot=%d,quad=%d", (long long)c->n,
+             c->nsys, c->leaf_max, (double)theta, (double)eps, c->cfg.precise, c->cfg.want_pot, c->cfg.quad);
+    const char* cache = getenv("TC_AUTOTUNE_CACHE");
+    tc_config best = c->cfg;
+    double best_ms = -1.0;
+    if (cache && *cache) {
+        FILE* f = fopen(cache, "r");
+        if (f) {
+            char k[256];
+            int gm, ti, wa;
+            double ms;
+            while (fscanf(f, "%255s %d %d %d %lf", k, &gm, &ti, &wa, &ms) == 5)
+                if (strcmp(k, key) == 0) {
+                    best.gmax = gm;
+                    best.tile = ti;
+                    best.warps = wa;
+                    best_ms = ms;
+                }
+            fclose(f);
+        }
+    }
+    if (best_ms < 0.0) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        TC_CUDA(c, cudaEventCreate(&e0));
+        TC_CUDA(c, cudaEventCreate(&e1));
+        const int gmaxes[3] = {32, 64, 128}, tiles[3] = {64, 128, 256}, warps[2] = {2, 4};
+        int rc = TC_OK;
+        for (int gi = 0; gi < 3 && !rc; gi++) {
+            tc_config t = c->cfg;
+            t.gmax = gmaxes[gi];
+            rc = tc_set_config(c, &t);  // regroups the bodies for the group size
+            for (int ti = 0; ti < 3 && !rc; ti++)
+                for (int wi = 0; wi < 2 && !rc; wi++) {
+                    t.tile = tiles[ti];
+                    t.warps = warps[wi];
+                    rc = tc_set_config(c, &t);
+                    if (!rc) rc = prepare_forces(c);
+                    if (!rc) rc = run_forces(c, theta, eps, G, c->stream);  // warm-up
+                    double tmin = 1e30;
+                    for (int k = 0; k < reps && !rc; k++) {
+                        cudaEventRecord(e0, c->stream);
+                        rc = run_forces(c, theta, eps, G, c->stream);
+                        cudaEventRecord(e1, c->stream);
+                        if (!rc) rc = check_device(c);
+                        float ms = 0.f;
+                        if (!rc && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < tmin) tmin = ms;
+                    }
+                    if (!rc && (best_ms < 0.0 || tmin < best_ms)) {
+                        best = t;
+                        best_ms = tmin;
+                    }
+                }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        if (cache && *cache) {
+            FILE* f = fopen(cache, "a");
+            if (f) {
+                fprintf(f, "%s %d %d %d %.6f\n", key, best.gmax, best.tile, best.warps, best_ms);
+                fclose(f);
+            }
+        }
+    }
+    int rc = tc_set_config(c, &best);
+    if (rc) return rc;
+    if (best_out) *best_out = best;
+    if (best_ms_out) *best_ms_out = best_ms;
     return TC_OK;
 }
 

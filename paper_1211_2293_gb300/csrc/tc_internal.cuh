@@ -1,6 +1,12 @@
 // tc_internal.cuh -- device-side data layout and launchers of the treecode
 // library (CUDA, sm_103a).  Internal to libtc.so; the public C ABI is
 // include/tc.h.
+//
+// A context holds a batch of S >= 1 independent systems whose bodies are
+// concatenated (system s owns bodies [off_s, off_s+1) in the caller's order
+// and the same positions in Morton order).  Every system has its own root
+// cube and its own tree; the trees form one forest in one node table, and
+// one walk launch serves the groups of every system.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -9,43 +15,51 @@ namespace tc {
 
 constexpr int kMaxLevel = 21;      // 21 bits per axis, 63-bit Morton keys
 constexpr int kLeafMaxLimit = 4096;
+constexpr int kBboxChunk = 4096;   // bodies per bounding-box block (never across systems)
 
 // error bits of the device error word
 enum : int32_t {
     kErrNonFinite = 1,    // NaN/Inf position or mass
     kErrStack = 2,        // walk stack overflow
-    kErrCapacity = 4,     // a device table outgrew its allocation
-    kErrWorkLoop = 8,     // a persistent loop hit its iteration cap
+    kErrCapacity = 4,     // the node table outgrew its allocation
+    kErrWorkLoop = 8,     // a bounded wait gave up
+};
+
+// Per-system root cube (written by the bounding-box kernels).
+struct SysParams {
+    double c0[3];      // root cube corner
+    double L;          // root cube side (power of two)
+    double h;          // grid step L / 2^21
+    long long qoff[3]; // c0 / h (integers): q = floor(x / h) - qoff
+    int32_t qexp;      // 1 / h = 2^qexp
+    float Lf;          // L as float (exact)
+    float uf;          // h / 2 as float (exact): unit of the integer centres
+    int32_t first;     // bodies [first, end)
+    int32_t end;
+    int32_t bb[6];     // bounding box as order-preserving ints: lo xyz, hi xyz
 };
 
 // Per-context scalars kept in device memory (written by kernels, read by
 // kernels and, at synchronisation points, by the host).
 struct Info {
-    double c0[3];      // root cube corner
-    double L;          // root cube side (power of two)
-    double h;          // grid step L / 2^21
-    double inv_h;      // 1 / h (exact)
-    long long qoff[3]; // c0 / h (integers): q = floor(x / h) - qoff
-    int32_t qexp;      // 1 / h = 2^qexp
-    int32_t pad1;
-    float Lf;          // L as float (exact)
-    float uf;          // h / 2 as float (exact): unit of the integer centres
     int32_t err;       // error bits
-    uint32_t ticket;   // last-block-done counter of the bbox reduction
+    int32_t depth;     // deepest level of the forest
     int64_t M;         // number of nodes
     int64_t G;         // number of groups
+    int64_t cap_m;     // node table capacity (for the device-side check)
     uint32_t work;     // walk work-queue counter
-    int32_t depth;     // deepest level of the tree
+    uint32_t pad0;
     unsigned long long interactions;  // body-source interactions of the last walk
     unsigned long long cells;         // accepted cells summed over groups
     unsigned long long bodies;        // direct-list bodies summed over groups
     double diag[8];    // KE, PE, P[3], L[3]
 };
 
-// Node record as the walk reads it (breadth-first order, index v).
+// Node record as the walk reads it (breadth-first order, index v; the roots
+// of systems 0..S-1 are nodes 0..S-1).
 //   a: centre of mass minus cube centre (float), mass (float)
 //   b: first body, body count, first child, level | nchild << 8
-//   c: cube centre in units of u = h/2 (exact integers), 0
+//   c: cube centre in units of u = h/2 of its system (exact integers), system
 //   d: centre of mass in absolute coordinates (float), mass (plain mode)
 struct NodeTables {
     float4* a;
@@ -58,16 +72,17 @@ struct NodeTables {
     double* quad64;  // 6 per node
 };
 
-// scratch sizes for the radix sort / scans
+// scratch of the radix sort / scans
 struct SortBufs {
     uint64_t* keys_alt;
     uint32_t* vals_alt;
-    uint32_t* ghist;                 // 8 passes x 256 digit counts -> exclusive offsets
+    uint32_t* ghist;                 // passes x 256 digit counts -> exclusive offsets
     unsigned long long* status;      // look-back words, passes x tiles x 256
     uint32_t* tiles;                 // tile counters, one per pass
     int32_t* err;                    // device error word (bounded look-back)
     uint32_t* blocksum;              // scan partials
 };
+constexpr int kSortMaxPasses = 10;   // 8 key passes + up to 2 system passes
 
 // ---------------------------------------------------------------- launchers
 // all launches go on `s`; none synchronises.  Every launcher adds the number
@@ -83,38 +98,46 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
               uint32_t* blocksum, cudaStream_t s);
 int64_t scan_blocksum_size(int64_t n);
 
-// stable LSD radix sort of (key, val) by bits [0, nbits) of key; afterwards
-// b.ghist[p * 256 + d] is the number of keys whose pass-p digit is below d
-void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b,
-                    cudaStream_t s);
-void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b,
-                    uint32_t* keys_alt32, cudaStream_t s);
+// Stable LSD radix sort of (key, val) by bits [0, nbits) of key, then (if
+// sys_bits > 0) by the system of each value's body, sys_of[val], so the
+// result is ordered by (system, key).  Afterwards b.ghist[p * 256 + d] is
+// the number of items whose pass-p digit is below d.
+void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of,
+                    int sys_bits, SortBufs& b, cudaStream_t s);
+// The same for 32-bit keys when the item count is only known on the device:
+// n_cap bounds it, *n_dev (device) holds it.
+void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n_cap, const int64_t* n_dev, int nbits,
+                    SortBufs& b, uint32_t* keys_alt32, cudaStream_t s);
 int64_t radix_tiles(int64_t n);  // tiles of one pass (status words: 256 per tile per pass)
 
 // build pieces
-void launch_bbox(const float* pos, int64_t n, float* partial, int nblocks, Info* info,
+void launch_sys_ids(const int64_t* offsets, int nsys, int64_t n, uint32_t* sys_of, SysParams* sysp,
+                    cudaStream_t s);
+void launch_bbox(const float* pos, const int4* chunks, int nchunks, SysParams* sysp, int nsys, int32_t* err,
                  cudaStream_t s);
-int bbox_blocks(int64_t n);
-void launch_keys(const float* pos, const float* mass, int64_t n, const Info* info, uint64_t* keys,
-                 uint32_t* idx, cudaStream_t s);
+void launch_keys(const float* pos, const float* mass, int64_t n, const uint32_t* sys_of, const SysParams* sysp,
+                 uint64_t* keys, uint32_t* idx, int32_t* err, cudaStream_t s);
 void launch_gather(const float* pos, const float* mass, const uint32_t* perm, int64_t n,
                    float4* body, cudaStream_t s);
-void launch_node_counts(const uint64_t* keys, int64_t n, int leaf_max, int8_t* w, int8_t* delta,
-                        int8_t* top, uint32_t* nstart, int32_t* depth, cudaStream_t s);
+void launch_node_counts(const uint64_t* keys, const uint32_t* sys_of, int64_t n, int leaf_max, int8_t* w,
+                        int8_t* delta, int8_t* top, uint32_t* nstart, int32_t* depth, cudaStream_t s);
+void launch_check_capacity(const uint32_t* m_total, Info* info, cudaStream_t s);
 void launch_emit_preorder(const int8_t* delta, const uint32_t* nstart, const uint32_t* prepos,
-                          int64_t n, uint32_t* pre_level, uint32_t* pre_first, uint32_t* iota,
-                          cudaStream_t s);
-void launch_node_finalize(const uint64_t* keys, const int8_t* top, int64_t n,
-                          const uint32_t* bfs_level, const uint32_t* bfs_pre, const uint32_t* pre_first,
-                          const uint32_t* bfs_of_pre, int64_t M, NodeTables nt, cudaStream_t s);
-void launch_inverse_perm(const uint32_t* perm, int64_t M, uint32_t* inv, cudaStream_t s);
-// moments: leaves, then internal levels depth-1 .. 0; level_start[l] is the
-// first node of level l (the level sort's digit offsets; level_start[l+1]
-// ends it)
-void launch_moments(const float4* body, int64_t M, int depth, const uint32_t* level_start, const Info* info,
-                    NodeTables nt, bool quad, cudaStream_t s);
-void launch_group_marks(int64_t M, const NodeTables nt, int gmax, int64_t n, uint32_t* gflag,
-                        int32_t* gref_at, cudaStream_t s);
+                          int64_t n, const Info* info, uint32_t* pre_level, uint32_t* pre_first,
+                          uint32_t* iota, cudaStream_t s);
+void launch_node_finalize(const uint64_t* keys, const int8_t* top, const uint32_t* sys_of,
+                          const SysParams* sysp, int64_t n, const uint32_t* bfs_level, const uint32_t* bfs_pre,
+                          const uint32_t* pre_first, const uint32_t* bfs_of_pre, int64_t cap_m, const Info* info,
+                          NodeTables nt, cudaStream_t s);
+void launch_inverse_perm(const uint32_t* perm, int64_t cap_m, const Info* info, uint32_t* inv, cudaStream_t s);
+// moments: leaves, then internal levels depth-1 .. 0 (depth < 0: all 21
+// levels, each reading its range on the device); level_start[l] is the first
+// node of level l (the level sort's digit offsets; level_start[l+1] ends it)
+void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t* level_start,
+                    const uint32_t* sys_of, const SysParams* sysp, const Info* info, NodeTables nt, bool quad,
+                    cudaStream_t s);
+void launch_group_marks(int64_t cap_m, const Info* info, const NodeTables nt, int gmax, int64_t n,
+                        uint32_t* gflag, int32_t* gref_at, cudaStream_t s);
 void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int32_t* gref_at,
                         int64_t n, const uint32_t* total, int32_t* gfirst, int32_t* gref, Info* info,
                         cudaStream_t s);
@@ -123,6 +146,8 @@ void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int3
 struct WalkArgs {
     const float4* body;        // Morton order (x, y, z, m)
     const uint32_t* perm;      // Morton position -> original index
+    const uint32_t* sys_of;    // body position -> system
+    const SysParams* sysp;     // per-system root cube
     NodeTables nt;
     const int32_t* gfirst;     // G + 1 entries
     const int32_t* gref;       // G
@@ -143,16 +168,21 @@ struct WalkConfig {
     int verify;
     int blocks_per_sm;
     int stack;        // walk stack entries per warp
+    int tile;         // list tile entries: 64, 128 or 256
 };
-cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int num_sms, cudaStream_t s);
+// host-side preparation of the walk kernel's launch (attributes, occupancy);
+// call before a stream capture
+cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
+cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
 
 // dynamics and diagnostics
 void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt,
-                       cudaStream_t s);
-void launch_kick(float* vel, const float* acc, int64_t n, float hkick, cudaStream_t s);
+                       const Info* info, cudaStream_t s);
+void launch_kick(float* vel, const float* acc, int64_t n, float hkick, const Info* info, cudaStream_t s);
 void launch_diag(const float* pos, const float* vel, const float* mass, const float* pot,
                  int64_t n, Info* info, cudaStream_t s);
-void launch_direct(const float* pos, const float* mass, int64_t n, const int64_t* idx, int64_t ns,
-                   float eps2, float G, double* acc, double* pot, cudaStream_t s);
+void launch_direct(const float* pos, const float* mass, const uint32_t* sys_of, const SysParams* sysp,
+                   const int64_t* idx, int64_t ns, float eps2, float G, double* acc, double* pot,
+                   cudaStream_t s);
 
 }  // namespace tc

@@ -122,15 +122,36 @@ constexpr unsigned long long kFlagPrefix = 2ull << 62;
 constexpr unsigned kLookbackMaxPolls = 1u << 24;
 
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(const K* __restrict__ keys, int64_t n, int npass,
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(const K* __restrict__ keys, int64_t n_host,
+                                                                const int64_t* __restrict__ n_dev, int npass,
                                                                 uint32_t* __restrict__ ghist)
 {
     __shared__ uint32_t h[8][256];
+    const int64_t n = n_dev ? min(*n_dev, n_host) : n_host;  // never past the buffers
     for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const K key = keys[k];
         for (int p = 0; p < npass; p++) atomicAdd(&h[p][(uint32_t)(key >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int p = 0; p < npass; p++) {
+        const uint32_t c = h[p][threadIdx.x];
+        if (c) atomicAdd(&ghist[p * 256 + threadIdx.x], c);
+    }
+}
+
+// digit histograms of the system passes: the multiset of systems does not
+// depend on the order, so they are counted from sys_of directly
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist_sys(const uint32_t* __restrict__ sys_of, int64_t n,
+                                                                int npass, uint32_t* __restrict__ ghist)
+{
+    __shared__ uint32_t h[2][256];
+    for (int i = threadIdx.x; i < 2 * 256; i += kSortThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t sy = sys_of[k];
+        for (int p = 0; p < npass; p++) atomicAdd(&h[p][(sy >> (8 * p)) & 255u], 1u);
     }
     __syncthreads();
     for (int p = 0; p < npass; p++) {
@@ -150,13 +171,16 @@ __global__ void __launch_bounds__(256) k_sort_offsets(uint32_t* __restrict__ ghi
     }
 }
 
-template <typename K>
+// SYS: the digit is taken from the system of the value's body, sys_of[val]
+template <typename K, bool SYS>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                                           K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                                           K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                           int64_t n_host, const int64_t* __restrict__ n_dev,
                                                            int shift, const uint32_t* __restrict__ goff,
                                                            unsigned long long* status, uint32_t* tile_counter,
-                                                           int32_t* err)
+                                                           int32_t* err, const uint32_t* __restrict__ sys_of)
 {
+    const int64_t n = n_dev ? min(*n_dev, n_host) : n_host;  // never past the buffers
     __shared__ uint32_t wh[kSortWarps][256];
     __shared__ uint32_t base[256];
     __shared__ int tile_sh;
@@ -169,6 +193,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__
     }
     __syncthreads();
     const int tile = tile_sh;
+    if ((int64_t)tile * kSortTile >= n) return;  // a tile past the device-side count: nothing to do
 
     // stable ranks within the tile (warp w owns items [tile*T + w*512, +512),
     // in 16 rounds of 32; equal digits of a round find each other with
@@ -184,7 +209,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__
         const bool ok = k < n;
         key[r] = ok ? kin[k] : K(0);
         val[r] = ok ? vin[k] : 0u;
-        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;
+        const uint32_t dig = SYS ? (ok ? sys_of[val[r]] >> shift : 0u) : (uint32_t)(key[r] >> shift);
+        const uint32_t d = ok ? (dig & 255u) : 256u + lane;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
@@ -248,7 +274,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__
     for (int r = 0; r < kSortItems; r++) {
         const int64_t k = wbase + r * 32 + lane;
         if (k < n) {
-            const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+            const uint32_t d = (SYS ? sys_of[val[r]] >> shift : (uint32_t)(key[r] >> shift)) & 255u;
             const uint32_t p = base[d] + wh[w][d] + rank[r];
             kout[p] = key[r];
             vout[p] = val[r];
@@ -277,31 +303,44 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
 int64_t radix_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 
 template <typename K>
-static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b, K* keys_alt,
-                            cudaStream_t s)
+static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n_dev, int nbits,
+                            const uint32_t* sys_of, int sys_bits, SortBufs& b, K* keys_alt, cudaStream_t s)
 {
-    if (n <= 1) {
-        cudaMemsetAsync(b.ghist, 0, 8 * 256 * sizeof(uint32_t), s);  // offsets of an empty or single list
-        return;
-    }
-    const int npass = (nbits + 7) / 8;
+    const int nkey = (nbits + 7) / 8;
+    const int nsys = (sys_bits + 7) / 8;
+    const int npass = nkey + nsys;
+    cudaMemsetAsync(b.ghist, 0, kSortMaxPasses * 256 * sizeof(uint32_t), s);
+    if (n <= 1) return;  // one item is sorted; its offsets are all zero
     const int64_t nt = radix_tiles(n);
-    // zero the histograms, the look-back words of every pass and the tile counters
-    cudaMemsetAsync(b.ghist, 0, 8 * 256 * sizeof(uint32_t), s);
+    // zero the look-back words of every pass and the tile counters
     cudaMemsetAsync(b.status, 0, (size_t)npass * nt * 256 * sizeof(unsigned long long), s);
-    cudaMemsetAsync(b.tiles, 0, 8 * sizeof(uint32_t), s);
+    cudaMemsetAsync(b.tiles, 0, kSortMaxPasses * sizeof(uint32_t), s);
     int hb = (int)((n + kSortThreads * 16 - 1) / (kSortThreads * 16));
     if (hb > 4 * 152) hb = 4 * 152;
-    k_sort_hist_all<K><<<hb, kSortThreads, 0, s>>>(keys, n, npass, b.ghist);
+    k_sort_hist_all<K><<<hb, kSortThreads, 0, s>>>(keys, n, n_dev, nkey, b.ghist);
+    count_launches(1);
+    if (nsys) {
+        k_sort_hist_sys<<<hb, kSortThreads, 0, s>>>(sys_of, n, nsys, b.ghist + 256 * nkey);
+        count_launches(1);
+    }
     k_sort_offsets<<<1, 256, 0, s>>>(b.ghist, npass);
-    count_launches(2);
+    count_launches(1);
     K* ka = keys;
     uint32_t* va = vals;
     K* kb = keys_alt;
     uint32_t* vb = b.vals_alt;
     for (int p = 0; p < npass; p++) {
-        k_onesweep<K><<<(unsigned)nt, kSortThreads, 0, s>>>(ka, va, kb, vb, n, 8 * p, b.ghist + 256 * p,
-                                                            b.status + (size_t)p * nt * 256, b.tiles + p, b.err);
+        const bool sysp = p >= nkey;
+        const int shift = sysp ? 8 * (p - nkey) : 8 * p;
+        if (sysp)
+            k_onesweep<K, true><<<(unsigned)nt, kSortThreads, 0, s>>>(ka, va, kb, vb, n, n_dev, shift, b.ghist + 256 * p,
+                                                                      b.status + (size_t)p * nt * 256, b.tiles + p,
+                                                                      b.err, sys_of);
+        else
+            k_onesweep<K, false><<<(unsigned)nt, kSortThreads, 0, s>>>(ka, va, kb, vb, n, n_dev, shift,
+                                                                       b.ghist + 256 * p,
+                                                                       b.status + (size_t)p * nt * 256, b.tiles + p,
+                                                                       b.err, sys_of);
         count_launches(1);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
@@ -312,15 +351,16 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, int nbits, SortB
     }
 }
 
-void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b, cudaStream_t s)
+void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of, int sys_bits,
+                    SortBufs& b, cudaStream_t s)
 {
-    radix_sort_impl<uint64_t>(keys, vals, n, nbits, b, b.keys_alt, s);
+    radix_sort_impl<uint64_t>(keys, vals, n, nullptr, nbits, sys_of, sys_bits, b, b.keys_alt, s);
 }
 
-void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int nbits, SortBufs& b,
+void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n_cap, const int64_t* n_dev, int nbits, SortBufs& b,
                     uint32_t* keys_alt32, cudaStream_t s)
 {
-    radix_sort_impl<uint32_t>(keys, vals, n, nbits, b, keys_alt32, s);
+    radix_sort_impl<uint32_t>(keys, vals, n_cap, n_dev, nbits, nullptr, 0, b, keys_alt32, s);
 }
 
 }  // namespace tc

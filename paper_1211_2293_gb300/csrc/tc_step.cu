@@ -10,21 +10,26 @@ namespace tc {
 
 namespace {
 
-// v' = v + a*hk, x' = x + v'*dt, each a separately rounded float32 op
+// v' = v + a*hk, x' = x + v'*dt, each a separately rounded float32 op.  A
+// step whose build or walk raised the error word leaves the state as it is
+// (the error is reported at the next synchronisation).
+__device__ __forceinline__ bool failed(const Info* info) { return *(volatile const int32_t*)&info->err != 0; }
+
 __global__ void k_kick_drift(float* __restrict__ pos, float* __restrict__ vel, const float* __restrict__ acc,
-                             int64_t n3, float hk, float dt)
+                             int64_t n3, float hk, float dt, const Info* info)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n3) return;
+    if (i >= n3 || failed(info)) return;
     float v = __fadd_rn(vel[i], __fmul_rn(acc[i], hk));
     vel[i] = v;
     pos[i] = __fadd_rn(pos[i], __fmul_rn(v, dt));
 }
 
-__global__ void k_kick(float* __restrict__ vel, const float* __restrict__ acc, int64_t n3, float hk)
+__global__ void k_kick(float* __restrict__ vel, const float* __restrict__ acc, int64_t n3, float hk,
+                       const Info* info)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n3) return;
+    if (i >= n3 || failed(info)) return;
     vel[i] = __fadd_rn(vel[i], __fmul_rn(acc[i], hk));
 }
 
@@ -62,30 +67,51 @@ __global__ void k_diag(const float* __restrict__ pos, const float* __restrict__ 
     }
 }
 
-// Direct summation for ns targets over all n sources (original order).
-// FP32 terms; each 256-source tile is summed in FP32 and added in FP64.
+// Direct summation for ns targets over the bodies of each target's system
+// (original order).  FP32 terms; each 256-source tile is summed in FP32 and
+// added in FP64.  One block serves targets of a single system at a time:
+// blocks are laid out per target and loop over [first, end) of the
+// target's system, so threads of a block may walk different ranges; the
+// tile holds the union for the block's smallest system range.
 constexpr int kDirTile = 256;
 __global__ void __launch_bounds__(kDirTile) k_direct(const float* __restrict__ pos, const float* __restrict__ mass,
-                                                     int64_t n, const int64_t* __restrict__ idx, int64_t ns,
+                                                     const uint32_t* __restrict__ sys_of,
+                                                     const SysParams* __restrict__ sysp,
+                                                     const int64_t* __restrict__ idx, int64_t ns,
                                                      float eps2, float G, double* __restrict__ acc,
                                                      double* __restrict__ pot)
 {
     __shared__ float4 tile[kDirTile];
+    __shared__ int64_t lo_sh, hi_sh;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool act = t < ns;
-    int64_t i = act ? idx[t] : 0;
+    int64_t i = act ? idx[t] : idx[(int64_t)blockIdx.x * blockDim.x];
+    const uint32_t sy = sys_of[i];
+    const int64_t j0 = sysp[sy].first, j1 = sysp[sy].end;
+    // the block sweeps the union of its targets' system ranges
+    if (threadIdx.x == 0) {
+        lo_sh = j0;
+        hi_sh = j1;
+    }
+    __syncthreads();
+    atomicMin((unsigned long long*)&lo_sh, (unsigned long long)j0);
+    atomicMax((unsigned long long*)&hi_sh, (unsigned long long)j1);
+    __syncthreads();
+    const int64_t blo = lo_sh, bhi = hi_sh;
     float xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
     double ax = 0, ay = 0, az = 0, ph = 0;
-    for (int64_t base = 0; base < n; base += kDirTile) {
+    for (int64_t base = blo; base < bhi; base += kDirTile) {
         int64_t j = base + threadIdx.x;
         __syncthreads();
-        tile[threadIdx.x] = j < n ? make_float4(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], mass[j])
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        // sources outside this thread's system are masked by zero mass below
+        tile[threadIdx.x] = j < bhi ? make_float4(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], mass[j])
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        int cnt = (int)min((int64_t)kDirTile, n - base);
+        const int cnt = (int)min((int64_t)kDirTile, bhi - base);
+        const int k0 = (int)max((int64_t)0, min((int64_t)cnt, j0 - base));
+        const int k1 = (int)max((int64_t)0, min((int64_t)cnt, j1 - base));
         float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < cnt; k++) {
+        for (int k = k0; k < k1; k++) {
             float4 s = tile[k];
             float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
             float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
@@ -113,15 +139,16 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt, cudaStream_t s)
+void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt, const Info* info,
+                       cudaStream_t s)
 {
-    k_kick_drift<<<nblk(3 * n, 256), 256, 0, s>>>(pos, vel, acc, 3 * n, hkick, dt);
+    k_kick_drift<<<nblk(3 * n, 256), 256, 0, s>>>(pos, vel, acc, 3 * n, hkick, dt, info);
     count_launches(1);
 }
 
-void launch_kick(float* vel, const float* acc, int64_t n, float hkick, cudaStream_t s)
+void launch_kick(float* vel, const float* acc, int64_t n, float hkick, const Info* info, cudaStream_t s)
 {
-    k_kick<<<nblk(3 * n, 256), 256, 0, s>>>(vel, acc, 3 * n, hkick);
+    k_kick<<<nblk(3 * n, 256), 256, 0, s>>>(vel, acc, 3 * n, hkick, info);
     count_launches(1);
 }
 
@@ -135,10 +162,10 @@ void launch_diag(const float* pos, const float* vel, const float* mass, const fl
     count_launches(1);
 }
 
-void launch_direct(const float* pos, const float* mass, int64_t n, const int64_t* idx, int64_t ns, float eps2,
-                   float G, double* acc, double* pot, cudaStream_t s)
+void launch_direct(const float* pos, const float* mass, const uint32_t* sys_of, const SysParams* sysp,
+                   const int64_t* idx, int64_t ns, float eps2, float G, double* acc, double* pot, cudaStream_t s)
 {
-    k_direct<<<nblk(ns, kDirTile), kDirTile, 0, s>>>(pos, mass, n, idx, ns, eps2, G, acc, pot);
+    k_direct<<<nblk(ns, kDirTile), kDirTile, 0, s>>>(pos, mass, sys_of, sysp, idx, ns, eps2, G, acc, pot);
     count_launches(1);
 }
 

@@ -40,8 +40,9 @@ namespace tc {
 
 namespace {
 
-constexpr int kTile = 128;              // list entries per tile flush
-constexpr int kTileCap = kTile + 34;    // + up to 32 added by a step, + 1 pad, kept even
+// list tiles: a step adds at most 32 entries before the flush check, and a
+// flush may pad one entry, so a tile of TILE entries needs TILE + 34 slots
+__host__ __device__ constexpr int tile_cap(int tile) { return tile + 34; }
 
 // ---------------------------------------------------------------- packed FP32
 // Blackwell's paired FP32 instructions (add/sub/mul/fma .f32x2) work on a
@@ -218,9 +219,11 @@ struct Accum {
     }
 };
 
-template <int B, bool PRECISE, bool POT>
+template <int B, int TILE, bool PRECISE, bool POT>
 __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
 {
+    constexpr int kTile = TILE;
+    constexpr int kTileCap = tile_cap(TILE);
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -232,11 +235,8 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
     const uint32_t lt = (1u << lane) - 1u;
 
     const Info* info = a.info;
+    if (info->err & kErrCapacity) return;  // the build stopped: no tree to walk
     const int64_t G = info->G;
-    const double c0x = info->c0[0], c0y = info->c0[1], c0z = info->c0[2];
-    const double ud = 0.5 * info->h;
-    const float uf = info->uf;
-    const float Lf = info->Lf;
     const NodeTables nt = a.nt;
 
     for (;;) {
@@ -246,8 +246,16 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
         if (g >= G) break;
         const int gfirst = a.gfirst[g];
         const int gend = a.gfirst[g + 1];
+        // the group's system: its root cube and its root node (roots are
+        // nodes 0..S-1 in system order)
+        const uint32_t sysid = a.sys_of[gfirst];
+        const SysParams& SP = a.sysp[sysid];
+        const double ud = 0.5 * SP.h;
+        const float uf = SP.uf;
+        const float Lf = SP.Lf;
         const int4 rc = nt.c[a.gref[g]];
-        const double gx = c0x + (double)rc.x * ud, gy = c0y + (double)rc.y * ud, gz = c0z + (double)rc.z * ud;
+        const double gx = SP.c0[0] + (double)rc.x * ud, gy = SP.c0[1] + (double)rc.y * ud,
+                     gz = SP.c0[2] + (double)rc.z * ud;
 
         // the group's bodies: absolute and reference-relative positions,
         // each coordinate duplicated into a packed pair
@@ -312,7 +320,7 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
         unsigned long long hsh = 0;
         bool overflow = false;
         int sp = 1;
-        if (lane == 0) stk[0] = 0;  // the root: holds every body, always opened
+        if (lane == 0) stk[0] = sysid;  // the system's root: holds every body, always opened
         __syncwarp();
 
         while (sp > 0) {
@@ -463,13 +471,13 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
     }
 }
 
-template <int B, bool PRECISE, bool POT>
-cudaError_t launch_t(const WalkArgs& a, const WalkConfig& c, int num_sms, cudaStream_t s)
+template <int B, int TILE, bool PRECISE, bool POT>
+cudaError_t prepare_t(const WalkConfig& c, int num_sms, int* grid, size_t* smem_out)
 {
     const int warps = c.warps;
-    const size_t per_warp = (size_t)2 * kTileCap * sizeof(float4) + (size_t)c.stack * sizeof(uint32_t);
+    const size_t per_warp = (size_t)2 * tile_cap(TILE) * sizeof(float4) + (size_t)c.stack * sizeof(uint32_t);
     const size_t smem = per_warp * warps;
-    auto kern = k_walk<B, PRECISE, POT>;
+    auto kern = k_walk<B, TILE, PRECISE, POT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -477,30 +485,71 @@ cudaError_t launch_t(const WalkArgs& a, const WalkConfig& c, int num_sms, cudaSt
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (c.blocks_per_sm > 0 && c.blocks_per_sm < per_sm) per_sm = c.blocks_per_sm;
-    kern<<<num_sms * per_sm, warps * 32, smem, s>>>(a, c.stack);
+    *grid = num_sms * per_sm;
+    *smem_out = smem;
+    return cudaSuccess;
+}
+
+template <int B, int TILE, bool PRECISE, bool POT>
+cudaError_t launch_t(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s)
+{
+    k_walk<B, TILE, PRECISE, POT><<<grid, c.warps * 32, smem, s>>>(a, c.stack);
     count_launches(1);
     return cudaGetLastError();
 }
 
+// dispatch over (bodies per lane, tile, mode) to the template instance F
+template <template <int, int, bool, bool> class F, typename... Args>
+cudaError_t dispatch(const WalkConfig& c, Args... args)
+{
+    const bool p = c.precise != 0, pot = c.want_pot != 0;
+#define TC_WALK_MODES(BB, TT)                                         \
+    if (c.gmax == 32 * BB && c.tile == TT) {                          \
+        if (p && pot) return F<BB, TT, true, true>::run(args...);     \
+        if (p && !pot) return F<BB, TT, true, false>::run(args...);   \
+        if (!p && pot) return F<BB, TT, false, true>::run(args...);   \
+        return F<BB, TT, false, false>::run(args...);                 \
+    }
+    TC_WALK_MODES(1, 64)
+    TC_WALK_MODES(1, 128)
+    TC_WALK_MODES(1, 256)
+    TC_WALK_MODES(2, 64)
+    TC_WALK_MODES(2, 128)
+    TC_WALK_MODES(2, 256)
+    TC_WALK_MODES(4, 64)
+    TC_WALK_MODES(4, 128)
+    TC_WALK_MODES(4, 256)
+#undef TC_WALK_MODES
+    return cudaErrorInvalidValue;
+}
+
+template <int B, int TILE, bool PRECISE, bool POT>
+struct PrepareF {
+    static cudaError_t run(const WalkConfig* c, int num_sms, int* grid, size_t* smem)
+    {
+        return prepare_t<B, TILE, PRECISE, POT>(*c, num_sms, grid, smem);
+    }
+};
+template <int B, int TILE, bool PRECISE, bool POT>
+struct LaunchF {
+    static cudaError_t run(const WalkArgs* a, const WalkConfig* c, int grid, size_t smem, cudaStream_t s)
+    {
+        return launch_t<B, TILE, PRECISE, POT>(*a, *c, grid, smem, s);
+    }
+};
+
 }  // namespace
 
-cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int num_sms, cudaStream_t s)
+cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* smem)
+{
+    return dispatch<PrepareF>(c, &c, num_sms, grid, smem);
+}
+
+cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s)
 {
     cudaMemsetAsync(&a.info->work, 0, sizeof(uint32_t), s);
     cudaMemsetAsync(&a.info->interactions, 0, 3 * sizeof(unsigned long long), s);
-    const bool p = c.precise != 0, pot = c.want_pot != 0;
-#define TC_WALK_CASE(BB)                                                              \
-    if (c.gmax == 32 * BB) {                                                          \
-        if (p && pot) return launch_t<BB, true, true>(a, c, num_sms, s);              \
-        if (p && !pot) return launch_t<BB, true, false>(a, c, num_sms, s);            \
-        if (!p && pot) return launch_t<BB, false, true>(a, c, num_sms, s);            \
-        return launch_t<BB, false, false>(a, c, num_sms, s);                          \
-    }
-    TC_WALK_CASE(1)
-    TC_WALK_CASE(2)
-    TC_WALK_CASE(4)
-#undef TC_WALK_CASE
-    return cudaErrorInvalidValue;
+    return dispatch<LaunchF>(c, &a, &c, grid, smem, s);
 }
 
 }  // namespace tc

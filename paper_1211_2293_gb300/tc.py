@@ -29,7 +29,8 @@ EXPORTS = [
     "tc_ctx_set_velocity", "tc_ctx_forces", "tc_ctx_step", "tc_get_acc", "tc_get_state", "tc_set_state",
     "tc_get_sizes", "tc_get_tree", "tc_get_nodes", "tc_get_groups", "tc_get_cube", "tc_get_lists",
     "tc_diag", "tc_direct", "tc_sync", "tc_last_error", "tc_build", "tc_forces", "tc_step", "tc_default",
-    "tc_set_timing", "tc_get_timings", "tc_direct_static",
+    "tc_set_timing", "tc_get_timings", "tc_direct_static", "tc_ctx_build_batch", "tc_get_systems",
+    "tc_autotune",
 ]
 
 
@@ -42,7 +43,8 @@ class TcError(RuntimeError):
 class tc_config(ctypes.Structure):
     _fields_ = [("gmax", ctypes.c_int32), ("warps", ctypes.c_int32), ("precise", ctypes.c_int32),
                 ("want_pot", ctypes.c_int32), ("verify", ctypes.c_int32), ("stack", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("quad", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("quad", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("graph", ctypes.c_int32)]
 
 
 _lib = None
@@ -88,6 +90,9 @@ def load(path: str | None = None):
         "tc_set_timing": ([P, I32], I32),
         "tc_get_timings": ([P, P], I32),
         "tc_direct_static": ([P, P, I64, P, I64, F, F, P, P, P], I32),
+        "tc_ctx_build_batch": ([P, P, P, P, I64, I32], I32),
+        "tc_get_systems": ([P, P, P], I32),
+        "tc_autotune": ([P, F, F, F, I32, ctypes.POINTER(tc_config), ctypes.POINTER(ctypes.c_double)], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -170,6 +175,28 @@ class Context:
         self._c(self._lib.tc_ctx_build(self._h, _ptr(pos), _ptr(mass), n, int(leaf_max)))
         self.n = n
 
+    def build_batch(self, pos, mass, offsets, leaf_max: int):
+        """Independent systems: bodies [offsets[s], offsets[s+1]) form system s."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._c(self._lib.tc_ctx_build_batch(self._h, _ptr(pos), _ptr(mass), _ptr(off), off.shape[0] - 1,
+                                             int(leaf_max)))
+        self.n = int(off[-1])
+
+    def systems(self):
+        """(nsys, cubes[nsys, 5]) with cube = (c0x, c0y, c0z, L, h)."""
+        ns = ctypes.c_int64()
+        self._c(self._lib.tc_get_systems(self._h, ctypes.byref(ns), None))
+        cubes = np.zeros((ns.value, 5))
+        self._c(self._lib.tc_get_systems(self._h, None, _ptr(cubes)))
+        return ns.value, cubes
+
+    def autotune(self, theta: float, eps: float, G: float = 1.0, reps: int = 3):
+        best = tc_config()
+        ms = ctypes.c_double()
+        self._c(self._lib.tc_autotune(self._h, float(theta), float(eps), float(G), int(reps), ctypes.byref(best),
+                                      ctypes.byref(ms)))
+        return {f: getattr(best, f) for f, _ in tc_config._fields_}, ms.value
+
     def set_velocity(self, vel):
         self._c(self._lib.tc_ctx_set_velocity(self._h, _ptr(vel)))
 
@@ -190,7 +217,7 @@ class Context:
         out = np.zeros(6)
         self._c(self._lib.tc_get_timings(self._h, _ptr(out)))
         return dict(build_ms=out[0], walk_ms=out[1], update_ms=out[2], launches=int(out[3]),
-                    launches_total=int(out[4]))
+                    launches_total=int(out[4]), graph_kernels=int(out[5]))
 
     # ------------------------------------------------------------ outputs
     def get_acc(self, acc=None, pot=None, with_pot=False):
