@@ -85,6 +85,14 @@ def _load():
     lib.or_kick.argtypes = [P, P, I64, D]
     lib.or_drift.argtypes = [P, P, I64, D]
     lib.or_diag.argtypes = [P, P, P, P, I64, P]
+    lib.or_mlp_features.argtypes = [P, I64, P, D, D, P]
+    lib.or_mlp_features.restype = None
+    lib.or_mlp_label.argtypes = [P, I64, P, D, D, P]
+    lib.or_mlp_label.restype = None
+    lib.or_mlp_forward.argtypes = [P, P, I64, P]
+    lib.or_mlp_forward.restype = None
+    lib.or_mlp_grad.argtypes = [P, P, P, I64, P]
+    lib.or_mlp_grad.restype = D
     _lib = lib
     return lib
 
@@ -212,6 +220,20 @@ class Tree:
     def test(self, group: int, node: int, theta: float) -> int:
         return int(self._lib.or_tree_test(self._h, int(group), int(node), float(theta)))
 
+    def mlp_features(self, node: int, x, eps: float, msys: float):
+        """13 features of (point x, cell node) for the learned correction."""
+        x = _f64(x)
+        f = np.zeros(13)
+        self._lib.or_mlp_features(self._h, int(node), _ptr(x), float(eps), float(msys), _ptr(f))
+        return f
+
+    def mlp_label(self, node: int, x, eps: float, G: float = 1.0):
+        """(a_exact - a_mono) r^2 / (G M) of cell node at point x."""
+        x = _f64(x)
+        t = np.zeros(3)
+        self._lib.or_mlp_label(self._h, int(node), _ptr(x), float(eps), float(G), _ptr(t))
+        return t
+
 
 def direct(pos, mass, eps, G=1.0, idx=None, want_pot=True):
     """Direct summation (exact result the treecode approximates), FP64.
@@ -276,3 +298,27 @@ def leapfrog_direct(pos, vel, mass, eps, G, dt, nsteps):
         acc, _ = direct(pos, mass, eps, G, want_pot=False)
         vel = kick(vel, acc, 0.5 * dt)
     return pos, vel
+
+
+MLP_NPARAM = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
+
+
+def mlp_forward(params, X):
+    """MLP 13 -> 64 -> 64 -> 3 (ReLU), FP64; params packed W1, b1, W2, b2, W3, b3."""
+    lib = _load()
+    params = _f64(params)
+    X = _f64(X).reshape(-1, 13)
+    Y = np.zeros((X.shape[0], 3))
+    lib.or_mlp_forward(_ptr(params), _ptr(X), X.shape[0], _ptr(Y))
+    return Y
+
+
+def mlp_grad(params, X, T):
+    """(loss, gradient) of the mean squared error, FP64."""
+    lib = _load()
+    params = _f64(params)
+    X = _f64(X).reshape(-1, 13)
+    T = _f64(T).reshape(-1, 3)
+    g = np.zeros(MLP_NPARAM)
+    loss = lib.or_mlp_grad(_ptr(params), _ptr(X), _ptr(T), X.shape[0], _ptr(g))
+    return float(loss), g

@@ -750,3 +750,123 @@ void or_diag(const double *pos, const double *vel, const double *mass, const dou
         out8[7] += m * (x[0] * v[1] - x[1] * v[0]);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned far-field correction: features, labels and the MLP.        */
+/* ------------------------------------------------------------------ */
+void or_mlp_features(const or_tree *t, int64_t v, const double *x, double eps, double msys, double *f)
+{
+    double s = cube_side(t, v);
+    double d[3], r2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        d[a] = t->com[3 * v + a] - x[a];
+        r2 += d[a] * d[a];
+    }
+    double r = sqrt(r2);
+    double M = t->mass[v];
+    for (int a = 0; a < 3; a++)
+        f[a] = d[a] / s;
+    f[3] = s / r;
+    f[4] = eps / s;
+    f[5] = log2((double)t->count[v]);
+    f[6] = M / msys;
+    for (int k = 0; k < 6; k++)
+        f[7 + k] = t->quad[6 * v + k] / (M * s * s);
+}
+
+void or_mlp_label(const or_tree *t, int64_t v, const double *x, double eps, double G, double *out)
+{
+    double eps2 = eps * eps, phi = 0.0, mag = 0.0;
+    double ae[3] = {0, 0, 0}, am[3] = {0, 0, 0};
+    for (int64_t j = t->first[v]; j < t->first[v] + t->count[v]; j++)
+        add_force(x, &t->xs[3 * j], t->ms[j], eps2, G, ae, &phi, &mag);
+    add_force(x, &t->com[3 * v], t->mass[v], eps2, G, am, &phi, &mag);
+    double r2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double d = t->com[3 * v + a] - x[a];
+        r2 += d * d;
+    }
+    for (int a = 0; a < 3; a++)
+        out[a] = (ae[a] - am[a]) * r2 / (G * t->mass[v]);
+}
+
+#define H 64
+static void mlp_layers(const double *p, const double *x, double *h1, double *h2, double *y)
+{
+    const double *W1 = p, *b1 = W1 + 13 * H, *W2 = b1 + H, *b2 = W2 + H * H, *W3 = b2 + H, *b3 = W3 + H * 3;
+    for (int j = 0; j < H; j++) {
+        double z = b1[j];
+        for (int i = 0; i < 13; i++)
+            z += x[i] * W1[i * H + j];
+        h1[j] = z > 0.0 ? z : 0.0;
+    }
+    for (int j = 0; j < H; j++) {
+        double z = b2[j];
+        for (int i = 0; i < H; i++)
+            z += h1[i] * W2[i * H + j];
+        h2[j] = z > 0.0 ? z : 0.0;
+    }
+    for (int k = 0; k < 3; k++) {
+        double z = b3[k];
+        for (int i = 0; i < H; i++)
+            z += h2[i] * W3[i * 3 + k];
+        y[k] = z;
+    }
+}
+
+void or_mlp_forward(const double *p, const double *X, int64_t n, double *Y)
+{
+    double h1[H], h2[H];
+    for (int64_t i = 0; i < n; i++)
+        mlp_layers(p, &X[13 * i], h1, h2, &Y[3 * i]);
+}
+
+double or_mlp_grad(const double *p, const double *X, const double *T, int64_t n, double *g)
+{
+    const double *W2 = p + 13 * H + H, *W3 = W2 + H * H + H;
+    double *gW1 = g, *gb1 = gW1 + 13 * H, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H, *gb3 = gW3 + H * 3;
+    memset(g, 0, OR_MLP_NPARAM * sizeof(double));
+    double loss = 0.0;
+    double h1[H], h2[H], y[3], dy[3], dh2[H], dh1[H];
+    for (int64_t i = 0; i < n; i++) {
+        const double *x = &X[13 * i];
+        mlp_layers(p, x, h1, h2, y);
+        for (int k = 0; k < 3; k++) {
+            double e = y[k] - T[3 * i + k];
+            loss += e * e;
+            dy[k] = 2.0 * e / (double)n;
+        }
+        /* output layer */
+        for (int k = 0; k < 3; k++) {
+            gb3[k] += dy[k];
+            for (int j = 0; j < H; j++)
+                gW3[j * 3 + k] += h2[j] * dy[k];
+        }
+        for (int j = 0; j < H; j++) {
+            double z = 0.0;
+            for (int k = 0; k < 3; k++)
+                z += W3[j * 3 + k] * dy[k];
+            dh2[j] = h2[j] > 0.0 ? z : 0.0;
+        }
+        /* second hidden layer */
+        for (int j = 0; j < H; j++) {
+            gb2[j] += dh2[j];
+            for (int i2 = 0; i2 < H; i2++)
+                gW2[i2 * H + j] += h1[i2] * dh2[j];
+        }
+        for (int i2 = 0; i2 < H; i2++) {
+            double z = 0.0;
+            for (int j = 0; j < H; j++)
+                z += W2[i2 * H + j] * dh2[j];
+            dh1[i2] = h1[i2] > 0.0 ? z : 0.0;
+        }
+        /* first hidden layer */
+        for (int j = 0; j < H; j++) {
+            gb1[j] += dh1[j];
+            for (int i1 = 0; i1 < 13; i1++)
+                gW1[i1 * H + j] += x[i1] * dh1[j];
+        }
+    }
+    return loss / (double)n;
+}
+#undef H

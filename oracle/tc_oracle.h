@@ -98,6 +98,25 @@ void or_drift(double *pos, const double *vel, int64_t n, double dt);
 void or_diag(const double *pos, const double *vel, const double *mass,
              const double *pot, int64_t n, double *out8);
 
+/* ---- Learned far-field correction (a growth of the method; no paper
+ * counterpart).  For a point x and a cell v (side s, mass M, centre of mass
+ * c, second moments Q about c, count bodies), with d = c - x and r = |d|:
+ *   features (13): d/s (3), s/r, eps/s, log2(count), M/msys, Q_ab/(M s^2)
+ *                  in the order xx, xy, xz, yy, yz, zz (6)
+ *   label (3):     (a_exact - a_mono) r^2 / (G M), where a_exact is the
+ *                  softened direct sum over the cell's bodies and a_mono the
+ *                  softened monopole G M d / (r^2 + eps^2)^(3/2).          */
+void or_mlp_features(const or_tree *t, int64_t node, const double *x, double eps, double msys, double *f13);
+void or_mlp_label(const or_tree *t, int64_t node, const double *x, double eps, double G, double *t3);
+
+/* MLP 13 -> 64 -> 64 -> 3 with ReLU after the hidden layers.  Parameters
+ * packed: W1[13][64], b1[64], W2[64][64], b2[64], W3[64][3], b3[3]
+ * (W[i][j] couples input i to output j), OR_MLP_NPARAM values. */
+#define OR_MLP_NPARAM (13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3)
+void or_mlp_forward(const double *params, const double *X, int64_t n, double *Y);
+/* loss L = (1/n) sum_i |Y_i - T_i|^2 and its gradient (packed like params) */
+double or_mlp_grad(const double *params, const double *X, const double *T, int64_t n, double *grad);
+
 #ifdef __cplusplus
 }
 #endif
