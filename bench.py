@@ -479,6 +479,105 @@ def run_precision(args, rank, world, local_rank):
     return 0
 
 
+def run_learned(args, rank, world, local_rank):
+    """Learned far-field correction against the plain walk on a Plummer
+    sphere.  Training: up to 2M body-cell pairs generated by the walk of a
+    2^20-body Plummer sphere (theta 0.9, band 0.5, exact labels from direct
+    sums over each cell's bodies), trained on the GPU (Adam, BF16 tensor
+    cores).  Evaluation on a fresh 2^22-body Plummer sphere (eps 1e-3, leaf
+    16): RMS relative force error against direct summation on 4096 sampled
+    bodies and the force phase's throughput (walk + force kernel, bodies/s),
+    for the plain walk at theta 0.5 and 0.9 and the learned walk at 0.9, and
+    for each path at the theta where its RMS error is 1e-3 (bisection)."""
+    import torch
+
+    from paper_1211_2293_gb300 import inputs, tc
+
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    tc.load()
+    eps, leaf, band, theta_tr = 1e-3, 16, 0.5, 0.9
+    n_tr, n_ev = 1 << 20, (args.n if args.n != N_DEFAULT else 1 << 22)
+    # ---- training pairs and training
+    p, _, m = inputs.plummer(n_tr, seed=100)
+    ctx = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
+    ctx.build(torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda(), leaf)
+    target = 2_000_000
+    Xs = ctx.mlp_pairs(theta_tr, eps, band, 0.05, 1, target)[0]
+    prob = min(1.0, 0.05 * target / max(1, len(Xs)))
+    t0 = time.perf_counter()
+    X, T, F, _, _ = ctx.mlp_pairs(theta_tr, eps, band, prob, 2, target)
+    pairs_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = ctx.mlp_train(X, T, ctx.mlp_weights(F), epochs=args.epochs, batch=1024, lr=2e-3, seed=3,
+                           band=band)
+    train_s = time.perf_counter() - t0
+    model, _ = ctx.mlp_get()
+    del ctx
+    # ---- evaluation system
+    p, _, m = inputs.plummer(n_ev, seed=101)
+    ctx = tc.Context(precise=1, quad=1, want_pot=0, verify=0, stack=4096)
+    ctx.build(torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda(), leaf)
+    ctx.mlp_set(model, band)
+    idx = inputs.sample_indices(n_ev, 4096, seed=1)
+    ad, _ = ctx.direct(idx, eps)
+
+    def measure(theta, learned, reps=5):
+        ctx.set_config(learned=int(learned))
+        ctx.forces(theta, eps)
+        ctx.sync()
+        a = ctx.get_acc()[idx].astype(np.float64)
+        rms = float(np.sqrt(np.mean(np.sum((a - ad) ** 2, 1) / np.sum(ad ** 2, 1))))
+        ctx.mlp_evals()
+        ctx.set_timing(True)
+        ctx.timings()
+        for _ in range(reps):
+            ctx.forces(theta, eps)
+        tim = ctx.timings()
+        ctx.set_timing(False)
+        walk_ms = tim["walk_ms"] / reps
+        st = ctx.lists(per_group=False)
+        ev = ctx.mlp_evals() / (reps + 0.0) if learned else 0
+        return {"theta": theta, "rms_err": rms, "walk_ms": walk_ms, "bodies_per_s": n_ev / (walk_ms / 1e3),
+                "interactions_per_body": st["interactions"] / n_ev, "mlp_evals_per_body": ev / n_ev}
+
+    def iso(learned, lo, hi, goal=1e-3, it=9):
+        """largest theta in [lo, hi] whose RMS error is <= goal (bisection)"""
+        if measure(lo, learned, reps=1)["rms_err"] > goal:
+            return None
+        for _ in range(it):
+            mid = 0.5 * (lo + hi)
+            if measure(mid, learned, reps=1)["rms_err"] <= goal:
+                lo = mid
+            else:
+                hi = mid
+        return measure(lo, learned)
+
+    res = {"plain_theta_0.5": measure(0.5, False), "plain_theta_0.9": measure(0.9, False),
+           "learned_theta_0.9": measure(0.9, True)}
+    iso_plain = iso(False, 0.35, 1.0)
+    iso_learned = iso(True, 0.35, 1.0)
+    value = iso_learned["bodies_per_s"] if iso_learned else None
+    line = {"metric": METRIC, "value": value, "unit": "bodies/s", "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32 force loop, bf16 tensor-core MLP (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"learned far-field correction: train on <= 2M body-cell pairs of a "
+                                   f"{n_tr}-body Plummer sphere (theta {theta_tr}, band {band}), evaluate on a "
+                                   f"fresh {n_ev}-body Plummer sphere, eps {eps}, leaf {leaf}, gmax 64; "
+                                   f"error vs direct sum on 4096 sampled bodies",
+                       "n_bodies": n_ev},
+            "value_is": "learned walk bodies/s at the largest theta with RMS error <= 1e-3",
+            "iso_accuracy_1e-3": {"plain": iso_plain, "learned": iso_learned,
+                                  "learned_over_plain": (iso_learned["bodies_per_s"] / iso_plain["bodies_per_s"]
+                                                         if iso_learned and iso_plain else None)},
+            "fixed_theta": res,
+            "training": {"pairs": int(len(X)), "pair_prob": prob, "pairs_s": pairs_s, "epochs": args.epochs,
+                         "batch": 1024, "lr": "2e-3, cosine decay", "loss_weights": "F^2 (acceleration error)",
+                         "train_s": train_s, "loss_first": float(losses[0]), "loss_last": float(losses[-1])}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,9 +589,11 @@ def main():
     ap.add_argument("--cpu-frac", type=int, default=8, help="oracle walks 1/cpu_frac of the groups")
     ap.add_argument("--ref-frac", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["uniform", "batch", "precision"], default="uniform",
+    ap.add_argument("--workload", choices=["uniform", "batch", "precision", "learned"], default="uniform",
                     help="uniform: the benchmark line; batch: 512 Plummer systems in one forest; "
-                         "precision: cell-relative vs plain float32 on two colliding Plummer spheres")
+                         "precision: cell-relative vs plain float32 on two colliding Plummer spheres; "
+                         "learned: the learned far-field correction against the plain walk")
+    ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--nsys", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -507,6 +608,8 @@ def main():
         return run_batch(args, rank, world, local_rank)
     if args.workload == "precision":
         return run_precision(args, rank, world, local_rank)
+    if args.workload == "learned":
+        return run_learned(args, rank, world, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -62,7 +62,10 @@ typedef struct tc_ctx tc_ctx;
  *             whole step -- kick, drift, rebuild, walk, kick -- with no host
  *             synchronisation; with phase timing on, the walk and the
  *             closing kick follow the graph as timed launches); 0: the same
- *             launches issued one by one                                  */
+ *             launches issued one by one
+ *   learned   1: add the learned far-field correction of tc_mlp_set /
+ *             tc_mlp_train to the walk (needs precise = 1, want_pot = 0,
+ *             quad = 1)                                                   */
 typedef struct {
     int32_t gmax;
     int32_t warps;
@@ -74,6 +77,7 @@ typedef struct {
     int32_t quad;
     int32_t tile;
     int32_t graph;
+    int32_t learned;
 } tc_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a
@@ -220,6 +224,64 @@ int tc_direct_static(const float *pos, const float *mass, int64_t n, const int64
  * names a file, results are looked up there first and appended after a
  * search (key: N, systems, leaf, theta, eps, precision, potential). */
 int tc_autotune(tc_ctx *ctx, float theta, float eps, float G, int reps, tc_config *best, double *best_ms);
+
+/* ---- Learned far-field correction (a growth of the method; the paper
+ * describes only the monopole walk).  An MLP 13 -> 64 -> 64 -> 3 (ReLU)
+ * predicts the error of a cell's monopole term at a point x.  With d =
+ * com - x, r = |d|, s the cell side and M its mass:
+ *   factor F = G M s^2 / r^4   (the scale of the quadrupole term)
+ *   label    = (a_exact - a_mono) / F
+ * where a_exact is the softened direct sum over the cell's bodies and a_mono
+ * the softened monopole; features (13): d/s (3), s/r, eps/s, log2(count),
+ * M / (system mass), Q_ab / (M s^2) (xx, xy, xz, yy, yz, zz), Q the second
+ * moments about the centre of mass.  BF16 operands on the tensor cores, FP32
+ * accumulation and master weights.  In the walk (learned = 1) every
+ * accepted cell holding two or more bodies with s >= band * d (d the
+ * distance from its centre of mass to the group's box) is evaluated once
+ * per group at the centre of the group's box, and F * label is added to
+ * every body of the group.
+ *
+ * A model is TC_MLP_NMODEL floats: the parameters W1[13][64], b1[64],
+ * W2[64][64], b2[64], W3[64][3], b3[3] (W[i][j]: input i to output j), then
+ * 13 feature means, 13 feature scales (features enter the network as
+ * (f - mean) * scale) and 3 output scales (label = output * scale).
+ * Array arguments may be host or device memory; the calls below return when
+ * their results are in place (they synchronise the context's stream). */
+#define TC_MLP_NPARAM (13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3)
+#define TC_MLP_NMODEL (TC_MLP_NPARAM + 13 + 13 + 3)
+/* Set the model (non-finite values: TC_EINVAL) and the band (>= 0). */
+int tc_mlp_set(tc_ctx *ctx, const float *model, float band);
+/* Read the model and band back (TC_ESTATE without a model); both nullable. */
+int tc_mlp_get(tc_ctx *ctx, float *model, float *band);
+/* labels (n x 3) of raw features X (n x 13) under the current model */
+int tc_mlp_forward(tc_ctx *ctx, const float *X, int64_t n, float *Y);
+/* loss (1/n) sum w_i |output_i - T_i / scale|^2 over the n pairs (W: n
+ * weights >= 0, NULL for all 1) and its gradient (TC_MLP_NPARAM, packed like
+ * the parameters) under the current model; grad and loss nullable */
+int tc_mlp_loss_grad(tc_ctx *ctx, const float *X, const float *T, const float *W, int64_t n, float *grad,
+                     float *loss);
+/* Train a fresh model (He initialisation from seed; feature means/scales
+ * and output RMS from the data) on n >= 16 pairs (X n x 13 features, T n x 3
+ * labels, W n loss weights or NULL) with Adam, learning rate lr decayed
+ * along a cosine over all steps, shuffled mini-batches of `batch` (>= 16),
+ * `epochs` passes; sets it as the context's model with the given band.
+ * losses[epochs] (nullable) gets the mean mini-batch loss of each pass.
+ * With W = F^2 (F from tc_mlp_pairs) the loss is the mean squared error of
+ * the corrected acceleration. */
+int tc_mlp_train(tc_ctx *ctx, const float *X, const float *T, const float *W, int64_t n, int epochs, int batch,
+                 float lr, uint64_t seed, float band, float *losses);
+/* Training pairs generated by the method itself: a walk at theta over the
+ * current bodies emits, with probability prob (seeded), every accepted cell
+ * holding two or more bodies with s >= band * d, paired with a body of the
+ * group; features at that body, the exact label and the factor F (G = 1).
+ * Outputs (any nullable except npairs): X (max_pairs x 13), T (max_pairs x
+ * 3), F (max_pairs), body (original index), node (breadth-first index);
+ * *npairs = pairs written (at most max_pairs).  Needs quad = 1; overwrites
+ * the context's accelerations. */
+int tc_mlp_pairs(tc_ctx *ctx, float theta, float eps, float band, float prob, uint64_t seed, int64_t max_pairs,
+                 float *X, float *T, float *F, int64_t *body, int64_t *node, int64_t *npairs);
+/* corrections evaluated by learned walks since the last call */
+int tc_mlp_evals(tc_ctx *ctx, int64_t *evals);
 
 /* Wait for the context's stream; report device errors. */
 int tc_sync(tc_ctx *ctx);

@@ -91,8 +91,12 @@ def _load():
     lib.or_mlp_label.restype = None
     lib.or_mlp_forward.argtypes = [P, P, I64, P]
     lib.or_mlp_forward.restype = None
-    lib.or_mlp_grad.argtypes = [P, P, P, I64, P]
+    lib.or_mlp_grad.argtypes = [P, P, P, P, I64, P]
+    lib.or_mlp_factor.argtypes = [P, I64, P, D]
+    lib.or_mlp_factor.restype = D
     lib.or_mlp_grad.restype = D
+    lib.or_tree_learned.argtypes = [P, D, D, D, D, P, P, I64, I64, P, P]
+    lib.or_tree_learned.restype = I64
     _lib = lib
     return lib
 
@@ -227,8 +231,31 @@ class Tree:
         self._lib.or_mlp_features(self._h, int(node), _ptr(x), float(eps), float(msys), _ptr(f))
         return f
 
+    def learned(self, theta, eps, band, params=None, maps=None, G=1.0, groups=None):
+        """Learned correction of the group walk (cells in the band evaluated
+        at the centre of the group's box).  params None: exact labels.
+        Returns (corr n x 3 original order, NaN outside the walked groups;
+        flag per group, -1 if not walked; number of evaluations)."""
+        if self.G == 0:
+            raise RuntimeError("make_groups first")
+        g0, g1 = (0, self.G) if groups is None else groups
+        corr = np.full((self.n, 3), np.nan)
+        flag = np.full(self.G, -1, dtype=np.int32)
+        p = None if params is None else _f64(params)
+        m = None if maps is None else _f64(maps)
+        if p is not None:
+            assert p.size == MLP_NPARAM and m is not None and m.size == 29
+        ev = self._lib.or_tree_learned(self._h, float(theta), float(eps), float(G), float(band),
+                                       None if p is None else _ptr(p), None if m is None else _ptr(m),
+                                       int(g0), int(g1), _ptr(corr), _ptr(flag))
+        return corr, flag, int(ev)
+
+    def mlp_factor(self, node: int, x, G: float = 1.0):
+        """G M s^2 / r^4 of cell node at point x (the acceleration unit of a label)."""
+        return float(self._lib.or_mlp_factor(self._h, int(node), _ptr(_f64(x)), float(G)))
+
     def mlp_label(self, node: int, x, eps: float, G: float = 1.0):
-        """(a_exact - a_mono) r^2 / (G M) of cell node at point x."""
+        """(a_exact - a_mono) / (G M s^2 / r^4) of cell node at point x."""
         x = _f64(x)
         t = np.zeros(3)
         self._lib.or_mlp_label(self._h, int(node), _ptr(x), float(eps), float(G), _ptr(t))
@@ -313,12 +340,13 @@ def mlp_forward(params, X):
     return Y
 
 
-def mlp_grad(params, X, T):
-    """(loss, gradient) of the mean squared error, FP64."""
+def mlp_grad(params, X, T, w=None):
+    """(loss, gradient) of the (weighted) mean squared error, FP64."""
     lib = _load()
     params = _f64(params)
     X = _f64(X).reshape(-1, 13)
     T = _f64(T).reshape(-1, 3)
+    w = None if w is None else _f64(w).reshape(-1)
     g = np.zeros(MLP_NPARAM)
-    loss = lib.or_mlp_grad(_ptr(params), _ptr(X), _ptr(T), X.shape[0], _ptr(g))
+    loss = lib.or_mlp_grad(_ptr(params), _ptr(X), _ptr(T), _ptr(w), X.shape[0], _ptr(g))
     return float(loss), g

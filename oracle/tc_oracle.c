@@ -774,6 +774,18 @@ void or_mlp_features(const or_tree *t, int64_t v, const double *x, double eps, d
         f[7 + k] = t->quad[6 * v + k] / (M * s * s);
 }
 
+/* G M s^2 / r^4: the acceleration unit of a label (the scaling of the
+ * quadrupole term, so that labels depend on direction and shape only). */
+double or_mlp_factor(const or_tree *t, int64_t v, const double *x, double G)
+{
+    double s = cube_side(t, v), r2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double d = t->com[3 * v + a] - x[a];
+        r2 += d * d;
+    }
+    return G * t->mass[v] * s * s / (r2 * r2);
+}
+
 void or_mlp_label(const or_tree *t, int64_t v, const double *x, double eps, double G, double *out)
 {
     double eps2 = eps * eps, phi = 0.0, mag = 0.0;
@@ -781,13 +793,9 @@ void or_mlp_label(const or_tree *t, int64_t v, const double *x, double eps, doub
     for (int64_t j = t->first[v]; j < t->first[v] + t->count[v]; j++)
         add_force(x, &t->xs[3 * j], t->ms[j], eps2, G, ae, &phi, &mag);
     add_force(x, &t->com[3 * v], t->mass[v], eps2, G, am, &phi, &mag);
-    double r2 = 0.0;
-    for (int a = 0; a < 3; a++) {
-        double d = t->com[3 * v + a] - x[a];
-        r2 += d * d;
-    }
+    double fac = or_mlp_factor(t, v, x, G);
     for (int a = 0; a < 3; a++)
-        out[a] = (ae[a] - am[a]) * r2 / (G * t->mass[v]);
+        out[a] = (ae[a] - am[a]) / fac;
 }
 
 #define H 64
@@ -821,7 +829,7 @@ void or_mlp_forward(const double *p, const double *X, int64_t n, double *Y)
         mlp_layers(p, &X[13 * i], h1, h2, &Y[3 * i]);
 }
 
-double or_mlp_grad(const double *p, const double *X, const double *T, int64_t n, double *g)
+double or_mlp_grad(const double *p, const double *X, const double *T, const double *w, int64_t n, double *g)
 {
     const double *W2 = p + 13 * H + H, *W3 = W2 + H * H + H;
     double *gW1 = g, *gb1 = gW1 + 13 * H, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H, *gb3 = gW3 + H * 3;
@@ -831,10 +839,11 @@ double or_mlp_grad(const double *p, const double *X, const double *T, int64_t n,
     for (int64_t i = 0; i < n; i++) {
         const double *x = &X[13 * i];
         mlp_layers(p, x, h1, h2, y);
+        double wi = w ? w[i] : 1.0;
         for (int k = 0; k < 3; k++) {
             double e = y[k] - T[3 * i + k];
-            loss += e * e;
-            dy[k] = 2.0 * e / (double)n;
+            loss += wi * e * e;
+            dy[k] = 2.0 * wi * e / (double)n;
         }
         /* output layer */
         for (int k = 0; k < 3; k++) {
@@ -870,3 +879,79 @@ double or_mlp_grad(const double *p, const double *X, const double *T, int64_t n,
     return loss / (double)n;
 }
 #undef H
+
+/* Learned correction of the group walk.  For each group: the accepted cells
+ * v of its walk holding two or more bodies with s >= band * d (d = distance
+ * from v's centre of mass to the group's box) are evaluated at the centre
+ * x_g of the group's box, and (G M_v / r^2) y is added to every body of the
+ * group (r = |com_v - x_g|).  y = network((f - mean) * scale) * yscale with
+ * maps = 13 means, 13 scales, 3 output scales; with params NULL, y is the
+ * exact label at x_g instead (what a perfect model would give). */
+int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, double band,
+                        const double *params, const double *maps, int64_t g_begin, int64_t g_end,
+                        double *corr, int32_t *flag)
+{
+    int64_t evals = 0;
+    walk_t w;
+    memset(&w, 0, sizeof(w));
+    double msys = t->mass[0];
+    for (int64_t g = g_begin; g < g_end; g++) {
+        w.gfirst = t->gfirst[g];
+        w.gcount = t->gcount[g];
+        w.theta = theta;
+        w.flagged = 0;
+        w.ncells = w.nleaves = w.nbody = 0;
+        for (int a = 0; a < 3; a++) {
+            w.lo[a] = INFINITY;
+            w.hi[a] = -INFINITY;
+        }
+        for (int64_t j = w.gfirst; j < w.gfirst + w.gcount; j++)
+            for (int a = 0; a < 3; a++) {
+                if (t->xs[3 * j + a] < w.lo[a])
+                    w.lo[a] = t->xs[3 * j + a];
+                if (t->xs[3 * j + a] > w.hi[a])
+                    w.hi[a] = t->xs[3 * j + a];
+            }
+        open_cube(t, &w, 0);
+        double xg[3], cg[3] = {0, 0, 0};
+        for (int a = 0; a < 3; a++)
+            xg[a] = 0.5 * (w.lo[a] + w.hi[a]);
+        for (int64_t k = 0; k < w.ncells; k++) {
+            int64_t v = w.cells[k];
+            if (t->count[v] < 2)
+                continue;
+            double s = cube_side(t, v);
+            double bd = band * dist_to_box(&t->com[3 * v], w.lo, w.hi);
+            if (fabs(s - bd) <= 1e-6 * bd)
+                w.flagged = 1;
+            if (s < bd)
+                continue;
+            double y[3];
+            if (params) {
+                double f[13], h1[64], h2[64];
+                or_mlp_features(t, v, xg, eps, msys, f);
+                for (int i = 0; i < 13; i++)
+                    f[i] = (f[i] - maps[i]) * maps[13 + i];
+                mlp_layers(params, f, h1, h2, y);
+                for (int a = 0; a < 3; a++)
+                    y[a] *= maps[26 + a];
+            } else {
+                or_mlp_label(t, v, xg, eps, G, y);
+            }
+            double fac = or_mlp_factor(t, v, xg, G);
+            for (int a = 0; a < 3; a++)
+                cg[a] += fac * y[a];
+            evals++;
+        }
+        for (int64_t i = w.gfirst; i < w.gfirst + w.gcount; i++) {
+            int64_t o = (int64_t)t->perm[i];
+            for (int a = 0; a < 3; a++)
+                corr[3 * o + a] = cg[a];
+        }
+        if (flag)
+            flag[g] = w.flagged;
+    }
+    free(w.cells);
+    free(w.leaves);
+    return evals;
+}

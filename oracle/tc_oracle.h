@@ -103,10 +103,12 @@ void or_diag(const double *pos, const double *vel, const double *mass,
  * c, second moments Q about c, count bodies), with d = c - x and r = |d|:
  *   features (13): d/s (3), s/r, eps/s, log2(count), M/msys, Q_ab/(M s^2)
  *                  in the order xx, xy, xz, yy, yz, zz (6)
- *   label (3):     (a_exact - a_mono) r^2 / (G M), where a_exact is the
+ *   factor:        G M s^2 / r^4, the scale of the quadrupole term
+ *   label (3):     (a_exact - a_mono) / factor, where a_exact is the
  *                  softened direct sum over the cell's bodies and a_mono the
  *                  softened monopole G M d / (r^2 + eps^2)^(3/2).          */
 void or_mlp_features(const or_tree *t, int64_t node, const double *x, double eps, double msys, double *f13);
+double or_mlp_factor(const or_tree *t, int64_t node, const double *x, double G);
 void or_mlp_label(const or_tree *t, int64_t node, const double *x, double eps, double G, double *t3);
 
 /* MLP 13 -> 64 -> 64 -> 3 with ReLU after the hidden layers.  Parameters
@@ -114,8 +116,23 @@ void or_mlp_label(const or_tree *t, int64_t node, const double *x, double eps, d
  * (W[i][j] couples input i to output j), OR_MLP_NPARAM values. */
 #define OR_MLP_NPARAM (13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3)
 void or_mlp_forward(const double *params, const double *X, int64_t n, double *Y);
-/* loss L = (1/n) sum_i |Y_i - T_i|^2 and its gradient (packed like params) */
-double or_mlp_grad(const double *params, const double *X, const double *T, int64_t n, double *grad);
+/* loss L = (1/n) sum_i w_i |Y_i - T_i|^2 (w NULL: all 1) and its gradient
+ * (packed like params) */
+double or_mlp_grad(const double *params, const double *X, const double *T, const double *w, int64_t n,
+                   double *grad);
+
+/* Learned correction of the group walk for groups [g_begin, g_end): every
+ * accepted cell of a group's walk with two or more bodies and s >= band * d
+ * (d = distance from its centre of mass to the group's box) is evaluated at
+ * the centre x_g of the group's box; factor(x_g) y (factor G M s^2 / r^4,
+ * r = |com - x_g|) is added to corr (n x 3, ORIGINAL order) for every body of the group.
+ *   y = network((f - maps[0..12]) * maps[13..25]) * maps[26..28]
+ * or, with params NULL, the exact label at x_g.  flag[g] (nullable) = 1 when
+ * an opening or band test of the group lay within 1e-6 relative of its
+ * bound.  Returns the number of cell evaluations. */
+int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, double band,
+                        const double *params, const double *maps, int64_t g_begin, int64_t g_end,
+                        double *corr, int32_t *flag);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["tc_sort.cu", "tc_build.cu", "tc_walk.cu", "tc_step.cu", "tc_api.cu", "tc_noalloc.cu"]
+SOURCES = ["tc_sort.cu", "tc_build.cu", "tc_walk.cu", "tc_step.cu", "tc_api.cu", "tc_noalloc.cu", "tc_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}"]

@@ -20,6 +20,8 @@
 
 using namespace tc;
 
+constexpr int kMlpNParamHost = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3;
+
 struct tc_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // a stream of our own to capture step graphs on
@@ -80,6 +82,28 @@ struct tc_ctx {
     size_t ev_used = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_phase[3];  // build, walk, update
     long long launches_mark = 0;
+
+    // learned far-field correction
+    float* mlp_params = nullptr;  // FP32 master parameters (packed)
+    float* mlp_maps = nullptr;    // feature means, feature scales, output scales
+    void* mlp_dev = nullptr;      // device model (BF16 weights)
+    float* mlp_m = nullptr;       // Adam moments
+    float* mlp_v = nullptr;
+    float* mlp_grad = nullptr;
+    float* mlp_loss = nullptr;
+    unsigned long long* mlp_evals = nullptr;
+    float* mlp_x = nullptr;       // scratch: features / normalised rows / outputs
+    float* mlp_t = nullptr;
+    float* mlp_w = nullptr;       // per-pair loss weights / label factors
+    int32_t* mlp_idx = nullptr;
+    int64_t mlp_cap = 0;
+    bool have_mlp = false;
+    float mlp_band = 0.5f;
+    std::vector<float> mlp_maps_h;  // host copy of the feature / output maps
+    int32_t* pair_b = nullptr;
+    int32_t* pair_v = nullptr;
+    unsigned long long* pair_n = nullptr;
+    int64_t pair_cap = 0;
 
     // the captured leapfrog step
     cudaGraphExec_t gexec = nullptr;
@@ -372,6 +396,7 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
                          c->cap_m, c->info, c->nt, s);
     // after the level sort, ghist[l] is the first breadth-first index of level l
     launch_moments(c->body, c->cap_m, depth, c->sb.ghist, c->sys_of, c->sysp, c->info, c->nt, c->cfg.quad != 0, s);
+    launch_sys_mass(c->sysp, c->nsys, c->nt, c->info, s);
     launch_group_marks(c->cap_m, c->info, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);
     launch_group_table(c->gflag, c->gscan, c->gref_at, n, &c->totals[1], c->gfirst, c->gref, c->info, s);
@@ -392,6 +417,7 @@ int prepare_forces(tc_ctx* c)
     wc.verify = c->cfg.verify;
     wc.blocks_per_sm = c->cfg.blocks_per_sm;
     wc.tile = c->cfg.tile;
+    wc.learned = c->cfg.learned && c->have_mlp;
     int64_t st = c->cfg.stack;
     if (c->cap_m < st) st = c->cap_m < 32 ? 32 : c->cap_m;  // a stack of M entries cannot overflow
     st = (st + 3) & ~(int64_t)3;                            // keeps every warp's tiles 16-byte aligned
@@ -424,6 +450,12 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
     a.eps2 = eps * eps;
     a.G = G;
     a.inv_eps = 1.0f / eps;
+    a.eps = eps;
+    if (c->walk_cfg.learned) {
+        a.mlp = c->mlp_dev;
+        a.band2 = c->mlp_band * c->mlp_band;
+        a.mlp_evals = c->mlp_evals;
+    }
     cudaEvent_t t0 = phase_begin(c, s);
     cudaError_t e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, s);
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk launch: %s", cudaGetErrorString(e));
@@ -572,7 +604,9 @@ void tc_destroy(tc_ctx* c)
                     c->sb.blocksum, c->w, c->delta, c->top, c->nstart, c->prepos, c->gflag, c->gscan, c->gref_at,
                     c->gfirst, c->gref, c->ncell, c->nbody, c->hash, c->totals, c->idx_dev, c->dir_out,
                     c->pre_level, c->pre_first, c->iota, c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c,
-                    c->nt.d, c->nt.quad, c->nt.mass64, c->nt.com64, c->nt.quad64, c->info};
+                    c->nt.d, c->nt.quad, c->nt.mass64, c->nt.com64, c->nt.quad64, c->info, c->mlp_params,
+                    c->mlp_maps, c->mlp_dev, c->mlp_m, c->mlp_v, c->mlp_grad, c->mlp_loss, c->mlp_evals, c->mlp_x,
+                    c->mlp_t, c->mlp_idx, c->pair_b, c->pair_v, c->pair_n};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->info_h) cudaFreeHost(c->info_h);
@@ -591,6 +625,8 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
     if (cfg->blocks_per_sm < 0) return fail(c, TC_EINVAL, "blocks_per_sm must be >= 0");
     if (cfg->tile != 64 && cfg->tile != 128 && cfg->tile != 256)
         return fail(c, TC_EINVAL, "tile must be 64, 128 or 256 (got %d)", cfg->tile);
+    if (cfg->learned && (!cfg->precise || cfg->want_pot || !cfg->quad))
+        return fail(c, TC_EINVAL, "learned = 1 needs precise = 1, want_pot = 0 and quad = 1");
     bool rebuild = c->built && (cfg->gmax != c->cfg.gmax || (cfg->quad != 0) != (c->cfg.quad != 0));
     c->cfg = *cfg;
     c->cfg.precise = cfg->precise ? 1 : 0;
@@ -598,6 +634,7 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
     c->cfg.verify = cfg->verify ? 1 : 0;
     c->cfg.quad = cfg->quad ? 1 : 0;
     c->cfg.graph = cfg->graph ? 1 : 0;
+    c->cfg.learned = cfg->learned ? 1 : 0;
     c->walk_ready = false;
     if (rebuild) return build_tree(c, true, c->stream);  // groups depend on gmax, moments on quad
     return TC_OK;
@@ -671,6 +708,7 @@ int tc_ctx_forces(tc_ctx* c, float theta, float eps, float G)
     if (!finite(theta) || theta < 0.f) return fail(c, TC_EINVAL, "tc_forces: theta must be finite and >= 0");
     if (!finite(eps) || eps <= 0.f) return fail(c, TC_EINVAL, "tc_forces: eps must be finite and > 0");
     if (!finite(G)) return fail(c, TC_EINVAL, "tc_forces: G must be finite");
+    if (c->cfg.learned && !c->have_mlp) return fail(c, TC_ESTATE, "tc_forces: learned = 1 but no model is set");
     int r = prepare_forces(c);
     if (r) return r;
     return run_forces(c, theta, eps, G, c->stream);
@@ -913,6 +951,372 @@ int tc_get_timings(tc_ctx* c, double* out6)
     out6[5] = (double)c->graph_kernels;
     return TC_OK;
 }
+}  // extern "C"
+
+// ---------------------------------------------------------------- learned correction
+namespace {
+
+// copies of the learned-correction calls run on the context's stream and are
+// waited for (host staging buffers are locals)
+#define TC_COPY(c, dst, src, bytes)                                                              \
+    do {                                                                                         \
+        TC_CUDA(c, cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyDefault, (c)->stream));       \
+        TC_CUDA(c, cudaStreamSynchronize((c)->stream));                                          \
+    } while (0)
+
+constexpr int kMlpNModel = kMlpNParamHost + 2 * 13 + 3;  // parameters + feature means, scales + output scales
+
+uint64_t smix(uint64_t& st)
+{
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double sunif(uint64_t& st) { return (double)(smix(st) >> 11) * (1.0 / 9007199254740992.0); }
+
+int mlp_alloc(tc_ctx* c)
+{
+    if (c->mlp_params) return TC_OK;
+    TC_GROW(c, c->mlp_params, kMlpNParamHost);
+    TC_GROW(c, c->mlp_maps, 32);
+    TC_GROW(c, *(char**)&c->mlp_dev, (int64_t)mlp_dev_size());
+    TC_GROW(c, c->mlp_m, kMlpNParamHost);
+    TC_GROW(c, c->mlp_v, kMlpNParamHost);
+    TC_GROW(c, c->mlp_grad, kMlpNParamHost);
+    TC_GROW(c, c->mlp_loss, 4);
+    TC_GROW(c, c->mlp_evals, 1);
+    TC_CUDA(c, cudaMemsetAsync(c->mlp_evals, 0, sizeof(*c->mlp_evals), c->stream));
+    return TC_OK;
+}
+
+int mlp_scratch(tc_ctx* c, int64_t n)
+{
+    if (n <= c->mlp_cap) return TC_OK;
+    TC_GROW(c, c->mlp_x, n * 16);
+    TC_GROW(c, c->mlp_t, n * 3);
+    TC_GROW(c, c->mlp_w, n);
+    TC_GROW(c, c->mlp_idx, n);
+    c->mlp_cap = n;
+    return TC_OK;
+}
+
+// raw features (n x 13, host or device) -> normalised padded rows on the host
+int mlp_rows_host(tc_ctx* c, const float* X, int64_t n, std::vector<float>& rows)
+{
+    std::vector<float> raw(n * 13);
+    TC_COPY(c, raw.data(), X, n * 13 * sizeof(float));
+    rows.assign(n * 16, 0.f);
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 13; k++)
+            rows[i * 16 + k] = (raw[i * 13 + k] - c->mlp_maps_h[k]) * c->mlp_maps_h[13 + k];
+    return TC_OK;
+}
+
+int mlp_targets_host(tc_ctx* c, const float* T, int64_t n, std::vector<float>& t)
+{
+    t.resize(n * 3);
+    TC_COPY(c, t.data(), T, n * 3 * sizeof(float));
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) t[i * 3 + k] /= c->mlp_maps_h[26 + k];
+    return TC_OK;
+}
+
+// per-pair weights (n, host or device; nullable) -> c->mlp_w; *wdev = the
+// device pointer to pass to the training kernel (null without weights)
+int mlp_weights(tc_ctx* c, const float* W, int64_t n, const float** wdev)
+{
+    *wdev = nullptr;
+    if (!W) return TC_OK;
+    std::vector<float> w(n);
+    TC_COPY(c, w.data(), W, n * sizeof(float));
+    for (float v : w)
+        if (!std::isfinite(v) || v < 0.f) return fail(c, TC_EINVAL, "mlp weights must be finite and >= 0");
+    TC_COPY(c, c->mlp_w, w.data(), n * sizeof(float));
+    *wdev = c->mlp_w;
+    return TC_OK;
+}
+
+int mlp_upload(tc_ctx* c, const float* model)
+{
+    int r = mlp_alloc(c);
+    if (r) return r;
+    std::vector<float> h(kMlpNModel);
+    TC_COPY(c, h.data(), model, kMlpNModel * sizeof(float));
+    for (float v : h)
+        if (!std::isfinite(v)) return fail(c, TC_EINVAL, "tc_mlp_set: non-finite model value");
+    c->mlp_maps_h.assign(h.begin() + kMlpNParamHost, h.end());
+    TC_COPY(c, c->mlp_params, h.data(), kMlpNParamHost * sizeof(float));
+    TC_COPY(c, c->mlp_maps, c->mlp_maps_h.data(), 29 * sizeof(float));
+    launch_mlp_pack(c->mlp_params, c->mlp_maps, c->mlp_dev, c->stream);
+    TC_CUDA(c, cudaGetLastError());
+    c->have_mlp = true;
+    c->walk_ready = false;
+    drop_graph(c);
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tc_mlp_set(tc_ctx* c, const float* model, float band)
+{
+    if (!c || !model) return fail(c, TC_EINVAL, "tc_mlp_set: null argument");
+    if (!finite(band) || band < 0.f) return fail(c, TC_EINVAL, "tc_mlp_set: band must be finite and >= 0");
+    c->mlp_band = band;
+    return mlp_upload(c, model);
+}
+
+int tc_mlp_get(tc_ctx* c, float* model, float* band)
+{
+    if (!c) return fail(c, TC_EINVAL, "tc_mlp_get: null context");
+    if (!c->have_mlp) return fail(c, TC_ESTATE, "tc_mlp_get: no model");
+    if (model) {
+        TC_COPY(c, model, c->mlp_params, kMlpNParamHost * sizeof(float));
+        TC_COPY(c, model + kMlpNParamHost, c->mlp_maps_h.data(), 29 * sizeof(float));
+    }
+    if (band) *band = c->mlp_band;
+    return TC_OK;
+}
+
+int tc_mlp_forward(tc_ctx* c, const float* X, int64_t n, float* Y)
+{
+    if (!c || !X || !Y) return fail(c, TC_EINVAL, "tc_mlp_forward: null argument");
+    if (!c->have_mlp) return fail(c, TC_ESTATE, "tc_mlp_forward: no model");
+    if (n < 1) return fail(c, TC_EINVAL, "tc_mlp_forward: n must be >= 1");
+    int r = mlp_scratch(c, n);
+    if (r) return r;
+    std::vector<float> rows;
+    r = mlp_rows_host(c, X, n, rows);
+    if (r) return r;
+    TC_CUDA(c, cudaMemcpyAsync(c->mlp_x, rows.data(), n * 16 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    launch_mlp_infer(c->mlp_x, n, c->mlp_dev, c->mlp_t, c->stream);
+    TC_CUDA(c, cudaGetLastError());
+    TC_CUDA(c, cudaMemcpyAsync(Y, c->mlp_t, n * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    return check_device(c);
+}
+
+int tc_mlp_loss_grad(tc_ctx* c, const float* X, const float* T, const float* W, int64_t n, float* grad, float* loss)
+{
+    if (!c || !X || !T) return fail(c, TC_EINVAL, "tc_mlp_loss_grad: null argument");
+    if (!c->have_mlp) return fail(c, TC_ESTATE, "tc_mlp_loss_grad: no model");
+    if (n < 1 || n >= (int64_t)1 << 31) return fail(c, TC_EINVAL, "tc_mlp_loss_grad: bad n");
+    int r = mlp_scratch(c, n);
+    if (r) return r;
+    std::vector<float> rows, t;
+    if ((r = mlp_rows_host(c, X, n, rows)) || (r = mlp_targets_host(c, T, n, t))) return r;
+    std::vector<int32_t> idx(n);
+    for (int64_t i = 0; i < n; i++) idx[i] = (int32_t)i;
+    TC_COPY(c, c->mlp_x, rows.data(), n * 16 * sizeof(float));
+    TC_COPY(c, c->mlp_t, t.data(), n * 3 * sizeof(float));
+    TC_COPY(c, c->mlp_idx, idx.data(), n * sizeof(int32_t));
+    const float* wdev = nullptr;
+    if ((r = mlp_weights(c, W, n, &wdev))) return r;
+    TC_CUDA(c, cudaMemsetAsync(c->mlp_grad, 0, kMlpNParamHost * sizeof(float), c->stream));
+    TC_CUDA(c, cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), c->stream));
+    int64_t blocks = (n + 63) / 64;
+    if (blocks > 2 * c->num_sms) blocks = 2 * c->num_sms;
+    cudaError_t e = launch_mlp_train(c->mlp_x, c->mlp_t, wdev, c->mlp_idx, (int)n, c->mlp_dev, c->mlp_grad,
+                                     c->mlp_loss, (int)blocks, c->stream);
+    if (e != cudaSuccess) return fail(c, TC_ECUDA, "mlp training kernel: %s", cudaGetErrorString(e));
+    if (grad) TC_CUDA(c, cudaMemcpyAsync(grad, c->mlp_grad, kMlpNParamHost * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (loss) TC_CUDA(c, cudaMemcpyAsync(loss, c->mlp_loss, sizeof(float), cudaMemcpyDefault, c->stream));
+    return check_device(c);
+}
+
+int tc_mlp_train(tc_ctx* c, const float* X, const float* T, const float* W, int64_t n, int epochs, int batch,
+                 float lr, uint64_t seed, float band, float* losses)
+{
+    if (!c || !X || !T) return fail(c, TC_EINVAL, "tc_mlp_train: null argument");
+    if (n < 16 || n >= (int64_t)1 << 31) return fail(c, TC_EINVAL, "tc_mlp_train: need 16 <= n < 2^31 pairs");
+    if (epochs < 1 || batch < 16 || !finite(lr) || lr <= 0.f || !finite(band) || band < 0.f)
+        return fail(c, TC_EINVAL, "tc_mlp_train: epochs >= 1, batch >= 16, lr > 0, band >= 0 required");
+    // normalisation: feature means and inverse standard deviations, output RMS
+    std::vector<float> raw(n * 13), tt(n * 3);
+    TC_COPY(c, raw.data(), X, n * 13 * sizeof(float));
+    TC_COPY(c, tt.data(), T, n * 3 * sizeof(float));
+    std::vector<float> model(kMlpNModel, 0.f);
+    for (int k = 0; k < 13; k++) {
+        double s1 = 0, s2 = 0;
+        for (int64_t i = 0; i < n; i++) {
+            s1 += raw[i * 13 + k];
+            s2 += (double)raw[i * 13 + k] * raw[i * 13 + k];
+        }
+        const double mean = s1 / n, var = std::max(0.0, s2 / n - mean * mean);
+        model[kMlpNParamHost + k] = (float)mean;
+        model[kMlpNParamHost + 13 + k] = var > 1e-30 ? (float)(1.0 / std::sqrt(var)) : 0.f;
+    }
+    for (int k = 0; k < 3; k++) {
+        double s2 = 0;
+        for (int64_t i = 0; i < n; i++) s2 += (double)tt[i * 3 + k] * tt[i * 3 + k];
+        const double rms = std::sqrt(s2 / n);
+        model[kMlpNParamHost + 26 + k] = rms > 1e-30 ? (float)rms : 1.f;
+    }
+    // He initialisation of the weights, zero biases
+    uint64_t st = seed;
+    auto normal = [&]() {
+        double u1 = std::max(sunif(st), 1e-300), u2 = sunif(st);
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    };
+    float* W1 = model.data();
+    float* W2 = W1 + 13 * 64 + 64;
+    float* W3 = W2 + 64 * 64 + 64;
+    for (int i = 0; i < 13 * 64; i++) W1[i] = (float)(normal() * std::sqrt(2.0 / 13));
+    for (int i = 0; i < 64 * 64; i++) W2[i] = (float)(normal() * std::sqrt(2.0 / 64));
+    for (int i = 0; i < 64 * 3; i++) W3[i] = (float)(normal() * std::sqrt(1.0 / 64));
+    c->mlp_band = band;
+    int r = mlp_upload(c, model.data());
+    if (r) return r;
+    r = mlp_scratch(c, n);
+    if (r) return r;
+    std::vector<float> rows, t;
+    if ((r = mlp_rows_host(c, X, n, rows)) || (r = mlp_targets_host(c, T, n, t))) return r;
+    TC_COPY(c, c->mlp_x, rows.data(), n * 16 * sizeof(float));
+    TC_COPY(c, c->mlp_t, t.data(), n * 3 * sizeof(float));
+    const float* wdev = nullptr;
+    if ((r = mlp_weights(c, W, n, &wdev))) return r;
+    TC_CUDA(c, cudaMemsetAsync(c->mlp_m, 0, kMlpNParamHost * sizeof(float), c->stream));
+    TC_CUDA(c, cudaMemsetAsync(c->mlp_v, 0, kMlpNParamHost * sizeof(float), c->stream));
+    std::vector<int32_t> idx(n);
+    for (int64_t i = 0; i < n; i++) idx[i] = (int32_t)i;
+    int step = 0;
+    const int64_t total_steps = (int64_t)epochs * ((n + batch - 1) / batch);
+    for (int ep = 0; ep < epochs; ep++) {
+        for (int64_t i = n - 1; i > 0; i--) {  // Fisher-Yates
+            const int64_t j = (int64_t)(smix(st) % (uint64_t)(i + 1));
+            std::swap(idx[i], idx[j]);
+        }
+        TC_CUDA(c, cudaMemcpyAsync(c->mlp_idx, idx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        TC_CUDA(c, cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), c->stream));
+        int nb = 0;
+        for (int64_t b0 = 0; b0 < n; b0 += batch) {
+            const int B = (int)std::min<int64_t>(batch, n - b0);
+            TC_CUDA(c, cudaMemsetAsync(c->mlp_grad, 0, kMlpNParamHost * sizeof(float), c->stream));
+            int64_t blocks = (B + 63) / 64;
+            if (blocks > 2 * c->num_sms) blocks = 2 * c->num_sms;
+            cudaError_t e = launch_mlp_train(c->mlp_x, c->mlp_t, wdev, c->mlp_idx + b0, B, c->mlp_dev,
+                                             c->mlp_grad, c->mlp_loss, (int)blocks, c->stream);
+            if (e != cudaSuccess) return fail(c, TC_ECUDA, "mlp training kernel: %s", cudaGetErrorString(e));
+            // cosine decay of the learning rate over all steps
+            const float lr_t = (float)(0.5 * lr * (1.0 + std::cos(3.141592653589793 * step / (double)total_steps)));
+            launch_adam(c->mlp_params, c->mlp_m, c->mlp_v, c->mlp_grad, kMlpNParamHost, lr_t, ++step, c->stream);
+            launch_mlp_pack(c->mlp_params, c->mlp_maps, c->mlp_dev, c->stream);
+            nb++;
+        }
+        // the host index buffer of this epoch must stay intact until it is copied
+        TC_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (losses) {
+            float l = 0.f;
+            TC_COPY(c, &l, c->mlp_loss, sizeof(float));
+            losses[ep] = l / (float)nb;
+        }
+    }
+    return check_device(c);
+}
+
+int tc_mlp_pairs(tc_ctx* c, float theta, float eps, float band, float prob, uint64_t seed, int64_t max_pairs, float* X,
+                 float* T, float* F, int64_t* body, int64_t* node, int64_t* npairs)
+{
+    if (!c || !npairs) return fail(c, TC_EINVAL, "tc_mlp_pairs: null argument");
+    if (!c->built) return fail(c, TC_ESTATE, "tc_mlp_pairs: build first");
+    if (!c->cfg.quad) return fail(c, TC_ESTATE, "tc_mlp_pairs: the features need quad = 1");
+    if (!finite(theta) || theta < 0.f || !finite(eps) || eps <= 0.f || !finite(band) || band < 0.f ||
+        !(prob > 0.f && prob <= 1.f) || max_pairs < 1)
+        return fail(c, TC_EINVAL, "tc_mlp_pairs: theta >= 0, eps > 0, band >= 0, 0 < prob <= 1, max_pairs >= 1");
+    if (max_pairs > c->pair_cap) {
+        TC_GROW(c, c->pair_b, max_pairs);
+        TC_GROW(c, c->pair_v, max_pairs);
+        TC_GROW(c, c->pair_n, 1);
+        c->pair_cap = max_pairs;
+    }
+    int r = mlp_scratch(c, max_pairs);
+    if (r) return r;
+    // a plain walk at theta that also emits pairs
+    tc_config keep = c->cfg;
+    c->cfg.learned = 0;
+    c->walk_ready = false;
+    r = prepare_forces(c);
+    c->cfg = keep;
+    if (r) return r;
+    WalkArgs a{};
+    a.body = c->body;
+    a.perm = c->perm;
+    a.sys_of = c->sys_of;
+    a.sysp = c->sysp;
+    a.nt = c->nt;
+    a.gfirst = c->gfirst;
+    a.gref = c->gref;
+    a.info = c->info;
+    a.acc = c->acc;
+    a.theta2 = theta * theta;
+    a.eps2 = eps * eps;
+    a.G = 1.f;
+    a.inv_eps = 1.f / eps;
+    a.eps = eps;
+    a.band2 = band * band;
+    a.pair_body = c->pair_b;
+    a.pair_node = c->pair_v;
+    a.pair_count = c->pair_n;
+    a.pair_cap = max_pairs;
+    a.pair_prob = prob;
+    a.pair_seed = seed;
+    TC_CUDA(c, cudaMemsetAsync(c->pair_n, 0, sizeof(unsigned long long), c->stream));
+    cudaError_t e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, c->stream);
+    c->walk_ready = false;
+    if (e != cudaSuccess) return fail(c, TC_ECUDA, "pair walk: %s", cudaGetErrorString(e));
+    c->have_forces = false;  // the accelerations of that walk use G = 1
+    unsigned long long cnt = 0;
+    r = check_device(c);
+    if (r) return r;
+    TC_COPY(c, &cnt, c->pair_n, sizeof(cnt));
+    const int64_t np = (int64_t)std::min<unsigned long long>(cnt, (unsigned long long)max_pairs);
+    *npairs = np;
+    if (np == 0) return TC_OK;
+    launch_pair_labels(c->pair_b, c->pair_v, np, c->body, c->sys_of, c->sysp, c->nt, eps, 1.f, c->mlp_x, c->mlp_t,
+                       c->mlp_w, c->stream);
+    TC_CUDA(c, cudaGetLastError());
+    r = check_device(c);
+    if (r) return r;
+    if (X) TC_COPY(c, X, c->mlp_x, np * 13 * sizeof(float));
+    if (T) TC_COPY(c, T, c->mlp_t, np * 3 * sizeof(float));
+    if (F) TC_COPY(c, F, c->mlp_w, np * sizeof(float));
+    if (body || node) {
+        std::vector<int32_t> pb(np), pv(np);
+        std::vector<uint32_t> perm(c->n);
+        TC_COPY(c, pb.data(), c->pair_b, np * sizeof(int32_t));
+        TC_COPY(c, pv.data(), c->pair_v, np * sizeof(int32_t));
+        TC_COPY(c, perm.data(), c->perm, c->n * sizeof(uint32_t));
+        std::vector<int64_t> ob(np), ov(np);
+        for (int64_t k = 0; k < np; k++) {
+            ob[k] = perm[pb[k]];
+            ov[k] = pv[k];
+        }
+        if (body) TC_COPY(c, body, ob.data(), np * sizeof(int64_t));
+        if (node) TC_COPY(c, node, ov.data(), np * sizeof(int64_t));
+    }
+    return TC_OK;
+}
+
+int tc_mlp_evals(tc_ctx* c, int64_t* evals)
+{
+    if (!c || !evals) return fail(c, TC_EINVAL, "tc_mlp_evals: null argument");
+    int r = mlp_alloc(c);
+    if (r) return r;
+    r = check_device(c);
+    if (r) return r;
+    unsigned long long v = 0;
+    TC_COPY(c, &v, c->mlp_evals, sizeof(v));
+    TC_CUDA(c, cudaMemsetAsync(c->mlp_evals, 0, sizeof(v), c->stream));
+    TC_CUDA(c, cudaStreamSynchronize(c->stream));
+    *evals = (int64_t)v;
+    return TC_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 
 // Launch-configuration autotuner: times the walk + force kernel for every
 // (group size, list tile, warps per block) on the context's current bodies

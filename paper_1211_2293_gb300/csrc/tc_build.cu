@@ -477,6 +477,14 @@ __global__ void k_level_moments(int lev, const uint32_t* __restrict__ level_star
     }
 }
 
+// total mass of each system: its root's mass
+__global__ void k_sys_mass(SysParams* __restrict__ sysp, int nsys, const NodeTables nt, const Info* info)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys || capacity_failed(info)) return;
+    sysp[s].msys = (float)nt.mass64[s];
+}
+
 // ------------------------------------------------------------------ groups
 // Bodies are walked in groups of at most gmax consecutive Morton-ordered
 // bodies of one system.  A cube holding more than gmax bodies is split into
@@ -643,6 +651,12 @@ void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t
         else k_level_moments<false><<<g, 128, 0, s>>>(lev, level_start, sysp, info, nt);
         count_launches(1);
     }
+}
+
+void launch_sys_mass(SysParams* sysp, int nsys, const NodeTables nt, const Info* info, cudaStream_t s)
+{
+    k_sys_mass<<<nblk(nsys, 128), 128, 0, s>>>(sysp, nsys, nt, info);
+    count_launches(1);
 }
 
 void launch_group_marks(int64_t cap_m, const Info* info, const NodeTables nt, int gmax, int64_t n, uint32_t* gflag,

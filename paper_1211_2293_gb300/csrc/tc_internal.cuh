@@ -37,6 +37,8 @@ struct SysParams {
     int32_t first;     // bodies [first, end)
     int32_t end;
     int32_t bb[6];     // bounding box as order-preserving ints: lo xyz, hi xyz
+    float msys;        // total mass (for the learned correction's features)
+    int32_t pad;
 };
 
 // Per-context scalars kept in device memory (written by kernels, read by
@@ -159,6 +161,19 @@ struct WalkArgs {
     unsigned long long* hash;
     float theta2, eps2, G;
     float inv_eps;             // 1/eps for the potential self term
+    // learned correction (null model: off)
+    const void* mlp;           // device MlpDev
+    float band2;               // accepted cells with s^2 >= band2 d^2 get a correction
+    float eps;
+    // training pairs (null: off): accepted cells with count >= 2 in the band
+    // are emitted with probability pair_prob as (a body of the group, cell)
+    int32_t* pair_body;
+    int32_t* pair_node;
+    unsigned long long* pair_count;
+    int64_t pair_cap;
+    float pair_prob;
+    unsigned long long pair_seed;
+    unsigned long long* mlp_evals;   // corrections evaluated (nullable)
 };
 struct WalkConfig {
     int gmax;         // 32, 64 or 128
@@ -169,11 +184,26 @@ struct WalkConfig {
     int blocks_per_sm;
     int stack;        // walk stack entries per warp
     int tile;         // list tile entries: 64, 128 or 256
+    int learned;      // 1: learned far-field correction (precise mode, no potential)
 };
 // host-side preparation of the walk kernel's launch (attributes, occupancy);
 // call before a stream capture
 cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
 cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
+
+// learned far-field correction (tc_mlp.cu)
+size_t mlp_dev_size();
+size_t mlp_train_smem();
+cudaError_t launch_mlp_train(const float* X, const float* T, const float* W, const int32_t* idx, int B,
+                             const void* model, float* grad, float* loss, int blocks, cudaStream_t s);
+void launch_mlp_pack(const float* params, const float* maps, void* model, cudaStream_t s);
+void launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, int t, cudaStream_t s);
+void launch_mlp_normalise(const float* raw, int64_t n, const void* model, float* X, cudaStream_t s);
+void launch_mlp_infer(const float* X, int64_t n, const void* model, float* Y, cudaStream_t s);
+void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const float4* body, const uint32_t* sys_of,
+                        const SysParams* sysp, NodeTables nt, float eps, float G, float* feat, float* lab,
+                        float* fac, cudaStream_t s);
+void launch_sys_mass(SysParams* sysp, int nsys, const NodeTables nt, const Info* info, cudaStream_t s);
 
 // dynamics and diagnostics
 void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt,

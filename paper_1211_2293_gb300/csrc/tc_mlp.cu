@@ -1,0 +1,471 @@
+// tc_mlp.cu -- the learned far-field correction's network on the GPU:
+// batch inference, training (forward, backward, Adam) and the exact labels
+// of training pairs.
+//
+// Network: 13 -> 64 -> 64 -> 3, ReLU after the hidden layers, BF16 operands
+// on the tensor cores (warp-level mma.sync m16n8k16), FP32 accumulation,
+// FP32 master weights.  Every kernel works on 16-row tiles, one warp each.
+//
+// Training loss: L = (1/B) sum_i w_i |y_i - t_i|^2 over a mini-batch of B
+// pairs (targets pre-divided by the output scale; w_i = 1 without weights).
+// Backward, per 16-row tile:
+//   dY = 2 w (Y - T) / B,  dW3 = H2^T dY,  dH2 = (dY W3^T) * [H2 > 0],
+//   dW2 = H1^T dH2,      dH1 = (dH2 W2^T) * [H1 > 0],   dW1 = X^T dH1,
+// biases by column sums; the transposed operands are staged in shared
+// memory.  Gradients are summed per block in shared memory, then added to
+// the global gradient; a separate kernel applies Adam.
+#include <cuda_bf16.h>
+
+#include "tc_internal.cuh"
+#include "tc_mma.cuh"
+
+namespace tc {
+
+namespace {
+
+constexpr int kTrainWarps = 4;
+
+// padded gradient layout in shared memory
+constexpr int kGW1 = 0;                                   // [16][64]
+constexpr int kGB1 = kGW1 + kMlpInPad * kMlpHid;          // [64]
+constexpr int kGW2 = kGB1 + kMlpHid;                      // [64][64]
+constexpr int kGB2 = kGW2 + kMlpHid * kMlpHid;            // [64]
+constexpr int kGW3 = kGB2 + kMlpHid;                      // [64][8]
+constexpr int kGB3 = kGW3 + kMlpHid * kMlpOutPad;         // [8]
+constexpr int kGPad = kGB3 + kMlpOutPad;
+
+// per-warp staging (BF16): X[16][16], H1[16][64], H2[16][64], dY[16][8],
+// dH2[16][64], dH1[16][64]
+constexpr int kStX = 0;
+constexpr int kStH1 = kStX + 16 * kMlpInPad;
+constexpr int kStH2 = kStH1 + 16 * kMlpHid;
+constexpr int kStDY = kStH2 + 16 * kMlpHid;
+constexpr int kStDH2 = kStDY + 16 * kMlpOutPad;
+constexpr int kStDH1 = kStDH2 + 16 * kMlpHid;
+constexpr int kStSize = kStDH1 + 16 * kMlpHid;
+
+// store a C tile (16 x 8, column block nb) into a row-major BF16 matrix
+__device__ __forceinline__ void store_c(__nv_bfloat16* M, int ld, int nb, const float (&c)[4], int lane)
+{
+    const int g = lane >> 2, q = lane & 3;
+    M[g * ld + nb * 8 + 2 * q] = __float2bfloat16_rn(c[0]);
+    M[g * ld + nb * 8 + 2 * q + 1] = __float2bfloat16_rn(c[1]);
+    M[(g + 8) * ld + nb * 8 + 2 * q] = __float2bfloat16_rn(c[2]);
+    M[(g + 8) * ld + nb * 8 + 2 * q + 1] = __float2bfloat16_rn(c[3]);
+}
+
+// A fragment of the transpose of a row-major BF16 matrix S (S is k x m:
+// A[m][k] = S[k][m]), m-tile mt, one 16-deep k-step at k = 0
+__device__ __forceinline__ void load_at(uint32_t (&a)[4], const __nv_bfloat16* S, int ld, int mt, int lane)
+{
+    const int g = lane >> 2, q = lane & 3;
+    const int m0 = mt * 16 + g, k0 = 2 * q;
+    a[0] = pack_raw(S[k0 * ld + m0], S[(k0 + 1) * ld + m0]);
+    a[1] = pack_raw(S[k0 * ld + m0 + 8], S[(k0 + 1) * ld + m0 + 8]);
+    a[2] = pack_raw(S[(k0 + 8) * ld + m0], S[(k0 + 9) * ld + m0]);
+    a[3] = pack_raw(S[(k0 + 8) * ld + m0 + 8], S[(k0 + 9) * ld + m0 + 8]);
+}
+
+// B fragment of a row-major BF16 matrix S (B[k][n] = S[k][n]), k-step 0,
+// column block nb
+__device__ __forceinline__ void load_bs(uint32_t (&b)[2], const __nv_bfloat16* S, int ld, int nb, int lane)
+{
+    const int g = lane >> 2, q = lane & 3;
+    const int n = nb * 8 + g, k = 2 * q;
+    b[0] = pack_raw(S[k * ld + n], S[(k + 1) * ld + n]);
+    b[1] = pack_raw(S[(k + 8) * ld + n], S[(k + 9) * ld + n]);
+}
+
+// B fragment of the transpose of a k-major weight W[n][k] (B[k][n] = W[n][k]
+// with W stored [n][ldk]), k-step ks, column block nb
+__device__ __forceinline__ void load_bt(uint32_t (&b)[2], const __nv_bfloat16* W, int ldk, int ks, int nb, int lane)
+{
+    const int g = lane >> 2, q = lane & 3;
+    const int n = nb * 8 + g, k = ks * 16 + 2 * q;
+    b[0] = pack_raw(W[n * ldk + k], W[n * ldk + k + 1]);
+    b[1] = pack_raw(W[n * ldk + k + 8], W[n * ldk + k + 9]);
+}
+
+__device__ __forceinline__ void add_c(float* G, int ld, int mt, int nb, const float (&c)[4], int lane)
+{
+    const int g = lane >> 2, q = lane & 3;
+    const int r = mt * 16 + g, col = nb * 8 + 2 * q;
+    atomicAdd(&G[r * ld + col], c[0]);
+    atomicAdd(&G[r * ld + col + 1], c[1]);
+    atomicAdd(&G[(r + 8) * ld + col], c[2]);
+    atomicAdd(&G[(r + 8) * ld + col + 1], c[3]);
+}
+
+// column sums of a C tile over its 16 rows into G[col]
+__device__ __forceinline__ void colsum_c(float* G, int nb, const float (&c)[4], int lane)
+{
+    float s0 = c[0] + c[2], s1 = c[1] + c[3];
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane < 4) {
+        atomicAdd(&G[nb * 8 + 2 * lane], s0);
+        atomicAdd(&G[nb * 8 + 2 * lane + 1], s1);
+    }
+}
+
+// X: n x 16 normalised features (FP32, padding zero); T: n x 3 scaled
+// targets; W: n weights (nullable); idx: the batch's row indices (B of them)
+__global__ void __launch_bounds__(kTrainWarps * 32) k_mlp_train(const float* __restrict__ X,
+                                                                 const float* __restrict__ T,
+                                                                 const float* __restrict__ W,
+                                                                 const int32_t* __restrict__ idx, int B,
+                                                                 const MlpDev* __restrict__ model,
+                                                                 float* __restrict__ grad, float* __restrict__ loss)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    MlpDev& m = *reinterpret_cast<MlpDev*>(smem);
+    float* gs = reinterpret_cast<float*>(smem + sizeof(MlpDev));
+    __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(gs + kGPad);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __nv_bfloat16* st = stage + w * kStSize;
+    for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(&m)[i] = reinterpret_cast<const uint32_t*>(model)[i];
+    for (int i = threadIdx.x; i < kGPad; i += blockDim.x) gs[i] = 0.f;
+    __syncthreads();
+    const int g = lane >> 2, q = lane & 3;
+    const float inv_b = 1.0f / (float)B;
+    float lsum = 0.f;
+    const int ntiles = (B + 15) / 16;
+    for (int tile = blockIdx.x * kTrainWarps + w; tile < ntiles; tile += gridDim.x * kTrainWarps) {
+        // rows of this tile (a row past B is all zero and has zero gradient)
+        const int r0 = tile * 16 + g, r1 = r0 + 8;
+        const bool v0 = r0 < B, v1 = r1 < B;
+        const int64_t i0 = v0 ? idx[r0] : 0, i1 = v1 ? idx[r1] : 0;
+        uint32_t x[4];
+        {
+            float a0 = v0 ? X[i0 * kMlpInPad + 2 * q] : 0.f, a1 = v0 ? X[i0 * kMlpInPad + 2 * q + 1] : 0.f;
+            float a2 = v1 ? X[i1 * kMlpInPad + 2 * q] : 0.f, a3 = v1 ? X[i1 * kMlpInPad + 2 * q + 1] : 0.f;
+            float a4 = v0 ? X[i0 * kMlpInPad + 2 * q + 8] : 0.f, a5 = v0 ? X[i0 * kMlpInPad + 2 * q + 9] : 0.f;
+            float a6 = v1 ? X[i1 * kMlpInPad + 2 * q + 8] : 0.f, a7 = v1 ? X[i1 * kMlpInPad + 2 * q + 9] : 0.f;
+            x[0] = pack_bf16(a0, a1);
+            x[1] = pack_bf16(a2, a3);
+            x[2] = pack_bf16(a4, a5);
+            x[3] = pack_bf16(a6, a7);
+            // X tile, row-major, for dW1 = X^T dH1
+            st[kStX + g * 16 + 2 * q] = __float2bfloat16_rn(a0);
+            st[kStX + g * 16 + 2 * q + 1] = __float2bfloat16_rn(a1);
+            st[kStX + (g + 8) * 16 + 2 * q] = __float2bfloat16_rn(a2);
+            st[kStX + (g + 8) * 16 + 2 * q + 1] = __float2bfloat16_rn(a3);
+            st[kStX + g * 16 + 2 * q + 8] = __float2bfloat16_rn(a4);
+            st[kStX + g * 16 + 2 * q + 9] = __float2bfloat16_rn(a5);
+            st[kStX + (g + 8) * 16 + 2 * q + 8] = __float2bfloat16_rn(a6);
+            st[kStX + (g + 8) * 16 + 2 * q + 9] = __float2bfloat16_rn(a7);
+        }
+        float h1[8][4], h2[8][4], y[4];
+        mlp16(m, x, h1, h2, y, lane);
+        // dY = 2 w (Y - T) / B on the 3 used columns of valid rows
+        float dy[4] = {0.f, 0.f, 0.f, 0.f};
+        {
+            const int c0 = 2 * q, c1 = 2 * q + 1;
+            const float w0 = (W && v0) ? W[i0] : 1.f, w1 = (W && v1) ? W[i1] : 1.f;
+            if (v0 && c0 < 3) { const float e = y[0] - T[i0 * 3 + c0]; lsum += w0 * e * e; dy[0] = 2.f * w0 * e * inv_b; }
+            if (v0 && c1 < 3) { const float e = y[1] - T[i0 * 3 + c1]; lsum += w0 * e * e; dy[1] = 2.f * w0 * e * inv_b; }
+            if (v1 && c0 < 3) { const float e = y[2] - T[i1 * 3 + c0]; lsum += w1 * e * e; dy[2] = 2.f * w1 * e * inv_b; }
+            if (v1 && c1 < 3) { const float e = y[3] - T[i1 * 3 + c1]; lsum += w1 * e * e; dy[3] = 2.f * w1 * e * inv_b; }
+        }
+        for (int nb = 0; nb < 8; nb++) {
+            store_c(st + kStH1, kMlpHid, nb, h1[nb], lane);
+            store_c(st + kStH2, kMlpHid, nb, h2[nb], lane);
+        }
+        store_c(st + kStDY, kMlpOutPad, 0, dy, lane);
+        __syncwarp();
+        colsum_c(gs + kGB3, 0, dy, lane);
+        // dW3 = H2^T dY
+        for (int mt = 0; mt < 4; mt++) {
+            uint32_t a[4], b[2];
+            load_at(a, st + kStH2, kMlpHid, mt, lane);
+            load_bs(b, st + kStDY, kMlpOutPad, 0, lane);
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_bf16(c, a, b);
+            add_c(gs + kGW3, kMlpOutPad, mt, 0, c, lane);
+        }
+        // dH2 = dY W3^T * [H2 > 0]; dY padded to a 16-deep k-step with zeros
+        float dh2[8][4];
+        {
+            uint32_t a[4];
+            a[0] = pack_bf16(dy[0], dy[1]);
+            a[1] = pack_bf16(dy[2], dy[3]);
+            a[2] = 0u;
+            a[3] = 0u;
+            for (int nb = 0; nb < 8; nb++) {
+                const int n = nb * 8 + g, k = 2 * q;
+                uint32_t b[2];
+                b[0] = pack_raw(m.w3[n * kMlpOutPad + k], m.w3[n * kMlpOutPad + k + 1]);
+                b[1] = 0u;
+                dh2[nb][0] = dh2[nb][1] = dh2[nb][2] = dh2[nb][3] = 0.f;
+                mma_bf16(dh2[nb], a, b);
+#pragma unroll
+                for (int e = 0; e < 4; e++) dh2[nb][e] = h2[nb][e] > 0.f ? dh2[nb][e] : 0.f;
+                store_c(st + kStDH2, kMlpHid, nb, dh2[nb], lane);
+                colsum_c(gs + kGB2, nb, dh2[nb], lane);
+            }
+        }
+        __syncwarp();
+        // dW2 = H1^T dH2
+        for (int mt = 0; mt < 4; mt++) {
+            uint32_t a[4];
+            load_at(a, st + kStH1, kMlpHid, mt, lane);
+            for (int nb = 0; nb < 8; nb++) {
+                uint32_t b[2];
+                load_bs(b, st + kStDH2, kMlpHid, nb, lane);
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_bf16(c, a, b);
+                add_c(gs + kGW2, kMlpHid, mt, nb, c, lane);
+            }
+        }
+        // dH1 = dH2 W2^T * [H1 > 0]
+        float dh1[8][4];
+        for (int nb = 0; nb < 8; nb++) dh1[nb][0] = dh1[nb][1] = dh1[nb][2] = dh1[nb][3] = 0.f;
+        for (int ks = 0; ks < 4; ks++) {
+            uint32_t a[4];
+            c_to_a(a, dh2[2 * ks], dh2[2 * ks + 1]);
+            for (int nb = 0; nb < 8; nb++) {
+                uint32_t b[2];
+                load_bt(b, m.w2, kMlpHid, ks, nb, lane);
+                mma_bf16(dh1[nb], a, b);
+            }
+        }
+        for (int nb = 0; nb < 8; nb++) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) dh1[nb][e] = h1[nb][e] > 0.f ? dh1[nb][e] : 0.f;
+            store_c(st + kStDH1, kMlpHid, nb, dh1[nb], lane);
+            colsum_c(gs + kGB1, nb, dh1[nb], lane);
+        }
+        __syncwarp();
+        // dW1 = X^T dH1
+        {
+            uint32_t a[4];
+            load_at(a, st + kStX, kMlpInPad, 0, lane);
+            for (int nb = 0; nb < 8; nb++) {
+                uint32_t b[2];
+                load_bs(b, st + kStDH1, kMlpHid, nb, lane);
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_bf16(c, a, b);
+                add_c(gs + kGW1, kMlpHid, 0, nb, c, lane);
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) atomicAdd(loss, lsum * inv_b);
+    __syncthreads();
+    // padded block sums -> packed global gradient (W1[13][64], b1, W2, b2, W3[64][3], b3)
+    for (int i = threadIdx.x; i < kMlpIn * kMlpHid; i += blockDim.x) atomicAdd(&grad[i], gs[kGW1 + i]);
+    float* gb1 = grad + kMlpIn * kMlpHid;
+    float* gw2 = gb1 + kMlpHid;
+    float* gb2 = gw2 + kMlpHid * kMlpHid;
+    float* gw3 = gb2 + kMlpHid;
+    float* gb3 = gw3 + kMlpHid * kMlpOut;
+    for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) {
+        atomicAdd(&gb1[i], gs[kGB1 + i]);
+        atomicAdd(&gb2[i], gs[kGB2 + i]);
+    }
+    for (int i = threadIdx.x; i < kMlpHid * kMlpHid; i += blockDim.x) atomicAdd(&gw2[i], gs[kGW2 + i]);
+    for (int i = threadIdx.x; i < kMlpHid * kMlpOut; i += blockDim.x)
+        atomicAdd(&gw3[i], gs[kGW3 + (i / kMlpOut) * kMlpOutPad + (i % kMlpOut)]);
+    if (threadIdx.x < kMlpOut) atomicAdd(&gb3[threadIdx.x], gs[kGB3 + threadIdx.x]);
+}
+
+// packed FP32 parameters + feature/output maps -> device BF16 model
+__global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict__ maps, MlpDev* __restrict__ m)
+{
+    const float* W1 = p;
+    const float* b1 = W1 + kMlpIn * kMlpHid;
+    const float* W2 = b1 + kMlpHid;
+    const float* b2 = W2 + kMlpHid * kMlpHid;
+    const float* W3 = b2 + kMlpHid;
+    const float* b3 = W3 + kMlpHid * kMlpOut;
+    for (int i = threadIdx.x; i < kMlpInPad * kMlpHid; i += blockDim.x) {
+        const int k = i / kMlpHid, n = i % kMlpHid;
+        m->w1[i] = __float2bfloat16_rn(k < kMlpIn ? W1[k * kMlpHid + n] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kMlpHid * kMlpHid; i += blockDim.x) m->w2[i] = __float2bfloat16_rn(W2[i]);
+    for (int i = threadIdx.x; i < kMlpHid * kMlpOutPad; i += blockDim.x) {
+        const int k = i / kMlpOutPad, n = i % kMlpOutPad;
+        m->w3[i] = __float2bfloat16_rn(n < kMlpOut ? W3[k * kMlpOut + n] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) {
+        m->b1[i] = b1[i];
+        m->b2[i] = b2[i];
+    }
+    for (int i = threadIdx.x; i < kMlpOutPad; i += blockDim.x) {
+        m->b3[i] = i < kMlpOut ? b3[i] : 0.f;
+        m->yscale[i] = i < kMlpOut ? maps[2 * kMlpIn + i] : 0.f;
+    }
+    for (int i = threadIdx.x; i < kMlpInPad; i += blockDim.x) {
+        m->xmean[i] = i < kMlpIn ? maps[i] : 0.f;
+        m->xscale[i] = i < kMlpIn ? maps[kMlpIn + i] : 0.f;
+    }
+}
+
+// Adam on the FP32 master parameters
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ mom, float* __restrict__ vel,
+                       const float* __restrict__ g, int n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * mom[i] + (1.f - b1) * gi;
+    const float vi = b2 * vel[i] + (1.f - b2) * gi * gi;
+    mom[i] = mi;
+    vel[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// raw features -> normalised, padded rows (n x 16)
+__global__ void k_mlp_normalise(const float* __restrict__ raw, int64_t n, const MlpDev* __restrict__ m,
+                                float* __restrict__ X)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < kMlpInPad; k++)
+        X[i * kMlpInPad + k] = k < kMlpIn ? (raw[i * kMlpIn + k] - m->xmean[k]) * m->xscale[k] : 0.f;
+}
+
+// batch inference: Y (n x 3) = network(X) * yscale, X normalised n x 16
+__global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ X, int64_t n,
+                                                   const MlpDev* __restrict__ model, float* __restrict__ Y)
+{
+    __shared__ MlpDev m;
+    for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(&m)[i] = reinterpret_cast<const uint32_t*>(model)[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int64_t ntiles = (n + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * 4 + w; tile < ntiles; tile += (int64_t)gridDim.x * 4) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        const bool v0 = r0 < n, v1 = r1 < n;
+        auto xv = [&](int64_t r, bool v, int c) { return v ? X[r * kMlpInPad + c] : 0.f; };
+        uint32_t x[4];
+        x[0] = pack_bf16(xv(r0, v0, 2 * q), xv(r0, v0, 2 * q + 1));
+        x[1] = pack_bf16(xv(r1, v1, 2 * q), xv(r1, v1, 2 * q + 1));
+        x[2] = pack_bf16(xv(r0, v0, 2 * q + 8), xv(r0, v0, 2 * q + 9));
+        x[3] = pack_bf16(xv(r1, v1, 2 * q + 8), xv(r1, v1, 2 * q + 9));
+        float h1[8][4], h2[8][4], y[4];
+        mlp16(m, x, h1, h2, y, lane);
+        const int c0 = 2 * q, c1 = 2 * q + 1;
+        if (v0 && c0 < 3) Y[r0 * 3 + c0] = y[0] * m.yscale[c0];
+        if (v0 && c1 < 3) Y[r0 * 3 + c1] = y[1] * m.yscale[c1];
+        if (v1 && c0 < 3) Y[r1 * 3 + c0] = y[2] * m.yscale[c0];
+        if (v1 && c1 < 3) Y[r1 * 3 + c1] = y[3] * m.yscale[c1];
+    }
+}
+
+// Features, exact label and label factor of (body, cell) pairs, one thread
+// per pair: features at the body's position; factor F = G M s^2 / r^4 (the
+// scale of the quadrupole term); label = (a_exact - a_mono) / F with a_exact
+// the softened sum over the cell's bodies (FP64 accumulation).
+__global__ void k_pair_labels(const int32_t* __restrict__ pb, const int32_t* __restrict__ pv, int64_t np,
+                              const float4* __restrict__ body, const uint32_t* __restrict__ sys_of,
+                              const SysParams* __restrict__ sysp, NodeTables nt, float eps, float G,
+                              float* __restrict__ feat, float* __restrict__ lab, float* __restrict__ fac)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const int64_t ib = pb[k], v = pv[k];
+    const float4 xb = body[ib];
+    const double x[3] = {xb.x, xb.y, xb.z};
+    const int4 b = nt.b[v];
+    const int4 cc = nt.c[v];
+    const SysParams& P = sysp[cc.w];
+    const double s = ldexp(P.L, -(b.w & 255));
+    const double M = nt.mass64[v];
+    const double* com = &nt.com64[3 * v];
+    double d[3], r2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        d[a] = com[a] - x[a];
+        r2 += d[a] * d[a];
+    }
+    const double r = sqrt(r2);
+    float* f = feat + k * kMlpIn;
+    for (int a = 0; a < 3; a++) f[a] = (float)(d[a] / s);
+    f[3] = (float)(s / r);
+    f[4] = (float)(eps / s);
+    f[5] = (float)log2((double)b.y);
+    f[6] = (float)(M / nt.mass64[cc.w]);  // the system's root is node cc.w
+    for (int q = 0; q < 6; q++) f[7 + q] = (float)(nt.quad64[6 * v + q] / (M * s * s));
+    const double e2 = (double)eps * (double)eps;
+    double ae[3] = {0, 0, 0};
+    for (int j = b.x; j < b.x + b.y; j++) {
+        const float4 y = body[j];
+        const double dx = (double)y.x - x[0], dy = (double)y.y - x[1], dz = (double)y.z - x[2];
+        const double q2 = dx * dx + dy * dy + dz * dz + e2;
+        const double ri = 1.0 / sqrt(q2);
+        const double fm = (double)y.w * ri * ri * ri;
+        ae[0] += fm * dx;
+        ae[1] += fm * dy;
+        ae[2] += fm * dz;
+    }
+    const double rm = 1.0 / sqrt(r2 + e2);
+    const double fmo = M * rm * rm * rm;
+    const double F = (double)G * M * s * s / (r2 * r2);
+    for (int a = 0; a < 3; a++) lab[k * 3 + a] = (float)((double)G * (ae[a] - fmo * d[a]) / F);
+    if (fac) fac[k] = (float)F;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+size_t mlp_train_smem() { return sizeof(MlpDev) + kGPad * sizeof(float) + (size_t)kTrainWarps * kStSize * 2; }
+
+cudaError_t launch_mlp_train(const float* X, const float* T, const float* W, const int32_t* idx, int B,
+                             const void* model, float* grad, float* loss, int blocks, cudaStream_t s)
+{
+    const size_t smem = mlp_train_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_mlp_train<<<blocks, kTrainWarps * 32, smem, s>>>(X, T, W, idx, B, (const MlpDev*)model, grad, loss);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+void launch_mlp_pack(const float* params, const float* maps, void* model, cudaStream_t s)
+{
+    k_mlp_pack<<<1, 256, 0, s>>>(params, maps, (MlpDev*)model);
+    count_launches(1);
+}
+
+void launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, int t, cudaStream_t s)
+{
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    k_adam<<<nblk(n, 256), 256, 0, s>>>(p, m, v, g, n, lr, b1, b2, 1e-8f, c1, c2);
+    count_launches(1);
+}
+
+void launch_mlp_normalise(const float* raw, int64_t n, const void* model, float* X, cudaStream_t s)
+{
+    k_mlp_normalise<<<nblk(n, 256), 256, 0, s>>>(raw, n, (const MlpDev*)model, X);
+    count_launches(1);
+}
+
+void launch_mlp_infer(const float* X, int64_t n, const void* model, float* Y, cudaStream_t s)
+{
+    int64_t g = (n + 63) / 64;
+    if (g > 4096) g = 4096;
+    k_mlp_infer<<<(unsigned)(g < 1 ? 1 : g), 128, 0, s>>>(X, n, (const MlpDev*)model, Y);
+    count_launches(1);
+}
+
+void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const float4* body, const uint32_t* sys_of,
+                        const SysParams* sysp, NodeTables nt, float eps, float G, float* feat, float* lab,
+                        float* fac, cudaStream_t s)
+{
+    k_pair_labels<<<nblk(np, 128), 128, 0, s>>>(pb, pv, np, body, sys_of, sysp, nt, eps, G, feat, lab, fac);
+    count_launches(1);
+}
+
+size_t mlp_dev_size() { return sizeof(MlpDev); }
+
+}  // namespace tc

@@ -35,6 +35,7 @@
 // (compensated accumulation); the plain mode uses absolute float centres of
 // mass and plain accumulation.
 #include "tc_internal.cuh"
+#include "tc_mma.cuh"
 
 namespace tc {
 
@@ -219,7 +220,44 @@ struct Accum {
     }
 };
 
-template <int B, int TILE, bool PRECISE, bool POT>
+// Learned correction rows: kMlpInPad normalised features + the factor that
+// turns a label into an acceleration, G M s^2 / r^4.  mlp_rows16 evaluates the first n
+// (<= 16) queued rows with the tensor cores and adds label x yscale x factor
+// to the lane's share of the group's correction (lanes of q = 0 hold x, y;
+// of q = 1 hold z).
+constexpr int kMlpRow = kMlpInPad + 1;
+constexpr int kMlpQueue = 48;  // < 16 left over + 32 added by a step
+__host__ __device__ constexpr size_t mlp_dev_bytes() { return sizeof(MlpDev); }
+
+__device__ __forceinline__ void mlp_rows16(const MlpDev& m, const float* mq, int n, float (&corr)[3], int lane)
+{
+    const int g = lane >> 2, q = lane & 3;
+    auto xv = [&](int r, int c) { return r < n ? mq[r * kMlpRow + c] : 0.f; };
+    uint32_t x[4];
+    x[0] = pack_bf16(xv(g, 2 * q), xv(g, 2 * q + 1));
+    x[1] = pack_bf16(xv(g + 8, 2 * q), xv(g + 8, 2 * q + 1));
+    x[2] = pack_bf16(xv(g, 2 * q + 8), xv(g, 2 * q + 9));
+    x[3] = pack_bf16(xv(g + 8, 2 * q + 8), xv(g + 8, 2 * q + 9));
+    float h1[8][4], h2[8][4], y[4];
+    mlp16(m, x, h1, h2, y, lane);
+    const float f0 = g < n ? mq[g * kMlpRow + kMlpInPad] : 0.f;
+    const float f1 = g + 8 < n ? mq[(g + 8) * kMlpRow + kMlpInPad] : 0.f;
+    if (q == 0) {
+        corr[0] += (y[0] * f0 + y[2] * f1) * m.yscale[0];
+        corr[1] += (y[1] * f0 + y[3] * f1) * m.yscale[1];
+    } else if (q == 1) {
+        corr[2] += (y[0] * f0 + y[2] * f1) * m.yscale[2];
+    }
+}
+
+// shared memory of one warp (learned mode adds a queue of MLP rows and the
+// block holds one copy of the network in front of the warps' regions)
+__host__ __device__ constexpr size_t walk_warp_bytes(int tile, int stack, bool learned)
+{
+    return (size_t)2 * tile_cap(tile) * 16 + (size_t)stack * 4 + (learned ? (size_t)kMlpQueue * kMlpRow * 4 : 0);
+}
+
+template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
 {
     constexpr int kTile = TILE;
@@ -227,10 +265,12 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)2 * kTileCap * sizeof(float4) + (size_t)stack_cap * sizeof(uint32_t);
-    float* ctile = reinterpret_cast<float*>(smem + wib * per_warp);
+    const size_t head = LEARNED ? ((mlp_dev_bytes() + 15) & ~(size_t)15) : 0;
+    const size_t per_warp = walk_warp_bytes(TILE, stack_cap, LEARNED);
+    float* ctile = reinterpret_cast<float*>(smem + head + wib * per_warp);
     float* btile = ctile + 4 * kTileCap;
     uint32_t* stk = reinterpret_cast<uint32_t*>(btile + 4 * kTileCap);
+    float* mq = reinterpret_cast<float*>(stk + stack_cap);  // learned: kMlpQueue rows of kMlpRow floats
     const f2 E2 = f2pack(a.eps2, a.eps2);
     const uint32_t lt = (1u << lane) - 1u;
 
@@ -238,6 +278,12 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
     if (info->err & kErrCapacity) return;  // the build stopped: no tree to walk
     const int64_t G = info->G;
     const NodeTables nt = a.nt;
+    MlpDev* mlp = reinterpret_cast<MlpDev*>(smem);
+    if (LEARNED) {
+        for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(mlp)[i] = reinterpret_cast<const uint32_t*>(a.mlp)[i];
+        __syncthreads();
+    }
 
     for (;;) {
         int g = 0;
@@ -313,6 +359,18 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             fhi[k] = __shfl_sync(0xffffffffu, fb, k + 3);
         }
 
+        // learned correction: evaluated at the centre of the group's box
+        // (reference-relative), summed over the group's band cells
+        float xgc[3] = {0.f, 0.f, 0.f};
+        float corr[3] = {0.f, 0.f, 0.f};
+        int qn = 0;
+        unsigned long long nevals = 0;
+        if (LEARNED) {
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                xgc[k] = 0.5f * (fmaf((float)klo[k], uf, flo[k]) + fmaf((float)khi[k], uf, fhi[k]));
+        }
+
         Accum<B, PRECISE, POT> cacc, bacc;
         cacc.init();
         bacc.init();
@@ -332,6 +390,7 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             int4 nb = make_int4(0, 0, 0, 0);
             bool acc = false, oleaf = false, oint = false;
             float4 src = make_float4(0.f, 0.f, 0.f, 0.f);
+            float band_e2 = 0.f;
             if (v >= 0) {
                 // the three node records are independent loads: issue together
                 nb = __ldg(&nt.b[v]);
@@ -352,8 +411,9 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
                     }
                     const float s = scalbnf(Lf, -(nb.w & 255));
                     acc = (s * s) < a.theta2 * e2;
+                    band_e2 = e2;
                     if (acc) {
-                        if (PRECISE) {
+                        if (PRECISE || LEARNED) {
                             src = make_float4(fmaf((float)D[0], uf, off[0]), fmaf((float)D[1], uf, off[1]),
                                               fmaf((float)D[2], uf, off[2]), na.w);
                         } else {
@@ -384,6 +444,68 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             }
             cn += __popc(am);
             Lc += __popc(am);
+            // band cells (s / d at or above the band, two bodies or more):
+            // training pairs and learned corrections
+            bool band = false;
+            if (acc && nb.y >= 2) {
+                const float sz = scalbnf(Lf, -(nb.w & 255));
+                band = sz * sz >= a.band2 * band_e2;
+            }
+            if (a.pair_body && band) {
+                const unsigned long long hh = mix64(a.pair_seed ^ (((unsigned long long)g << 32) | (unsigned)v));
+                if ((float)(hh >> 40) * (1.0f / 16777216.0f) < a.pair_prob) {
+                    const unsigned long long k = atomicAdd(a.pair_count, 1ull);
+                    if ((int64_t)k < a.pair_cap) {
+                        a.pair_body[k] = gfirst + (int)((hh & 0xffffffffull) % (unsigned)(gend - gfirst));
+                        a.pair_node[k] = v;
+                    }
+                }
+            }
+            if (LEARNED) {
+                const unsigned bm = __ballot_sync(0xffffffffu, band);
+                if (band) {
+                    float* row = mq + (qn + __popc(bm & lt)) * kMlpRow;
+                    const float sz = scalbnf(Lf, -(nb.w & 255));
+                    const float inv_s = 1.0f / sz;
+                    const float dx = src.x - xgc[0], dy = src.y - xgc[1], dz = src.z - xgc[2];
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    const float rr = sqrtf(r2);
+                    const float Mc = src.w;
+                    const float* qd = nt.quad + 6 * (int64_t)v;
+                    const float iq = 1.0f / (Mc * sz * sz);
+                    float f[kMlpIn];
+                    f[0] = dx * inv_s;
+                    f[1] = dy * inv_s;
+                    f[2] = dz * inv_s;
+                    f[3] = sz / rr;
+                    f[4] = a.eps * inv_s;
+                    f[5] = log2f((float)nb.y);
+                    f[6] = Mc / SP.msys;
+#pragma unroll
+                    for (int k = 0; k < 6; k++) f[7 + k] = __ldg(qd + k) * iq;
+#pragma unroll
+                    for (int k = 0; k < kMlpIn; k++) row[k] = (f[k] - mlp->xmean[k]) * mlp->xscale[k];
+#pragma unroll
+                    for (int k = kMlpIn; k < kMlpInPad; k++) row[k] = 0.f;
+                    row[kMlpInPad] = a.G * Mc * sz * sz / (r2 * r2);  // label -> acceleration
+                }
+                qn += __popc(bm);
+                __syncwarp();
+                while (qn >= 16) {
+                    mlp_rows16(*mlp, mq, 16, corr, lane);
+                    nevals += 16;
+                    // move the rows past the first 16 to the front (read all, then write)
+                    const bool mv = lane < qn - 16;
+                    float tmp[kMlpRow];
+                    if (mv)
+                        for (int k = 0; k < kMlpRow; k++) tmp[k] = mq[(16 + lane) * kMlpRow + k];
+                    __syncwarp();
+                    if (mv)
+                        for (int k = 0; k < kMlpRow; k++) mq[lane * kMlpRow + k] = tmp[k];
+                    qn -= 16;
+                    __syncwarp();
+                }
+            }
             // opened leaves -> body tile.  The bodies of all leaves opened in
             // this step are gathered 32 at a time: lane j takes body t of the
             // concatenated ranges, finding its leaf by a binary search over
@@ -429,6 +551,16 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
         if (PRECISE) cacc.flush(ctile, cn, XR, YR, ZR, E2);
         else cacc.flush(ctile, cn, XA, YA, ZA, E2);
         bacc.flush(btile, bn, XA, YA, ZA, E2);
+        if (LEARNED) {
+            if (qn > 0) {
+                mlp_rows16(*mlp, mq, qn, corr, lane);
+                nevals += qn;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+#pragma unroll
+                for (int o = 16; o; o >>= 1) corr[k] += __shfl_xor_sync(0xffffffffu, corr[k], o);
+        }
 
         // results, scattered back to the original body order
 #pragma unroll
@@ -446,9 +578,9 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             const float fy = (cy_ + by_) + (ky + qy);
             const float fz = (cz_ + bz_) + (kz + qz);
             const float fp = (cp_ + bp_) + (kp + qp);
-            a.acc[3 * o + 0] = a.G * fx;
-            a.acc[3 * o + 1] = a.G * fy;
-            a.acc[3 * o + 2] = a.G * fz;
+            a.acc[3 * o + 0] = a.G * fx + corr[0];
+            a.acc[3 * o + 1] = a.G * fy + corr[1];
+            a.acc[3 * o + 2] = a.G * fz + corr[2];
             if (POT) {
                 // remove the body's own term, -m_i / eps, summed with the list
                 const float self = mi[b] * rsqrtf(a.eps2);
@@ -463,6 +595,7 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             atomicAdd(&a.info->interactions, (unsigned long long)gc * (unsigned long long)(Lc + Lb));
             atomicAdd(&a.info->cells, (unsigned long long)Lc);
             atomicAdd(&a.info->bodies, (unsigned long long)Lb);
+            if (LEARNED && a.mlp_evals) atomicAdd(a.mlp_evals, nevals);
             if (a.ncell) a.ncell[g] = Lc;
             if (a.nbody) a.nbody[g] = Lb;
             if (a.hash) a.hash[g] = hsh;
@@ -471,13 +604,13 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
     }
 }
 
-template <int B, int TILE, bool PRECISE, bool POT>
+template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 cudaError_t prepare_t(const WalkConfig& c, int num_sms, int* grid, size_t* smem_out)
 {
     const int warps = c.warps;
-    const size_t per_warp = (size_t)2 * tile_cap(TILE) * sizeof(float4) + (size_t)c.stack * sizeof(uint32_t);
-    const size_t smem = per_warp * warps;
-    auto kern = k_walk<B, TILE, PRECISE, POT>;
+    const size_t head = LEARNED ? ((mlp_dev_bytes() + 15) & ~(size_t)15) : 0;
+    const size_t smem = head + walk_warp_bytes(TILE, c.stack, LEARNED) * warps;
+    auto kern = k_walk<B, TILE, PRECISE, POT, LEARNED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -490,25 +623,28 @@ cudaError_t prepare_t(const WalkConfig& c, int num_sms, int* grid, size_t* smem_
     return cudaSuccess;
 }
 
-template <int B, int TILE, bool PRECISE, bool POT>
+template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 cudaError_t launch_t(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s)
 {
-    k_walk<B, TILE, PRECISE, POT><<<grid, c.warps * 32, smem, s>>>(a, c.stack);
+    k_walk<B, TILE, PRECISE, POT, LEARNED><<<grid, c.warps * 32, smem, s>>>(a, c.stack);
     count_launches(1);
     return cudaGetLastError();
 }
 
-// dispatch over (bodies per lane, tile, mode) to the template instance F
-template <template <int, int, bool, bool> class F, typename... Args>
+// dispatch over (bodies per lane, tile, mode) to the template instance F;
+// the learned correction exists in the precise mode without potential
+template <template <int, int, bool, bool, bool> class F, typename... Args>
 cudaError_t dispatch(const WalkConfig& c, Args... args)
 {
     const bool p = c.precise != 0, pot = c.want_pot != 0;
-#define TC_WALK_MODES(BB, TT)                                         \
-    if (c.gmax == 32 * BB && c.tile == TT) {                          \
-        if (p && pot) return F<BB, TT, true, true>::run(args...);     \
-        if (p && !pot) return F<BB, TT, true, false>::run(args...);   \
-        if (!p && pot) return F<BB, TT, false, true>::run(args...);   \
-        return F<BB, TT, false, false>::run(args...);                 \
+    if (c.learned && (!p || pot)) return cudaErrorInvalidValue;
+#define TC_WALK_MODES(BB, TT)                                                \
+    if (c.gmax == 32 * BB && c.tile == TT) {                                 \
+        if (c.learned) return F<BB, TT, true, false, true>::run(args...);    \
+        if (p && pot) return F<BB, TT, true, true, false>::run(args...);     \
+        if (p && !pot) return F<BB, TT, true, false, false>::run(args...);   \
+        if (!p && pot) return F<BB, TT, false, true, false>::run(args...);   \
+        return F<BB, TT, false, false, false>::run(args...);                 \
     }
     TC_WALK_MODES(1, 64)
     TC_WALK_MODES(1, 128)
@@ -523,18 +659,18 @@ cudaError_t dispatch(const WalkConfig& c, Args... args)
     return cudaErrorInvalidValue;
 }
 
-template <int B, int TILE, bool PRECISE, bool POT>
+template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 struct PrepareF {
     static cudaError_t run(const WalkConfig* c, int num_sms, int* grid, size_t* smem)
     {
-        return prepare_t<B, TILE, PRECISE, POT>(*c, num_sms, grid, smem);
+        return prepare_t<B, TILE, PRECISE, POT, LEARNED>(*c, num_sms, grid, smem);
     }
 };
-template <int B, int TILE, bool PRECISE, bool POT>
+template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 struct LaunchF {
     static cudaError_t run(const WalkArgs* a, const WalkConfig* c, int grid, size_t smem, cudaStream_t s)
     {
-        return launch_t<B, TILE, PRECISE, POT>(*a, *c, grid, smem, s);
+        return launch_t<B, TILE, PRECISE, POT, LEARNED>(*a, *c, grid, smem, s);
     }
 };
 

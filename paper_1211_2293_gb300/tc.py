@@ -30,8 +30,12 @@ EXPORTS = [
     "tc_get_sizes", "tc_get_tree", "tc_get_nodes", "tc_get_groups", "tc_get_cube", "tc_get_lists",
     "tc_diag", "tc_direct", "tc_sync", "tc_last_error", "tc_build", "tc_forces", "tc_step", "tc_default",
     "tc_set_timing", "tc_get_timings", "tc_direct_static", "tc_ctx_build_batch", "tc_get_systems",
-    "tc_autotune",
+    "tc_autotune", "tc_mlp_set", "tc_mlp_get", "tc_mlp_forward", "tc_mlp_loss_grad", "tc_mlp_train",
+    "tc_mlp_pairs", "tc_mlp_evals",
 ]
+
+MLP_NPARAM = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
+MLP_NMODEL = MLP_NPARAM + 13 + 13 + 3
 
 
 class TcError(RuntimeError):
@@ -44,7 +48,7 @@ class tc_config(ctypes.Structure):
     _fields_ = [("gmax", ctypes.c_int32), ("warps", ctypes.c_int32), ("precise", ctypes.c_int32),
                 ("want_pot", ctypes.c_int32), ("verify", ctypes.c_int32), ("stack", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("quad", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("graph", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("learned", ctypes.c_int32)]
 
 
 _lib = None
@@ -93,6 +97,13 @@ def load(path: str | None = None):
         "tc_ctx_build_batch": ([P, P, P, P, I64, I32], I32),
         "tc_get_systems": ([P, P, P], I32),
         "tc_autotune": ([P, F, F, F, I32, ctypes.POINTER(tc_config), ctypes.POINTER(ctypes.c_double)], I32),
+        "tc_mlp_set": ([P, P, F], I32),
+        "tc_mlp_get": ([P, P, P], I32),
+        "tc_mlp_forward": ([P, P, I64, P], I32),
+        "tc_mlp_loss_grad": ([P, P, P, P, I64, P, P], I32),
+        "tc_mlp_train": ([P, P, P, P, I64, I32, I32, F, ctypes.c_uint64, F, P], I32),
+        "tc_mlp_pairs": ([P, F, F, F, F, ctypes.c_uint64, I64, P, P, P, P, P, P], I32),
+        "tc_mlp_evals": ([P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -196,6 +207,70 @@ class Context:
         self._c(self._lib.tc_autotune(self._h, float(theta), float(eps), float(G), int(reps), ctypes.byref(best),
                                       ctypes.byref(ms)))
         return {f: getattr(best, f) for f, _ in tc_config._fields_}, ms.value
+
+    # ---------------------------------------------------------- learned correction
+    def mlp_set(self, model, band: float):
+        model = np.ascontiguousarray(model, dtype=np.float32)
+        assert model.size == MLP_NMODEL
+        self._c(self._lib.tc_mlp_set(self._h, _ptr(model), float(band)))
+
+    def mlp_get(self):
+        model = np.zeros(MLP_NMODEL, np.float32)
+        band = ctypes.c_float()
+        self._c(self._lib.tc_mlp_get(self._h, _ptr(model), ctypes.byref(band)))
+        return model, band.value
+
+    def mlp_forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 13)
+        Y = np.zeros((X.shape[0], 3), np.float32)
+        self._c(self._lib.tc_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(Y)))
+        return Y
+
+    def mlp_loss_grad(self, X, T, W=None):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 13)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1, 3)
+        W = None if W is None else np.ascontiguousarray(W, dtype=np.float32).reshape(-1)
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = ctypes.c_float()
+        self._c(self._lib.tc_mlp_loss_grad(self._h, _ptr(X), _ptr(T), _ptr(W), X.shape[0], _ptr(g),
+                                           ctypes.byref(loss)))
+        return loss.value, g
+
+    def mlp_train(self, X, T, W=None, epochs=40, batch=1024, lr=2e-3, seed=0, band=0.5):
+        """Train a fresh model on pairs (X, T) with loss weights W (None: 1)."""
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 13)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1, 3)
+        W = None if W is None else np.ascontiguousarray(W, dtype=np.float32).reshape(-1)
+        losses = np.zeros(int(epochs), np.float32)
+        self._c(self._lib.tc_mlp_train(self._h, _ptr(X), _ptr(T), _ptr(W), X.shape[0], int(epochs), int(batch),
+                                       float(lr), int(seed), float(band), _ptr(losses)))
+        return losses
+
+    def mlp_pairs(self, theta, eps, band, prob, seed, max_pairs):
+        """(X, T, F, body, node) of pairs generated by a walk at theta."""
+        X = np.zeros((max_pairs, 13), np.float32)
+        T = np.zeros((max_pairs, 3), np.float32)
+        F = np.zeros(max_pairs, np.float32)
+        b = np.zeros(max_pairs, np.int64)
+        v = np.zeros(max_pairs, np.int64)
+        npairs = ctypes.c_int64()
+        self._c(self._lib.tc_mlp_pairs(self._h, float(theta), float(eps), float(band), float(prob), int(seed),
+                                       int(max_pairs), _ptr(X), _ptr(T), _ptr(F), _ptr(b), _ptr(v),
+                                       ctypes.byref(npairs)))
+        k = npairs.value
+        return X[:k], T[:k], F[:k], b[:k], v[:k]
+
+    @staticmethod
+    def mlp_weights(F):
+        """Loss weights that make the training loss the mean squared error of
+        the corrected acceleration: F^2, normalised to mean 1."""
+        w = np.asarray(F, np.float64) ** 2
+        return (w / w.mean()).astype(np.float32)
+
+    def mlp_evals(self):
+        v = ctypes.c_int64()
+        self._c(self._lib.tc_mlp_evals(self._h, ctypes.byref(v)))
+        return v.value
 
     def set_velocity(self, vel):
         self._c(self._lib.tc_ctx_set_velocity(self._h, _ptr(vel)))
