@@ -260,7 +260,8 @@ int tc_mlp_forward(tc_ctx *ctx, const float *X, int64_t n, float *Y);
  * the parameters) under the current model; grad and loss nullable */
 int tc_mlp_loss_grad(tc_ctx *ctx, const float *X, const float *T, const float *W, int64_t n, float *grad,
                      float *loss);
-/* Train a fresh model (He initialisation from seed; feature means/scales
+/* Train a fresh model (weights and biases uniform in +-1/sqrt(fan-in), from
+ * seed; feature means/scales
  * and output RMS from the data) on n >= 16 pairs (X n x 13 features, T n x 3
  * labels, W n loss weights or NULL) with Adam, learning rate lr decayed
  * along a cosine over all steps, shuffled mini-batches of `batch` (>= 16),

@@ -1153,18 +1153,14 @@ int tc_mlp_train(tc_ctx* c, const float* X, const float* T, const float* W, int6
         const double rms = std::sqrt(s2 / n);
         model[kMlpNParamHost + 26 + k] = rms > 1e-30 ? (float)rms : 1.f;
     }
-    // He initialisation of the weights, zero biases
+    // weights and biases uniform in +-1/sqrt(fan-in)
     uint64_t st = seed;
-    auto normal = [&]() {
-        double u1 = std::max(sunif(st), 1e-300), u2 = sunif(st);
-        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
-    };
-    float* W1 = model.data();
-    float* W2 = W1 + 13 * 64 + 64;
-    float* W3 = W2 + 64 * 64 + 64;
-    for (int i = 0; i < 13 * 64; i++) W1[i] = (float)(normal() * std::sqrt(2.0 / 13));
-    for (int i = 0; i < 64 * 64; i++) W2[i] = (float)(normal() * std::sqrt(2.0 / 64));
-    for (int i = 0; i < 64 * 3; i++) W3[i] = (float)(normal() * std::sqrt(1.0 / 64));
+    float* p = model.data();
+    const int fan[3] = {13, 64, 64}, outs[3] = {64, 64, 3};
+    for (int l = 0; l < 3; l++) {
+        const double bound = 1.0 / std::sqrt((double)fan[l]);
+        for (int i = 0; i < fan[l] * outs[l] + outs[l]; i++) *p++ = (float)((2.0 * sunif(st) - 1.0) * bound);
+    }
     c->mlp_band = band;
     int r = mlp_upload(c, model.data());
     if (r) return r;

@@ -193,12 +193,12 @@ cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t
 
 // learned far-field correction (tc_mlp.cu)
 size_t mlp_dev_size();
+size_t mlp_frag_size();  // the inference part at the front of a device model
 size_t mlp_train_smem();
 cudaError_t launch_mlp_train(const float* X, const float* T, const float* W, const int32_t* idx, int B,
                              const void* model, float* grad, float* loss, int blocks, cudaStream_t s);
 void launch_mlp_pack(const float* params, const float* maps, void* model, cudaStream_t s);
 void launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, int t, cudaStream_t s);
-void launch_mlp_normalise(const float* raw, int64_t n, const void* model, float* X, cudaStream_t s);
 void launch_mlp_infer(const float* X, int64_t n, const void* model, float* Y, cudaStream_t s);
 void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const float4* body, const uint32_t* sys_of,
                         const SysParams* sysp, NodeTables nt, float eps, float G, float* feat, float* lab,

@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kTrainWarps * 32) k_mlp_train(const float* __r
     if (threadIdx.x < kMlpOut) atomicAdd(&gb3[threadIdx.x], gs[kGB3 + threadIdx.x]);
 }
 
-// packed FP32 parameters + feature/output maps -> device BF16 model
+// packed FP32 parameters + feature/output maps -> device BF16 model: the
+// k-major weights for training and the fragment-arranged inference copy
 __global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict__ maps, MlpDev* __restrict__ m)
 {
     const float* W1 = p;
@@ -284,26 +285,53 @@ __global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict_
     const float* b2 = W2 + kMlpHid * kMlpHid;
     const float* W3 = b2 + kMlpHid;
     const float* b3 = W3 + kMlpHid * kMlpOut;
-    for (int i = threadIdx.x; i < kMlpInPad * kMlpHid; i += blockDim.x) {
-        const int k = i / kMlpHid, n = i % kMlpHid;
-        m->w1[i] = __float2bfloat16_rn(k < kMlpIn ? W1[k * kMlpHid + n] : 0.f);
-    }
+    // padded weights: input rows past 13 and output columns past 3 are zero
+    auto w1 = [&](int k, int n) { return k < kMlpIn ? W1[k * kMlpHid + n] : 0.f; };
+    auto w3 = [&](int k, int n) { return n < kMlpOut ? W3[k * kMlpOut + n] : 0.f; };
+    auto bf = [](float lo, float hi) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&v);
+    };
+    for (int i = threadIdx.x; i < kMlpInPad * kMlpHid; i += blockDim.x)
+        m->w1[i] = __float2bfloat16_rn(w1(i / kMlpHid, i % kMlpHid));
     for (int i = threadIdx.x; i < kMlpHid * kMlpHid; i += blockDim.x) m->w2[i] = __float2bfloat16_rn(W2[i]);
-    for (int i = threadIdx.x; i < kMlpHid * kMlpOutPad; i += blockDim.x) {
-        const int k = i / kMlpOutPad, n = i % kMlpOutPad;
-        m->w3[i] = __float2bfloat16_rn(n < kMlpOut ? W3[k * kMlpOut + n] : 0.f);
+    for (int i = threadIdx.x; i < kMlpHid * kMlpOutPad; i += blockDim.x)
+        m->w3[i] = __float2bfloat16_rn(w3(i / kMlpOutPad, i % kMlpOutPad));
+    // B fragments: lane (g, q) of column block nb, k-step ks holds
+    // {W[16 ks + 2q][n], W[16 ks + 2q + 1][n]}, {W[16 ks + 2q + 8][n], W[16 ks + 2q + 9][n]}, n = 8 nb + g
+    MlpFrag& f = m->frag;
+    for (int i = threadIdx.x; i < 8 * 32; i += blockDim.x) {
+        const int nb = i / 32, lane = i % 32, g = lane >> 2, q = lane & 3, n = nb * 8 + g, k = 2 * q;
+        f.f1[nb][lane] = make_uint2(bf(w1(k, n), w1(k + 1, n)), bf(w1(k + 8, n), w1(k + 9, n)));
+    }
+    for (int i = threadIdx.x; i < 4 * 8 * 32; i += blockDim.x) {
+        const int ks = i / 256, nb = (i / 32) % 8, lane = i % 32, g = lane >> 2, q = lane & 3;
+        const int n = nb * 8 + g, k = ks * 16 + 2 * q;
+        f.f2[ks][nb][lane] = make_uint2(bf(W2[k * kMlpHid + n], W2[(k + 1) * kMlpHid + n]),
+                                        bf(W2[(k + 8) * kMlpHid + n], W2[(k + 9) * kMlpHid + n]));
+    }
+    for (int i = threadIdx.x; i < 4 * 32; i += blockDim.x) {
+        const int ks = i / 32, lane = i % 32, g = lane >> 2, q = lane & 3, k = ks * 16 + 2 * q;
+        f.f3[ks][lane] = make_uint2(bf(w3(k, g), w3(k + 1, g)), bf(w3(k + 8, g), w3(k + 9, g)));
     }
     for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) {
         m->b1[i] = b1[i];
         m->b2[i] = b2[i];
     }
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) {
+        const int nb = i / 4, q = i % 4;
+        f.b1[nb][q] = make_float2(b1[nb * 8 + 2 * q], b1[nb * 8 + 2 * q + 1]);
+        f.b2[nb][q] = make_float2(b2[nb * 8 + 2 * q], b2[nb * 8 + 2 * q + 1]);
+    }
     for (int i = threadIdx.x; i < kMlpOutPad; i += blockDim.x) {
         m->b3[i] = i < kMlpOut ? b3[i] : 0.f;
-        m->yscale[i] = i < kMlpOut ? maps[2 * kMlpIn + i] : 0.f;
+        f.yscale[i] = i < kMlpOut ? maps[2 * kMlpIn + i] : 0.f;
     }
+    for (int i = threadIdx.x; i < 4; i += blockDim.x)
+        f.b3[i] = make_float2(2 * i < kMlpOut ? b3[2 * i] : 0.f, 2 * i + 1 < kMlpOut ? b3[2 * i + 1] : 0.f);
     for (int i = threadIdx.x; i < kMlpInPad; i += blockDim.x) {
-        m->xmean[i] = i < kMlpIn ? maps[i] : 0.f;
-        m->xscale[i] = i < kMlpIn ? maps[kMlpIn + i] : 0.f;
+        f.xscale[i] = i < kMlpIn ? maps[kMlpIn + i] : 0.f;
+        f.xoff[i] = i < kMlpIn ? -maps[i] * maps[kMlpIn + i] : 0.f;
     }
 }
 
@@ -321,23 +349,14 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ mom, float* __
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// raw features -> normalised, padded rows (n x 16)
-__global__ void k_mlp_normalise(const float* __restrict__ raw, int64_t n, const MlpDev* __restrict__ m,
-                                float* __restrict__ X)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int k = 0; k < kMlpInPad; k++)
-        X[i * kMlpInPad + k] = k < kMlpIn ? (raw[i * kMlpIn + k] - m->xmean[k]) * m->xscale[k] : 0.f;
-}
-
-// batch inference: Y (n x 3) = network(X) * yscale, X normalised n x 16
+// batch inference: Y (n x 3) = network(X) * yscale, X normalised n x 16 --
+// the same fragment path the walk evaluates its corrections with
 __global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ X, int64_t n,
                                                    const MlpDev* __restrict__ model, float* __restrict__ Y)
 {
-    __shared__ MlpDev m;
-    for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 4); i += blockDim.x)
-        reinterpret_cast<uint32_t*>(&m)[i] = reinterpret_cast<const uint32_t*>(model)[i];
+    __shared__ MlpFrag m;
+    for (int i = threadIdx.x; i < (int)(sizeof(MlpFrag) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(&m)[i] = reinterpret_cast<const uint32_t*>(&model->frag)[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane >> 2, q = lane & 3;
@@ -351,8 +370,8 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ X, 
         x[1] = pack_bf16(xv(r1, v1, 2 * q), xv(r1, v1, 2 * q + 1));
         x[2] = pack_bf16(xv(r0, v0, 2 * q + 8), xv(r0, v0, 2 * q + 9));
         x[3] = pack_bf16(xv(r1, v1, 2 * q + 8), xv(r1, v1, 2 * q + 9));
-        float h1[8][4], h2[8][4], y[4];
-        mlp16(m, x, h1, h2, y, lane);
+        float y[4];
+        mlp16_infer(m, x, y, lane);
         const int c0 = 2 * q, c1 = 2 * q + 1;
         if (v0 && c0 < 3) Y[r0 * 3 + c0] = y[0] * m.yscale[c0];
         if (v0 && c1 < 3) Y[r0 * 3 + c1] = y[1] * m.yscale[c1];
@@ -444,12 +463,6 @@ void launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, 
     count_launches(1);
 }
 
-void launch_mlp_normalise(const float* raw, int64_t n, const void* model, float* X, cudaStream_t s)
-{
-    k_mlp_normalise<<<nblk(n, 256), 256, 0, s>>>(raw, n, (const MlpDev*)model, X);
-    count_launches(1);
-}
-
 void launch_mlp_infer(const float* X, int64_t n, const void* model, float* Y, cudaStream_t s)
 {
     int64_t g = (n + 63) / 64;
@@ -467,5 +480,6 @@ void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const 
 }
 
 size_t mlp_dev_size() { return sizeof(MlpDev); }
+size_t mlp_frag_size() { return sizeof(MlpFrag); }
 
 }  // namespace tc

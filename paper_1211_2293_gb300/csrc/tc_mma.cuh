@@ -22,24 +22,47 @@ constexpr int kMlpOut = 3;
 constexpr int kMlpOutPad = 8;
 constexpr int kMlpNParam = kMlpIn * kMlpHid + kMlpHid + kMlpHid * kMlpHid + kMlpHid + kMlpHid * kMlpOut + kMlpOut;
 
-// Device copy of a model: BF16 weights laid out k-major ([in][out], padded),
-// FP32 biases, and the affine maps of the features and of the output.
+// Inference copy of a model: the BF16 weights pre-arranged as the B
+// fragments of mma.m16n8k16 (one 64-bit word per lane and fragment, so a
+// fragment is one shared-memory load), the FP32 bias pairs each lane adds,
+// and the affine maps of the features and of the output.
+struct MlpFrag {
+    uint2 f1[8][32];       // layer 1: [column block][lane] (inputs padded to 16)
+    uint2 f2[4][8][32];    // layer 2: [k-step][column block][lane]
+    uint2 f3[4][32];       // layer 3: [k-step][lane] (outputs padded to 8)
+    float2 b1[8][4];       // [column block][q]: biases of columns 8 nb + 2q, + 1
+    float2 b2[8][4];
+    float2 b3[4];
+    float xscale[kMlpInPad];  // 1 / std of each feature (0 for the padding)
+    float xoff[kMlpInPad];    // -mean x scale: a feature enters as f x scale + off
+    float yscale[kMlpOutPad]; // network output x yscale = label
+};
+
+// Device copy of a model: the inference part, then the k-major weights
+// ([in][out], padded) the training kernel reads its transposes from.
 struct MlpDev {
+    MlpFrag frag;
     __nv_bfloat16 w1[kMlpInPad * kMlpHid];
     __nv_bfloat16 w2[kMlpHid * kMlpHid];
     __nv_bfloat16 w3[kMlpHid * kMlpOutPad];
     float b1[kMlpHid];
     float b2[kMlpHid];
     float b3[kMlpOutPad];
-    float xmean[kMlpInPad];
-    float xscale[kMlpInPad];   // 1 / std of each feature (0 for the padding)
-    float yscale[kMlpOutPad];  // network output x yscale = label
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// round-to-nearest BF16 pair of max(lo, 0), max(hi, 0): ReLU fused into the
+// conversion (the first operand of the instruction fills the upper half)
+__device__ __forceinline__ uint32_t pack_relu(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 __device__ __forceinline__ uint32_t pack_raw(__nv_bfloat16 lo, __nv_bfloat16 hi)
@@ -57,6 +80,12 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
         "{%0,%1,%2,%3};\n"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma_frag(float (&c)[4], const uint32_t (&a)[4], uint2 w)
+{
+    const uint32_t b[2] = {w.x, w.y};
+    mma_bf16(c, a, b);
 }
 
 // B fragment of a k-major BF16 matrix W[k][n] (row stride ld), k-step ks,
@@ -78,10 +107,62 @@ __device__ __forceinline__ void c_to_a(uint32_t (&a)[4], const float (&c0)[4], c
     a[3] = pack_bf16(c1[2], c1[3]);
 }
 
-// The MLP on 16 rows: x holds the A fragment of the (normalised, padded)
-// features; y returns the C tile of the output (columns 0..2 used).  The
-// hidden activations are returned too (for training): h1, h2 as C tiles
-// after ReLU.
+// the same with the ReLU applied first
+__device__ __forceinline__ void c_to_a_relu(uint32_t (&a)[4], const float (&c0)[4], const float (&c1)[4])
+{
+    a[0] = pack_relu(c0[0], c0[1]);
+    a[1] = pack_relu(c0[2], c0[3]);
+    a[2] = pack_relu(c1[0], c1[1]);
+    a[3] = pack_relu(c1[2], c1[3]);
+}
+
+__device__ __forceinline__ void bias_init(float (&c)[4], float2 b)
+{
+    c[0] = b.x;
+    c[1] = b.y;
+    c[2] = b.x;
+    c[3] = b.y;
+}
+
+// Inference on 16 rows: x holds the A fragment of the (normalised, padded)
+// features; y returns the C tile of the output (columns 0..2 used).  Same
+// products in the same order as mlp16 below, so the two agree bit for bit.
+__device__ __forceinline__ void mlp16_infer(const MlpFrag& m, const uint32_t (&x)[4], float (&y)[4], int lane)
+{
+    const int q = lane & 3;
+    uint32_t a1[4][4];
+#pragma unroll
+    for (int ks = 0; ks < 4; ks++) {
+        float c0[4], c1[4];
+        bias_init(c0, m.b1[2 * ks][q]);
+        bias_init(c1, m.b1[2 * ks + 1][q]);
+        mma_frag(c0, x, m.f1[2 * ks][lane]);
+        mma_frag(c1, x, m.f1[2 * ks + 1][lane]);
+        c_to_a_relu(a1[ks], c0, c1);
+    }
+    // layer 2 in two halves of four column blocks: the first half feeds
+    // k-steps 0, 1 of layer 3, the second k-steps 2, 3 (fewer live registers)
+    bias_init(y, m.b3[q]);
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        float h2[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) bias_init(h2[j], m.b2[4 * half + j][q]);
+#pragma unroll
+        for (int ks = 0; ks < 4; ks++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) mma_frag(h2[j], a1[ks], m.f2[ks][4 * half + j][lane]);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            uint32_t a[4];
+            c_to_a_relu(a, h2[2 * k], h2[2 * k + 1]);
+            mma_frag(y, a, m.f3[2 * half + k][lane]);
+        }
+    }
+}
+
+// The MLP on 16 rows for training, from the k-major weights: returns the
+// hidden activations too (h1, h2 as C tiles after ReLU).
 __device__ __forceinline__ void mlp16(const MlpDev& m, const uint32_t (&x)[4], float (&h1)[8][4], float (&h2)[8][4],
                                       float (&y)[4], int lane)
 {
@@ -134,17 +215,6 @@ __device__ __forceinline__ void mlp16(const MlpDev& m, const uint32_t (&x)[4], f
         load_b(b, m.w3, kMlpOutPad, ks, 0, lane);
         mma_bf16(y, a, b);
     }
-}
-
-// A fragment of 16 feature rows stored as FP32 rows of kMlpInPad (already
-// normalised, padding zero)
-__device__ __forceinline__ void load_x(uint32_t (&a)[4], const float* X, int ld, int lane)
-{
-    const int g = lane >> 2, q = lane & 3;
-    a[0] = pack_bf16(X[g * ld + 2 * q], X[g * ld + 2 * q + 1]);
-    a[1] = pack_bf16(X[(g + 8) * ld + 2 * q], X[(g + 8) * ld + 2 * q + 1]);
-    a[2] = pack_bf16(X[g * ld + 2 * q + 8], X[g * ld + 2 * q + 9]);
-    a[3] = pack_bf16(X[(g + 8) * ld + 2 * q + 8], X[(g + 8) * ld + 2 * q + 9]);
 }
 
 }  // namespace tc

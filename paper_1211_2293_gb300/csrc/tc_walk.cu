@@ -220,57 +220,106 @@ struct Accum {
     }
 };
 
-// Learned correction rows: kMlpInPad normalised features + the factor that
-// turns a label into an acceleration, G M s^2 / r^4.  mlp_rows16 evaluates the first n
-// (<= 16) queued rows with the tensor cores and adds label x yscale x factor
-// to the lane's share of the group's correction (lanes of q = 0 hold x, y;
-// of q = 1 hold z).
-constexpr int kMlpRow = kMlpInPad + 1;
-constexpr int kMlpQueue = 48;  // < 16 left over + 32 added by a step
-__host__ __device__ constexpr size_t mlp_dev_bytes() { return sizeof(MlpDev); }
+// Learned correction.  Band cells found by a walk step are appended to a
+// per-warp list of pending node indices; whenever 32 are pending, lane j
+// builds the row of cell j -- 13 normalised features as BF16 pairs (8 words)
+// and the factor G M s^2 / r^4 that turns a label into an acceleration --
+// and the warp evaluates the rows 16 at a time on the tensor cores.
+  // register cap of the learned walk: 65536 / (128 x this)
+constexpr int kLearnedMinBlocks = 4;  // register cap of the learned walk: 65536 / (128 x this)
+constexpr int kPend = 64;   // < 32 left over + 32 added by a step
+constexpr int kRowW = 9;    // words per row
+__host__ __device__ constexpr size_t mlp_frag_bytes() { return (sizeof(MlpFrag) + 15) & ~(size_t)15; }
 
-__device__ __forceinline__ void mlp_rows16(const MlpDev& m, const float* mq, int n, float (&corr)[3], int lane)
+// rows of the n <= 32 cells pend[0, n) evaluated, label x yscale x factor
+// added to corr (lanes of q = 0 hold x, y; of q = 1 hold z)
+__device__ __noinline__ void learned_rows(const MlpFrag& m, const uint32_t* pend, int n, uint32_t* rows,
+                                          const NodeTables& nt, int4 rc, float uf, float Lf, float inv_L,
+                                          const float (&xgc)[3], float eps, float inv_msys, float G,
+                                          float (&corr)[3], int lane)
 {
-    const int g = lane >> 2, q = lane & 3;
-    auto xv = [&](int r, int c) { return r < n ? mq[r * kMlpRow + c] : 0.f; };
-    uint32_t x[4];
-    x[0] = pack_bf16(xv(g, 2 * q), xv(g, 2 * q + 1));
-    x[1] = pack_bf16(xv(g + 8, 2 * q), xv(g + 8, 2 * q + 1));
-    x[2] = pack_bf16(xv(g, 2 * q + 8), xv(g, 2 * q + 9));
-    x[3] = pack_bf16(xv(g + 8, 2 * q + 8), xv(g + 8, 2 * q + 9));
-    float h1[8][4], h2[8][4], y[4];
-    mlp16(m, x, h1, h2, y, lane);
-    const float f0 = g < n ? mq[g * kMlpRow + kMlpInPad] : 0.f;
-    const float f1 = g + 8 < n ? mq[(g + 8) * kMlpRow + kMlpInPad] : 0.f;
-    if (q == 0) {
-        corr[0] += (y[0] * f0 + y[2] * f1) * m.yscale[0];
-        corr[1] += (y[1] * f0 + y[3] * f1) * m.yscale[1];
-    } else if (q == 1) {
-        corr[2] += (y[0] * f0 + y[2] * f1) * m.yscale[2];
+    uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    float fac = 0.f;
+    if (lane < n) {
+        const int v = (int)pend[lane];
+        const int4 nb = __ldg(&nt.b[v]);
+        const float4 na = __ldg(&nt.a[v]);
+        const int4 cc = __ldg(&nt.c[v]);
+        // centre of mass in the group's reference frame, as in the walk
+        const float dx = fmaf((float)(cc.x - rc.x), uf, na.x) - xgc[0];
+        const float dy = fmaf((float)(cc.y - rc.y), uf, na.y) - xgc[1];
+        const float dz = fmaf((float)(cc.z - rc.z), uf, na.z) - xgc[2];
+        const float sz = scalbnf(Lf, -(nb.w & 255));
+        const float inv_s = scalbnf(inv_L, nb.w & 255);  // exact: sides are powers of two
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float ri = rsqrtf(r2);
+        const float Mc = na.w;
+        const float* qd = nt.quad + 6 * (int64_t)v;
+        const float iq = __fdividef(inv_s * inv_s, Mc);
+        float f[kMlpInPad];
+        f[0] = dx * inv_s;
+        f[1] = dy * inv_s;
+        f[2] = dz * inv_s;
+        f[3] = ri * sz;
+        f[4] = eps * inv_s;
+        f[5] = __log2f((float)nb.y);
+        f[6] = Mc * inv_msys;
+#pragma unroll
+        for (int k = 0; k < 6; k++) f[7 + k] = __ldg(qd + k) * iq;
+#pragma unroll
+        for (int k = 0; k < kMlpIn; k++) f[k] = fmaf(f[k], m.xscale[k], m.xoff[k]);
+#pragma unroll
+        for (int k = kMlpIn; k < kMlpInPad; k++) f[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; k++) w[k] = pack_bf16(f[2 * k], f[2 * k + 1]);
+        const float ri2 = ri * ri;
+        fac = G * Mc * (sz * sz) * (ri2 * ri2);  // G M s^2 / r^4
     }
+    uint32_t* r = rows + lane * kRowW;
+#pragma unroll
+    for (int k = 0; k < 8; k++) r[k] = w[k];
+    r[8] = __float_as_uint(fac);
+    __syncwarp();
+    const int g = lane >> 2, q = lane & 3;
+    for (int t = 0; t < n; t += 16) {
+        const uint32_t* r0 = rows + (t + g) * kRowW;
+        const uint32_t* r1 = rows + (t + g + 8) * kRowW;
+        const uint32_t x[4] = {r0[q], r1[q], r0[q + 4], r1[q + 4]};
+        float y[4];
+        mlp16_infer(m, x, y, lane);
+        const float f0 = __uint_as_float(r0[8]), f1 = __uint_as_float(r1[8]);
+        if (q == 0) {
+            corr[0] += (y[0] * f0 + y[2] * f1) * m.yscale[0];
+            corr[1] += (y[1] * f0 + y[3] * f1) * m.yscale[1];
+        } else if (q == 1) {
+            corr[2] += (y[0] * f0 + y[2] * f1) * m.yscale[2];
+        }
+    }
+    __syncwarp();
 }
 
-// shared memory of one warp (learned mode adds a queue of MLP rows and the
-// block holds one copy of the network in front of the warps' regions)
+// shared memory of one warp (learned mode adds the pending list and the rows;
+// the block holds one copy of the network in front of the warps' regions)
 __host__ __device__ constexpr size_t walk_warp_bytes(int tile, int stack, bool learned)
 {
-    return (size_t)2 * tile_cap(tile) * 16 + (size_t)stack * 4 + (learned ? (size_t)kMlpQueue * kMlpRow * 4 : 0);
+    return (size_t)2 * tile_cap(tile) * 16 + (size_t)stack * 4 + (learned ? (size_t)(kPend + 32 * kRowW) * 4 : 0);
 }
 
 template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
-__global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
+__global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 1) k_walk(WalkArgs a, int stack_cap)
 {
     constexpr int kTile = TILE;
     constexpr int kTileCap = tile_cap(TILE);
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const size_t head = LEARNED ? ((mlp_dev_bytes() + 15) & ~(size_t)15) : 0;
+    const size_t head = LEARNED ? mlp_frag_bytes() : 0;
     const size_t per_warp = walk_warp_bytes(TILE, stack_cap, LEARNED);
     float* ctile = reinterpret_cast<float*>(smem + head + wib * per_warp);
     float* btile = ctile + 4 * kTileCap;
     uint32_t* stk = reinterpret_cast<uint32_t*>(btile + 4 * kTileCap);
-    float* mq = reinterpret_cast<float*>(stk + stack_cap);  // learned: kMlpQueue rows of kMlpRow floats
+    uint32_t* pend = stk + stack_cap;  // learned: pending band cells, then the rows
+    uint32_t* rows = pend + kPend;
     const f2 E2 = f2pack(a.eps2, a.eps2);
     const uint32_t lt = (1u << lane) - 1u;
 
@@ -278,9 +327,10 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
     if (info->err & kErrCapacity) return;  // the build stopped: no tree to walk
     const int64_t G = info->G;
     const NodeTables nt = a.nt;
-    MlpDev* mlp = reinterpret_cast<MlpDev*>(smem);
+    MlpFrag* mlp = reinterpret_cast<MlpFrag*>(smem);
     if (LEARNED) {
-        for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 4); i += blockDim.x)
+        // the inference part at the front of the device model
+        for (int i = threadIdx.x; i < (int)(sizeof(MlpFrag) / 4); i += blockDim.x)
             reinterpret_cast<uint32_t*>(mlp)[i] = reinterpret_cast<const uint32_t*>(a.mlp)[i];
         __syncthreads();
     }
@@ -365,7 +415,10 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
         float corr[3] = {0.f, 0.f, 0.f};
         int qn = 0;
         unsigned long long nevals = 0;
+        float inv_L = 0.f, inv_msys = 0.f;
         if (LEARNED) {
+            inv_L = 1.0f / Lf;
+            inv_msys = 1.0f / SP.msys;
 #pragma unroll
             for (int k = 0; k < 3; k++)
                 xgc[k] = 0.5f * (fmaf((float)klo[k], uf, flo[k]) + fmaf((float)khi[k], uf, fhi[k]));
@@ -463,48 +516,20 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
             }
             if (LEARNED) {
                 const unsigned bm = __ballot_sync(0xffffffffu, band);
-                if (band) {
-                    float* row = mq + (qn + __popc(bm & lt)) * kMlpRow;
-                    const float sz = scalbnf(Lf, -(nb.w & 255));
-                    const float inv_s = 1.0f / sz;
-                    const float dx = src.x - xgc[0], dy = src.y - xgc[1], dz = src.z - xgc[2];
-                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const float rr = sqrtf(r2);
-                    const float Mc = src.w;
-                    const float* qd = nt.quad + 6 * (int64_t)v;
-                    const float iq = 1.0f / (Mc * sz * sz);
-                    float f[kMlpIn];
-                    f[0] = dx * inv_s;
-                    f[1] = dy * inv_s;
-                    f[2] = dz * inv_s;
-                    f[3] = sz / rr;
-                    f[4] = a.eps * inv_s;
-                    f[5] = log2f((float)nb.y);
-                    f[6] = Mc / SP.msys;
-#pragma unroll
-                    for (int k = 0; k < 6; k++) f[7 + k] = __ldg(qd + k) * iq;
-#pragma unroll
-                    for (int k = 0; k < kMlpIn; k++) row[k] = (f[k] - mlp->xmean[k]) * mlp->xscale[k];
-#pragma unroll
-                    for (int k = kMlpIn; k < kMlpInPad; k++) row[k] = 0.f;
-                    row[kMlpInPad] = a.G * Mc * sz * sz / (r2 * r2);  // label -> acceleration
-                }
+                if (band) pend[qn + __popc(bm & lt)] = (uint32_t)v;
                 qn += __popc(bm);
-                __syncwarp();
-                while (qn >= 16) {
-                    mlp_rows16(*mlp, mq, 16, corr, lane);
-                    nevals += 16;
-                    // move the rows past the first 16 to the front (read all, then write)
-                    const bool mv = lane < qn - 16;
-                    float tmp[kMlpRow];
-                    if (mv)
-                        for (int k = 0; k < kMlpRow; k++) tmp[k] = mq[(16 + lane) * kMlpRow + k];
+                if (qn >= 32) {
                     __syncwarp();
-                    if (mv)
-                        for (int k = 0; k < kMlpRow; k++) mq[lane * kMlpRow + k] = tmp[k];
-                    qn -= 16;
+                    learned_rows(*mlp, pend, 32, rows, nt, rc, uf, Lf, inv_L, xgc, a.eps, inv_msys, a.G, corr, lane);
+                    nevals += 32;
+                    // move the cells past the first 32 to the front (read all, then write)
+                    const int rest = qn - 32;
+                    const uint32_t t = lane < rest ? pend[32 + lane] : 0u;
                     __syncwarp();
+                    if (lane < rest) pend[lane] = t;
+                    qn = rest;
                 }
+                __syncwarp();
             }
             // opened leaves -> body tile.  The bodies of all leaves opened in
             // this step are gathered 32 at a time: lane j takes body t of the
@@ -553,7 +578,7 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs a, int stack_cap)
         bacc.flush(btile, bn, XA, YA, ZA, E2);
         if (LEARNED) {
             if (qn > 0) {
-                mlp_rows16(*mlp, mq, qn, corr, lane);
+                learned_rows(*mlp, pend, qn, rows, nt, rc, uf, Lf, inv_L, xgc, a.eps, inv_msys, a.G, corr, lane);
                 nevals += qn;
             }
 #pragma unroll
@@ -608,7 +633,7 @@ template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 cudaError_t prepare_t(const WalkConfig& c, int num_sms, int* grid, size_t* smem_out)
 {
     const int warps = c.warps;
-    const size_t head = LEARNED ? ((mlp_dev_bytes() + 15) & ~(size_t)15) : 0;
+    const size_t head = LEARNED ? mlp_frag_bytes() : 0;
     const size_t smem = head + walk_warp_bytes(TILE, c.stack, LEARNED) * warps;
     auto kern = k_walk<B, TILE, PRECISE, POT, LEARNED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -232,19 +232,20 @@ def test_training_pairs_match_oracle(tc):
 
 
 def test_training_reduces_loss_and_error(tc):
+    """Pairs from one Plummer sphere train the network on the GPU; on another
+    sphere the learned walk at theta 0.9 has a smaller RMS error against the
+    direct sum than the plain walk at the same theta."""
     theta, eps, band = 0.9, 1e-3, 0.5
-    ctx_tr, _, _ = _built(tc, 65536, 21)
+    ctx_tr, _, _ = _built(tc, 131072, 21)
     X, T, F, _, _ = ctx_tr.mlp_pairs(theta, eps, band, 1.0, 5, 2_000_000)
-    assert len(X) > 50000
+    assert len(X) > 200000
     losses = ctx_tr.mlp_train(X, T, ctx_tr.mlp_weights(F), epochs=40, batch=1024, lr=2e-3, seed=3, band=band)
     assert np.all(np.isfinite(losses))
-    assert losses[-1] < 0.5 * losses[0]
+    assert losses[-1] < 0.2 * losses[0]
     model, _ = ctx_tr.mlp_get()
-    # a different system: plain vs learned at the same theta against the
-    # oracle's direct sum on a sample
-    n = 32768
+    n = 65536
     ctx, p, m = _built(tc, n, 22)
-    idx = inputs.sample_indices(n, 1024, 23)
+    idx = inputs.sample_indices(n, 2048, 23)
     ad, _ = oracle.direct(p, m, eps, 1.0, idx=idx, want_pot=False)
     ctx.forces(theta, eps)
     a_plain = ctx.get_acc()[idx].astype(np.float64)
@@ -257,8 +258,9 @@ def test_training_reduces_loss_and_error(tc):
         return np.sqrt(np.mean(np.sum((a - ad) ** 2, 1) / np.sum(ad ** 2, 1)))
 
     e_plain, e_learn = rms(a_plain), rms(a_learn)
-    print(f"theta {theta}: plain rms {e_plain:.3e}, learned rms {e_learn:.3e}")
-    assert e_learn < 0.9 * e_plain
+    print(f"theta {theta}: plain rms {e_plain:.3e}, learned rms {e_learn:.3e}, losses {losses[0]:.3g} -> "
+          f"{losses[-1]:.3g}")
+    assert e_learn < 0.85 * e_plain
 
 
 def test_learned_step_and_config_errors(tc):
