@@ -117,6 +117,28 @@ __device__ __forceinline__ int warp_incl_scan_i(int x)
     return x;
 }
 
+// exclusive warp prefix sum of x in [0, 15] (and the warp total) from four
+// ballots: no shuffle chain
+__device__ __forceinline__ int warp_excl_small(int x, unsigned lt, int& total)
+{
+    int e = 0, t = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const unsigned bk = __ballot_sync(0xffffffffu, (x >> k) & 1);
+        e += __popc(bk & lt) << k;
+        t += __popc(bk) << k;
+    }
+    total = t;
+    return e;
+}
+
+// Lf x 2^-level for a power-of-two Lf: exponent arithmetic when the result
+// stays a normal float (fast, decided once per group), scalbnf otherwise
+__device__ __forceinline__ float pow2_down(float Lf, int level, bool fast)
+{
+    return fast ? __int_as_float(__float_as_int(Lf) - (level << 23)) : scalbnf(Lf, -level);
+}
+
 // error-free sum: s + c absorbs x (Knuth's TwoSum)
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x)
 {
@@ -125,6 +147,15 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x)
     float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
     s = t;
     c = __fadd_rn(c, e);
+}
+
+// 1/sqrt(x) on the SFU, flushing subnormals (x >= eps^2 > 0 is normal here),
+// so no range fix-up surrounds the approximation
+__device__ __forceinline__ float rsqrt_sfu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // The force loop: npairs pairs of sources against the lane's B bodies.
@@ -137,7 +168,7 @@ __device__ __forceinline__ void sum_tile(const float* __restrict__ tile, int npa
                                          f2 (&ay)[B], f2 (&az)[B], f2 (&ph)[B])
 {
     const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
-#pragma unroll 2
+#pragma unroll 8
     for (int p = 0; p < npairs; p++) {
         const ulonglong2 xy = t2[2 * p];
         const ulonglong2 zm = t2[2 * p + 1];
@@ -149,7 +180,7 @@ __device__ __forceinline__ void sum_tile(const float* __restrict__ tile, int npa
             const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2fma(dx, dx, E2)));
             float r2a, r2b;
             f2unpack(r2, r2a, r2b);
-            const f2 ri = f2pack(rsqrtf(r2a), rsqrtf(r2b));
+            const f2 ri = f2pack(rsqrt_sfu(r2a), rsqrt_sfu(r2b));
             const f2 mri = f2mul(zm.y, ri);
             const f2 mri3 = f2mul(mri, f2mul(ri, ri));
             ax[b] = f2fma(dx, mri3, ax[b]);
@@ -306,7 +337,7 @@ __host__ __device__ constexpr size_t walk_warp_bytes(int tile, int stack, bool l
 }
 
 template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
-__global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 1) k_walk(WalkArgs a, int stack_cap)
+__global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 4) k_walk(WalkArgs a, int stack_cap)
 {
     constexpr int kTile = TILE;
     constexpr int kTileCap = tile_cap(TILE);
@@ -429,6 +460,8 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 1) k_walk(W
         bacc.init();
         int cn = 0, bn = 0, Lc = 0, Lb = 0;
         unsigned long long hsh = 0;
+        const bool want_hash = a.hash != nullptr;  // list hashes only for verification
+        const bool fast_side = ((__float_as_int(Lf) >> 23) & 255) > kMaxLevel + 1;
         bool overflow = false;
         int sp = 1;
         if (lane == 0) stk[0] = sysid;  // the system's root: holds every body, always opened
@@ -462,7 +495,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 1) k_walk(W
                         const float e = fmaxf(fmaxf(lo_c - off[k], off[k] - hi_c), 0.f);
                         e2 = fmaf(e, e, e2);
                     }
-                    const float s = scalbnf(Lf, -(nb.w & 255));
+                    const float s = pow2_down(Lf, nb.w & 255, fast_side);
                     acc = (s * s) < a.theta2 * e2;
                     band_e2 = e2;
                     if (acc) {
@@ -480,20 +513,20 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 1) k_walk(W
                 }
             }
             // opened internal nodes push their children
-            const int npush = oint ? (nb.w >> 8) : 0;
-            const int incl = warp_incl_scan_i(npush);
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            const int npush = oint ? (nb.w >> 8) : 0;  // at most 8
+            int tot;
+            const int excl = warp_excl_small(npush, lt, tot);
             if (sp + tot > stack_cap) {
                 overflow = true;
                 break;
             }
-            for (int k = 0; k < npush; k++) stk[sp + incl - npush + k] = (uint32_t)(nb.z + k);
+            for (int k = 0; k < npush; k++) stk[sp + excl + k] = (uint32_t)(nb.z + k);
             sp += tot;
             // accepted cells -> cell tile
             const unsigned am = __ballot_sync(0xffffffffu, acc);
             if (acc) {
                 put_entry(ctile, cn + __popc(am & lt), src);
-                hsh += mix64(2ull * (unsigned)v + 1ull);
+                if (want_hash) hsh += mix64(2ull * (unsigned)v + 1ull);
             }
             cn += __popc(am);
             Lc += __popc(am);
@@ -537,7 +570,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 1) k_walk(W
             // the lanes' exclusive offsets.
             const unsigned lm = __ballot_sync(0xffffffffu, oleaf);
             if (lm) {
-                if (oleaf) hsh += mix64(2ull * (unsigned)v + 2ull);
+                if (want_hash && oleaf) hsh += mix64(2ull * (unsigned)v + 2ull);
                 const int cnt = oleaf ? nb.y : 0;
                 const int incl_c = warp_incl_scan_i(cnt);
                 const int excl_c = incl_c - cnt;
@@ -613,8 +646,10 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 1) k_walk(W
             }
         }
         // per-group list statistics
+        if (want_hash) {
 #pragma unroll
-        for (int o = 16; o; o >>= 1) hsh += __shfl_xor_sync(0xffffffffu, hsh, o);
+            for (int o = 16; o; o >>= 1) hsh += __shfl_xor_sync(0xffffffffu, hsh, o);
+        }
         if (lane == 0) {
             const int gc = gend - gfirst;
             atomicAdd(&a.info->interactions, (unsigned long long)gc * (unsigned long long)(Lc + Lb));
