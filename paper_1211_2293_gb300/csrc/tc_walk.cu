@@ -168,7 +168,7 @@ __device__ __forceinline__ void sum_tile(const float* __restrict__ tile, int npa
                                          f2 (&ay)[B], f2 (&az)[B], f2 (&ph)[B])
 {
     const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
-#pragma unroll 8
+#pragma unroll(B >= 4 ? 2 : 8)
     for (int p = 0; p < npairs; p++) {
         const ulonglong2 xy = t2[2 * p];
         const ulonglong2 zm = t2[2 * p + 1];
