@@ -162,13 +162,13 @@ __device__ __forceinline__ float rsqrt_sfu(float x)
 // Body coordinates are held duplicated ({x, x}); the two halves of each
 // accumulator collect the even and the odd sources of the tile.
 //   r2 = |d|^2 + eps^2, ri = rsqrt(r2), a += d * m * ri^3, pot -= m * ri
-template <int B, bool POT>
+template <int B, bool POT, int UNROLL>
 __device__ __forceinline__ void sum_tile(const float* __restrict__ tile, int npairs, const f2 (&X)[B],
                                          const f2 (&Y)[B], const f2 (&Z)[B], f2 E2, f2 (&ax)[B],
                                          f2 (&ay)[B], f2 (&az)[B], f2 (&ph)[B])
 {
     const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
-#pragma unroll(B >= 4 ? 2 : 8)
+#pragma unroll(UNROLL)
     for (int p = 0; p < npairs; p++) {
         const ulonglong2 xy = t2[2 * p];
         const ulonglong2 zm = t2[2 * p + 1];
@@ -191,7 +191,7 @@ __device__ __forceinline__ void sum_tile(const float* __restrict__ tile, int npa
     }
 }
 
-template <int B, bool PRECISE, bool POT>
+template <int B, bool PRECISE, bool POT, int UNROLL>
 struct Accum {
     f2 ax[B], ay[B], az[B], ph[B];        // packed running sums (plain mode)
     float sx[B], sy[B], sz[B], sp[B];     // running sums (precise mode)
@@ -215,7 +215,7 @@ struct Accum {
             f2 tx[B], ty[B], tz[B], tp[B];
 #pragma unroll
             for (int b = 0; b < B; b++) tx[b] = ty[b] = tz[b] = tp[b] = 0ull;
-            sum_tile<B, POT>(tile, np, X, Y, Z, E2, tx, ty, tz, tp);
+            sum_tile<B, POT, UNROLL>(tile, np, X, Y, Z, E2, tx, ty, tz, tp);
 #pragma unroll
             for (int b = 0; b < B; b++) {
                 two_sum_acc(sx[b], cx[b], f2sum(tx[b]));
@@ -224,7 +224,7 @@ struct Accum {
                 if (POT) two_sum_acc(sp[b], cp[b], f2sum(tp[b]));
             }
         } else {
-            sum_tile<B, POT>(tile, np, X, Y, Z, E2, ax, ay, az, ph);
+            sum_tile<B, POT, UNROLL>(tile, np, X, Y, Z, E2, ax, ay, az, ph);
         }
         __syncwarp();
     }
@@ -337,7 +337,7 @@ __host__ __device__ constexpr size_t walk_warp_bytes(int tile, int stack, bool l
 }
 
 template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
-__global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 4) k_walk(WalkArgs a, int stack_cap)
+__global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3 : 4)) k_walk(WalkArgs a, int stack_cap)
 {
     constexpr int kTile = TILE;
     constexpr int kTileCap = tile_cap(TILE);
@@ -455,7 +455,11 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : 4) k_walk(W
                 xgc[k] = 0.5f * (fmaf((float)klo[k], uf, flo[k]) + fmaf((float)khi[k], uf, fhi[k]));
         }
 
-        Accum<B, PRECISE, POT> cacc, bacc;
+        // force-loop unroll: deep for one or two bodies per lane; shallow with
+        // four (registers) and in the learned walk (its code must stay in the
+        // instruction cache next to the network's)
+        constexpr int kUnroll = LEARNED ? 2 : (B >= 4 ? 4 : 8);
+        Accum<B, PRECISE, POT, kUnroll> cacc, bacc;
         cacc.init();
         bacc.init();
         int cn = 0, bn = 0, Lc = 0, Lb = 0;
