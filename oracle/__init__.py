@@ -76,6 +76,8 @@ def _load():
     lib.or_tree_get_groups.argtypes = [P, P, P, P]
     lib.or_tree_walk.argtypes = [P, D, D, D, I64, I64, P, P, P, P, P, P, P]
     lib.or_tree_walk.restype = I64
+    lib.or_tree_walk_order.argtypes = [P, D, D, D, ctypes.c_int, I64, I64, P, P, P, P, P, P, P]
+    lib.or_tree_walk_order.restype = I64
     lib.or_tree_test.argtypes = [P, I64, I64, D]
     lib.or_tree_test.restype = ctypes.c_int
     lib.or_direct.argtypes = [P, P, I64, D, D, P, I64, P, P]
@@ -197,13 +199,13 @@ class Tree:
         lv = self.level if v is None else self.level[v]
         return np.ldexp(self.L, -np.asarray(lv))
 
-    def walk(self, theta, eps, G=1.0, groups=None, want_pot=True):
+    def walk(self, theta, eps, G=1.0, groups=None, want_pot=True, quadrupole=False):
         """Walk + force for a range of groups (default: all).
 
         Returns dict with acc (n x 3, original order; NaN for bodies outside
         the walked groups), pot, amag (sum of |term| per body), ncell, nbody,
         hash, flag (per group, -1 for groups not walked) and the number of
-        interactions."""
+        interactions.  quadrupole: accepted cells add their quadrupole term."""
         if self.G == 0:
             raise RuntimeError("make_groups first")
         g0, g1 = (0, self.G) if groups is None else groups
@@ -214,8 +216,8 @@ class Tree:
         nbody = np.full(self.G, -1, dtype=np.int64)
         hsh = np.zeros(self.G, dtype=np.uint64)
         flag = np.full(self.G, -1, dtype=np.int32)
-        inter = self._lib.or_tree_walk(
-            self._h, float(theta), float(eps), float(G), int(g0), int(g1),
+        inter = self._lib.or_tree_walk_order(
+            self._h, float(theta), float(eps), float(G), int(bool(quadrupole)), int(g0), int(g1),
             _ptr(acc), _ptr(pot), _ptr(amag), _ptr(ncell), _ptr(nbody), _ptr(hsh), _ptr(flag),
         )
         return dict(acc=acc, pot=pot, amag=amag, ncell=ncell, nbody=nbody, hash=hsh, flag=flag,

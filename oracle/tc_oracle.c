@@ -582,6 +582,32 @@ static void add_force(const double *x, const double *y, double m, double eps2, d
     *mag += fabs(f) * sqrt(dx * dx + dy * dy + dz * dz);
 }
 
+/* Quadrupole term of a cell (mass centre y, second moments Q about it) on a
+ * body at x, from the second-order Taylor expansion of the softened
+ * potential -G m / sqrt(|x - y'|^2 + eps^2) about y'= y: with d = y - x and
+ * rho^2 = |d|^2 + eps^2,
+ *   phi_Q = -(G/2) (3 d.Qd / rho^5 - tr Q / rho^3)
+ *   a_Q   = G (-3 Qd / rho^5 + (7.5 d.Qd / rho^7 - 1.5 tr Q / rho^5) d). */
+static void add_quad(const double *x, const double *y, const double *q, double eps2, double G, double *a,
+                     double *phi, double *mag)
+{
+    double d[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+    double Qd[3] = {q[0] * d[0] + q[1] * d[1] + q[2] * d[2], q[1] * d[0] + q[3] * d[1] + q[4] * d[2],
+                    q[2] * d[0] + q[4] * d[1] + q[5] * d[2]};
+    double dQd = d[0] * Qd[0] + d[1] * Qd[1] + d[2] * Qd[2];
+    double tr = q[0] + q[3] + q[5];
+    double rho2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
+    double ri = 1.0 / sqrt(rho2);
+    double ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
+    double c = 7.5 * dQd * ri7 - 1.5 * tr * ri5;
+    for (int k = 0; k < 3; k++) {
+        double term = G * (-3.0 * Qd[k] * ri5 + c * d[k]);
+        a[k] += term;
+        *mag += fabs(term);
+    }
+    *phi -= 0.5 * G * (3.0 * dQd * ri5 - tr * ri3);
+}
+
 int or_tree_test(const or_tree *t, int64_t group, int64_t node, double theta)
 {
     walk_t w;
@@ -606,6 +632,13 @@ int or_tree_test(const or_tree *t, int64_t group, int64_t node, double theta)
 int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G, int64_t g_begin,
                      int64_t g_end, double *acc, double *pot, double *amag, int64_t *ncell,
                      int64_t *nbody, uint64_t *hash, int32_t *flag)
+{
+    return or_tree_walk_order(t, theta, eps, G, 0, g_begin, g_end, acc, pot, amag, ncell, nbody, hash, flag);
+}
+
+int64_t or_tree_walk_order(const or_tree *t, double theta, double eps, double G, int quadrupole,
+                           int64_t g_begin, int64_t g_end, double *acc, double *pot, double *amag,
+                           int64_t *ncell, int64_t *nbody, uint64_t *hash, int32_t *flag)
 {
     int64_t inter = 0;
     double eps2 = eps * eps;
@@ -639,6 +672,8 @@ int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G, int64
             for (int64_t k = 0; k < w.ncells; k++) {
                 int64_t c = w.cells[k];
                 add_force(xi, &t->com[3 * c], t->mass[c], eps2, G, a, &phi, &mag);
+                if (quadrupole)
+                    add_quad(xi, &t->com[3 * c], &t->quad[6 * c], eps2, G, a, &phi, &mag);
             }
             for (int64_t k = 0; k < w.nleaves; k++) {
                 int64_t v = w.leaves[k];

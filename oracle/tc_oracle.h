@@ -78,6 +78,17 @@ int64_t or_tree_walk(const or_tree *t, double theta, double eps, double G,
                      int64_t g_begin, int64_t g_end, double *acc, double *pot, double *amag,
                      int64_t *ncell, int64_t *nbody, uint64_t *hash, int32_t *flag);
 
+/* The same walk with, for quadrupole != 0, every accepted cell's quadrupole
+ * term added to its monopole: with d = com - x, rho^2 = |d|^2 + eps^2 and Q
+ * the cell's second moments about its centre of mass (second-order Taylor
+ * expansion of the softened potential),
+ *   phi_Q = -(G/2) (3 d.Qd / rho^5 - tr Q / rho^3)
+ *   a_Q   = G (-3 Qd / rho^5 + (7.5 d.Qd / rho^7 - 1.5 tr Q / rho^5) d).
+ * amag then also sums |a_Q| per component. */
+int64_t or_tree_walk_order(const or_tree *t, double theta, double eps, double G, int quadrupole,
+                           int64_t g_begin, int64_t g_end, double *acc, double *pot, double *amag,
+                           int64_t *ncell, int64_t *nbody, uint64_t *hash, int32_t *flag);
+
 /* For tests: the opening-test decision of one (group, node) pair:
  * 0 = open (contains a group body), 1 = open (too close), 2 = accept. */
 int or_tree_test(const or_tree *t, int64_t group, int64_t node, double theta);
