@@ -39,6 +39,7 @@ METRIC = "force evals (bodies/s) at RMS force err 1e-3: plain vs learned; % FP32
 N_DEFAULT = 1 << 20
 LEAF, EPS, DT, THETA, SEED = 16, 1e-3, 1e-4, 0.5, 0
 FLOPS_PER_INTERACTION = 20
+QUAD_FLOPS_PER_CELL = 55  # monopole + quadrupole term of one cell (FMA = 2)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "walk_uniform_1m.txt")
 WALK_SRC = os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", "tc_walk.cu")
@@ -525,10 +526,10 @@ def run_learned(args, rank, world, local_rank):
     idx = inputs.sample_indices(n_ev, 4096, seed=1)
     ad, _ = ctx.direct(idx, eps)
 
-    def measure(theta, learned, reps=5, band_eval=None):
+    def measure(theta, learned, reps=5, band_eval=None, quadrupole=False):
         if learned and band_eval is not None:
             ctx.mlp_set(model, band_eval)
-        ctx.set_config(learned=int(learned))
+        ctx.set_config(learned=int(learned), quadrupole=int(quadrupole))
         ctx.forces(theta, eps)
         ctx.sync()
         a = ctx.get_acc()[idx].astype(np.float64)
@@ -543,20 +544,24 @@ def run_learned(args, rank, world, local_rank):
         walk_ms = tim["walk_ms"] / reps
         st = ctx.lists(per_group=False)
         ev = ctx.mlp_evals() / (reps + 0.0) if learned else 0
+        flops = st["cells"] * (QUAD_FLOPS_PER_CELL if quadrupole else FLOPS_PER_INTERACTION) + \
+            st["bodies"] * FLOPS_PER_INTERACTION
+        ctx.set_config(quadrupole=0)
         return {"theta": theta, "rms_err": rms, "walk_ms": walk_ms, "bodies_per_s": n_ev / (walk_ms / 1e3),
-                "interactions_per_body": st["interactions"] / n_ev, "mlp_evals_per_body": ev / n_ev}
+                "interactions_per_body": st["interactions"] / n_ev, "mlp_evals_per_body": ev / n_ev,
+                "fp32_tflops": flops / (walk_ms / 1e3) / 1e12}
 
-    def iso(learned, lo, hi, goal=1e-3, it=9, band_eval=None):
+    def iso(learned, lo, hi, goal=1e-3, it=9, band_eval=None, quadrupole=False):
         """largest theta in [lo, hi] whose RMS error is <= goal (bisection)"""
-        if measure(lo, learned, reps=1, band_eval=band_eval)["rms_err"] > goal:
+        if measure(lo, learned, reps=1, band_eval=band_eval, quadrupole=quadrupole)["rms_err"] > goal:
             return None
         for _ in range(it):
             mid = 0.5 * (lo + hi)
-            if measure(mid, learned, reps=1, band_eval=band_eval)["rms_err"] <= goal:
+            if measure(mid, learned, reps=1, band_eval=band_eval, quadrupole=quadrupole)["rms_err"] <= goal:
                 lo = mid
             else:
                 hi = mid
-        r = measure(lo, learned, band_eval=band_eval)
+        r = measure(lo, learned, band_eval=band_eval, quadrupole=quadrupole)
         if learned:
             r["band"] = band_eval
         return r
@@ -564,6 +569,9 @@ def run_learned(args, rank, world, local_rank):
     res = {"plain_theta_0.5": measure(0.5, False), "plain_theta_0.9": measure(0.9, False),
            "learned_theta_0.9": measure(0.9, True, band_eval=0.5)}
     iso_plain = iso(False, 0.5, 1.0)
+    # the classical comparator: every accepted cell's quadrupole term
+    iso_quad = iso(False, 0.5, 1.2, quadrupole=True)
+    res["quadrupole_theta_0.9"] = measure(0.9, False, quadrupole=True)
     # the band is the correction's one free parameter: each candidate at its
     # own iso-accuracy theta, the fastest reported
     iso_bands = [r for r in (iso(True, 0.5, 1.0, band_eval=b) for b in (0.4, 0.5, 0.6)) if r is not None]
@@ -578,6 +586,9 @@ def run_learned(args, rank, world, local_rank):
                        "n_bodies": n_ev},
             "value_is": "learned walk bodies/s at the largest theta with RMS error <= 1e-3",
             "iso_accuracy_1e-3": {"plain": iso_plain, "learned": iso_learned, "learned_per_band": iso_bands,
+                                  "quadrupole": iso_quad,
+                                  "quadrupole_over_plain": (iso_quad["bodies_per_s"] / iso_plain["bodies_per_s"]
+                                                            if iso_quad and iso_plain else None),
                                   "learned_over_plain": (iso_learned["bodies_per_s"] / iso_plain["bodies_per_s"]
                                                          if iso_learned and iso_plain else None)},
             "fixed_theta": res,

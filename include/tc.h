@@ -65,7 +65,10 @@ typedef struct tc_ctx tc_ctx;
  *             launches issued one by one
  *   learned   1: add the learned far-field correction of tc_mlp_set /
  *             tc_mlp_train to the walk (needs precise = 1, want_pot = 0,
- *             quad = 1)                                                   */
+ *             quad = 1, quadrupole = 0)
+ *   quadrupole 1: every accepted cell adds its quadrupole term to its
+ *             monopole (second-order expansion of the softened potential
+ *             about the centre of mass; needs precise = 1, quad = 1)      */
 typedef struct {
     int32_t gmax;
     int32_t warps;
@@ -78,6 +81,7 @@ typedef struct {
     int32_t tile;
     int32_t graph;
     int32_t learned;
+    int32_t quadrupole;
 } tc_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a
@@ -162,8 +166,9 @@ int tc_get_systems(tc_ctx *ctx, int64_t *nsys, double *cubes);
 
 /* Per-group list lengths of the last force phase (needs verify = 1):
  * accepted cells, bodies of opened leaves, order-independent hash of the
- * accepted cells and opened leaves; and totals (interactions = sum over
- * groups of group size x list length).  Any pointer may be NULL. */
+ * accepted cells and opened leaves; and totals over groups of group size x
+ * list length: interactions = cells + bodies, cells = body-cell terms,
+ * bodies = body-body terms.  Any pointer may be NULL. */
 int tc_get_lists(tc_ctx *ctx, int32_t *ncell, int32_t *nbody, uint64_t *hash,
                  int64_t *interactions, int64_t *cells, int64_t *bodies);
 

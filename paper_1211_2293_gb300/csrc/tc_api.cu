@@ -418,6 +418,7 @@ int prepare_forces(tc_ctx* c)
     wc.blocks_per_sm = c->cfg.blocks_per_sm;
     wc.tile = c->cfg.tile;
     wc.learned = c->cfg.learned && c->have_mlp;
+    wc.quadw = c->cfg.quadrupole;
     int64_t st = c->cfg.stack;
     if (c->cap_m < st) st = c->cap_m < 32 ? 32 : c->cap_m;  // a stack of M entries cannot overflow
     st = (st + 3) & ~(int64_t)3;                            // keeps every warp's tiles 16-byte aligned
@@ -589,6 +590,8 @@ int tc_create(tc_ctx** out, void* stream)
     c->cfg.quad = 0;
     c->cfg.tile = 128;
     c->cfg.graph = 1;
+    c->cfg.learned = 0;
+    c->cfg.quadrupole = 0;
     *out = c;
     return TC_OK;
 }
@@ -625,8 +628,10 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
     if (cfg->blocks_per_sm < 0) return fail(c, TC_EINVAL, "blocks_per_sm must be >= 0");
     if (cfg->tile != 64 && cfg->tile != 128 && cfg->tile != 256)
         return fail(c, TC_EINVAL, "tile must be 64, 128 or 256 (got %d)", cfg->tile);
-    if (cfg->learned && (!cfg->precise || cfg->want_pot || !cfg->quad))
-        return fail(c, TC_EINVAL, "learned = 1 needs precise = 1, want_pot = 0 and quad = 1");
+    if (cfg->learned && (!cfg->precise || cfg->want_pot || !cfg->quad || cfg->quadrupole))
+        return fail(c, TC_EINVAL, "learned = 1 needs precise = 1, want_pot = 0, quad = 1 and quadrupole = 0");
+    if (cfg->quadrupole && (!cfg->precise || !cfg->quad))
+        return fail(c, TC_EINVAL, "quadrupole = 1 needs precise = 1 and quad = 1");
     bool rebuild = c->built && (cfg->gmax != c->cfg.gmax || (cfg->quad != 0) != (c->cfg.quad != 0));
     c->cfg = *cfg;
     c->cfg.precise = cfg->precise ? 1 : 0;
@@ -635,6 +640,7 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
     c->cfg.quad = cfg->quad ? 1 : 0;
     c->cfg.graph = cfg->graph ? 1 : 0;
     c->cfg.learned = cfg->learned ? 1 : 0;
+    c->cfg.quadrupole = cfg->quadrupole ? 1 : 0;
     c->walk_ready = false;
     if (rebuild) return build_tree(c, true, c->stream);  // groups depend on gmax, moments on quad
     return TC_OK;
@@ -1231,6 +1237,7 @@ int tc_mlp_pairs(tc_ctx* c, float theta, float eps, float band, float prob, uint
     // a plain walk at theta that also emits pairs
     tc_config keep = c->cfg;
     c->cfg.learned = 0;
+    c->cfg.quadrupole = 0;
     c->walk_ready = false;
     r = prepare_forces(c);
     c->cfg = keep;

@@ -52,8 +52,8 @@ struct Info {
     uint32_t work;     // walk work-queue counter
     uint32_t pad0;
     unsigned long long interactions;  // body-source interactions of the last walk
-    unsigned long long cells;         // accepted cells summed over groups
-    unsigned long long bodies;        // direct-list bodies summed over groups
+    unsigned long long cells;         // body-cell interactions (group size x accepted cells)
+    unsigned long long bodies;        // body-body interactions (group size x direct-list bodies)
     double diag[8];    // KE, PE, P[3], L[3]
 };
 
@@ -185,6 +185,7 @@ struct WalkConfig {
     int stack;        // walk stack entries per warp
     int tile;         // list tile entries: 64, 128 or 256
     int learned;      // 1: learned far-field correction (precise mode, no potential)
+    int quadw;        // 1: accepted cells add their quadrupole term (precise mode)
 };
 // host-side preparation of the walk kernel's launch (attributes, occupancy);
 // call before a stream capture

@@ -1,755 +1,36 @@
-// tc_walk.cu -- the force phase: tree walk with the cell-opening test,
-// interaction lists staged in shared memory, softened monopole force loop.
-//
-// Paper, Sec. 3.1: the force on a body is evaluated by traversing the tree
-// from the root; a cell distant enough joins the interaction list, otherwise
-// the traversal continues with its children; the accumulated list of cells
-// and bodies is then looped through with F = G m_a m_b / r^2.  Sec. 3.2: the
-// summation for each body over its list is independent of every other body.
-//
-// GPU design.  One warp walks the tree once for a whole group of up to
-// 32*B Morton-consecutive bodies (B bodies per lane) -- the list is built for
-// the group, so every body of the group uses the same list.  The walk is a
-// LIFO of node indices in shared memory; each step pops up to 32 nodes, one
-// per lane, and applies the opening test in parallel:
-//   * a node holding a body of the group is opened;
-//   * otherwise, with s its cube side and d the distance from its centre of
-//     mass to the group's bounding box, it is accepted iff s < theta * d
-//     (compared as s^2 < theta^2 d^2);
-//   * an opened internal node pushes its (contiguous) children, an opened
-//     leaf sends its bodies to the body tile, an accepted node sends its
-//     (centre of mass, mass) to the cell tile.
-// Ballots and prefix sums compact the three outcomes.  When a tile reaches
-// kTile entries every lane sums it for its B bodies (the force loop: one
-// rsqrt and 12 FP32 FMA-pipe instructions per interaction) and the tile is
-// reused, so lists never go to HBM.
-//
-// Precision.  The opening test and the cell sources are evaluated in a frame
-// centred on the group's reference cube: cube centres are exact integers in
-// units u = h/2, the group box is split into an integer part (units of u)
-// and a float remainder, so every difference is formed without cancellation
-// and the test's relative error stays ~1e-7.  Body-body terms use absolute
-// float positions (their differences are exact or correctly rounded).  In
-// the precise mode cell terms use the cell-relative frame and each tile's
-// partial sum enters the per-body total through an error-free TwoSum
-// (compensated accumulation); the plain mode uses absolute float centres of
-// mass and plain accumulation.
+// tc_walk.cu -- launchers of the walk + force kernels: the group size picks
+// the translation unit holding the kernels for that many bodies per lane.
 #include "tc_internal.cuh"
-#include "tc_mma.cuh"
 
 namespace tc {
 
-namespace {
-
-// list tiles: a step adds at most 32 entries before the flush check, and a
-// flush may pad one entry, so a tile of TILE entries needs TILE + 34 slots
-__host__ __device__ constexpr int tile_cap(int tile) { return tile + 34; }
-
-// ---------------------------------------------------------------- packed FP32
-// Blackwell's paired FP32 instructions (add/sub/mul/fma .f32x2) work on a
-// 64-bit register holding two floats.  A list tile is stored pair-interleaved
-// -- {x_j, x_j+1}, {y_j, y_j+1}, {z_j, z_j+1}, {m_j, m_j+1} per pair of
-// entries -- so one pair of 16-byte shared loads yields two sources already
-// packed, and every FP32 operation of the force loop serves two sources.
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 f2pack(float a, float b)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2unpack(f2 r, float& a, float& b)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ f2 f2sub(f2 a, f2 b)
-{
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 f2mul(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ float f2sum(f2 a)
-{
-    float x, y;
-    f2unpack(a, x, y);
-    return x + y;
-}
-
-// entry k of a pair-interleaved tile
-__device__ __forceinline__ void put_entry(float* tile, int k, float4 q)
-{
-    float* t = tile + 8 * (k >> 1) + (k & 1);
-    t[0] = q.x;
-    t[2] = q.y;
-    t[4] = q.z;
-    t[6] = q.w;
-}
-
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
-{
-    z += 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ int warp_incl_scan_i(int x)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-// exclusive warp prefix sum of x in [0, 15] (and the warp total) from four
-// ballots: no shuffle chain
-__device__ __forceinline__ int warp_excl_small(int x, unsigned lt, int& total)
-{
-    int e = 0, t = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const unsigned bk = __ballot_sync(0xffffffffu, (x >> k) & 1);
-        e += __popc(bk & lt) << k;
-        t += __popc(bk) << k;
-    }
-    total = t;
-    return e;
-}
-
-// Lf x 2^-level for a power-of-two Lf: exponent arithmetic when the result
-// stays a normal float (fast, decided once per group), scalbnf otherwise
-__device__ __forceinline__ float pow2_down(float Lf, int level, bool fast)
-{
-    return fast ? __int_as_float(__float_as_int(Lf) - (level << 23)) : scalbnf(Lf, -level);
-}
-
-// error-free sum: s + c absorbs x (Knuth's TwoSum)
-__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x)
-{
-    float t = __fadd_rn(s, x);
-    float z = __fsub_rn(t, s);
-    float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
-    s = t;
-    c = __fadd_rn(c, e);
-}
-
-// 1/sqrt(x) on the SFU, flushing subnormals (x >= eps^2 > 0 is normal here),
-// so no range fix-up surrounds the approximation
-__device__ __forceinline__ float rsqrt_sfu(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// The force loop: npairs pairs of sources against the lane's B bodies.
-// Body coordinates are held duplicated ({x, x}); the two halves of each
-// accumulator collect the even and the odd sources of the tile.
-//   r2 = |d|^2 + eps^2, ri = rsqrt(r2), a += d * m * ri^3, pot -= m * ri
-template <int B, bool POT, int UNROLL>
-__device__ __forceinline__ void sum_tile(const float* __restrict__ tile, int npairs, const f2 (&X)[B],
-                                         const f2 (&Y)[B], const f2 (&Z)[B], f2 E2, f2 (&ax)[B],
-                                         f2 (&ay)[B], f2 (&az)[B], f2 (&ph)[B])
-{
-    const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
-#pragma unroll(UNROLL)
-    for (int p = 0; p < npairs; p++) {
-        const ulonglong2 xy = t2[2 * p];
-        const ulonglong2 zm = t2[2 * p + 1];
-#pragma unroll
-        for (int b = 0; b < B; b++) {
-            const f2 dx = f2sub(xy.x, X[b]);
-            const f2 dy = f2sub(xy.y, Y[b]);
-            const f2 dz = f2sub(zm.x, Z[b]);
-            const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2fma(dx, dx, E2)));
-            float r2a, r2b;
-            f2unpack(r2, r2a, r2b);
-            const f2 ri = f2pack(rsqrt_sfu(r2a), rsqrt_sfu(r2b));
-            const f2 mri = f2mul(zm.y, ri);
-            const f2 mri3 = f2mul(mri, f2mul(ri, ri));
-            ax[b] = f2fma(dx, mri3, ax[b]);
-            ay[b] = f2fma(dy, mri3, ay[b]);
-            az[b] = f2fma(dz, mri3, az[b]);
-            if (POT) ph[b] = f2sub(ph[b], mri);
-        }
-    }
-}
-
-template <int B, bool PRECISE, bool POT, int UNROLL>
-struct Accum {
-    f2 ax[B], ay[B], az[B], ph[B];        // packed running sums (plain mode)
-    float sx[B], sy[B], sz[B], sp[B];     // running sums (precise mode)
-    float cx[B], cy[B], cz[B], cp[B];     // their compensations
-    __device__ void init()
-    {
-#pragma unroll
-        for (int b = 0; b < B; b++) {
-            ax[b] = ay[b] = az[b] = ph[b] = 0ull;
-            sx[b] = sy[b] = sz[b] = sp[b] = cx[b] = cy[b] = cz[b] = cp[b] = 0.f;
-        }
-    }
-    // sums tile[0, n) (pads an odd count with a massless entry)
-    __device__ void flush(float* tile, int n, const f2 (&X)[B], const f2 (&Y)[B], const f2 (&Z)[B], f2 E2)
-    {
-        if (n <= 0) return;
-        if ((n & 1) && (threadIdx.x & 31) == 0) put_entry(tile, n, make_float4(0.f, 0.f, 0.f, 0.f));
-        __syncwarp();
-        const int np = (n + 1) >> 1;
-        if (PRECISE) {
-            f2 tx[B], ty[B], tz[B], tp[B];
-#pragma unroll
-            for (int b = 0; b < B; b++) tx[b] = ty[b] = tz[b] = tp[b] = 0ull;
-            sum_tile<B, POT, UNROLL>(tile, np, X, Y, Z, E2, tx, ty, tz, tp);
-#pragma unroll
-            for (int b = 0; b < B; b++) {
-                two_sum_acc(sx[b], cx[b], f2sum(tx[b]));
-                two_sum_acc(sy[b], cy[b], f2sum(ty[b]));
-                two_sum_acc(sz[b], cz[b], f2sum(tz[b]));
-                if (POT) two_sum_acc(sp[b], cp[b], f2sum(tp[b]));
-            }
-        } else {
-            sum_tile<B, POT, UNROLL>(tile, np, X, Y, Z, E2, ax, ay, az, ph);
-        }
-        __syncwarp();
-    }
-    __device__ void result(int b, float& fx, float& fy, float& fz, float& fp) const
-    {
-        if (PRECISE) {
-            fx = sx[b];
-            fy = sy[b];
-            fz = sz[b];
-            fp = sp[b];
-        } else {
-            fx = f2sum(ax[b]);
-            fy = f2sum(ay[b]);
-            fz = f2sum(az[b]);
-            fp = f2sum(ph[b]);
-        }
-    }
-    __device__ void comp(int b, float& fx, float& fy, float& fz, float& fp) const
-    {
-        fx = PRECISE ? cx[b] : 0.f;
-        fy = PRECISE ? cy[b] : 0.f;
-        fz = PRECISE ? cz[b] : 0.f;
-        fp = PRECISE ? cp[b] : 0.f;
-    }
-};
-
-// Learned correction.  Band cells found by a walk step are appended to a
-// per-warp list of pending node indices; whenever 32 are pending, lane j
-// builds the row of cell j -- 13 normalised features as BF16 pairs (8 words)
-// and the factor G M s^2 / r^4 that turns a label into an acceleration --
-// and the warp evaluates the rows 16 at a time on the tensor cores.
-  // register cap of the learned walk: 65536 / (128 x this)
-constexpr int kLearnedMinBlocks = 4;  // register cap of the learned walk: 65536 / (128 x this)
-constexpr int kPend = 64;   // < 32 left over + 32 added by a step
-constexpr int kRowW = 9;    // words per row
-__host__ __device__ constexpr size_t mlp_frag_bytes() { return (sizeof(MlpFrag) + 15) & ~(size_t)15; }
-
-// rows of the n <= 32 cells pend[0, n) evaluated, label x yscale x factor
-// added to corr (lanes of q = 0 hold x, y; of q = 1 hold z)
-__device__ __noinline__ void learned_rows(const MlpFrag& m, const uint32_t* pend, int n, uint32_t* rows,
-                                          const NodeTables& nt, int4 rc, float uf, float Lf, float inv_L,
-                                          const float (&xgc)[3], float eps, float inv_msys, float G,
-                                          float (&corr)[3], int lane)
-{
-    uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    float fac = 0.f;
-    if (lane < n) {
-        const int v = (int)pend[lane];
-        const int4 nb = __ldg(&nt.b[v]);
-        const float4 na = __ldg(&nt.a[v]);
-        const int4 cc = __ldg(&nt.c[v]);
-        // centre of mass in the group's reference frame, as in the walk
-        const float dx = fmaf((float)(cc.x - rc.x), uf, na.x) - xgc[0];
-        const float dy = fmaf((float)(cc.y - rc.y), uf, na.y) - xgc[1];
-        const float dz = fmaf((float)(cc.z - rc.z), uf, na.z) - xgc[2];
-        const float sz = scalbnf(Lf, -(nb.w & 255));
-        const float inv_s = scalbnf(inv_L, nb.w & 255);  // exact: sides are powers of two
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float ri = rsqrtf(r2);
-        const float Mc = na.w;
-        const float* qd = nt.quad + 6 * (int64_t)v;
-        const float iq = __fdividef(inv_s * inv_s, Mc);
-        float f[kMlpInPad];
-        f[0] = dx * inv_s;
-        f[1] = dy * inv_s;
-        f[2] = dz * inv_s;
-        f[3] = ri * sz;
-        f[4] = eps * inv_s;
-        f[5] = __log2f((float)nb.y);
-        f[6] = Mc * inv_msys;
-#pragma unroll
-        for (int k = 0; k < 6; k++) f[7 + k] = __ldg(qd + k) * iq;
-#pragma unroll
-        for (int k = 0; k < kMlpIn; k++) f[k] = fmaf(f[k], m.xscale[k], m.xoff[k]);
-#pragma unroll
-        for (int k = kMlpIn; k < kMlpInPad; k++) f[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; k++) w[k] = pack_bf16(f[2 * k], f[2 * k + 1]);
-        const float ri2 = ri * ri;
-        fac = G * Mc * (sz * sz) * (ri2 * ri2);  // G M s^2 / r^4
-    }
-    uint32_t* r = rows + lane * kRowW;
-#pragma unroll
-    for (int k = 0; k < 8; k++) r[k] = w[k];
-    r[8] = __float_as_uint(fac);
-    __syncwarp();
-    const int g = lane >> 2, q = lane & 3;
-    for (int t = 0; t < n; t += 16) {
-        const uint32_t* r0 = rows + (t + g) * kRowW;
-        const uint32_t* r1 = rows + (t + g + 8) * kRowW;
-        const uint32_t x[4] = {r0[q], r1[q], r0[q + 4], r1[q + 4]};
-        float y[4];
-        mlp16_infer(m, x, y, lane);
-        const float f0 = __uint_as_float(r0[8]), f1 = __uint_as_float(r1[8]);
-        if (q == 0) {
-            corr[0] += (y[0] * f0 + y[2] * f1) * m.yscale[0];
-            corr[1] += (y[1] * f0 + y[3] * f1) * m.yscale[1];
-        } else if (q == 1) {
-            corr[2] += (y[0] * f0 + y[2] * f1) * m.yscale[2];
-        }
-    }
-    __syncwarp();
-}
-
-// shared memory of one warp (learned mode adds the pending list and the rows;
-// the block holds one copy of the network in front of the warps' regions)
-__host__ __device__ constexpr size_t walk_warp_bytes(int tile, int stack, bool learned)
-{
-    return (size_t)2 * tile_cap(tile) * 16 + (size_t)stack * 4 + (learned ? (size_t)(kPend + 32 * kRowW) * 4 : 0);
-}
-
-template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
-__global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3 : 4)) k_walk(WalkArgs a, int stack_cap)
-{
-    constexpr int kTile = TILE;
-    constexpr int kTileCap = tile_cap(TILE);
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const size_t head = LEARNED ? mlp_frag_bytes() : 0;
-    const size_t per_warp = walk_warp_bytes(TILE, stack_cap, LEARNED);
-    float* ctile = reinterpret_cast<float*>(smem + head + wib * per_warp);
-    float* btile = ctile + 4 * kTileCap;
-    uint32_t* stk = reinterpret_cast<uint32_t*>(btile + 4 * kTileCap);
-    uint32_t* pend = stk + stack_cap;  // learned: pending band cells, then the rows
-    uint32_t* rows = pend + kPend;
-    const f2 E2 = f2pack(a.eps2, a.eps2);
-    const uint32_t lt = (1u << lane) - 1u;
-
-    const Info* info = a.info;
-    if (info->err & kErrCapacity) return;  // the build stopped: no tree to walk
-    const int64_t G = info->G;
-    const NodeTables nt = a.nt;
-    MlpFrag* mlp = reinterpret_cast<MlpFrag*>(smem);
-    if (LEARNED) {
-        // the inference part at the front of the device model
-        for (int i = threadIdx.x; i < (int)(sizeof(MlpFrag) / 4); i += blockDim.x)
-            reinterpret_cast<uint32_t*>(mlp)[i] = reinterpret_cast<const uint32_t*>(a.mlp)[i];
-        __syncthreads();
-    }
-
-    for (;;) {
-        int g = 0;
-        if (lane == 0) g = (int)atomicAdd(&a.info->work, 1u);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= G) break;
-        const int gfirst = a.gfirst[g];
-        const int gend = a.gfirst[g + 1];
-        // the group's system: its root cube and its root node (roots are
-        // nodes 0..S-1 in system order)
-        const uint32_t sysid = a.sys_of[gfirst];
-        const SysParams& SP = a.sysp[sysid];
-        const double ud = 0.5 * SP.h;
-        const float uf = SP.uf;
-        const float Lf = SP.Lf;
-        const int4 rc = nt.c[a.gref[g]];
-        const double gx = SP.c0[0] + (double)rc.x * ud, gy = SP.c0[1] + (double)rc.y * ud,
-                     gz = SP.c0[2] + (double)rc.z * ud;
-
-        // the group's bodies: absolute and reference-relative positions,
-        // each coordinate duplicated into a packed pair
-        f2 XA[B], YA[B], ZA[B], XR[B], YR[B], ZR[B];
-        bool act[B];
-        float mi[B];
-        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-#pragma unroll
-        for (int b = 0; b < B; b++) {
-            int i = gfirst + lane + 32 * b;
-            act[b] = i < gend;
-            float4 q = a.body[act[b] ? i : gfirst];
-            XA[b] = f2pack(q.x, q.x);
-            YA[b] = f2pack(q.y, q.y);
-            ZA[b] = f2pack(q.z, q.z);
-            mi[b] = q.w;
-            if (PRECISE) {
-                const float rx = (float)((double)q.x - gx), ry = (float)((double)q.y - gy),
-                            rz = (float)((double)q.z - gz);
-                XR[b] = f2pack(rx, rx);
-                YR[b] = f2pack(ry, ry);
-                ZR[b] = f2pack(rz, rz);
-            }
-            lo[0] = fminf(lo[0], q.x); hi[0] = fmaxf(hi[0], q.x);
-            lo[1] = fminf(lo[1], q.y); hi[1] = fmaxf(hi[1], q.y);
-            lo[2] = fminf(lo[2], q.z); hi[2] = fmaxf(hi[2], q.z);
-        }
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-                hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
-            }
-        }
-        // group box relative to the reference centre: integer part (units
-        // of u) + float remainder in [0, u).  Lane k < 6 splits one bound.
-        int kb = 0;
-        float fb = 0.f;
-        if (lane < 6) {
-            const int ax = lane % 3;
-            const double gref = ax == 0 ? gx : (ax == 1 ? gy : gz);
-            const double t = (double)(lane < 3 ? lo[ax] : hi[ax]) - gref;
-            const double kf = floor(t / ud);
-            kb = (int)kf;
-            fb = (float)(t - kf * ud);
-        }
-        int klo[3], khi[3];
-        float flo[3], fhi[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            klo[k] = __shfl_sync(0xffffffffu, kb, k);
-            khi[k] = __shfl_sync(0xffffffffu, kb, k + 3);
-            flo[k] = __shfl_sync(0xffffffffu, fb, k);
-            fhi[k] = __shfl_sync(0xffffffffu, fb, k + 3);
-        }
-
-        // learned correction: evaluated at the centre of the group's box
-        // (reference-relative), summed over the group's band cells
-        float xgc[3] = {0.f, 0.f, 0.f};
-        float corr[3] = {0.f, 0.f, 0.f};
-        int qn = 0;
-        unsigned long long nevals = 0;
-        float inv_L = 0.f, inv_msys = 0.f;
-        if (LEARNED) {
-            inv_L = 1.0f / Lf;
-            inv_msys = 1.0f / SP.msys;
-#pragma unroll
-            for (int k = 0; k < 3; k++)
-                xgc[k] = 0.5f * (fmaf((float)klo[k], uf, flo[k]) + fmaf((float)khi[k], uf, fhi[k]));
-        }
-
-        // force-loop unroll: deep for one or two bodies per lane; shallow with
-        // four (registers) and in the learned walk (its code must stay in the
-        // instruction cache next to the network's)
-        constexpr int kUnroll = LEARNED ? 2 : (B >= 4 ? 4 : 8);
-        Accum<B, PRECISE, POT, kUnroll> cacc, bacc;
-        cacc.init();
-        bacc.init();
-        int cn = 0, bn = 0, Lc = 0, Lb = 0;
-        unsigned long long hsh = 0;
-        const bool want_hash = a.hash != nullptr;  // list hashes only for verification
-        const bool fast_side = ((__float_as_int(Lf) >> 23) & 255) > kMaxLevel + 1;
-        bool overflow = false;
-        int sp = 1;
-        if (lane == 0) stk[0] = sysid;  // the system's root: holds every body, always opened
-        __syncwarp();
-
-        while (sp > 0) {
-            const int np = min(sp, 32);
-            int v = -1;
-            if (lane < np) v = (int)stk[sp - np + lane];
-            sp -= np;
-            __syncwarp();
-            int4 nb = make_int4(0, 0, 0, 0);
-            bool acc = false, oleaf = false, oint = false;
-            float4 src = make_float4(0.f, 0.f, 0.f, 0.f);
-            float band_e2 = 0.f;
-            if (v >= 0) {
-                // the three node records are independent loads: issue together
-                nb = __ldg(&nt.b[v]);
-                const float4 na = __ldg(&nt.a[v]);
-                const int4 cc = __ldg(&nt.c[v]);
-                const int nch = nb.w >> 8;
-                const bool overlap = (nb.x < gend) && (gfirst < nb.x + nb.y);
-                if (!overlap) {
-                    const int D[3] = {cc.x - rc.x, cc.y - rc.y, cc.z - rc.z};
-                    const float off[3] = {na.x, na.y, na.z};
-                    float e2 = 0.f;
-#pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        const float lo_c = fmaf((float)(klo[k] - D[k]), uf, flo[k]);  // box lo - cube centre
-                        const float hi_c = fmaf((float)(khi[k] - D[k]), uf, fhi[k]);
-                        const float e = fmaxf(fmaxf(lo_c - off[k], off[k] - hi_c), 0.f);
-                        e2 = fmaf(e, e, e2);
-                    }
-                    const float s = pow2_down(Lf, nb.w & 255, fast_side);
-                    acc = (s * s) < a.theta2 * e2;
-                    band_e2 = e2;
-                    if (acc) {
-                        if (PRECISE || LEARNED) {
-                            src = make_float4(fmaf((float)D[0], uf, off[0]), fmaf((float)D[1], uf, off[1]),
-                                              fmaf((float)D[2], uf, off[2]), na.w);
-                        } else {
-                            src = nt.d[v];
-                        }
-                    }
-                }
-                if (!acc) {
-                    oleaf = (nch == 0);
-                    oint = (nch != 0);
-                }
-            }
-            // opened internal nodes push their children
-            const int npush = oint ? (nb.w >> 8) : 0;  // at most 8
-            int tot;
-            const int excl = warp_excl_small(npush, lt, tot);
-            if (sp + tot > stack_cap) {
-                overflow = true;
-                break;
-            }
-            for (int k = 0; k < npush; k++) stk[sp + excl + k] = (uint32_t)(nb.z + k);
-            sp += tot;
-            // accepted cells -> cell tile
-            const unsigned am = __ballot_sync(0xffffffffu, acc);
-            if (acc) {
-                put_entry(ctile, cn + __popc(am & lt), src);
-                if (want_hash) hsh += mix64(2ull * (unsigned)v + 1ull);
-            }
-            cn += __popc(am);
-            Lc += __popc(am);
-            // band cells (s / d at or above the band, two bodies or more):
-            // training pairs and learned corrections
-            bool band = false;
-            if (acc && nb.y >= 2) {
-                const float sz = scalbnf(Lf, -(nb.w & 255));
-                band = sz * sz >= a.band2 * band_e2;
-            }
-            if (a.pair_body && band) {
-                const unsigned long long hh = mix64(a.pair_seed ^ (((unsigned long long)g << 32) | (unsigned)v));
-                if ((float)(hh >> 40) * (1.0f / 16777216.0f) < a.pair_prob) {
-                    const unsigned long long k = atomicAdd(a.pair_count, 1ull);
-                    if ((int64_t)k < a.pair_cap) {
-                        a.pair_body[k] = gfirst + (int)((hh & 0xffffffffull) % (unsigned)(gend - gfirst));
-                        a.pair_node[k] = v;
-                    }
-                }
-            }
-            if (LEARNED) {
-                const unsigned bm = __ballot_sync(0xffffffffu, band);
-                if (band) pend[qn + __popc(bm & lt)] = (uint32_t)v;
-                qn += __popc(bm);
-                if (qn >= 32) {
-                    __syncwarp();
-                    learned_rows(*mlp, pend, 32, rows, nt, rc, uf, Lf, inv_L, xgc, a.eps, inv_msys, a.G, corr, lane);
-                    nevals += 32;
-                    // move the cells past the first 32 to the front (read all, then write)
-                    const int rest = qn - 32;
-                    const uint32_t t = lane < rest ? pend[32 + lane] : 0u;
-                    __syncwarp();
-                    if (lane < rest) pend[lane] = t;
-                    qn = rest;
-                }
-                __syncwarp();
-            }
-            // opened leaves -> body tile.  The bodies of all leaves opened in
-            // this step are gathered 32 at a time: lane j takes body t of the
-            // concatenated ranges, finding its leaf by a binary search over
-            // the lanes' exclusive offsets.
-            const unsigned lm = __ballot_sync(0xffffffffu, oleaf);
-            if (lm) {
-                if (want_hash && oleaf) hsh += mix64(2ull * (unsigned)v + 2ull);
-                const int cnt = oleaf ? nb.y : 0;
-                const int incl_c = warp_incl_scan_i(cnt);
-                const int excl_c = incl_c - cnt;
-                const int T = __shfl_sync(0xffffffffu, incl_c, 31);
-                Lb += T;
-                for (int o = 0; o < T; o += 32) {
-                    const int t = min(o + lane, T - 1);
-                    int pos = 0;
-#pragma unroll
-                    for (int step = 16; step; step >>= 1) {
-                        const int e = __shfl_sync(0xffffffffu, excl_c, pos + step);
-                        if (e <= t) pos += step;
-                    }
-                    const int f = __shfl_sync(0xffffffffu, nb.x, pos);
-                    const int e0 = __shfl_sync(0xffffffffu, excl_c, pos);
-                    if (o + lane < T) put_entry(btile, bn + lane, __ldg(&a.body[f + (t - e0)]));
-                    bn += min(32, T - o);
-                    if (bn >= kTile) {
-                        bacc.flush(btile, bn, XA, YA, ZA, E2);
-                        bn = 0;
-                    }
-                }
-            }
-            __syncwarp();
-            if (cn >= kTile) {
-                if (PRECISE) cacc.flush(ctile, cn, XR, YR, ZR, E2);
-                else cacc.flush(ctile, cn, XA, YA, ZA, E2);
-                cn = 0;
-            }
-        }
-        if (overflow) {
-            if (lane == 0) atomicOr(&a.info->err, kErrStack);
-            __syncwarp();
-            continue;
-        }
-        if (PRECISE) cacc.flush(ctile, cn, XR, YR, ZR, E2);
-        else cacc.flush(ctile, cn, XA, YA, ZA, E2);
-        bacc.flush(btile, bn, XA, YA, ZA, E2);
-        if (LEARNED) {
-            if (qn > 0) {
-                learned_rows(*mlp, pend, qn, rows, nt, rc, uf, Lf, inv_L, xgc, a.eps, inv_msys, a.G, corr, lane);
-                nevals += qn;
-            }
-#pragma unroll
-            for (int k = 0; k < 3; k++)
-#pragma unroll
-                for (int o = 16; o; o >>= 1) corr[k] += __shfl_xor_sync(0xffffffffu, corr[k], o);
-        }
-
-        // results, scattered back to the original body order
-#pragma unroll
-        for (int b = 0; b < B; b++) {
-            if (!act[b]) continue;
-            const int i = gfirst + lane + 32 * b;
-            const int64_t o = a.perm[i];
-            float cx_, cy_, cz_, cp_, bx_, by_, bz_, bp_, kx, ky, kz, kp, qx, qy, qz, qp;
-            cacc.result(b, cx_, cy_, cz_, cp_);
-            bacc.result(b, bx_, by_, bz_, bp_);
-            cacc.comp(b, kx, ky, kz, kp);
-            bacc.comp(b, qx, qy, qz, qp);
-            // (cell sum) + (body sum), each carried with its compensation
-            const float fx = (cx_ + bx_) + (kx + qx);
-            const float fy = (cy_ + by_) + (ky + qy);
-            const float fz = (cz_ + bz_) + (kz + qz);
-            const float fp = (cp_ + bp_) + (kp + qp);
-            a.acc[3 * o + 0] = a.G * fx + corr[0];
-            a.acc[3 * o + 1] = a.G * fy + corr[1];
-            a.acc[3 * o + 2] = a.G * fz + corr[2];
-            if (POT) {
-                // remove the body's own term, -m_i / eps, summed with the list
-                const float self = mi[b] * rsqrtf(a.eps2);
-                a.pot[o] = a.G * (fp + self);
-            }
-        }
-        // per-group list statistics
-        if (want_hash) {
-#pragma unroll
-            for (int o = 16; o; o >>= 1) hsh += __shfl_xor_sync(0xffffffffu, hsh, o);
-        }
-        if (lane == 0) {
-            const int gc = gend - gfirst;
-            atomicAdd(&a.info->interactions, (unsigned long long)gc * (unsigned long long)(Lc + Lb));
-            atomicAdd(&a.info->cells, (unsigned long long)Lc);
-            atomicAdd(&a.info->bodies, (unsigned long long)Lb);
-            if (LEARNED && a.mlp_evals) atomicAdd(a.mlp_evals, nevals);
-            if (a.ncell) a.ncell[g] = Lc;
-            if (a.nbody) a.nbody[g] = Lb;
-            if (a.hash) a.hash[g] = hsh;
-        }
-        __syncwarp();
-    }
-}
-
-template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
-cudaError_t prepare_t(const WalkConfig& c, int num_sms, int* grid, size_t* smem_out)
-{
-    const int warps = c.warps;
-    const size_t head = LEARNED ? mlp_frag_bytes() : 0;
-    const size_t smem = head + walk_warp_bytes(TILE, c.stack, LEARNED) * warps;
-    auto kern = k_walk<B, TILE, PRECISE, POT, LEARNED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (c.blocks_per_sm > 0 && c.blocks_per_sm < per_sm) per_sm = c.blocks_per_sm;
-    *grid = num_sms * per_sm;
-    *smem_out = smem;
-    return cudaSuccess;
-}
-
-template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
-cudaError_t launch_t(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s)
-{
-    k_walk<B, TILE, PRECISE, POT, LEARNED><<<grid, c.warps * 32, smem, s>>>(a, c.stack);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-// dispatch over (bodies per lane, tile, mode) to the template instance F;
-// the learned correction exists in the precise mode without potential
-template <template <int, int, bool, bool, bool> class F, typename... Args>
-cudaError_t dispatch(const WalkConfig& c, Args... args)
-{
-    const bool p = c.precise != 0, pot = c.want_pot != 0;
-    if (c.learned && (!p || pot)) return cudaErrorInvalidValue;
-#define TC_WALK_MODES(BB, TT)                                                \
-    if (c.gmax == 32 * BB && c.tile == TT) {                                 \
-        if (c.learned) return F<BB, TT, true, false, true>::run(args...);    \
-        if (p && pot) return F<BB, TT, true, true, false>::run(args...);     \
-        if (p && !pot) return F<BB, TT, true, false, false>::run(args...);   \
-        if (!p && pot) return F<BB, TT, false, true, false>::run(args...);   \
-        return F<BB, TT, false, false, false>::run(args...);                 \
-    }
-    TC_WALK_MODES(1, 64)
-    TC_WALK_MODES(1, 128)
-    TC_WALK_MODES(1, 256)
-    TC_WALK_MODES(2, 64)
-    TC_WALK_MODES(2, 128)
-    TC_WALK_MODES(2, 256)
-    TC_WALK_MODES(4, 64)
-    TC_WALK_MODES(4, 128)
-    TC_WALK_MODES(4, 256)
-#undef TC_WALK_MODES
-    return cudaErrorInvalidValue;
-}
-
-template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
-struct PrepareF {
-    static cudaError_t run(const WalkConfig* c, int num_sms, int* grid, size_t* smem)
-    {
-        return prepare_t<B, TILE, PRECISE, POT, LEARNED>(*c, num_sms, grid, smem);
-    }
-};
-template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
-struct LaunchF {
-    static cudaError_t run(const WalkArgs* a, const WalkConfig* c, int grid, size_t smem, cudaStream_t s)
-    {
-        return launch_t<B, TILE, PRECISE, POT, LEARNED>(*a, *c, grid, smem, s);
-    }
-};
-
-}  // namespace
+cudaError_t prepare_walk_b1(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
+cudaError_t prepare_walk_b2(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
+cudaError_t prepare_walk_b4(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
+cudaError_t launch_walk_b1(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_walk_b2(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_walk_b4(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
 
 cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* smem)
 {
-    return dispatch<PrepareF>(c, &c, num_sms, grid, smem);
+    switch (c.gmax) {
+    case 32: return prepare_walk_b1(c, num_sms, grid, smem);
+    case 64: return prepare_walk_b2(c, num_sms, grid, smem);
+    case 128: return prepare_walk_b4(c, num_sms, grid, smem);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s)
 {
     cudaMemsetAsync(&a.info->work, 0, sizeof(uint32_t), s);
     cudaMemsetAsync(&a.info->interactions, 0, 3 * sizeof(unsigned long long), s);
-    return dispatch<LaunchF>(c, &a, &c, grid, smem, s);
+    switch (c.gmax) {
+    case 32: return launch_walk_b1(a, c, grid, smem, s);
+    case 64: return launch_walk_b2(a, c, grid, smem, s);
+    case 128: return launch_walk_b4(a, c, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace tc
