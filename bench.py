@@ -42,7 +42,7 @@ FLOPS_PER_INTERACTION = 20
 QUAD_FLOPS_PER_CELL = 55  # monopole + quadrupole term of one cell (FMA = 2)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "walk_uniform_1m.txt")
-WALK_SRC = os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", "tc_walk.cu")
+WALK_SRC = os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", "tc_walk.cuh")
 
 
 def workload_config(n, theta):

@@ -171,9 +171,15 @@ __global__ void __launch_bounds__(256) k_sort_offsets(uint32_t* __restrict__ ghi
     }
 }
 
+// Dynamic shared memory of one onesweep tile: the tile's items in their
+// locally sorted order (keys, then values), staged so that the write to the
+// output is one contiguous run per digit instead of a scatter per item.
+template <typename K>
+constexpr size_t onesweep_smem() { return (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t)); }
+
 // SYS: the digit is taken from the system of the value's body, sys_of[val]
 template <typename K, bool SYS>
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n_host, const int64_t* __restrict__ n_dev,
                                                            int shift, const uint32_t* __restrict__ goff,
@@ -181,8 +187,13 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__
                                                            int32_t* err, const uint32_t* __restrict__ sys_of)
 {
     const int64_t n = n_dev ? min(*n_dev, n_host) : n_host;  // never past the buffers
+    extern __shared__ __align__(16) unsigned char dsm[];
+    K* skey = reinterpret_cast<K*>(dsm);
+    uint32_t* sval = reinterpret_cast<uint32_t*>(dsm + (size_t)kSortTile * sizeof(K));
     __shared__ uint32_t wh[kSortWarps][256];
     __shared__ uint32_t base[256];
+    __shared__ uint32_t tstart[256];
+    __shared__ uint32_t wsum[kSortWarps];
     __shared__ int tile_sh;
     __shared__ int fail_sh;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -194,6 +205,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__
     __syncthreads();
     const int tile = tile_sh;
     if ((int64_t)tile * kSortTile >= n) return;  // a tile past the device-side count: nothing to do
+    const int tile_n = (int)min((int64_t)kSortTile, n - (int64_t)tile * kSortTile);
 
     // stable ranks within the tile (warp w owns items [tile*T + w*512, +512),
     // in 16 rounds of 32; equal digits of a round find each other with
@@ -224,17 +236,31 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__
     }
     __syncthreads();
 
-    // per digit: offsets of the warps inside the tile, the tile's count,
-    // then the decoupled look-back over the preceding tiles
-    {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
+    // per digit: offsets of the warps inside the tile and the tile's count;
+    // the digits' starts inside the tile (block scan); then the decoupled
+    // look-back over the preceding tiles
+    const int d = threadIdx.x;
+    uint32_t run = 0;
 #pragma unroll
-        for (int ww = 0; ww < kSortWarps; ww++) {
-            const uint32_t c = wh[ww][d];
-            wh[ww][d] = run;
-            run += c;
+    for (int ww = 0; ww < kSortWarps; ww++) {
+        const uint32_t c = wh[ww][d];
+        wh[ww][d] = run;
+        run += c;
+    }
+    {
+        uint32_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int ww = 0; ww < w; ww++) before += wsum[ww];
+        tstart[d] = before + x - run;
+    }
+    {
         volatile unsigned long long* st = status;
         if (tile == 0) {
             st[d] = kFlagPrefix | run;
@@ -269,16 +295,26 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K* __restrict__
         }
     }
     __syncthreads();
-    if (fail_sh) return;  // positions unknown: write nothing
+    // stage the tile in its sorted order (positions are inside [0, tile_n))
 #pragma unroll
     for (int r = 0; r < kSortItems; r++) {
-        const int64_t k = wbase + r * 32 + lane;
-        if (k < n) {
-            const uint32_t d = (SYS ? sys_of[val[r]] >> shift : (uint32_t)(key[r] >> shift)) & 255u;
-            const uint32_t p = base[d] + wh[w][d] + rank[r];
-            kout[p] = key[r];
-            vout[p] = val[r];
+        if (wbase + r * 32 + lane < n) {
+            const uint32_t dd = (SYS ? sys_of[val[r]] >> shift : (uint32_t)(key[r] >> shift)) & 255u;
+            const uint32_t lp = tstart[dd] + wh[w][dd] + rank[r];
+            skey[lp] = key[r];
+            sval[lp] = val[r];
         }
+    }
+    __syncthreads();
+    if (fail_sh) return;  // positions unknown: write nothing
+    // write out: consecutive items of one digit go to consecutive places
+    for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
+        const K kk = skey[i];
+        const uint32_t vv = sval[i];
+        const uint32_t dd = (SYS ? sys_of[vv] >> shift : (uint32_t)(kk >> shift)) & 255u;
+        const uint32_t p = base[dd] + (uint32_t)i - tstart[dd];
+        kout[p] = kk;
+        vout[p] = vv;
     }
 }
 
@@ -329,15 +365,25 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
     uint32_t* va = vals;
     K* kb = keys_alt;
     uint32_t* vb = b.vals_alt;
+    // the staging buffer needs more than the default 48 KB of shared memory
+    // (a host-side attribute, set before any stream capture: every context
+    // builds eagerly once before it captures a step)
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[0]) {
+        cudaFuncSetAttribute(k_onesweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<K>());
+        cudaFuncSetAttribute(k_onesweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<K>());
+        attr_set[0] = attr_set[1] = true;
+    }
+    const size_t dsm = onesweep_smem<K>();
     for (int p = 0; p < npass; p++) {
         const bool sysp = p >= nkey;
         const int shift = sysp ? 8 * (p - nkey) : 8 * p;
         if (sysp)
-            k_onesweep<K, true><<<(unsigned)nt, kSortThreads, 0, s>>>(ka, va, kb, vb, n, n_dev, shift, b.ghist + 256 * p,
+            k_onesweep<K, true><<<(unsigned)nt, kSortThreads, dsm, s>>>(ka, va, kb, vb, n, n_dev, shift, b.ghist + 256 * p,
                                                                       b.status + (size_t)p * nt * 256, b.tiles + p,
                                                                       b.err, sys_of);
         else
-            k_onesweep<K, false><<<(unsigned)nt, kSortThreads, 0, s>>>(ka, va, kb, vb, n, n_dev, shift,
+            k_onesweep<K, false><<<(unsigned)nt, kSortThreads, dsm, s>>>(ka, va, kb, vb, n, n_dev, shift,
                                                                        b.ghist + 256 * p,
                                                                        b.status + (size_t)p * nt * 256, b.tiles + p,
                                                                        b.err, sys_of);
