@@ -599,6 +599,51 @@ def run_learned(args, rank, world, local_rank):
     return 0
 
 
+def run_profile_case(args):
+    """One small case of a kernel family, for an ncu capture, then exit:
+    build: a uniform cube built twice (eager builds; capture the second);
+    learned: one learned walk (seeded random network, band 0.5, theta 0.9)
+    on a 2^20-body Plummer sphere; quadrupole: one quadrupole walk (theta
+    0.7) on the same sphere."""
+    import torch
+
+    from paper_1211_2293_gb300 import inputs, tc
+
+    tc.load()
+    case = args.profile_case
+    if case == "build":
+        n = args.n
+        p, _, m = inputs.uniform_cube(n, SEED)
+        P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
+        ctx = tc.Context(want_pot=0, verify=0)
+        for _ in range(2):
+            ctx.build(P, M, LEAF)
+            ctx.sync()
+        print(f"built twice: uniform cube N={n}")
+        return 0
+    n = 1 << 20
+    p, _, m = inputs.plummer(n, seed=101)
+    P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
+    if case == "learned":
+        ctx = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
+        ctx.build(P, M, 16)
+        rng = np.random.default_rng(0)
+        params = (rng.standard_normal(tc.MLP_NPARAM) * 0.1).astype(np.float32)
+        model = np.concatenate([params, np.zeros(13), np.ones(13), np.full(3, 1e-3)]).astype(np.float32)
+        ctx.mlp_set(model, 0.5)
+        ctx.set_config(learned=1)
+        ctx.forces(0.9, 1e-3)
+        ctx.sync()
+        print(f"learned walk: Plummer N={n}, evals {ctx.mlp_evals()}")
+    else:
+        ctx = tc.Context(precise=1, quad=1, quadrupole=1, want_pot=0, verify=0)
+        ctx.build(P, M, 16)
+        ctx.forces(0.7, 1e-3)
+        ctx.sync()
+        print(f"quadrupole walk: Plummer N={n}")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,6 +662,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")
     ap.add_argument("--nsys", type=int, default=512)
+    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole"], default=None,
+                    help="run one small case of a kernel family for an ncu capture and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -624,6 +671,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.workload == "batch":
