@@ -186,6 +186,19 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ ours
+def aggregate_over_ranks(ms, n_per_rank, world, dist=None, device="cpu"):
+    """Replicas: every rank runs its own system of n_per_rank bodies.  The
+    slowest rank bounds the job, so the step time is the maximum over ranks
+    and the whole-job throughput is world x n_per_rank bodies per that time."""
+    if dist is not None and world > 1:
+        import torch
+
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, n_per_rank * world / (ms / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -246,12 +259,7 @@ def run_ours(args, rank, world, local_rank):
     tim = ctx.timings()
     ctx.set_timing(False)
 
-    ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * world / (ms / 1e3)
+    ms, value = aggregate_over_ranks(statistics.mean(step_ms), n, world, dist, dev)
 
     walk_ms = tim["walk_ms"] / args.steps
     inter_avg = statistics.mean(inter)
@@ -290,7 +298,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_val = n * world / (statistics.mean(e2e_ms) / 1e3)
+    _, e2e_val = aggregate_over_ranks(statistics.mean(e2e_ms), n, world, dist, dev)
 
     line = None
     if rank == 0:
