@@ -44,7 +44,9 @@ extern "C" {
 typedef struct tc_ctx tc_ctx;
 
 /* Tuning of the force phase (the autotuner's output).
- *   gmax      bodies per group walk: 32, 64 or 128 (1, 2 or 4 bodies per lane)
+ *   gmax      bodies per group walk: 1..32, 64 or 128 (one, two or four
+ *             bodies per lane); gmax = 1 gives every body its own walk and
+ *             list (the paper's per-body lists; one lane in 32 sums)
  *   warps     warps per block of the walk kernel, 1..4
  *   precise   1: cell-relative coordinates for cell sources and compensated
  *             (TwoSum) accumulation across list tiles; 0: absolute float32

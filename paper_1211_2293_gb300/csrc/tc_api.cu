@@ -621,8 +621,8 @@ void tc_destroy(tc_ctx* c)
 int tc_set_config(tc_ctx* c, const tc_config* cfg)
 {
     if (!c || !cfg) return fail(c, TC_EINVAL, "tc_set_config: null argument");
-    if (cfg->gmax != 32 && cfg->gmax != 64 && cfg->gmax != 128)
-        return fail(c, TC_EINVAL, "gmax must be 32, 64 or 128 (got %d)", cfg->gmax);
+    if (!((cfg->gmax >= 1 && cfg->gmax <= 32) || cfg->gmax == 64 || cfg->gmax == 128))
+        return fail(c, TC_EINVAL, "gmax must be 1..32, 64 or 128 (got %d)", cfg->gmax);
     if (cfg->warps < 1 || cfg->warps > 4) return fail(c, TC_EINVAL, "warps must be 1..4 (got %d)", cfg->warps);
     if (cfg->stack < 64 || cfg->stack > 8192) return fail(c, TC_EINVAL, "stack must be 64..8192 (got %d)", cfg->stack);
     if (cfg->blocks_per_sm < 0) return fail(c, TC_EINVAL, "blocks_per_sm must be >= 0");

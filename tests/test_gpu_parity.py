@@ -392,3 +392,30 @@ def test_allocation_cap_is_reported(tc, monkeypatch):
     monkeypatch.delenv("TC_ALLOC_CAP_BYTES")
     ctx2 = _ctx(tc)
     ctx2.build(_dev(p), _dev(m), 8)
+
+
+@pytest.mark.parametrize("gmax,theta", [(1, 0.5), (1, 0.8), (8, 0.6), (17, 0.7)])
+def test_small_groups_and_per_body_lists(tc, gmax, theta):
+    """gmax = 1 is the paper's per-body list: every body walks the tree with
+    its own opening test (the group box is the body itself)."""
+    n = 2000
+    p, _, m = _bodies("plummer", n, 21)
+    ctx = _ctx(tc, gmax=gmax)
+    ctx.build(_dev(p), _dev(m), 8)
+    ctx.forces(theta, 0.01)
+    acc, pot = ctx.get_acc(with_pot=True)
+    L = ctx.lists()
+    t = oracle.Tree(p, m, 8, gmax)
+    _compare_tree(ctx, t, gmax)
+    if gmax == 1:
+        assert t.G == n
+    w = t.walk(theta, 0.01)
+    ok = w["flag"] == 0
+    assert ok.mean() > 0.9
+    assert np.array_equal(L["ncell"][ok], w["ncell"][ok])
+    assert np.array_equal(L["nbody"][ok], w["nbody"][ok])
+    assert np.array_equal(L["hash"][ok], w["hash"][ok])
+    body_ok = np.zeros(n, bool)
+    for g in np.where(ok)[0]:
+        body_ok[t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]] = True
+    _check_forces(acc, pot, w, t, body_ok)
