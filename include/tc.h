@@ -166,6 +166,17 @@ int tc_get_cube(tc_ctx *ctx, double *out5);
 /* Number of systems and their root cubes (nsys x 5, as tc_get_cube). */
 int tc_get_systems(tc_ctx *ctx, int64_t *nsys, double *cubes);
 
+/* List-export mode: the interaction list of one group (the paper's
+ * ComputeForces receives a body with its list, Sec. 3.2) at opening angle
+ * theta on the current tree: the accepted cells and the opened leaves as
+ * breadth-first node indices (tc_get_nodes), in the walk's discovery order.
+ * cells / leaves (host or device, nullable) receive at most cap entries
+ * each; *ncells / *nleaves the full lengths.  With gmax = 1 a group is one
+ * body and this is its per-body list.  The context's forces and list totals
+ * are left as they were.  TC_EINVAL for a group outside [0, G). */
+int tc_get_group_list(tc_ctx *ctx, int64_t group, float theta, int32_t *cells, int32_t *leaves, int64_t cap,
+                      int64_t *ncells, int64_t *nleaves);
+
 /* Per-group list lengths of the last force phase (needs verify = 1):
  * accepted cells, bodies of opened leaves, order-independent hash of the
  * accepted cells and opened leaves; and totals over groups of group size x

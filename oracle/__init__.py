@@ -97,6 +97,8 @@ def _load():
     lib.or_mlp_factor.argtypes = [P, I64, P, D]
     lib.or_mlp_factor.restype = D
     lib.or_mlp_grad.restype = D
+    lib.or_tree_group_list.argtypes = [P, D, I64, P, I64, P, I64, P, P]
+    lib.or_tree_group_list.restype = None
     lib.or_tree_learned.argtypes = [P, D, D, D, D, P, P, I64, I64, P, P]
     lib.or_tree_learned.restype = I64
     _lib = lib
@@ -222,6 +224,17 @@ class Tree:
         )
         return dict(acc=acc, pot=pot, amag=amag, ncell=ncell, nbody=nbody, hash=hsh, flag=flag,
                     interactions=int(inter))
+
+    def group_list(self, group: int, theta: float):
+        """(accepted cells, opened leaves) of one group's walk, in walk order."""
+        nc, nl = ctypes.c_int64(), ctypes.c_int64()
+        self._lib.or_tree_group_list(self._h, float(theta), int(group), None, 0, None, 0, ctypes.byref(nc),
+                                     ctypes.byref(nl))
+        cells = np.zeros(nc.value, np.int64)
+        leaves = np.zeros(nl.value, np.int64)
+        self._lib.or_tree_group_list(self._h, float(theta), int(group), _ptr(cells), nc.value, _ptr(leaves),
+                                     nl.value, ctypes.byref(nc), ctypes.byref(nl))
+        return cells, leaves
 
     def test(self, group: int, node: int, theta: float) -> int:
         return int(self._lib.or_tree_test(self._h, int(group), int(node), float(theta)))

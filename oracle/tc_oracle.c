@@ -990,3 +990,36 @@ int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, do
     free(w.leaves);
     return evals;
 }
+
+/* The interaction list of one group at theta: accepted cells and opened
+ * leaves in the walk's order (depth first, children in octant order).
+ * Writes at most cap_c / cap_l entries; *nc / *nl get the full lengths. */
+void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cells, int64_t cap_c,
+                        int64_t *leaves, int64_t cap_l, int64_t *nc, int64_t *nl)
+{
+    walk_t w;
+    memset(&w, 0, sizeof(w));
+    w.gfirst = t->gfirst[g];
+    w.gcount = t->gcount[g];
+    w.theta = theta;
+    for (int a = 0; a < 3; a++) {
+        w.lo[a] = INFINITY;
+        w.hi[a] = -INFINITY;
+    }
+    for (int64_t j = w.gfirst; j < w.gfirst + w.gcount; j++)
+        for (int a = 0; a < 3; a++) {
+            if (t->xs[3 * j + a] < w.lo[a])
+                w.lo[a] = t->xs[3 * j + a];
+            if (t->xs[3 * j + a] > w.hi[a])
+                w.hi[a] = t->xs[3 * j + a];
+        }
+    open_cube(t, &w, 0);
+    for (int64_t k = 0; k < w.ncells && k < cap_c; k++)
+        cells[k] = w.cells[k];
+    for (int64_t k = 0; k < w.nleaves && k < cap_l; k++)
+        leaves[k] = w.leaves[k];
+    *nc = w.ncells;
+    *nl = w.nleaves;
+    free(w.cells);
+    free(w.leaves);
+}

@@ -89,6 +89,12 @@ int64_t or_tree_walk_order(const or_tree *t, double theta, double eps, double G,
                            int64_t g_begin, int64_t g_end, double *acc, double *pot, double *amag,
                            int64_t *ncell, int64_t *nbody, uint64_t *hash, int32_t *flag);
 
+/* The interaction list of group g at theta: accepted cells and opened
+ * leaves (node indices) in the walk's order; at most cap_c / cap_l written,
+ * *nc / *nl = the full lengths. */
+void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cells, int64_t cap_c,
+                        int64_t *leaves, int64_t cap_l, int64_t *nc, int64_t *nl);
+
 /* For tests: the opening-test decision of one (group, node) pair:
  * 0 = open (contains a group body), 1 = open (too close), 2 = accept. */
 int or_tree_test(const or_tree *t, int64_t group, int64_t node, double theta);

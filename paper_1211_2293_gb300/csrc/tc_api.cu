@@ -100,6 +100,9 @@ struct tc_ctx {
     bool have_mlp = false;
     float mlp_band = 0.5f;
     std::vector<float> mlp_maps_h;  // host copy of the feature / output maps
+    int32_t* list_buf = nullptr;    // list export scratch: cells, then leaves
+    int64_t list_cap = 0;
+    int64_t* list_n = nullptr;
     int32_t* pair_b = nullptr;
     int32_t* pair_v = nullptr;
     unsigned long long* pair_n = nullptr;
@@ -1320,6 +1323,69 @@ int tc_mlp_evals(tc_ctx* c, int64_t* evals)
 
 extern "C" {
 
+
+// The interaction list of one group (list-export mode): a walk of that group
+// alone that writes its accepted cells and opened leaves instead of forces.
+int tc_get_group_list(tc_ctx* c, int64_t group, float theta, int32_t* cells, int32_t* leaves, int64_t cap,
+                      int64_t* ncells, int64_t* nleaves)
+{
+    if (!c || !ncells || !nleaves) return fail(c, TC_EINVAL, "tc_get_group_list: null argument");
+    if (!c->built) return fail(c, TC_ESTATE, "tc_get_group_list: build first");
+    if (!finite(theta) || theta < 0.f || cap < 0) return fail(c, TC_EINVAL, "tc_get_group_list: theta >= 0, cap >= 0");
+    int r = check_device(c);
+    if (r) return r;
+    if (group < 0 || group >= c->info_h->G) return fail(c, TC_EINVAL, "tc_get_group_list: no group %lld", (long long)group);
+    const int64_t want = cap < 1 ? 1 : cap;
+    if (want > c->list_cap) {
+        TC_GROW(c, c->list_buf, 2 * want);
+        c->list_cap = want;
+    }
+    if (!c->list_n) TC_GROW(c, c->list_n, 2);
+    // the plain walk defines the lists (the learned and quadrupole variants
+    // walk the same way)
+    tc_config keep = c->cfg;
+    c->cfg.learned = 0;
+    c->cfg.quadrupole = 0;
+    c->walk_ready = false;
+    r = prepare_forces(c);
+    c->cfg = keep;
+    if (r) return r;
+    WalkArgs a{};
+    a.body = c->body;
+    a.perm = c->perm;
+    a.sys_of = c->sys_of;
+    a.sysp = c->sysp;
+    a.nt = c->nt;
+    a.gfirst = c->gfirst;
+    a.gref = c->gref;
+    a.info = c->info;
+    a.acc = c->acc;  // not written in list mode
+    a.theta2 = theta * theta;
+    a.eps2 = 1.f;
+    a.G = 1.f;
+    a.inv_eps = 1.f;
+    a.eps = 1.f;
+    a.list_cells = c->list_buf;
+    a.list_leaves = c->list_buf + c->list_cap;
+    a.list_cap = cap;
+    a.list_n = c->list_n;
+    a.list_group = (int32_t)group;
+    TC_CUDA(c, cudaMemsetAsync(c->list_n, 0, 2 * sizeof(int64_t), c->stream));
+    cudaError_t e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, c->stream);
+    c->walk_ready = false;
+    if (e != cudaSuccess) return fail(c, TC_ECUDA, "list walk: %s", cudaGetErrorString(e));
+    r = check_device(c);
+    if (r) return r;
+    int64_t nn[2] = {0, 0};
+    TC_CUDA(c, cudaMemcpy(nn, c->list_n, sizeof(nn), cudaMemcpyDeviceToHost));
+    *ncells = nn[0];
+    *nleaves = nn[1];
+    const int64_t kc = std::min<int64_t>(nn[0], cap), kl = std::min<int64_t>(nn[1], cap);
+    if (cells && kc > 0) TC_CUDA(c, cudaMemcpy(cells, c->list_buf, kc * sizeof(int32_t), cudaMemcpyDefault));
+    if (leaves && kl > 0)
+        TC_CUDA(c, cudaMemcpy(leaves, c->list_buf + c->list_cap, kl * sizeof(int32_t), cudaMemcpyDefault));
+    return TC_OK;
+}
 
 // Launch-configuration autotuner: times the walk + force kernel for every
 // (group size, list tile, warps per block) on the context's current bodies

@@ -174,6 +174,14 @@ struct WalkArgs {
     float pair_prob;
     unsigned long long pair_seed;
     unsigned long long* mlp_evals;   // corrections evaluated (nullable)
+    // list export (null: off): walk group list_group only, write its accepted
+    // cells and opened leaves (walk order, at most list_cap each) and their
+    // counts to list_n[0..1]; no forces or totals are written
+    int32_t* list_cells;
+    int32_t* list_leaves;
+    int64_t list_cap;
+    int64_t* list_n;
+    int32_t list_group;
 };
 struct WalkConfig {
     int gmax;         // 32, 64 or 128

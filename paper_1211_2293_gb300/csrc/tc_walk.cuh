@@ -456,7 +456,10 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
 
     const Info* info = a.info;
     if (info->err & kErrCapacity) return;  // the build stopped: no tree to walk
-    const int64_t G = info->G;
+    const bool list_mode = a.list_cells != nullptr;
+    // list export walks one group: queue position 0 maps to list_group
+    const int64_t G = list_mode ? (int64_t)a.list_group + 1 : info->G;
+    const int g_shift = list_mode ? a.list_group : 0;
     const NodeTables nt = a.nt;
     MlpFrag* mlp = reinterpret_cast<MlpFrag*>(smem);
     if (LEARNED) {
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
 
     for (;;) {
         int g = 0;
-        if (lane == 0) g = (int)atomicAdd(&a.info->work, 1u);
+        if (lane == 0) g = (int)atomicAdd(&a.info->work, 1u) + g_shift;
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= G) break;
         const int gfirst = a.gfirst[g];
@@ -563,7 +566,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
         Accum<B, PRECISE, POT, kUnroll> cacc, bacc;
         cacc.init();
         bacc.init();
-        int cn = 0, bn = 0, Lc = 0, Lb = 0;
+        int cn = 0, bn = 0, Lc = 0, Lb = 0, nleaf = 0;
         unsigned long long hsh = 0;
         const bool want_hash = a.hash != nullptr;  // list hashes only for verification
         const bool fast_side = ((__float_as_int(Lf) >> 23) & 255) > kMaxLevel + 1;
@@ -629,6 +632,10 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             sp += tot;
             // accepted cells -> cell tile
             const unsigned am = __ballot_sync(0xffffffffu, acc);
+            if (list_mode && acc) {
+                const int k = Lc + __popc(am & lt);
+                if (k < a.list_cap) a.list_cells[k] = v;
+            }
             if (acc) {
                 put_entry(ctile, cn + __popc(am & lt), src);
                 if (QUADW) put_quad(qtile, cn + __popc(am & lt), nt.quad + 6 * (int64_t)v);
@@ -675,6 +682,11 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             // concatenated ranges, finding its leaf by a binary search over
             // the lanes' exclusive offsets.
             const unsigned lm = __ballot_sync(0xffffffffu, oleaf);
+            if (list_mode && oleaf) {
+                const int k = nleaf + __popc(lm & lt);
+                if (k < a.list_cap) a.list_leaves[k] = v;
+            }
+            nleaf += __popc(lm);
             if (lm) {
                 if (want_hash && oleaf) hsh += mix64(2ull * (unsigned)v + 2ull);
                 const int cnt = oleaf ? nb.y : 0;
@@ -728,6 +740,14 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
                 for (int o = 16; o; o >>= 1) corr[k] += __shfl_xor_sync(0xffffffffu, corr[k], o);
         }
 
+        if (list_mode) {
+            if (lane == 0) {
+                a.list_n[0] = Lc;
+                a.list_n[1] = nleaf;
+            }
+            __syncwarp();
+            continue;
+        }
         // results, scattered back to the original body order
 #pragma unroll
         for (int b = 0; b < B; b++) {

@@ -31,7 +31,7 @@ EXPORTS = [
     "tc_diag", "tc_direct", "tc_sync", "tc_last_error", "tc_build", "tc_forces", "tc_step", "tc_default",
     "tc_set_timing", "tc_get_timings", "tc_direct_static", "tc_ctx_build_batch", "tc_get_systems",
     "tc_autotune", "tc_mlp_set", "tc_mlp_get", "tc_mlp_forward", "tc_mlp_loss_grad", "tc_mlp_train",
-    "tc_mlp_pairs", "tc_mlp_evals",
+    "tc_mlp_pairs", "tc_mlp_evals", "tc_get_group_list",
 ]
 
 MLP_NPARAM = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
@@ -104,6 +104,7 @@ def load(path: str | None = None):
         "tc_mlp_train": ([P, P, P, P, I64, I32, I32, F, ctypes.c_uint64, F, P], I32),
         "tc_mlp_pairs": ([P, F, F, F, F, ctypes.c_uint64, I64, P, P, P, P, P, P], I32),
         "tc_mlp_evals": ([P, P], I32),
+        "tc_get_group_list": ([P, I64, F, P, P, I64, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -351,6 +352,18 @@ class Context:
         self._c(self._lib.tc_get_lists(self._h, _ptr(nc), _ptr(nb), _ptr(hs), ctypes.byref(it),
                                        ctypes.byref(ce), ctypes.byref(bo)))
         return dict(ncell=nc, nbody=nb, hash=hs, interactions=it.value, cells=ce.value, bodies=bo.value)
+
+    def group_list(self, group: int, theta: float):
+        """(accepted cells, opened leaves) of one group's walk, in walk order."""
+        nc, nl = ctypes.c_int64(), ctypes.c_int64()
+        self._c(self._lib.tc_get_group_list(self._h, int(group), float(theta), None, None, 0, ctypes.byref(nc),
+                                            ctypes.byref(nl)))
+        cap = max(nc.value, nl.value)
+        cells = np.zeros(cap, np.int32)
+        leaves = np.zeros(cap, np.int32)
+        self._c(self._lib.tc_get_group_list(self._h, int(group), float(theta), _ptr(cells), _ptr(leaves), cap,
+                                            ctypes.byref(nc), ctypes.byref(nl)))
+        return cells[:nc.value], leaves[:nl.value]
 
     def diag(self):
         out = np.zeros(8)

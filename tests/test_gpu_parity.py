@@ -419,3 +419,43 @@ def test_small_groups_and_per_body_lists(tc, gmax, theta):
     for g in np.where(ok)[0]:
         body_ok[t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]] = True
     _check_forces(acc, pot, w, t, body_ok)
+
+
+@pytest.mark.parametrize("gmax,theta", [(64, 0.6), (1, 0.7), (32, 0.0)])
+def test_group_list_export_matches_oracle(tc, gmax, theta):
+    n = 3000
+    p, _, m = _bodies("plummer", n, 22)
+    ctx = _ctx(tc, gmax=gmax)
+    ctx.build(_dev(p), _dev(m), 8)
+    ctx.forces(0.5, 0.01)
+    acc0 = ctx.get_acc().copy()
+    L0 = ctx.lists(per_group=False)
+    t = oracle.Tree(p, m, 8, gmax)
+    w = t.walk(theta, 0.01, want_pot=False)
+    G = ctx.sizes()[2]
+    checked = 0
+    for g in np.unique(np.linspace(0, G - 1, 12).astype(int)):
+        if w["flag"][g]:
+            continue
+        cells, leaves = ctx.group_list(int(g), theta)
+        oc, ol = t.group_list(int(g), theta)
+        assert np.array_equal(np.sort(cells), np.sort(oc))
+        assert np.array_equal(np.sort(leaves), np.sort(ol))
+        checked += 1
+    assert checked >= 8
+    # forces and totals of the last force phase are untouched
+    assert np.array_equal(ctx.get_acc(), acc0)
+    assert ctx.lists(per_group=False)["interactions"] == L0["interactions"]
+    # a short buffer gets the first entries, the lengths stay full
+    import ctypes
+    nc, nl = ctypes.c_int64(), ctypes.c_int64()
+    buf_c = np.zeros(3, np.int32)
+    buf_l = np.zeros(3, np.int32)
+    rc = ctx._lib.tc_get_group_list(ctx._h, 0, ctypes.c_float(theta), buf_c.ctypes.data_as(ctypes.c_void_p),
+                                    buf_l.ctypes.data_as(ctypes.c_void_p), 3, ctypes.byref(nc), ctypes.byref(nl))
+    assert rc == 0
+    full_c, full_l = ctx.group_list(0, theta)
+    assert nc.value == len(full_c) and nl.value == len(full_l)
+    assert np.array_equal(buf_c[:min(3, len(full_c))], full_c[:3])
+    with pytest.raises(tc.TcError):
+        ctx.group_list(G, theta)

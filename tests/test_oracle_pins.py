@@ -418,3 +418,23 @@ def test_plummer_generator_matches_closed_forms():
     d = oracle.diag(pos, vel, mass, pot)
     assert d[1] == pytest.approx(-3 * math.pi / 32, rel=0.05)
     assert d[0] == pytest.approx(3 * math.pi / 64, rel=0.05)
+
+
+def test_group_list_export_partitions_the_bodies():
+    """A group's exported list (accepted cells + opened leaves) covers every
+    body exactly once and is the set the walk's hash and lengths describe."""
+    from tests.helpers import mix64
+
+    p, _, m = inputs.plummer(600, 31)
+    t = oracle.Tree(p, m, 4, gmax=16)
+    w = t.walk(0.7, 0.01)
+    for g in (0, 5, t.G // 2, t.G - 1):
+        cells, leaves = t.group_list(g, 0.7)
+        assert len(cells) == w["ncell"][g]
+        assert int(t.count[leaves].sum()) == w["nbody"][g]
+        cover = np.zeros(t.n, np.int64)
+        for v in list(cells) + list(leaves):
+            cover[t.first[v]:t.first[v] + t.count[v]] += 1
+        assert np.all(cover == 1)
+        h = sum(mix64(2 * int(v) + 1) for v in cells) + sum(mix64(2 * int(v) + 2) for v in leaves)
+        assert (h % (1 << 64)) == int(w["hash"][g])
