@@ -74,6 +74,14 @@ struct tc_ctx {
     bool walk_ready = false;
     int walk_grid = 0;
     size_t walk_smem = 0;
+    // groups split by size (walks of up to 64 / 128 bodies): class k goes to
+    // the kernel with 2^k bodies per lane
+    int32_t* glists = nullptr;   // 3 x cap_n group indices
+    int32_t* glist_n = nullptr;  // 3 counts
+    int walk_ncls = 0;
+    WalkConfig walk_cls[3]{};
+    int walk_cls_grid[3] = {0, 0, 0};
+    size_t walk_cls_smem[3] = {0, 0, 0};
     WalkConfig walk_cfg{};
 
     // phase timers (CUDA events on the context stream), when enabled
@@ -233,6 +241,8 @@ int ensure_bodies(tc_ctx* c, int64_t n)
     TC_GROW(c, c->nbody, cap);
     TC_GROW(c, c->hash, cap);
     TC_GROW(c, c->totals, 4);
+    TC_GROW(c, c->glists, 3 * cap);
+    TC_GROW(c, c->glist_n, 3);
     c->cap_n = cap;
     c->cap_m = 0;  // node tables are sized with the first build at this capacity
     return TC_OK;
@@ -403,6 +413,7 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
     launch_group_marks(c->cap_m, c->info, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);
     launch_group_table(c->gflag, c->gscan, c->gref_at, n, &c->totals[1], c->gfirst, c->gref, c->info, s);
+    if (c->cfg.gmax > 32) launch_group_split(c->gfirst, c->info, c->cap_n, c->glists, c->glist_n, s);
     TC_CUDA(c, cudaGetLastError());
     phase_end(c, 0, t0, s);
     c->built = true;
@@ -429,6 +440,16 @@ int prepare_forces(tc_ctx* c)
     if (c->walk_ready && memcmp(&wc, &c->walk_cfg, sizeof(wc)) == 0) return TC_OK;
     cudaError_t e = prepare_walk(wc, c->num_sms, &c->walk_grid, &c->walk_smem);
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk kernel set-up: %s", cudaGetErrorString(e));
+    // size classes: groups of up to 32 bodies one per lane, up to 64 two per
+    // lane, more four per lane (the launch for the context's gmax is kept for
+    // single-group walks)
+    c->walk_ncls = wc.gmax > 32 ? (wc.gmax == 64 ? 2 : 3) : 0;
+    for (int k = 0; k < c->walk_ncls; k++) {
+        c->walk_cls[k] = wc;
+        c->walk_cls[k].gmax = 32 << k;
+        e = prepare_walk(c->walk_cls[k], c->num_sms, &c->walk_cls_grid[k], &c->walk_cls_smem[k]);
+        if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk kernel set-up: %s", cudaGetErrorString(e));
+    }
     c->walk_cfg = wc;
     c->walk_ready = true;
     return TC_OK;
@@ -461,7 +482,16 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
         a.mlp_evals = c->mlp_evals;
     }
     cudaEvent_t t0 = phase_begin(c, s);
-    cudaError_t e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, s);
+    cudaError_t e = cudaSuccess;
+    if (c->walk_ncls == 0) {
+        e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, s);
+    } else {
+        for (int k = 0; k < c->walk_ncls && e == cudaSuccess; k++) {
+            a.glist = c->glists + (int64_t)k * c->cap_n;
+            a.glist_n = c->glist_n + k;
+            e = launch_walk(a, c->walk_cls[k], c->walk_cls_grid[k], c->walk_cls_smem[k], s, k == 0);
+        }
+    }
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk launch: %s", cudaGetErrorString(e));
     phase_end(c, 1, t0, s);
     c->have_forces = true;

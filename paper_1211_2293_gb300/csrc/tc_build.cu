@@ -558,6 +558,51 @@ __global__ void k_group_table(const uint32_t* __restrict__ gflag, const uint32_t
     gref[g] = gref_at[s];
 }
 
+// Groups split by size for the walk, so that a group of at most 32 bodies is
+// summed one body per lane and one of at most 64 two per lane: class 0
+// holds at most 32 bodies, class 1 at most 64, class 2 more.  One block
+// walks the groups in chunks of 1024; warp ballots and per-warp counts give
+// every group its place, keeping the group order within each class.
+__global__ void __launch_bounds__(1024) k_group_split(const int32_t* __restrict__ gfirst, const Info* info,
+                                                      int64_t cap_g, int32_t* __restrict__ lists,
+                                                      int32_t* __restrict__ counts)
+{
+    __shared__ int wcnt[32][3];
+    __shared__ int base[3];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t G = capacity_failed(info) ? 0 : info->G;
+    if (tid < 3) base[tid] = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t c0 = 0; c0 < G; c0 += 1024) {
+        const int64_t g = c0 + tid;
+        int cls = -1;
+        if (g < G) {
+            const int cnt = gfirst[g + 1] - gfirst[g];
+            cls = cnt <= 32 ? 0 : (cnt <= 64 ? 1 : 2);
+        }
+        unsigned m[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) m[k] = __ballot_sync(0xffffffffu, cls == k);
+        __syncthreads();  // the previous chunk's readers of wcnt and base are done
+        if (lane == 0)
+            for (int k = 0; k < 3; k++) wcnt[w][k] = __popc(m[k]);
+        __syncthreads();
+        if (cls >= 0) {
+            int off = base[cls] + __popc(m[cls] & lt);
+            for (int ww = 0; ww < w; ww++) off += wcnt[ww][cls];
+            lists[cls * cap_g + off] = (int32_t)g;
+        }
+        __syncthreads();
+        if (tid < 3) {
+            int t = 0;
+            for (int ww = 0; ww < 32; ww++) t += wcnt[ww][tid];
+            base[tid] += t;
+        }
+    }
+    __syncthreads();
+    if (tid < 3) counts[tid] = base[tid];
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // grid of a grid-stride kernel over a device-side count bounded by cap
 inline unsigned gsgrid(int64_t cap, int t)
@@ -651,6 +696,13 @@ void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t
         else k_level_moments<false><<<g, 128, 0, s>>>(lev, level_start, sysp, info, nt);
         count_launches(1);
     }
+}
+
+void launch_group_split(const int32_t* gfirst, const Info* info, int64_t cap_g, int32_t* lists, int32_t* counts,
+                        cudaStream_t s)
+{
+    k_group_split<<<1, 1024, 0, s>>>(gfirst, info, cap_g, lists, counts);
+    count_launches(1);
 }
 
 void launch_sys_mass(SysParams* sysp, int nsys, const NodeTables nt, const Info* info, cudaStream_t s)

@@ -140,6 +140,10 @@ void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t
                     cudaStream_t s);
 void launch_group_marks(int64_t cap_m, const Info* info, const NodeTables nt, int gmax, int64_t n,
                         uint32_t* gflag, int32_t* gref_at, cudaStream_t s);
+// groups by size class, stable: lists[k * cap_g + i], counts[k], class 0
+// holding at most 32 bodies, class 1 at most 64, class 2 more
+void launch_group_split(const int32_t* gfirst, const Info* info, int64_t cap_g, int32_t* lists, int32_t* counts,
+                        cudaStream_t s);
 void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int32_t* gref_at,
                         int64_t n, const uint32_t* total, int32_t* gfirst, int32_t* gref, Info* info,
                         cudaStream_t s);
@@ -182,6 +186,9 @@ struct WalkArgs {
     int64_t list_cap;
     int64_t* list_n;
     int32_t list_group;
+    // group list (null: every group 0..G-1): walk glist[0, *glist_n) only
+    const int32_t* glist;
+    const int32_t* glist_n;
 };
 struct WalkConfig {
     int gmax;         // 32, 64 or 128
@@ -198,7 +205,10 @@ struct WalkConfig {
 // host-side preparation of the walk kernel's launch (attributes, occupancy);
 // call before a stream capture
 cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
-cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
+// reset_totals: zero the interaction totals first (the first launch of a
+// force phase that is split over several group classes)
+cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s,
+                        bool reset_totals = true);
 
 // learned far-field correction (tc_mlp.cu)
 size_t mlp_dev_size();

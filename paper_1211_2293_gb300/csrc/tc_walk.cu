@@ -22,10 +22,11 @@ cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* sm
     }
 }
 
-cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s,
+                        bool reset_totals)
 {
     cudaMemsetAsync(&a.info->work, 0, sizeof(uint32_t), s);
-    if (!a.list_cells)  // list export leaves the last force phase's totals alone
+    if (reset_totals && !a.list_cells)  // list export leaves the last force phase's totals alone
         cudaMemsetAsync(&a.info->interactions, 0, 3 * sizeof(unsigned long long), s);
     if (c.gmax >= 1 && c.gmax <= 32) return launch_walk_b1(a, c, grid, smem, s);
     switch (c.gmax) {

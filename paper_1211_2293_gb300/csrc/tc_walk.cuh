@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
     if (info->err & kErrCapacity) return;  // the build stopped: no tree to walk
     const bool list_mode = a.list_cells != nullptr;
     // list export walks one group: queue position 0 maps to list_group
-    const int64_t G = list_mode ? (int64_t)a.list_group + 1 : info->G;
+    const int64_t G = list_mode ? (int64_t)a.list_group + 1 : (a.glist ? (int64_t)*a.glist_n : info->G);
     const int g_shift = list_mode ? a.list_group : 0;
     const NodeTables nt = a.nt;
     MlpFrag* mlp = reinterpret_cast<MlpFrag*>(smem);
@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
         if (lane == 0) g = (int)atomicAdd(&a.info->work, 1u) + g_shift;
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= G) break;
+        if (a.glist) g = __ldg(a.glist + g);  // this launch's size class
         const int gfirst = a.gfirst[g];
         const int gend = a.gfirst[g + 1];
         // the group's system: its root cube and its root node (roots are
