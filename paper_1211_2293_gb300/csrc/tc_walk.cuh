@@ -559,11 +559,11 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
                 xgc[k] = 0.5f * (fmaf((float)klo[k], uf, flo[k]) + fmaf((float)khi[k], uf, fhi[k]));
         }
 
-        // force-loop unroll: deep for one or two bodies per lane; shallow with
-        // four (registers), in the quadrupole walk (registers) and in the
-        // learned walk (its code must stay in the instruction cache next to
-        // the network's)
-        constexpr int kUnroll = (LEARNED || QUADW) ? 2 : (B >= 4 ? 4 : 8);
+        // force-loop unroll: deep for one or two bodies per lane; shallower
+        // with four (registers), in the quadrupole walk (registers) and in
+        // the learned walk (its code must stay in the instruction cache next
+        // to the network's: 8 deep stalls on instruction fetch)
+        constexpr int kUnroll = QUADW ? 2 : (LEARNED || B >= 4 ? 4 : 8);
         Accum<B, PRECISE, POT, kUnroll> cacc, bacc;
         cacc.init();
         bacc.init();
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             // training pairs and learned corrections
             bool band = false;
             if (acc && nb.y >= 2) {
-                const float sz = scalbnf(Lf, -(nb.w & 255));
+                const float sz = pow2_down(Lf, nb.w & 255, fast_side);
                 band = sz * sz >= a.band2 * band_e2;
             }
             if (a.pair_body && band) {
