@@ -4,6 +4,8 @@
 // stable sort), so bodies sharing a leaf are ordered by key, then by index.
 // Both primitives are written here (no CUB); they are HBM/L2-bound map and
 // scatter passes.
+#include <mutex>
+
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -14,6 +16,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;  // 4096
 
+constexpr int kMaxDevices = 64;
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;                         // per thread
@@ -365,14 +368,23 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
     uint32_t* va = vals;
     K* kb = keys_alt;
     uint32_t* vb = b.vals_alt;
-    // the staging buffer needs more than the default 48 KB of shared memory
-    // (a host-side attribute, set before any stream capture: every context
-    // builds eagerly once before it captures a step)
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[0]) {
-        cudaFuncSetAttribute(k_onesweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<K>());
-        cudaFuncSetAttribute(k_onesweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<K>());
-        attr_set[0] = attr_set[1] = true;
+    // the staging buffer needs more than the default 48 KB of shared memory:
+    // a per-device function attribute, set once per device (before any
+    // stream capture: every context builds eagerly once before it captures
+    // a step)
+    {
+        static std::mutex mu;
+        static bool done[kMaxDevices] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < kMaxDevices && !done[dev]) {
+            cudaFuncSetAttribute(k_onesweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)onesweep_smem<K>());
+            cudaFuncSetAttribute(k_onesweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)onesweep_smem<K>());
+            done[dev] = true;
+        }
     }
     const size_t dsm = onesweep_smem<K>();
     for (int p = 0; p < npass; p++) {
