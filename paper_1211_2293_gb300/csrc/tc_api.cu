@@ -16,6 +16,8 @@
 #include <vector>
 
 #include "../../include/tc.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "tc_internal.cuh"
 
 using namespace tc;
@@ -322,9 +324,14 @@ cudaEvent_t take_event(tc_ctx* c)
     return c->ev_pool[c->ev_used++];
 }
 
-// records the start of a timed phase; returns the event (or null)
-cudaEvent_t phase_begin(tc_ctx* c, cudaStream_t s)
+// records the start of a timed phase; returns the event (or null).  Every
+// phase is also an NVTX range on the host timeline (build, walk + force,
+// update), visible to a profiler attached to the process.
+const char* const kPhaseName[3] = {"tc build", "tc walk+force", "tc update"};
+
+cudaEvent_t phase_begin(tc_ctx* c, cudaStream_t s, int phase)
 {
+    nvtxRangePushA(kPhaseName[phase]);
     if (!c->timing) return nullptr;
     cudaEvent_t e = take_event(c);
     if (e) cudaEventRecord(e, s);
@@ -333,6 +340,7 @@ cudaEvent_t phase_begin(tc_ctx* c, cudaStream_t s)
 
 void phase_end(tc_ctx* c, int phase, cudaEvent_t start, cudaStream_t s)
 {
+    nvtxRangePop();
     if (!start) return;
     cudaEvent_t e = take_event(c);
     if (!e) return;
@@ -375,7 +383,7 @@ int setup_systems(tc_ctx* c, const int64_t* off, int nsys)
 int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
 {
     const int64_t n = c->n;
-    cudaEvent_t t0 = phase_begin(c, s);
+    cudaEvent_t t0 = phase_begin(c, s, 0);
     if (synced) TC_CUDA(c, cudaMemsetAsync(&c->info->err, 0, sizeof(int32_t), s));
     launch_bbox(c->pos, c->chunks, c->nchunks, c->sysp, c->nsys, &c->info->err, s);
     launch_keys(c->pos, c->mass, n, c->sys_of, c->sysp, c->keys, c->perm, &c->info->err, s);
@@ -481,7 +489,7 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
         a.band2 = c->mlp_band * c->mlp_band;
         a.mlp_evals = c->mlp_evals;
     }
-    cudaEvent_t t0 = phase_begin(c, s);
+    cudaEvent_t t0 = phase_begin(c, s, 1);
     cudaError_t e = cudaSuccess;
     if (c->walk_ncls == 0) {
         e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, s);
@@ -508,14 +516,14 @@ int step_eager(tc_ctx* c, float dt)
     cudaStream_t s = c->stream;
     int r = prepare_forces(c);
     if (r) return r;
-    cudaEvent_t t0 = phase_begin(c, s);
+    cudaEvent_t t0 = phase_begin(c, s, 2);
     launch_kick_drift(c->pos, c->vel, c->acc, c->n, 0.5f * dt, dt, c->info, s);
     phase_end(c, 2, t0, s);
     r = build_tree(c, false, s);
     if (r) return r;
     r = run_forces(c, c->theta, c->eps, c->Gc, s);
     if (r) return r;
-    t0 = phase_begin(c, s);
+    t0 = phase_begin(c, s, 2);
     launch_kick(c->vel, c->acc, c->n, 0.5f * dt, c->info, s);
     phase_end(c, 2, t0, s);
     TC_CUDA(c, cudaGetLastError());
@@ -575,14 +583,14 @@ int step_graph(tc_ctx* c, float dt)
         }
         c->gkey = key;
     }
-    cudaEvent_t t0 = phase_begin(c, c->stream);
+    cudaEvent_t t0 = phase_begin(c, c->stream, 0);
     TC_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
     count_launches((int)c->graph_kernels);
     phase_end(c, 0, t0, c->stream);  // (timing mode: kick + drift + rebuild)
     if (timing) {
         int r = run_forces(c, c->theta, c->eps, c->Gc, c->stream);
         if (r) return r;
-        t0 = phase_begin(c, c->stream);
+        t0 = phase_begin(c, c->stream, 2);
         launch_kick(c->vel, c->acc, c->n, 0.5f * dt, c->info, c->stream);
         phase_end(c, 2, t0, c->stream);
         TC_CUDA(c, cudaGetLastError());
