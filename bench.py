@@ -313,6 +313,7 @@ def run_ours(args, rank, world, local_rank):
             "config": workload_config(n, args.theta),
             "rms_force_err": rms,
             "interactions_per_step": inter_avg,
+            "interactions_per_s": inter_avg / (walk_ms / 1e3),
             "phase_ms_per_step": {"build": tim["build_ms"] / args.steps, "walk_force": walk_ms,
                                   "update": tim["update_ms"] / args.steps},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
