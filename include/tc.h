@@ -302,6 +302,14 @@ int tc_mlp_pairs(tc_ctx *ctx, float theta, float eps, float band, float prob, ui
 /* corrections evaluated by learned walks since the last call */
 int tc_mlp_evals(tc_ctx *ctx, int64_t *evals);
 
+/* Self-test of the failure path: runs one radix pass tile whose predecessor
+ * never publishes, so its bounded look-back gives up (after about a second)
+ * instead of waiting forever.  *err_bits receives the device error word it
+ * set (8: a bounded device wait gave up), *elapsed_ms (nullable) the time
+ * the kernel took.  Uses its own buffers and stream on the current device;
+ * returns TC_OK when the kernel completed (whatever it reported). */
+int tc_selftest_bounded_wait(int32_t *err_bits, double *elapsed_ms);
+
 /* Wait for the context's stream; report device errors. */
 int tc_sync(tc_ctx *ctx);
 

@@ -1509,6 +1509,72 @@ int tc_autotune(tc_ctx* c, float theta, float eps, float G, int reps, tc_config*
     return TC_OK;
 }
 
+// Failure-path self-test: a device wait that can never be satisfied must
+// give up within its limit, report itself in the error word and leave the
+// device usable.
+int tc_selftest_bounded_wait(int32_t* err_bits, double* elapsed_ms)
+{
+    if (!err_bits) {
+        set_thread_error("tc_selftest_bounded_wait: null argument");
+        return TC_EINVAL;
+    }
+    const int64_t n = sort_selftest_items();
+    uint64_t* keys = nullptr;
+    uint64_t* kout = nullptr;
+    uint32_t *vals = nullptr, *vout = nullptr, *counter = nullptr, *goff = nullptr;
+    unsigned long long* status = nullptr;
+    int32_t* err = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = TC_OK;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) {
+        if (x != cudaSuccess && e == cudaSuccess) e = x;
+    };
+    chk(cudaMalloc(&keys, n * sizeof(uint64_t)));
+    chk(cudaMalloc(&kout, n * sizeof(uint64_t)));
+    chk(cudaMalloc(&vals, n * sizeof(uint32_t)));
+    chk(cudaMalloc(&vout, n * sizeof(uint32_t)));
+    chk(cudaMalloc(&status, 2 * 256 * sizeof(unsigned long long)));
+    chk(cudaMalloc(&counter, sizeof(uint32_t)));
+    chk(cudaMalloc(&goff, 256 * sizeof(uint32_t)));
+    chk(cudaMalloc(&err, sizeof(int32_t)));
+    chk(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    chk(cudaEventCreate(&e0));
+    chk(cudaEventCreate(&e1));
+    if (e == cudaSuccess) {
+        chk(cudaMemsetAsync(keys, 0, n * sizeof(uint64_t), s));
+        chk(cudaMemsetAsync(vals, 0, n * sizeof(uint32_t), s));
+        chk(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+        chk(cudaEventRecord(e0, s));
+        chk(sort_wait_selftest(keys, vals, kout, vout, status, counter, goff, err, s));
+        chk(cudaEventRecord(e1, s));
+        chk(cudaStreamSynchronize(s));
+        int32_t bits = 0;
+        chk(cudaMemcpy(&bits, err, sizeof(bits), cudaMemcpyDeviceToHost));
+        float ms = 0.f;
+        chk(cudaEventElapsedTime(&ms, e0, e1));
+        *err_bits = bits;
+        if (elapsed_ms) *elapsed_ms = ms;
+    }
+    if (e != cudaSuccess) {
+        set_thread_error("tc_selftest_bounded_wait: CUDA error");
+        rc = TC_ECUDA;
+    }
+    cudaFree(keys);
+    cudaFree(kout);
+    cudaFree(vals);
+    cudaFree(vout);
+    cudaFree(status);
+    cudaFree(counter);
+    cudaFree(goff);
+    cudaFree(err);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    return rc;
+}
+
 const char* tc_last_error(tc_ctx* c)
 {
     if (!c) {

@@ -111,6 +111,11 @@ void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const 
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n_cap, const int64_t* n_dev, int nbits,
                     SortBufs& b, uint32_t* keys_alt32, cudaStream_t s);
 int64_t radix_tiles(int64_t n);  // tiles of one pass (status words: 256 per tile per pass)
+// self-test of the radix pass's bounded look-back (see tc_sort.cu)
+cudaError_t sort_wait_selftest(uint64_t* keys, uint32_t* vals, uint64_t* kout, uint32_t* vout,
+                               unsigned long long* status, uint32_t* counter, uint32_t* goff, int32_t* err,
+                               cudaStream_t s);
+int64_t sort_selftest_items();
 
 // build pieces
 void launch_sys_ids(const int64_t* offsets, int nsys, int64_t n, uint32_t* sys_of, SysParams* sysp,

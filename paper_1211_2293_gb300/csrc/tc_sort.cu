@@ -122,7 +122,7 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restric
 // is bounded; a tile that gives up sets the error word and writes nothing.
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPrefix = 2ull << 62;
-constexpr unsigned kLookbackMaxPolls = 1u << 24;
+constexpr unsigned kLookbackMaxPolls = 1u << 22;  // about a second of polling
 
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(const K* __restrict__ keys, int64_t n_host,
@@ -408,6 +408,30 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
         cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     }
 }
+
+// Self-test of the look-back's wait limit: one block is handed tile 1 of a
+// two-tile pass whose tile 0 never runs, so its look-back finds no
+// predecessor, gives up after kLookbackMaxPolls polls, sets kErrWorkLoop in
+// *err and writes nothing.  All buffers are the caller's device memory:
+// keys/vals/kout/vout 2 * kSortTile items, status 2 * 256 words (zeroed
+// here), counter 1 word.
+cudaError_t sort_wait_selftest(uint64_t* keys, uint32_t* vals, uint64_t* kout, uint32_t* vout,
+                               unsigned long long* status, uint32_t* counter, uint32_t* goff, int32_t* err,
+                               cudaStream_t s)
+{
+    const int64_t n = 2 * (int64_t)kSortTile;
+    cudaMemsetAsync(status, 0, 2 * 256 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(goff, 0, 256 * sizeof(uint32_t), s);
+    const uint32_t one = 1;  // the only block launched takes tile 1
+    cudaMemcpyAsync(counter, &one, sizeof(one), cudaMemcpyHostToDevice, s);
+    cudaFuncSetAttribute(k_onesweep<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)onesweep_smem<uint64_t>());
+    k_onesweep<uint64_t, false><<<1, kSortThreads, onesweep_smem<uint64_t>(), s>>>(
+        keys, vals, kout, vout, n, nullptr, 0, goff, status, counter, err, nullptr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+int64_t sort_selftest_items() { return 2 * (int64_t)kSortTile; }
 
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of, int sys_bits,
                     SortBufs& b, cudaStream_t s)

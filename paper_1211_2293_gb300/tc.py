@@ -31,7 +31,7 @@ EXPORTS = [
     "tc_diag", "tc_direct", "tc_sync", "tc_last_error", "tc_build", "tc_forces", "tc_step", "tc_default",
     "tc_set_timing", "tc_get_timings", "tc_direct_static", "tc_ctx_build_batch", "tc_get_systems",
     "tc_autotune", "tc_mlp_set", "tc_mlp_get", "tc_mlp_forward", "tc_mlp_loss_grad", "tc_mlp_train",
-    "tc_mlp_pairs", "tc_mlp_evals", "tc_get_group_list",
+    "tc_mlp_pairs", "tc_mlp_evals", "tc_get_group_list", "tc_selftest_bounded_wait",
 ]
 
 MLP_NPARAM = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
@@ -105,6 +105,7 @@ def load(path: str | None = None):
         "tc_mlp_pairs": ([P, F, F, F, F, ctypes.c_uint64, I64, P, P, P, P, P, P], I32),
         "tc_mlp_evals": ([P, P], I32),
         "tc_get_group_list": ([P, I64, F, P, P, I64, P, P], I32),
+        "tc_selftest_bounded_wait": ([P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -137,6 +138,15 @@ def _current_stream():
     import torch
 
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def selftest_bounded_wait():
+    """(error bits, elapsed ms) of a device wait made to run out (see tc.h)."""
+    lib = load()
+    bits = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(lib.tc_selftest_bounded_wait(ctypes.byref(bits), ctypes.byref(ms)))
+    return bits.value, ms.value
 
 
 class Context:

@@ -159,3 +159,18 @@ def test_autotune_picks_a_valid_config_and_caches(tc, tmp_path, monkeypatch):
     assert len(cache.read_text().splitlines()) == 1
     ctx.forces(0.6, 0.01)
     ctx.get_acc()
+
+
+def test_bounded_device_wait_gives_up_and_reports(tc):
+    """Failure path without a GPU fault: a radix tile whose predecessor never
+    publishes polls for a bounded time, sets its error bit (8) and returns;
+    the device stays usable."""
+    bits, ms = tc.selftest_bounded_wait()
+    assert bits & 8
+    assert 0 < ms < 20000
+    # the device still works: a small build and force evaluation
+    pos, _, mass, off = _batch([2000], 1)
+    ctx = tc.Context()
+    ctx.build(_dev(pos), _dev(mass), 8)
+    ctx.forces(0.5, 0.01)
+    assert np.all(np.isfinite(ctx.get_acc()))
