@@ -492,7 +492,8 @@ def run_precision(args, rank, world, local_rank):
 def run_learned(args, rank, world, local_rank):
     """Learned far-field correction against the plain walk on a Plummer
     sphere.  Training: up to 2M body-cell pairs generated by the walk of a
-    2^20-body Plummer sphere (theta --theta-train, default 0.7; band 0.4;
+    2^20-body Plummer sphere (theta --theta-train, default 0.7; band
+    --band-train, default 0.4;
     exact labels from direct sums over each cell's bodies), trained on the
     GPU (Adam, BF16 tensor cores, loss weighted to the acceleration error).  Evaluation on a fresh 2^22-body Plummer sphere (eps 1e-3, leaf
     16): RMS relative force error against direct summation on 4096 sampled
@@ -509,7 +510,7 @@ def run_learned(args, rank, world, local_rank):
         return 0
     torch.cuda.set_device(local_rank)
     tc.load()
-    eps, leaf, band, theta_tr = 1e-3, 16, 0.4, args.theta_train
+    eps, leaf, band, theta_tr = 1e-3, 16, args.band_train, args.theta_train
     n_tr, n_ev = 1 << 20, (args.n if args.n != N_DEFAULT else 1 << 22)
     # ---- training pairs and training
     p, _, m = inputs.plummer(n_tr, seed=100)
@@ -670,6 +671,7 @@ def main():
                          "learned: the learned far-field correction against the plain walk")
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")
+    ap.add_argument("--band-train", type=float, default=0.4, help="learned: band of the training pairs")
     ap.add_argument("--nsys", type=int, default=512)
     ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole"], default=None,
                     help="run one small case of a kernel family for an ncu capture and exit")
