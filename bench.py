@@ -15,11 +15,13 @@ on one GPU), timed with CUDA events around each step, L2 flushed (a 256 MiB
 write) between steps.  ``roofline`` is the walk + force kernel against the
 FP32 CUDA-core peak (20 flops per body-source interaction), timed with the
 library's CUDA events on its own stream.  ``--impl reference`` times the CPU
-oracle (plain FP64 C, one core) on a bounded sample of the same workload.
+oracle (plain FP64 C; tree build on one thread, the walk over the host's
+cores) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -129,22 +131,36 @@ def _traffic_from_profile():
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(p, m, v, theta, frac_groups=8, gmax=64):
-    """One sampled oracle step: full tree build, the walk for 1/frac_groups of
-    the groups (evenly spread), the leapfrog update; returns the extrapolated
-    seconds of a whole step and what was sampled."""
+def oracle_sample(p, m, v, theta, frac_groups=8, gmax=64, threads=1, tree=None):
+    """One sampled oracle step: full tree build (one thread), the walk for
+    1/frac_groups of the groups (evenly spread; over `threads` host threads,
+    each walking its own chunks of groups -- the oracle's C walk runs
+    outside Python's lock), the leapfrog update; returns the extrapolated
+    seconds of a whole step, what was sampled and the wall time."""
+    import concurrent.futures as cf
+
     import oracle
 
     n = p.shape[0]
     t0 = time.perf_counter()
     t = oracle.Tree(p, m, LEAF, gmax)
     t1 = time.perf_counter()
-    nchunks = 16
+    nchunks = max(16, 4 * threads)
     per = max(1, t.G // (frac_groups * nchunks))
-    walked = 0
-    for g0 in np.linspace(0, t.G - per, nchunks).astype(int):
-        t.walk(theta, EPS, groups=(int(g0), int(g0) + per), want_pot=False)
-        walked += per
+    starts = [int(g0) for g0 in np.linspace(0, t.G - per, nchunks).astype(int)]
+
+    acc_all = np.zeros((n, 3))  # groups own disjoint bodies: one shared output
+
+    def walk(g0):
+        t._lib.or_tree_walk(t._h, float(theta), float(EPS), 1.0, g0, g0 + per,
+                            acc_all.ctypes.data_as(ctypes.c_void_p), None, None, None, None, None, None)
+        return per
+
+    if threads > 1:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            walked = sum(ex.map(walk, starts))
+    else:
+        walked = sum(walk(g0) for g0 in starts)
     t2 = time.perf_counter()
     acc = np.zeros((n, 3))
     vv = oracle.kick(v.astype(np.float64), acc, DT / 2)
@@ -153,9 +169,16 @@ def oracle_sample(p, m, v, theta, frac_groups=8, gmax=64):
     t3 = time.perf_counter()
     scale = t.G / walked
     est = (t1 - t0) + (t2 - t1) * scale + (t3 - t2)
-    sample = (f"oracle tree build of all {n} bodies + walk/force of {walked} of {t.G} groups "
-              f"(x{scale:.1f} extrapolated) + leapfrog update")
+    sample = (f"oracle tree build of all {n} bodies (1 thread) + walk/force of {walked} of {t.G} groups "
+              f"on {threads} thread(s) (x{scale:.1f} extrapolated) + leapfrog update")
     return est, sample, (t3 - t0)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def run_reference(args, rank, world):
@@ -165,10 +188,11 @@ def run_reference(args, rank, world):
 
     n = args.n
     p, v, m = inputs.uniform_cube(n, SEED)
+    cores = host_cores()
     times = []
     sample = ""
     for k in range(args.warmup + args.steps):
-        est, sample, _ = oracle_sample(p, m, v, args.theta, frac_groups=args.ref_frac)
+        est, sample, _ = oracle_sample(p, m, v, args.theta, frac_groups=args.ref_frac, threads=cores)
         if k >= args.warmup:
             times.append(est)
     sec = statistics.mean(times)
@@ -178,7 +202,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": workload_config(n, args.theta),
-        "cpu_baseline": {"value": value, "unit": "bodies/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "bodies/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "bodies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -304,8 +328,11 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            est, sample, _ = oracle_sample(p, m, v, args.theta, frac_groups=args.cpu_frac)
-            cpu = {"value": n / est, "unit": "bodies/s", "cores": 1, "kind": "oracle", "sample": sample}
+            cores = host_cores()
+            est, sample, _ = oracle_sample(p, m, v, args.theta, frac_groups=args.cpu_frac, threads=cores)
+            est1, sample1, _ = oracle_sample(p, m, v, args.theta, frac_groups=4 * args.cpu_frac, threads=1)
+            cpu = {"value": n / est, "unit": "bodies/s", "cores": cores, "kind": "oracle", "sample": sample,
+                   "single_thread": {"value": n / est1, "cores": 1, "sample": sample1}}
         line = {
             "metric": METRIC, "value": value, "unit": "bodies/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
