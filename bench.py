@@ -290,6 +290,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = inter_avg * FLOPS_PER_INTERACTION / (walk_ms / 1e3) / 1e12
     peak = fp32_peak_tflops()
     traffic = _traffic_from_profile()
+    probe = {"scalar_fma": tc.probe_fp32(False), "paired_fma": tc.probe_fp32(True)}
 
     # accuracy against direct summation (4096 sampled bodies), current state
     ctx.forces(args.theta, EPS)
@@ -348,7 +349,9 @@ def run_ours(args, rank, world, local_rank):
                          "kernel": "k_walk (walk + force)",
                          "peak_basis": "2 flops x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)",
                          "frac_at_measured_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])
-                                                    if clk.get("sm_mhz") else None)},
+                                                    if clk.get("sm_mhz") else None),
+                         "fp32_probe_tflops": probe,
+                         "frac_of_probe": achieved / probe["scalar_fma"] if probe["scalar_fma"] else None},
             "e2e": {"value": e2e_val, "unit": "bodies/s", "h2d_bytes_per_step": int(16 * n),
                     "d2h_bytes_per_step": int(12 * n),
                     "what": "force evaluation from pinned host pos/mass: upload, build, walk/force, "

@@ -302,6 +302,12 @@ int tc_mlp_pairs(tc_ctx *ctx, float theta, float eps, float band, float prob, ui
 /* corrections evaluated by learned walks since the last call */
 int tc_mlp_evals(tc_ctx *ctx, int64_t *evals);
 
+/* Measured FP32 throughput of the current device in TFLOP/s (FMA = 2
+ * flops): a grid of 8 x 256-thread blocks per SM, each thread running 8
+ * independent chains of scalar (paired = 0) or paired f32x2 (paired = 1)
+ * fused multiply-adds; best of three timed launches. */
+int tc_probe_fp32(int paired, double *tflops);
+
 /* Self-test of the failure path: runs one radix pass tile whose predecessor
  * never publishes, so its bounded look-back gives up (after about a second)
  * instead of waiting forever.  *err_bits receives the device error word it

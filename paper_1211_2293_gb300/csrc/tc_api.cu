@@ -1509,6 +1509,50 @@ int tc_autotune(tc_ctx* c, float theta, float eps, float G, int reps, tc_config*
     return TC_OK;
 }
 
+// Measured FP32 throughput of the current device: 8 resident blocks of 256
+// threads per SM, each thread 8 independent chains of fused multiply-adds;
+// the best of three timed launches.
+int tc_probe_fp32(int paired, double* tflops)
+{
+    if (!tflops) {
+        set_thread_error("tc_probe_fp32: null argument");
+        return TC_EINVAL;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    float* out = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(float));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int blocks = 8 * sms, iters = 1 << 14;
+    double best = 0.0;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+        cudaEventRecord(e0, s);
+        launch_fp32_probe(paired != 0, blocks, iters, out, s);
+        cudaEventRecord(e1, s);
+        e = cudaStreamSynchronize(s);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        // flops: threads x 8 chains x iters x 2 (a paired instruction does two)
+        const double flops = (double)blocks * 256 * 8 * iters * 2.0;
+        if (e == cudaSuccess && rep > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        set_thread_error("tc_probe_fp32: CUDA error");
+        return TC_ECUDA;
+    }
+    *tflops = best;
+    return TC_OK;
+}
+
 // Failure-path self-test: a device wait that can never be satisfied must
 // give up within its limit, report itself in the error word and leave the
 // device usable.

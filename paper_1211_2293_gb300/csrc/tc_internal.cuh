@@ -229,6 +229,10 @@ void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const 
                         float* fac, cudaStream_t s);
 void launch_sys_mass(SysParams* sysp, int nsys, const NodeTables nt, const Info* info, cudaStream_t s);
 
+// FP32 throughput probe (8 independent FMA chains per thread, scalar or
+// paired f32x2 instructions)
+void launch_fp32_probe(bool paired, int blocks, int iters, float* out, cudaStream_t s);
+
 // dynamics and diagnostics
 void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt,
                        const Info* info, cudaStream_t s);

@@ -152,6 +152,54 @@ void launch_kick(float* vel, const float* acc, int64_t n, float hkick, const Inf
     count_launches(1);
 }
 
+// FP32 throughput probe: every thread runs 8 independent chains of `iters`
+// fused multiply-adds (scalar, or paired f32x2 instructions), 2 flops each;
+// the chains' ends are folded into one store so nothing is dead code.
+template <bool PAIRED>
+__global__ void __launch_bounds__(256) k_fp32_probe(int iters, float seed, float* out)
+{
+    if (PAIRED) {
+        unsigned long long a[4], m, c;
+        const float x = seed + threadIdx.x * 1e-7f;
+        asm("mov.b64 %0, {%1, %1};" : "=l"(m) : "f"(0.999999f));
+        asm("mov.b64 %0, {%1, %1};" : "=l"(c) : "f"(1e-7f));
+#pragma unroll
+        for (int k = 0; k < 4; k++) asm("mov.b64 %0, {%1, %2};" : "=l"(a[k]) : "f"(x + k), "f"(x - k));
+        for (int i = 0; i < iters; i++) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[k]) : "l"(m), "l"(c));
+        }
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            float lo, hi;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[k]));
+            sum += lo + hi;
+        }
+        if (sum == 12345.f) out[0] = sum;
+    } else {
+        float a[8];
+        const float x = seed + threadIdx.x * 1e-7f;
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = x + k;
+        for (int i = 0; i < iters; i++) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(a[k]) : "f"(0.999999f), "f"(1e-7f));
+        }
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; k++) sum += a[k];
+        if (sum == 12345.f) out[0] = sum;
+    }
+}
+
+void launch_fp32_probe(bool paired, int blocks, int iters, float* out, cudaStream_t s)
+{
+    if (paired) k_fp32_probe<true><<<blocks, 256, 0, s>>>(iters, 1.0f, out);
+    else k_fp32_probe<false><<<blocks, 256, 0, s>>>(iters, 1.0f, out);
+    count_launches(1);
+}
+
 void launch_diag(const float* pos, const float* vel, const float* mass, const float* pot, int64_t n, Info* info,
                  cudaStream_t s)
 {

@@ -32,6 +32,7 @@ EXPORTS = [
     "tc_set_timing", "tc_get_timings", "tc_direct_static", "tc_ctx_build_batch", "tc_get_systems",
     "tc_autotune", "tc_mlp_set", "tc_mlp_get", "tc_mlp_forward", "tc_mlp_loss_grad", "tc_mlp_train",
     "tc_mlp_pairs", "tc_mlp_evals", "tc_get_group_list", "tc_selftest_bounded_wait",
+    "tc_probe_fp32",
 ]
 
 MLP_NPARAM = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
@@ -106,6 +107,7 @@ def load(path: str | None = None):
         "tc_mlp_evals": ([P, P], I32),
         "tc_get_group_list": ([P, I64, F, P, P, I64, P, P], I32),
         "tc_selftest_bounded_wait": ([P, P], I32),
+        "tc_probe_fp32": ([I32, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -138,6 +140,14 @@ def _current_stream():
     import torch
 
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def probe_fp32(paired: bool = False) -> float:
+    """Measured FP32 TFLOP/s of the current device (FMA chains; see tc.h)."""
+    lib = load()
+    t = ctypes.c_double()
+    _check(lib.tc_probe_fp32(int(bool(paired)), ctypes.byref(t)))
+    return t.value
 
 
 def selftest_bounded_wait():
