@@ -113,8 +113,9 @@ class ClockSampler:
 
 
 def _traffic_from_profile():
-    """dram bytes per walk launch from the committed ncu summary, or None if
-    the walk kernel's source changed since it was captured."""
+    """dram bytes of one force phase (both size-class launches of the walk)
+    from the committed ncu summary, or None if the walk kernel's source
+    changed since it was captured."""
     try:
         txt = open(PROFILE_TRAFFIC).read()
         cur = hashlib.sha256(open(WALK_SRC, "rb").read()).hexdigest()[:16]
@@ -125,7 +126,7 @@ def _traffic_from_profile():
                 kv[k.strip()] = v.strip()
         if kv.get("walk_source_sha256_16") != cur:
             return None
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv["dram_bytes_per_phase"])
     except Exception:
         return None
 
@@ -346,7 +347,7 @@ def run_ours(args, rank, world, local_rank):
                                   "update": tim["update_ms"] / args.steps},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_walk (walk + force)",
+                         "kernel": "k_walk (walk + force; one force phase = one launch per group-size class)",
                          "peak_basis": "2 flops x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)",
                          "frac_at_measured_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])
                                                     if clk.get("sm_mhz") else None),
