@@ -70,7 +70,13 @@ typedef struct tc_ctx tc_ctx;
  *             quad = 1, quadrupole = 0)
  *   quadrupole 1: every accepted cell adds its quadrupole term to its
  *             monopole (second-order expansion of the softened potential
- *             about the centre of mass; needs precise = 1, quad = 1)      */
+ *             about the centre of mass; needs precise = 1, quad = 1)
+ *   classes   1: with gmax 64 or 128 the walk runs one launch per group
+ *             size class, largest first: a group of at most 32 bodies is
+ *             summed one body per lane, one of at most 64 two per lane, a
+ *             larger one four (the default); 0: one launch, gmax / 32
+ *             bodies per lane for every group.  Lists and forces are the
+ *             same in both.                                               */
 typedef struct {
     int32_t gmax;
     int32_t warps;
@@ -84,6 +90,7 @@ typedef struct {
     int32_t graph;
     int32_t learned;
     int32_t quadrupole;
+    int32_t classes;
 } tc_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a

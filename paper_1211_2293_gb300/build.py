@@ -22,9 +22,12 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-# the three walk units are the longest compiles: listed first
-SOURCES = ["tc_walk_b2.cu", "tc_walk_b1.cu", "tc_walk_b4.cu", "tc_walk.cu", "tc_sort.cu", "tc_build.cu", "tc_step.cu",
-           "tc_api.cu", "tc_noalloc.cu", "tc_mlp.cu"]
+# (object, source, defines): the walk kernels, one object per (bodies per
+# lane, tile), are the longest compiles and go first
+WALK_UNITS = [(f"tc_walk_b{b}_t{t}", "tc_walk_unit.cu", [f"-DTC_WALK_B={b}", f"-DTC_WALK_TILE={t}"])
+              for b in (4, 2, 1) for t in (128, 64, 256)]
+UNITS = WALK_UNITS + [(s[:-3], s, []) for s in ["tc_api.cu", "tc_walk.cu", "tc_sort.cu", "tc_build.cu", "tc_step.cu",
+                                               "tc_noalloc.cu", "tc_mlp.cu"]]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}"]
@@ -54,14 +57,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     nvcc = _nvcc()
     hdrs = _headers()
     jobs = []
-    for src in SOURCES:
+    for obj, src, defs in UNITS:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, obj + ".o")
         if force or _stale(o, [s, *hdrs]):
-            cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o]
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defs, "-c", s, "-o", o]
             if ptxas_v:
                 cmd += ["-Xptxas", "-v"]
-            jobs.append((src, cmd))
+            jobs.append((obj, cmd))
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             futs = {ex.submit(subprocess.run, cmd, capture_output=True, text=True): src for src, cmd in jobs}
@@ -74,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
                     errs.append(f"{futs[f]}:\n{r.stderr}")
             if errs:
                 raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(BUILD, obj + ".o") for obj, _, _ in UNITS]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]

@@ -79,7 +79,7 @@ struct tc_ctx {
     // groups split by size (walks of up to 64 / 128 bodies): class k goes to
     // the kernel with 2^k bodies per lane
     int32_t* glists = nullptr;   // 3 x cap_n group indices
-    int32_t* glist_n = nullptr;  // 3 counts
+    int32_t* glist_n = nullptr;  // 3 counts, then the split's scratch
     int walk_ncls = 0;
     WalkConfig walk_cls[3]{};
     int walk_cls_grid[3] = {0, 0, 0};
@@ -244,7 +244,7 @@ int ensure_bodies(tc_ctx* c, int64_t n)
     TC_GROW(c, c->hash, cap);
     TC_GROW(c, c->totals, 4);
     TC_GROW(c, c->glists, 3 * cap);
-    TC_GROW(c, c->glist_n, 3);
+    TC_GROW(c, c->glist_n, 3 + (int64_t)group_split_scratch());
     c->cap_n = cap;
     c->cap_m = 0;  // node tables are sized with the first build at this capacity
     return TC_OK;
@@ -421,7 +421,7 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
     launch_group_marks(c->cap_m, c->info, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);
     launch_group_table(c->gflag, c->gscan, c->gref_at, n, &c->totals[1], c->gfirst, c->gref, c->info, s);
-    if (c->cfg.gmax > 32) launch_group_split(c->gfirst, c->info, c->cap_n, c->glists, c->glist_n, s);
+    if (c->cfg.gmax > 32) launch_group_split(c->gfirst, c->info, c->cap_n, c->glists, c->glist_n, c->glist_n + 3, s);
     TC_CUDA(c, cudaGetLastError());
     phase_end(c, 0, t0, s);
     c->built = true;
@@ -441,6 +441,7 @@ int prepare_forces(tc_ctx* c)
     wc.tile = c->cfg.tile;
     wc.learned = c->cfg.learned && c->have_mlp;
     wc.quadw = c->cfg.quadrupole;
+    wc.classes = c->cfg.gmax > 32 ? c->cfg.classes : 0;
     int64_t st = c->cfg.stack;
     if (c->cap_m < st) st = c->cap_m < 32 ? 32 : c->cap_m;  // a stack of M entries cannot overflow
     st = (st + 3) & ~(int64_t)3;                            // keeps every warp's tiles 16-byte aligned
@@ -448,10 +449,10 @@ int prepare_forces(tc_ctx* c)
     if (c->walk_ready && memcmp(&wc, &c->walk_cfg, sizeof(wc)) == 0) return TC_OK;
     cudaError_t e = prepare_walk(wc, c->num_sms, &c->walk_grid, &c->walk_smem);
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk kernel set-up: %s", cudaGetErrorString(e));
-    // size classes: groups of up to 32 bodies one per lane, up to 64 two per
-    // lane, more four per lane (the launch for the context's gmax is kept for
-    // single-group walks)
-    c->walk_ncls = wc.gmax > 32 ? (wc.gmax == 64 ? 2 : 3) : 0;
+    // one launch per size class: groups of up to 32 bodies one per lane, up
+    // to 64 two per lane, more four per lane (the launch for the context's
+    // gmax walks every group, or single groups)
+    c->walk_ncls = wc.classes ? (wc.gmax == 64 ? 2 : 3) : 0;
     for (int k = 0; k < c->walk_ncls; k++) {
         c->walk_cls[k] = wc;
         c->walk_cls[k].gmax = 32 << k;
@@ -494,10 +495,11 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
     if (c->walk_ncls == 0) {
         e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, s);
     } else {
-        for (int k = 0; k < c->walk_ncls && e == cudaSuccess; k++) {
+        for (int k = c->walk_ncls - 1; k >= 0 && e == cudaSuccess; k--) {
             a.glist = c->glists + (int64_t)k * c->cap_n;
             a.glist_n = c->glist_n + k;
-            e = launch_walk(a, c->walk_cls[k], c->walk_cls_grid[k], c->walk_cls_smem[k], s, k == 0);
+            e = launch_walk(a, c->walk_cls[k], c->walk_cls_grid[k], c->walk_cls_smem[k], s,
+                            k == c->walk_ncls - 1);
         }
     }
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk launch: %s", cudaGetErrorString(e));
@@ -533,10 +535,11 @@ int step_eager(tc_ctx* c, float dt)
 std::string graph_key(tc_ctx* c, float dt)
 {
     char b[512];
-    snprintf(b, sizeof(b), "%lld/%lld/%d/%d/%a/%a/%a/%a/%d/%d/%d/%d/%d/%d/%d/%d/%d", (long long)c->n,
+    snprintf(b, sizeof(b), "%lld/%lld/%d/%d/%a/%a/%a/%a/%d/%d/%d/%d/%d/%d/%d/%d/%d/%d/%a/%d/%d", (long long)c->n,
              (long long)c->cap_m, c->nsys, c->leaf_max, (double)dt, (double)c->theta, (double)c->eps, (double)c->Gc,
              c->cfg.gmax, c->cfg.warps, c->cfg.precise, c->cfg.want_pot, c->cfg.verify, c->cfg.stack,
-             c->cfg.blocks_per_sm, c->cfg.quad, c->cfg.tile);
+             c->cfg.blocks_per_sm, c->cfg.quad, c->cfg.tile, c->cfg.learned && c->have_mlp, (double)c->mlp_band,
+             c->cfg.quadrupole, c->cfg.classes);
     return b;
 }
 
@@ -633,6 +636,7 @@ int tc_create(tc_ctx** out, void* stream)
     c->cfg.graph = 1;
     c->cfg.learned = 0;
     c->cfg.quadrupole = 0;
+    c->cfg.classes = 1;
     *out = c;
     return TC_OK;
 }
@@ -673,6 +677,7 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
         return fail(c, TC_EINVAL, "learned = 1 needs precise = 1, want_pot = 0, quad = 1 and quadrupole = 0");
     if (cfg->quadrupole && (!cfg->precise || !cfg->quad))
         return fail(c, TC_EINVAL, "quadrupole = 1 needs precise = 1 and quad = 1");
+    if (cfg->classes < 0 || cfg->classes > 1) return fail(c, TC_EINVAL, "classes must be 0 or 1 (got %d)", cfg->classes);
     bool rebuild = c->built && (cfg->gmax != c->cfg.gmax || (cfg->quad != 0) != (c->cfg.quad != 0));
     c->cfg = *cfg;
     c->cfg.precise = cfg->precise ? 1 : 0;

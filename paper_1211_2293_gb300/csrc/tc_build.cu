@@ -560,30 +560,104 @@ __global__ void k_group_table(const uint32_t* __restrict__ gflag, const uint32_t
 
 // Groups split by size for the walk, so that a group of at most 32 bodies is
 // summed one body per lane and one of at most 64 two per lane: class 0
-// holds at most 32 bodies, class 1 at most 64, class 2 more.  One block
-// walks the groups in chunks of 1024; warp ballots and per-warp counts give
-// every group its place, keeping the group order within each class.
-__global__ void __launch_bounds__(1024) k_group_split(const int32_t* __restrict__ gfirst, const Info* info,
-                                                      int64_t cap_g, int32_t* __restrict__ lists,
-                                                      int32_t* __restrict__ counts)
+// holds at most 32 bodies, class 1 at most 64, class 2 more.  Block b of
+// kSplitBlocks takes the b-th contiguous range of the group table; a first
+// pass counts each range's groups per class, a second gives every group its
+// place (the counts of the ranges before it, then warp ballots within the
+// range), keeping the group order within each class.
+constexpr int kSplitBlocks = 256;
+constexpr int kSplitThreads = 256;
+
+__device__ __forceinline__ int size_class(const int32_t* __restrict__ gfirst, int64_t g)
 {
-    __shared__ int wcnt[32][3];
+    const int cnt = gfirst[g + 1] - gfirst[g];
+    return cnt <= 32 ? 0 : (cnt <= 64 ? 1 : 2);
+}
+
+__device__ __forceinline__ void split_range(const Info* info, int64_t& lo, int64_t& hi)
+{
+    const int64_t G = capacity_failed(info) ? 0 : info->G;
+    const int64_t per = (G + gridDim.x - 1) / gridDim.x;
+    lo = min(G, (int64_t)blockIdx.x * per);
+    hi = min(G, lo + per);
+}
+
+__device__ __forceinline__ int warp_sum_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_split_count(const int32_t* __restrict__ gfirst, const Info* info,
+                                                               int32_t* __restrict__ bcount)
+{
+    __shared__ int red[kSplitThreads / 32][3];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int64_t lo, hi;
+    split_range(info, lo, hi);
+    int c[3] = {0, 0, 0};
+    for (int64_t g = lo + tid; g < hi; g += blockDim.x) {
+        const int k = size_class(gfirst, g);
+        c[0] += k == 0;
+        c[1] += k == 1;
+        c[2] += k == 2;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int v = warp_sum_i(c[k]);
+        if (lane == 0) red[w][k] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        int t = 0;
+        for (int ww = 0; ww < kSplitThreads / 32; ww++) t += red[ww][tid];
+        bcount[3 * blockIdx.x + tid] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_split_scatter(const int32_t* __restrict__ gfirst, const Info* info,
+                                                                 const int32_t* __restrict__ bcount, int64_t cap_g,
+                                                                 int32_t* __restrict__ lists,
+                                                                 int32_t* __restrict__ counts)
+{
+    constexpr int W = kSplitThreads / 32;
+    __shared__ int red[W][6];
+    __shared__ int wcnt[W][3];
     __shared__ int base[3];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int64_t G = capacity_failed(info) ? 0 : info->G;
-    if (tid < 3) base[tid] = 0;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int64_t c0 = 0; c0 < G; c0 += 1024) {
-        const int64_t g = c0 + tid;
-        int cls = -1;
-        if (g < G) {
-            const int cnt = gfirst[g + 1] - gfirst[g];
-            cls = cnt <= 32 ? 0 : (cnt <= 64 ? 1 : 2);
+    // this range's offsets (the ranges before it) and the class totals
+    int v[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = tid; j < (int)gridDim.x; j += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int x = bcount[3 * j + k];
+            if (j < (int)blockIdx.x) v[k] += x;
+            v[3 + k] += x;
         }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const int s = warp_sum_i(v[k]);
+        if (lane == 0) red[w][k] = s;
+    }
+    __syncthreads();
+    if (tid < 6) {
+        int t = 0;
+        for (int ww = 0; ww < W; ww++) t += red[ww][tid];
+        if (tid < 3) base[tid] = t;
+        else if (blockIdx.x == 0) counts[tid - 3] = t;
+    }
+    int64_t lo, hi;
+    split_range(info, lo, hi);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t c0 = lo; c0 < hi; c0 += kSplitThreads) {
+        const int64_t g = c0 + tid;
+        const int cls = g < hi ? size_class(gfirst, g) : -1;
         unsigned m[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) m[k] = __ballot_sync(0xffffffffu, cls == k);
-        __syncthreads();  // the previous chunk's readers of wcnt and base are done
+        __syncthreads();  // base is set; the previous chunk's readers of wcnt and base are done
         if (lane == 0)
             for (int k = 0; k < 3; k++) wcnt[w][k] = __popc(m[k]);
         __syncthreads();
@@ -595,12 +669,10 @@ __global__ void __launch_bounds__(1024) k_group_split(const int32_t* __restrict_
         __syncthreads();
         if (tid < 3) {
             int t = 0;
-            for (int ww = 0; ww < 32; ww++) t += wcnt[ww][tid];
+            for (int ww = 0; ww < W; ww++) t += wcnt[ww][tid];
             base[tid] += t;
         }
     }
-    __syncthreads();
-    if (tid < 3) counts[tid] = base[tid];
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -698,11 +770,14 @@ void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t
     }
 }
 
+size_t group_split_scratch() { return (size_t)3 * kSplitBlocks; }
+
 void launch_group_split(const int32_t* gfirst, const Info* info, int64_t cap_g, int32_t* lists, int32_t* counts,
-                        cudaStream_t s)
+                        int32_t* scratch, cudaStream_t s)
 {
-    k_group_split<<<1, 1024, 0, s>>>(gfirst, info, cap_g, lists, counts);
-    count_launches(1);
+    k_split_count<<<kSplitBlocks, kSplitThreads, 0, s>>>(gfirst, info, scratch);
+    k_split_scatter<<<kSplitBlocks, kSplitThreads, 0, s>>>(gfirst, info, scratch, cap_g, lists, counts);
+    count_launches(2);
 }
 
 void launch_sys_mass(SysParams* sysp, int nsys, const NodeTables nt, const Info* info, cudaStream_t s)

@@ -49,8 +49,7 @@ struct Info {
     int64_t M;         // number of nodes
     int64_t G;         // number of groups
     int64_t cap_m;     // node table capacity (for the device-side check)
-    uint32_t work;     // walk work-queue counter
-    uint32_t pad0;
+    uint32_t work[2];  // walk work-queue counter (work[0]), padding
     unsigned long long interactions;  // body-source interactions of the last walk
     unsigned long long cells;         // body-cell interactions (group size x accepted cells)
     unsigned long long bodies;        // body-body interactions (group size x direct-list bodies)
@@ -146,9 +145,11 @@ void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t
 void launch_group_marks(int64_t cap_m, const Info* info, const NodeTables nt, int gmax, int64_t n,
                         uint32_t* gflag, int32_t* gref_at, cudaStream_t s);
 // groups by size class, stable: lists[k * cap_g + i], counts[k], class 0
-// holding at most 32 bodies, class 1 at most 64, class 2 more
+// holding at most 32 bodies, class 1 at most 64, class 2 more; scratch holds
+// group_split_scratch() ints
+size_t group_split_scratch();
 void launch_group_split(const int32_t* gfirst, const Info* info, int64_t cap_g, int32_t* lists, int32_t* counts,
-                        cudaStream_t s);
+                        int32_t* scratch, cudaStream_t s);
 void launch_group_table(const uint32_t* gflag, const uint32_t* gscan, const int32_t* gref_at,
                         int64_t n, const uint32_t* total, int32_t* gfirst, int32_t* gref, Info* info,
                         cudaStream_t s);
@@ -206,12 +207,13 @@ struct WalkConfig {
     int tile;         // list tile entries: 64, 128 or 256
     int learned;      // 1: learned far-field correction (precise mode, no potential)
     int quadw;        // 1: accepted cells add their quadrupole term (precise mode)
+    int classes;      // 1: one launch per group size class, largest first; 0: one launch
 };
 // host-side preparation of the walk kernel's launch (attributes, occupancy);
 // call before a stream capture
 cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
 // reset_totals: zero the interaction totals first (the first launch of a
-// force phase that is split over several group classes)
+// force phase that is split over several launches, one per size class)
 cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s,
                         bool reset_totals = true);
 

@@ -1,39 +1,61 @@
 // tc_walk.cu -- launchers of the walk + force kernels: the group size picks
-// the translation unit holding the kernels for that many bodies per lane
-// (groups of up to 32 bodies, down to the paper's one-body lists: one).
+// the bodies per lane (groups of up to 32 bodies, down to the paper's
+// one-body lists: one; 64: two; 128: four) and the tile size the object
+// (tc_walk_unit.cu, compiled once per pair) holding those kernels.
 #include "tc_internal.cuh"
 
 namespace tc {
 
-cudaError_t prepare_walk_b1(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
-cudaError_t prepare_walk_b2(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
-cudaError_t prepare_walk_b4(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
-cudaError_t launch_walk_b1(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_walk_b2(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_walk_b4(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s);
+#define TC_WALK_DECL(B, T)                                                                                 \
+    cudaError_t prepare_walk_b##B##_t##T(const WalkConfig& c, int num_sms, int* grid, size_t* smem);       \
+    cudaError_t launch_walk_b##B##_t##T(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem,     \
+                                        cudaStream_t s);
+#define TC_WALK_DECL_B(B) TC_WALK_DECL(B, 64) TC_WALK_DECL(B, 128) TC_WALK_DECL(B, 256)
+TC_WALK_DECL_B(1)
+TC_WALK_DECL_B(2)
+TC_WALK_DECL_B(4)
+#undef TC_WALK_DECL_B
+#undef TC_WALK_DECL
+
+namespace {
+
+int bodies_per_lane(int gmax)
+{
+    if (gmax >= 1 && gmax <= 32) return 1;
+    return gmax == 64 ? 2 : (gmax == 128 ? 4 : 0);
+}
+
+}  // namespace
+
+#define TC_WALK_PICK(fn, ...)                                                              \
+    switch (bodies_per_lane(c.gmax) * 1000 + c.tile) {                                    \
+    case 1064: return fn##_b1_t64(__VA_ARGS__);                                           \
+    case 1128: return fn##_b1_t128(__VA_ARGS__);                                          \
+    case 1256: return fn##_b1_t256(__VA_ARGS__);                                          \
+    case 2064: return fn##_b2_t64(__VA_ARGS__);                                           \
+    case 2128: return fn##_b2_t128(__VA_ARGS__);                                          \
+    case 2256: return fn##_b2_t256(__VA_ARGS__);                                          \
+    case 4064: return fn##_b4_t64(__VA_ARGS__);                                           \
+    case 4128: return fn##_b4_t128(__VA_ARGS__);                                          \
+    case 4256: return fn##_b4_t256(__VA_ARGS__);                                          \
+    default: return cudaErrorInvalidValue;                                                \
+    }
 
 cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* smem)
 {
-    if (c.gmax >= 1 && c.gmax <= 32) return prepare_walk_b1(c, num_sms, grid, smem);
-    switch (c.gmax) {
-    case 64: return prepare_walk_b2(c, num_sms, grid, smem);
-    case 128: return prepare_walk_b4(c, num_sms, grid, smem);
-    default: return cudaErrorInvalidValue;
-    }
+    TC_WALK_PICK(prepare_walk, c, num_sms, grid, smem)
 }
 
 cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s,
                         bool reset_totals)
 {
-    cudaMemsetAsync(&a.info->work, 0, sizeof(uint32_t), s);
+    if (bodies_per_lane(c.gmax) == 0) return cudaErrorInvalidValue;
+    cudaMemsetAsync(&a.info->work[0], 0, sizeof(a.info->work), s);
     if (reset_totals && !a.list_cells)  // list export leaves the last force phase's totals alone
         cudaMemsetAsync(&a.info->interactions, 0, 3 * sizeof(unsigned long long), s);
-    if (c.gmax >= 1 && c.gmax <= 32) return launch_walk_b1(a, c, grid, smem, s);
-    switch (c.gmax) {
-    case 64: return launch_walk_b2(a, c, grid, smem, s);
-    case 128: return launch_walk_b4(a, c, grid, smem, s);
-    default: return cudaErrorInvalidValue;
-    }
+    TC_WALK_PICK(launch_walk, a, c, grid, smem, s)
 }
+
+#undef TC_WALK_PICK
 
 }  // namespace tc

@@ -1,8 +1,9 @@
 // tc_walk.cuh -- the force phase: tree walk with the cell-opening test,
 // interaction lists staged in shared memory, softened monopole (optionally
-// quadrupole) force loop.  The kernel templates live here; tc_walk_b1.cu,
-// tc_walk_b2.cu and tc_walk_b4.cu instantiate them for 1, 2 and 4 bodies per
-// lane (compiled in parallel), tc_walk.cu holds the launchers.
+// quadrupole) force loop.  The kernel templates live here; tc_walk_unit.cu
+// instantiates them for one (bodies per lane, tile) pair per object (the
+// build compiles it nine times, in parallel), tc_walk.cu holds the
+// launchers.
 //
 // Paper, Sec. 3.1: the force on a body is evaluated by traversing the tree
 // from the root; a cell distant enough joins the interaction list, otherwise
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
 
     for (;;) {
         int g = 0;
-        if (lane == 0) g = (int)atomicAdd(&a.info->work, 1u) + g_shift;
+        if (lane == 0) g = (int)atomicAdd(&a.info->work[0], 1u) + g_shift;
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= G) break;
         if (a.glist) g = __ldg(a.glist + g);  // this launch's size class
@@ -820,30 +821,22 @@ cudaError_t launch_t(const WalkArgs& a, const WalkConfig& c, int grid, size_t sm
     return cudaGetLastError();
 }
 
-// dispatch over (tile, mode) for B bodies per lane to the template instance
-// F; the learned correction exists in the precise mode without potential,
-// the quadrupole walk in the precise mode
-template <int B, template <int, int, bool, bool, bool, bool> class F, typename... Args>
-cudaError_t dispatch_b(const WalkConfig& c, Args... args)
+// dispatch over the mode for B bodies per lane and tiles of TT entries to
+// the template instance F; the learned correction exists in the precise
+// mode without potential, the quadrupole walk in the precise mode
+template <int B, int TT, template <int, int, bool, bool, bool, bool> class F, typename... Args>
+cudaError_t dispatch_modes(const WalkConfig& c, Args... args)
 {
     const bool p = c.precise != 0, pot = c.want_pot != 0;
     if ((c.learned || c.quadw) && !p) return cudaErrorInvalidValue;
     if (c.learned && (pot || c.quadw)) return cudaErrorInvalidValue;
-#define TC_WALK_MODES(TT)                                                               \
-    if (c.tile == TT) {                                                                 \
-        if (c.learned) return F<B, TT, true, false, true, false>::run(args...);         \
-        if (c.quadw && pot) return F<B, TT, true, true, false, true>::run(args...);     \
-        if (c.quadw) return F<B, TT, true, false, false, true>::run(args...);           \
-        if (p && pot) return F<B, TT, true, true, false, false>::run(args...);          \
-        if (p && !pot) return F<B, TT, true, false, false, false>::run(args...);        \
-        if (!p && pot) return F<B, TT, false, true, false, false>::run(args...);        \
-        return F<B, TT, false, false, false, false>::run(args...);                      \
-    }
-    TC_WALK_MODES(64)
-    TC_WALK_MODES(128)
-    TC_WALK_MODES(256)
-#undef TC_WALK_MODES
-    return cudaErrorInvalidValue;
+    if (c.learned) return F<B, TT, true, false, true, false>::run(args...);
+    if (c.quadw && pot) return F<B, TT, true, true, false, true>::run(args...);
+    if (c.quadw) return F<B, TT, true, false, false, true>::run(args...);
+    if (p && pot) return F<B, TT, true, true, false, false>::run(args...);
+    if (p && !pot) return F<B, TT, true, false, false, false>::run(args...);
+    if (!p && pot) return F<B, TT, false, true, false, false>::run(args...);
+    return F<B, TT, false, false, false, false>::run(args...);
 }
 
 template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED, bool QUADW>

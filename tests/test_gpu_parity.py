@@ -459,3 +459,41 @@ def test_group_list_export_matches_oracle(tc, gmax, theta):
     assert np.array_equal(buf_c[:min(3, len(full_c))], full_c[:3])
     with pytest.raises(tc.TcError):
         ctx.group_list(G, theta)
+
+
+@pytest.mark.parametrize("gmax", [64, 128])
+def test_size_class_modes_agree(tc, gmax):
+    """The walk's size classes change which kernel sums a group (one, two or
+    four bodies per lane), never a body's list or the order of its sums:
+    classes = 0 (one launch) and 1 (one launch per class) give the same
+    lists and the same bits, both the oracle's forces to float32 rounding."""
+    p, _, m = _bodies("plummer", 20000, 23)
+    t = oracle.Tree(p, m, 16, gmax)
+    # the workload mixes the classes: groups of <= 16, <= 32, <= 48, <= 64
+    # (and more)
+    c = t.gcount
+    assert (c <= 16).any() and ((c > 16) & (c <= 32)).any()
+    assert ((c > 32) & (c <= 48)).any() and ((c > 48) & (c <= 64)).any()
+    if gmax == 128:
+        assert ((c > 64) & (c <= 96)).any() and (c > 112).any()
+    w = t.walk(0.6, 0.01)
+    ok = w["flag"] == 0
+    body_ok = np.zeros(len(p), bool)
+    for g in np.where(ok)[0]:
+        body_ok[t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]] = True
+    lists, accs = {}, {}
+    for classes in (0, 1):
+        ctx = _ctx(tc, gmax=gmax, classes=classes)
+        ctx.build(_dev(p), _dev(m), 16)
+        ctx.forces(0.6, 0.01)
+        acc, pot = ctx.get_acc(with_pot=True)
+        L = ctx.lists()
+        lists[classes] = L
+        accs[classes] = (acc.copy(), pot.copy())
+        assert np.array_equal(L["ncell"][ok], w["ncell"][ok])
+        assert np.array_equal(L["nbody"][ok], w["nbody"][ok])
+        _check_forces(acc, pot, w, t, body_ok)
+    for k in ("ncell", "nbody", "hash"):
+        assert np.array_equal(lists[0][k], lists[1][k]), k
+    assert lists[0]["interactions"] == lists[1]["interactions"]
+    assert np.array_equal(accs[0][0], accs[1][0]) and np.array_equal(accs[0][1], accs[1][1])
