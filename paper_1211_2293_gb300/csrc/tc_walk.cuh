@@ -565,9 +565,10 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
         // the learned walk (its code must stay in the instruction cache next
         // to the network's: 8 deep stalls on instruction fetch)
         constexpr int kUnroll = QUADW ? 2 : (LEARNED || B >= 4 ? 4 : 8);
-        Accum<B, PRECISE, POT, kUnroll> cacc, bacc;
-        cacc.init();
-        bacc.init();
+        // one running (compensated) sum per body collects the cell tiles and
+        // the body tiles alike
+        Accum<B, PRECISE, POT, kUnroll> fsum;
+        fsum.init();
         int cn = 0, bn = 0, Lc = 0, Lb = 0, nleaf = 0;
         unsigned long long hsh = 0;
         const bool want_hash = a.hash != nullptr;  // list hashes only for verification
@@ -709,16 +710,16 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
                     if (o + lane < T) put_entry(btile, bn + lane, __ldg(&a.body[f + (t - e0)]));
                     bn += min(32, T - o);
                     if (bn >= kTile) {
-                        bacc.flush(btile, bn, XA, YA, ZA, E2);
+                        fsum.flush(btile, bn, XA, YA, ZA, E2);
                         bn = 0;
                     }
                 }
             }
             __syncwarp();
             if (cn >= kTile) {
-                if (QUADW) cacc.flush_quad(ctile, qtile, cn, XR, YR, ZR, E2);
-                else if (PRECISE) cacc.flush(ctile, cn, XR, YR, ZR, E2);
-                else cacc.flush(ctile, cn, XA, YA, ZA, E2);
+                if (QUADW) fsum.flush_quad(ctile, qtile, cn, XR, YR, ZR, E2);
+                else if (PRECISE) fsum.flush(ctile, cn, XR, YR, ZR, E2);
+                else fsum.flush(ctile, cn, XA, YA, ZA, E2);
                 cn = 0;
             }
         }
@@ -727,10 +728,10 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             __syncwarp();
             continue;
         }
-        if (QUADW) cacc.flush_quad(ctile, qtile, cn, XR, YR, ZR, E2);
-        else if (PRECISE) cacc.flush(ctile, cn, XR, YR, ZR, E2);
-        else cacc.flush(ctile, cn, XA, YA, ZA, E2);
-        bacc.flush(btile, bn, XA, YA, ZA, E2);
+        if (QUADW) fsum.flush_quad(ctile, qtile, cn, XR, YR, ZR, E2);
+        else if (PRECISE) fsum.flush(ctile, cn, XR, YR, ZR, E2);
+        else fsum.flush(ctile, cn, XA, YA, ZA, E2);
+        fsum.flush(btile, bn, XA, YA, ZA, E2);
         if (LEARNED) {
             if (qn > 0) {
                 learned_rows(*mlp, pend, qn, rows, nt, rc, uf, Lf, inv_L, xgc, a.eps, inv_msys, a.G, corr, lane);
@@ -756,16 +757,14 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             if (!act[b]) continue;
             const int i = gfirst + lane + 32 * b;
             const int64_t o = a.perm[i];
-            float cx_, cy_, cz_, cp_, bx_, by_, bz_, bp_, kx, ky, kz, kp, qx, qy, qz, qp;
-            cacc.result(b, cx_, cy_, cz_, cp_);
-            bacc.result(b, bx_, by_, bz_, bp_);
-            cacc.comp(b, kx, ky, kz, kp);
-            bacc.comp(b, qx, qy, qz, qp);
-            // (cell sum) + (body sum), each carried with its compensation
-            const float fx = (cx_ + bx_) + (kx + qx);
-            const float fy = (cy_ + by_) + (ky + qy);
-            const float fz = (cz_ + bz_) + (kz + qz);
-            const float fp = (cp_ + bp_) + (kp + qp);
+            float sx_, sy_, sz_, sp_, kx, ky, kz, kp;
+            fsum.result(b, sx_, sy_, sz_, sp_);
+            fsum.comp(b, kx, ky, kz, kp);
+            // the running sum with its compensation
+            const float fx = sx_ + kx;
+            const float fy = sy_ + ky;
+            const float fz = sz_ + kz;
+            const float fp = sp_ + kp;
             a.acc[3 * o + 0] = a.G * fx + corr[0];
             a.acc[3 * o + 1] = a.G * fy + corr[1];
             a.acc[3 * o + 2] = a.G * fz + corr[2];
