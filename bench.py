@@ -40,6 +40,7 @@ if ROOT not in sys.path:
 METRIC = "force evals (bodies/s) at RMS force err 1e-3: plain vs learned; % FP32 peak"
 N_DEFAULT = 1 << 20
 LEAF, EPS, DT, THETA, SEED = 16, 1e-3, 1e-4, 0.5, 0
+THETA_ALT = 0.7  # the uniform workload's second opening angle
 FLOPS_PER_INTERACTION = 20
 QUAD_FLOPS_PER_CELL = 55  # monopole + quadrupole term of one cell (FMA = 2)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
@@ -301,6 +302,38 @@ def run_ours(args, rank, world, local_rank):
     a = acc[idx].astype(np.float64)
     rms = float(np.sqrt(np.mean(np.sum((a - ad) ** 2, 1) / np.sum(ad ** 2, 1))))
 
+    # the same step at the second opening angle: step and walk times over a
+    # few timed steps (L2 flushed between them) and the accuracy
+    alt = None
+    if args.theta != THETA_ALT:
+        ctx.forces(THETA_ALT, EPS)
+        for _ in range(2):
+            ctx.step(DT)
+        ctx.sync()
+        ctx.set_timing(True)
+        alt_ms, alt_inter = [], []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.step(DT)
+            e1.record(stream)
+            e1.synchronize()
+            alt_ms.append(e0.elapsed_time(e1))
+            alt_inter.append(ctx.lists(per_group=False)["interactions"])
+        atim = ctx.timings()
+        ctx.set_timing(False)
+        ctx.forces(THETA_ALT, EPS)
+        a7 = ctx.get_acc()[idx].astype(np.float64)
+        ad7, _ = ctx.direct(idx, EPS)
+        a_walk = atim["walk_ms"] / len(alt_ms)
+        alt = {"theta": THETA_ALT, "ms_per_step": statistics.mean(alt_ms),
+               "bodies_per_s": n / (statistics.mean(alt_ms) / 1e3), "walk_ms": a_walk,
+               "interactions_per_step": statistics.mean(alt_inter),
+               "fp32_tflops": statistics.mean(alt_inter) * FLOPS_PER_INTERACTION / (a_walk / 1e3) / 1e12,
+               "rms_force_err": float(np.sqrt(np.mean(np.sum((a7 - ad7) ** 2, 1) / np.sum(ad7 ** 2, 1))))}
+
     # end to end through the C ABI with host buffers: upload, build, forces,
     # download of the accelerations
     hp = torch.from_numpy(p).pin_memory()
@@ -341,6 +374,7 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(n, args.theta),
             "rms_force_err": rms,
+            "at_theta_0.7": alt,
             "interactions_per_step": inter_avg,
             "interactions_per_s": inter_avg / (walk_ms / 1e3),
             "phase_ms_per_step": {"build": tim["build_ms"] / args.steps, "walk_force": walk_ms,
