@@ -535,7 +535,11 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             kb = (int)kf;
             fb = (float)(t - kf * ud);
         }
+        // the same bounds and the reference cube's centre as floats: integers
+        // below 2^24, so their differences with a node's centre are exact
         int klo[3], khi[3];
+        float klof[3], khif[3];
+        const float rcf[3] = {(float)rc.x, (float)rc.y, (float)rc.z};
         float flo[3], fhi[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -543,6 +547,8 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             khi[k] = __shfl_sync(0xffffffffu, kb, k + 3);
             flo[k] = __shfl_sync(0xffffffffu, fb, k);
             fhi[k] = __shfl_sync(0xffffffffu, fb, k + 3);
+            klof[k] = (float)klo[k];
+            khif[k] = (float)khi[k];
         }
 
         // learned correction: evaluated at the centre of the group's box
@@ -596,13 +602,13 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
                 const int nch = nb.w >> 8;
                 const bool overlap = (nb.x < gend) && (gfirst < nb.x + nb.y);
                 if (!overlap) {
-                    const int D[3] = {cc.x - rc.x, cc.y - rc.y, cc.z - rc.z};
+                    const float D[3] = {(float)cc.x - rcf[0], (float)cc.y - rcf[1], (float)cc.z - rcf[2]};
                     const float off[3] = {na.x, na.y, na.z};
                     float e2 = 0.f;
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
-                        const float lo_c = fmaf((float)(klo[k] - D[k]), uf, flo[k]);  // box lo - cube centre
-                        const float hi_c = fmaf((float)(khi[k] - D[k]), uf, fhi[k]);
+                        const float lo_c = fmaf(klof[k] - D[k], uf, flo[k]);  // box lo - cube centre
+                        const float hi_c = fmaf(khif[k] - D[k], uf, fhi[k]);
                         const float e = fmaxf(fmaxf(lo_c - off[k], off[k] - hi_c), 0.f);
                         e2 = fmaf(e, e, e2);
                     }
@@ -611,8 +617,8 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
                     band_e2 = e2;
                     if (acc) {
                         if (PRECISE || LEARNED) {
-                            src = make_float4(fmaf((float)D[0], uf, off[0]), fmaf((float)D[1], uf, off[1]),
-                                              fmaf((float)D[2], uf, off[2]), na.w);
+                            src = make_float4(fmaf(D[0], uf, off[0]), fmaf(D[1], uf, off[1]),
+                                              fmaf(D[2], uf, off[2]), na.w);
                         } else {
                             src = nt.d[v];
                         }
