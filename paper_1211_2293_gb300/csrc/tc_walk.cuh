@@ -568,8 +568,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
 
         // force-loop unroll: deep for one or two bodies per lane; shallower
         // with four (registers), in the quadrupole walk (registers) and in
-        // the learned walk (its code must stay in the instruction cache next
-        // to the network's: 8 deep stalls on instruction fetch)
+        // the learned walk (measured: 4 deep is the fastest there)
         constexpr int kUnroll = QUADW ? 2 : (LEARNED || B >= 4 ? 4 : 8);
         // one running (compensated) sum per body collects the cell tiles and
         // the body tiles alike
