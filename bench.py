@@ -293,6 +293,7 @@ def run_ours(args, rank, world, local_rank):
     peak = fp32_peak_tflops()
     traffic = _traffic_from_profile()
     probe = {"scalar_fma": tc.probe_fp32(False), "paired_fma": tc.probe_fp32(True)}
+    force_probe = tc.probe_force()
 
     # accuracy against direct summation (4096 sampled bodies), current state
     ctx.forces(args.theta, EPS)
@@ -386,7 +387,9 @@ def run_ours(args, rank, world, local_rank):
                          "frac_at_measured_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])
                                                     if clk.get("sm_mhz") else None),
                          "fp32_probe_tflops": probe,
-                         "frac_of_probe": achieved / probe["scalar_fma"] if probe["scalar_fma"] else None},
+                         "frac_of_probe": achieved / probe["scalar_fma"] if probe["scalar_fma"] else None,
+                         "force_loop_alone_tflops": force_probe,
+                         "force_loop_alone_frac": force_probe / peak},
             "e2e": {"value": e2e_val, "unit": "bodies/s", "h2d_bytes_per_step": int(16 * n),
                     "d2h_bytes_per_step": int(12 * n),
                     "what": "force evaluation from pinned host pos/mass: upload, build, walk/force, "

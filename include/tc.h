@@ -315,6 +315,14 @@ int tc_mlp_evals(tc_ctx *ctx, int64_t *evals);
  * fused multiply-adds; best of three timed launches. */
 int tc_probe_fp32(int paired, double *tflops);
 
+/* Measured throughput of the walk's force loop alone, in TFLOP/s at 20
+ * flops per body-source interaction: 4 blocks of 4 warps per SM (the walk's
+ * occupancy), each warp summing a 128-entry list tile in shared memory
+ * against two bodies per lane through the walk's own flush (paired FP32
+ * loop, SFU rsqrt, compensated accumulation), 4096 times; best of three
+ * timed launches.  No tree, no walk: the ceiling of the loop as written. */
+int tc_probe_force(double *tflops);
+
 /* Self-test of the failure path: runs one radix pass tile whose predecessor
  * never publishes, so its bounded look-back gives up (after about a second)
  * instead of waiting forever.  *err_bits receives the device error word it

@@ -1558,6 +1558,45 @@ int tc_probe_fp32(int paired, double* tflops)
     return TC_OK;
 }
 
+int tc_probe_force(double* tflops)
+{
+    if (!tflops) {
+        set_thread_error("tc_probe_force: null argument");
+        return TC_EINVAL;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    float* out = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(float));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int blocks = 4 * sms, reps = 4096;
+    double best = 0.0;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+        cudaEventRecord(e0, s);
+        const double inter = launch_force_probe(blocks, reps, out, s);
+        cudaEventRecord(e1, s);
+        e = cudaStreamSynchronize(s);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && ms > 0.f) best = std::max(best, 20.0 * inter / (ms * 1e-3) / 1e12);
+    }
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        set_thread_error("tc_probe_force: CUDA error");
+        return TC_ECUDA;
+    }
+    *tflops = best;
+    return TC_OK;
+}
+
 // Failure-path self-test: a device wait that can never be satisfied must
 // give up within its limit, report itself in the error word and leave the
 // device usable.

@@ -217,6 +217,10 @@ cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* sm
 cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s,
                         bool reset_totals = true);
 
+// the walk's force loop alone (tc_force_probe.cu); returns the interactions
+// the launch sums
+double launch_force_probe(int blocks, int reps, float* out, cudaStream_t s);
+
 // learned far-field correction (tc_mlp.cu)
 size_t mlp_dev_size();
 size_t mlp_frag_size();  // the inference part at the front of a device model

@@ -33,6 +33,7 @@ EXPORTS = [
     "tc_autotune", "tc_mlp_set", "tc_mlp_get", "tc_mlp_forward", "tc_mlp_loss_grad", "tc_mlp_train",
     "tc_mlp_pairs", "tc_mlp_evals", "tc_get_group_list", "tc_selftest_bounded_wait",
     "tc_probe_fp32",
+    "tc_probe_force",
 ]
 
 MLP_NPARAM = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
@@ -109,6 +110,7 @@ def load(path: str | None = None):
         "tc_get_group_list": ([P, I64, F, P, P, I64, P, P], I32),
         "tc_selftest_bounded_wait": ([P, P], I32),
         "tc_probe_fp32": ([I32, P], I32),
+        "tc_probe_force": ([P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -148,6 +150,15 @@ def probe_fp32(paired: bool = False) -> float:
     lib = load()
     t = ctypes.c_double()
     _check(lib.tc_probe_fp32(int(bool(paired)), ctypes.byref(t)))
+    return t.value
+
+
+def probe_force() -> float:
+    """Measured TFLOP/s of the walk's force loop alone, 20 flops per
+    interaction (see tc.h)."""
+    lib = load()
+    t = ctypes.c_double()
+    _check(lib.tc_probe_force(ctypes.byref(t)))
     return t.value
 
 

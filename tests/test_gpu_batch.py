@@ -174,3 +174,19 @@ def test_bounded_device_wait_gives_up_and_reports(tc):
     ctx.build(_dev(pos), _dev(mass), 8)
     ctx.forces(0.5, 0.01)
     assert np.all(np.isfinite(ctx.get_acc()))
+
+
+def test_fp32_and_force_loop_probes(tc):
+    """The FP32 probe reaches the derived CUDA-core peak (2 flops x 128 lanes x
+    SMs x clock, within the clock's reach), and the force loop alone stays
+    under the ceiling its instruction mix sets: 12 FMA-pipe operations per
+    interaction counted as 20 flops, 20/24 of the FP32 peak."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = 2 * 128 * sms * 2.07e9 / 1e12
+    scalar, paired = tc.probe_fp32(False), tc.probe_fp32(True)
+    assert 0.5 * peak < scalar < 1.05 * peak
+    assert 0.5 * peak < paired < 1.05 * peak
+    loop = tc.probe_force()
+    assert 0.1 * peak < loop <= 20.0 / 24.0 * 1.02 * max(scalar, paired)
