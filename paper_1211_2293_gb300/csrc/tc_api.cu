@@ -498,6 +498,7 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
         for (int k = c->walk_ncls - 1; k >= 0 && e == cudaSuccess; k--) {
             a.glist = c->glists + (int64_t)k * c->cap_n;
             a.glist_n = c->glist_n + k;
+            a.work_slot = k;
             e = launch_walk(a, c->walk_cls[k], c->walk_cls_grid[k], c->walk_cls_smem[k], s,
                             k == c->walk_ncls - 1);
         }

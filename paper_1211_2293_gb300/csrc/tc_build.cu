@@ -762,10 +762,14 @@ void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t
     if (quad) k_leaf_moments<true><<<g, 128, 0, s>>>(body, sysp, info, nt);
     else k_leaf_moments<false><<<g, 128, 0, s>>>(body, sysp, info, nt);
     count_launches(1);
+    // the level launches take a small grid (4 blocks per SM of a 152-SM
+    // part): most levels hold few internal cells, the launches past the
+    // tree's depth none, and a large grid costs more to start than they work
+    const unsigned gl = g < 608u ? g : 608u;
     const int top = depth < 0 ? kMaxLevel : depth;
     for (int lev = top - 1; lev >= 0; lev--) {
-        if (quad) k_level_moments<true><<<g, 128, 0, s>>>(lev, level_start, sysp, info, nt);
-        else k_level_moments<false><<<g, 128, 0, s>>>(lev, level_start, sysp, info, nt);
+        if (quad) k_level_moments<true><<<gl, 128, 0, s>>>(lev, level_start, sysp, info, nt);
+        else k_level_moments<false><<<gl, 128, 0, s>>>(lev, level_start, sysp, info, nt);
         count_launches(1);
     }
 }

@@ -49,7 +49,7 @@ struct Info {
     int64_t M;         // number of nodes
     int64_t G;         // number of groups
     int64_t cap_m;     // node table capacity (for the device-side check)
-    uint32_t work[2];  // walk work-queue counter (work[0]), padding
+    uint32_t work[4];  // walk work-queue counters, one per launch of a force phase
     unsigned long long interactions;  // body-source interactions of the last walk
     unsigned long long cells;         // body-cell interactions (group size x accepted cells)
     unsigned long long bodies;        // body-body interactions (group size x direct-list bodies)
@@ -195,6 +195,7 @@ struct WalkArgs {
     // group list (null: every group 0..G-1): walk glist[0, *glist_n) only
     const int32_t* glist;
     const int32_t* glist_n;
+    int work_slot;  // this launch's work-queue counter, info->work[work_slot]
 };
 struct WalkConfig {
     int gmax;         // 32, 64 or 128
@@ -212,8 +213,10 @@ struct WalkConfig {
 // host-side preparation of the walk kernel's launch (attributes, occupancy);
 // call before a stream capture
 cudaError_t prepare_walk(const WalkConfig& c, int num_sms, int* grid, size_t* smem);
-// reset_totals: zero the interaction totals first (the first launch of a
-// force phase that is split over several launches, one per size class)
+// reset_totals: zero the work-queue counters and (outside list export) the
+// interaction totals first -- the first launch of a force phase; the later
+// launches of a phase split over size classes count on counters of their own
+// (a.work_slot) zeroed with the first
 cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s,
                         bool reset_totals = true);
 

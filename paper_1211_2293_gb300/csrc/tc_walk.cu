@@ -2,6 +2,8 @@
 // the bodies per lane (groups of up to 32 bodies, down to the paper's
 // one-body lists: one; 64: two; 128: four) and the tile size the object
 // (tc_walk_unit.cu, compiled once per pair) holding those kernels.
+#include <cstddef>
+
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -16,6 +18,11 @@ TC_WALK_DECL_B(2)
 TC_WALK_DECL_B(4)
 #undef TC_WALK_DECL_B
 #undef TC_WALK_DECL
+
+// the walk's one memset spans the counters and the totals behind them
+static_assert(offsetof(Info, interactions) == offsetof(Info, work) + sizeof(Info::work) &&
+                  offsetof(Info, bodies) == offsetof(Info, interactions) + 2 * sizeof(unsigned long long),
+              "work counters and interaction totals must be contiguous");
 
 namespace {
 
@@ -50,9 +57,13 @@ cudaError_t launch_walk(const WalkArgs& a, const WalkConfig& c, int grid, size_t
                         bool reset_totals)
 {
     if (bodies_per_lane(c.gmax) == 0) return cudaErrorInvalidValue;
-    cudaMemsetAsync(&a.info->work[0], 0, sizeof(a.info->work), s);
-    if (reset_totals && !a.list_cells)  // list export leaves the last force phase's totals alone
-        cudaMemsetAsync(&a.info->interactions, 0, 3 * sizeof(unsigned long long), s);
+    if (a.work_slot < 0 || a.work_slot >= 4) return cudaErrorInvalidValue;
+    // the counters and the totals behind them in one memset (list export
+    // leaves the last force phase's totals alone)
+    if (reset_totals)
+        cudaMemsetAsync(&a.info->work[0], 0,
+                        a.list_cells ? sizeof(a.info->work)
+                                     : sizeof(a.info->work) + 3 * sizeof(unsigned long long), s);
     TC_WALK_PICK(launch_walk, a, c, grid, smem, s)
 }
 

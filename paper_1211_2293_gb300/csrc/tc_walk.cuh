@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
 
     for (;;) {
         int g = 0;
-        if (lane == 0) g = (int)atomicAdd(&a.info->work[0], 1u) + g_shift;
+        if (lane == 0) g = (int)atomicAdd(&a.info->work[a.work_slot], 1u) + g_shift;
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= G) break;
         if (a.glist) g = __ldg(a.glist + g);  // this launch's size class
