@@ -406,22 +406,27 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
         const int4 c = nt.c[v];
         double C[3];
         cube_centre(sysp[c.w], c, C);
+        // m and sum m x in absolute coordinates (the product of two floats is
+        // exact in FP64, so each term is one fused multiply-add): GB300 runs
+        // FP64 at a small fraction of its FP32 rate and this kernel is bound
+        // by it
         double m = 0.0, S[3] = {0, 0, 0};
         for (int j = b.x; j < b.x + b.y; j++) {
             const float4 q = body[j];
-            m += (double)q.w;
-            S[0] += (double)q.w * ((double)q.x - C[0]);
-            S[1] += (double)q.w * ((double)q.y - C[1]);
-            S[2] += (double)q.w * ((double)q.z - C[2]);
+            const double w = (double)q.w;
+            m += w;
+            S[0] = fma(w, (double)q.x, S[0]);
+            S[1] = fma(w, (double)q.y, S[1]);
+            S[2] = fma(w, (double)q.z, S[2]);
         }
         const double inv = 1.0 / m;
-        const double off[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
+        const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
         double Q[6] = {0, 0, 0, 0, 0, 0};
         for (int j = b.x; QUAD && j < b.x + b.y; j++) {
             const float4 q = body[j];
-            const double dx = ((double)q.x - C[0]) - off[0];
-            const double dy = ((double)q.y - C[1]) - off[1];
-            const double dz = ((double)q.z - C[2]) - off[2];
+            const double dx = (double)q.x - com[0];
+            const double dy = (double)q.y - com[1];
+            const double dz = (double)q.z - com[2];
             const double mj = (double)q.w;
             Q[0] += mj * dx * dx;
             Q[1] += mj * dx * dy;
@@ -430,7 +435,6 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
             Q[4] += mj * dy * dz;
             Q[5] += mj * dz * dz;
         }
-        const double com[3] = {C[0] + off[0], C[1] + off[1], C[2] + off[2]};
         store_node<QUAD>(nt, v, m, com, Q, C);
     }
 }
