@@ -285,6 +285,61 @@ __global__ void k_node_counts(const uint64_t* __restrict__ keys, const uint32_t*
     if ((threadIdx.x & 31) == 0) atomicMax(depth, t);
 }
 
+// The same two steps in one kernel for leaf_max <= kTileWindow: a block of
+// kCountThreads sorted bodies stages the keys and systems of
+// [b0 - leaf_max, b0 + kCountThreads + leaf_max) in shared memory, forms the
+// window digits cd(key_j, key_j+leaf_max) of [b0 - leaf_max, b0 + kCountThreads)
+// there, and takes each body's window maximum from them.
+constexpr int kCountThreads = 256;
+constexpr int kTileWindow = 256;
+
+__global__ void __launch_bounds__(kCountThreads) k_node_counts_tiled(const uint64_t* __restrict__ keys,
+                                                                     const uint32_t* __restrict__ sys_of, int64_t n,
+                                                                     int leaf_max, int8_t* __restrict__ delta,
+                                                                     int8_t* __restrict__ top,
+                                                                     uint32_t* __restrict__ nstart,
+                                                                     int32_t* __restrict__ depth)
+{
+    __shared__ uint64_t sk[kCountThreads + 2 * kTileWindow];
+    __shared__ uint32_t ss[kCountThreads + 2 * kTileWindow];
+    __shared__ int8_t sw[kCountThreads + kTileWindow];
+    const int64_t b0 = (int64_t)blockIdx.x * kCountThreads;
+    const int64_t base = b0 - leaf_max;  // smem index 0 holds body base
+    const int nk = kCountThreads + 2 * leaf_max;
+    for (int i = threadIdx.x; i < nk; i += kCountThreads) {
+        const int64_t j = base + i;
+        const bool in = j >= 0 && j < n;
+        sk[i] = in ? keys[j] : 0ull;
+        ss[i] = in ? sys_of[j] : 0xffffffffu;
+    }
+    __syncthreads();
+    // window digits of bodies base .. b0 + kCountThreads - 1
+    const int nw = kCountThreads + leaf_max;
+    for (int i = threadIdx.x; i < nw; i += kCountThreads) {
+        const int64_t j = base + i;
+        int8_t v = -1;
+        if (j >= 0 && j + leaf_max < n && ss[i] == ss[i + leaf_max]) v = (int8_t)common_digits(sk[i], sk[i + leaf_max]);
+        sw[i] = v;
+    }
+    __syncthreads();
+    const int64_t s = b0 + threadIdx.x;
+    int t = 0;
+    if (s < n) {
+        const int i = threadIdx.x + leaf_max;  // smem index of body s
+        const int d = (s == 0 || ss[i] != ss[i - 1]) ? -1 : common_digits(sk[i - 1], sk[i]);
+        int W = -1;
+        const int i0 = s - leaf_max < 0 ? (int)(leaf_max - s) : 0;  // window clipped at body 0
+        for (int k = i0; k <= leaf_max; k++) W = max(W, (int)sw[threadIdx.x + k]);
+        t = min(W + 1, kMaxLevel);
+        delta[s] = (int8_t)d;
+        top[s] = (int8_t)t;
+        nstart[s] = (uint32_t)max(0, t - d);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(depth, t);
+}
+
 __global__ void k_check_capacity(const uint32_t* __restrict__ m_total, Info* info)
 {
     const int64_t M = *m_total;
@@ -723,6 +778,12 @@ void launch_gather(const float* pos, const float* mass, const uint32_t* perm, in
 void launch_node_counts(const uint64_t* keys, const uint32_t* sys_of, int64_t n, int leaf_max, int8_t* w,
                         int8_t* delta, int8_t* top, uint32_t* nstart, int32_t* depth, cudaStream_t s)
 {
+    if (leaf_max <= kTileWindow) {
+        k_node_counts_tiled<<<nblk(n, kCountThreads), kCountThreads, 0, s>>>(keys, sys_of, n, leaf_max, delta, top,
+                                                                            nstart, depth);
+        count_launches(1);
+        return;
+    }
     k_window<<<nblk(n, 256), 256, 0, s>>>(keys, sys_of, n, leaf_max, w);
     k_node_counts<<<nblk(n, 256), 256, 0, s>>>(keys, sys_of, w, n, leaf_max, delta, top, nstart, depth);
     count_launches(2);

@@ -83,7 +83,8 @@ def _compare_tree(ctx, t, gmax):
 @pytest.mark.parametrize("kind,n,leaf,gmax", [
     ("plummer", 4096, 8, 64), ("random", 1, 1, 32), ("random", 2, 1, 32), ("random", 9, 8, 32),
     ("random", 17, 4, 64), ("random", 100, 3, 128), ("uniform", 5000, 16, 64), ("coincident", 40, 4, 32),
-    ("random", 3000, 1, 32), ("plummer", 20000, 64, 128)])
+    ("random", 3000, 1, 32), ("plummer", 20000, 64, 128), ("plummer", 30000, 256, 128),
+    ("uniform", 30000, 300, 64)])
 def test_tree_bit_exact(tc, kind, n, leaf, gmax):
     p, _, m = _bodies(kind, n, 7)
     ctx = _ctx(tc, gmax=gmax)
