@@ -81,6 +81,7 @@ struct tc_ctx {
     int32_t* glists = nullptr;   // 3 x cap_n group indices
     int32_t* glist_n = nullptr;  // 3 counts, then the split's scratch
     int walk_ncls = 0;
+    int depth_hint = -1;  // tree depth of the last build the host saw (-1: none)
     WalkConfig walk_cls[3]{};
     int walk_cls_grid[3] = {0, 0, 0};
     size_t walk_cls_smem[3] = {0, 0, 0};
@@ -406,6 +407,7 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
         c->cap_m_h = c->cap_m;
         TC_CUDA(c, cudaMemcpyAsync(&c->info->cap_m, &c->cap_m_h, sizeof(int64_t), cudaMemcpyHostToDevice, s));
         depth = c->info_h->depth;
+        c->depth_hint = depth;
     }
     launch_check_capacity(&c->totals[0], c->info, s);
     launch_emit_preorder(c->delta, c->nstart, c->prepos, n, c->info, c->pre_level, c->pre_first, c->iota, s);
@@ -416,7 +418,7 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
     launch_node_finalize(c->keys, c->top, c->sys_of, c->sysp, n, c->pre_level, c->iota, c->pre_first, c->bfs_of_pre,
                          c->cap_m, c->info, c->nt, s);
     // after the level sort, ghist[l] is the first breadth-first index of level l
-    launch_moments(c->body, c->cap_m, depth, c->sb.ghist, c->sys_of, c->sysp, c->info, c->nt, c->cfg.quad != 0, s);
+    launch_moments(c->body, c->cap_m, depth, c->depth_hint, c->sb.ghist, c->sys_of, c->sysp, c->info, c->nt, c->cfg.quad != 0, s);
     launch_sys_mass(c->sysp, c->nsys, c->nt, c->info, s);
     launch_group_marks(c->cap_m, c->info, c->nt, c->cfg.gmax, n, c->gflag, c->gref_at, s);
     scan_u32(c->gflag, c->gscan, n, &c->totals[1], c->sb.blocksum, s);

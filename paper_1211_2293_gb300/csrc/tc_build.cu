@@ -494,6 +494,41 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
     }
 }
 
+// one internal cell v from its children (a leaf returns at once)
+template <bool QUAD>
+__device__ __forceinline__ void level_node(int64_t v, const SysParams* __restrict__ sysp, NodeTables& nt)
+{
+    const int4 pb = nt.b[v];
+    const int nch = pb.w >> 8;
+    if (nch == 0) return;  // leaf: done by k_leaf_moments
+    double m = 0.0, S[3] = {0, 0, 0};
+    for (int k = 0; k < nch; k++) {
+        const int64_t c = pb.z + k;
+        const double mc = nt.mass64[c];
+        m += mc;
+        for (int a = 0; a < 3; a++) S[a] += mc * nt.com64[3 * c + a];
+    }
+    const double inv = 1.0 / m;
+    const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; QUAD && k < nch; k++) {
+        const int64_t c = pb.z + k;
+        const double mc = nt.mass64[c];
+        double d[3];
+        for (int a = 0; a < 3; a++) d[a] = nt.com64[3 * c + a] - com[a];
+        Q[0] += nt.quad64[6 * c + 0] + mc * d[0] * d[0];
+        Q[1] += nt.quad64[6 * c + 1] + mc * d[0] * d[1];
+        Q[2] += nt.quad64[6 * c + 2] + mc * d[0] * d[2];
+        Q[3] += nt.quad64[6 * c + 3] + mc * d[1] * d[1];
+        Q[4] += nt.quad64[6 * c + 4] + mc * d[1] * d[2];
+        Q[5] += nt.quad64[6 * c + 5] + mc * d[2] * d[2];
+    }
+    const int4 cc = nt.c[v];
+    double C[3];
+    cube_centre(sysp[cc.w], cc, C);
+    store_node<QUAD>(nt, v, m, com, Q, C);
+}
+
 // internal cells of level `lev`: [level_start[lev], level_start[lev + 1])
 template <bool QUAD>
 __global__ void k_level_moments(int lev, const uint32_t* __restrict__ level_start,
@@ -503,36 +538,23 @@ __global__ void k_level_moments(int lev, const uint32_t* __restrict__ level_star
     const int64_t start = level_start[lev];
     const int64_t end = level_start[lev + 1];
     for (int64_t v = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < end;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int4 pb = nt.b[v];
-        const int nch = pb.w >> 8;
-        if (nch == 0) continue;  // leaf: done by k_leaf_moments
-        double m = 0.0, S[3] = {0, 0, 0};
-        for (int k = 0; k < nch; k++) {
-            const int64_t c = pb.z + k;
-            const double mc = nt.mass64[c];
-            m += mc;
-            for (int a = 0; a < 3; a++) S[a] += mc * nt.com64[3 * c + a];
-        }
-        const double inv = 1.0 / m;
-        const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
-        double Q[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = 0; QUAD && k < nch; k++) {
-            const int64_t c = pb.z + k;
-            const double mc = nt.mass64[c];
-            double d[3];
-            for (int a = 0; a < 3; a++) d[a] = nt.com64[3 * c + a] - com[a];
-            Q[0] += nt.quad64[6 * c + 0] + mc * d[0] * d[0];
-            Q[1] += nt.quad64[6 * c + 1] + mc * d[0] * d[1];
-            Q[2] += nt.quad64[6 * c + 2] + mc * d[0] * d[2];
-            Q[3] += nt.quad64[6 * c + 3] + mc * d[1] * d[1];
-            Q[4] += nt.quad64[6 * c + 4] + mc * d[1] * d[2];
-            Q[5] += nt.quad64[6 * c + 5] + mc * d[2] * d[2];
-        }
-        const int4 cc = nt.c[v];
-        double C[3];
-        cube_centre(sysp[cc.w], cc, C);
-        store_node<QUAD>(nt, v, m, com, Q, C);
+         v += (int64_t)gridDim.x * blockDim.x)
+        level_node<QUAD>(v, sysp, nt);
+}
+
+// every level from the deepest possible down to lev_lo, in one block: the
+// cells past the depth a captured step expects (normally none)
+template <bool QUAD>
+__global__ void __launch_bounds__(256) k_level_moments_deep(int lev_lo, const uint32_t* __restrict__ level_start,
+                                                             const SysParams* __restrict__ sysp, const Info* info,
+                                                             NodeTables nt)
+{
+    if (capacity_failed(info)) return;
+    for (int lev = kMaxLevel - 1; lev >= lev_lo; lev--) {
+        const int64_t start = level_start[lev];
+        const int64_t end = level_start[lev + 1];
+        for (int64_t v = start + threadIdx.x; v < end; v += blockDim.x) level_node<QUAD>(v, sysp, nt);
+        __syncthreads();
     }
 }
 
@@ -818,7 +840,7 @@ void launch_node_finalize(const uint64_t* keys, const int8_t* top, const uint32_
     count_launches(1);
 }
 
-void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t* level_start,
+void launch_moments(const float4* body, int64_t cap_m, int depth, int depth_hint, const uint32_t* level_start,
                     const uint32_t* sys_of, const SysParams* sysp, const Info* info, NodeTables nt, bool quad,
                     cudaStream_t s)
 {
@@ -831,7 +853,15 @@ void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t
     // part): most levels hold few internal cells, the launches past the
     // tree's depth none, and a large grid costs more to start than they work
     const unsigned gl = g < 608u ? g : 608u;
-    const int top = depth < 0 ? kMaxLevel : depth;
+    int top = depth < 0 ? kMaxLevel : depth;
+    if (depth < 0 && depth_hint >= 0 && depth_hint + 3 < kMaxLevel) {
+        // depth unknown on the host (a captured step): the levels from the
+        // expected depth + 3 down get a launch each, any deeper ones one block
+        top = depth_hint + 3;
+        if (quad) k_level_moments_deep<true><<<1, 256, 0, s>>>(top, level_start, sysp, info, nt);
+        else k_level_moments_deep<false><<<1, 256, 0, s>>>(top, level_start, sysp, info, nt);
+        count_launches(1);
+    }
     for (int lev = top - 1; lev >= 0; lev--) {
         if (quad) k_level_moments<true><<<gl, 128, 0, s>>>(lev, level_start, sysp, info, nt);
         else k_level_moments<false><<<gl, 128, 0, s>>>(lev, level_start, sysp, info, nt);

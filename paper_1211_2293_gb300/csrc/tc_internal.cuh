@@ -136,10 +136,13 @@ void launch_node_finalize(const uint64_t* keys, const int8_t* top, const uint32_
                           const uint32_t* pre_first, const uint32_t* bfs_of_pre, int64_t cap_m, const Info* info,
                           NodeTables nt, cudaStream_t s);
 void launch_inverse_perm(const uint32_t* perm, int64_t cap_m, const Info* info, uint32_t* inv, cudaStream_t s);
-// moments: leaves, then internal levels depth-1 .. 0 (depth < 0: all 21
-// levels, each reading its range on the device); level_start[l] is the first
-// node of level l (the level sort's digit offsets; level_start[l+1] ends it)
-void launch_moments(const float4* body, int64_t cap_m, int depth, const uint32_t* level_start,
+// moments: leaves, then internal levels depth-1 .. 0 (depth < 0: the depth
+// is known on the device only; with depth_hint >= 0, the depth of an earlier
+// build, levels depth_hint+2 .. 0 get a launch each and any deeper ones one
+// block, else all 21 levels get a launch); each level reads its range on the
+// device: level_start[l] is the first node of level l (the level sort's
+// digit offsets; level_start[l+1] ends it)
+void launch_moments(const float4* body, int64_t cap_m, int depth, int depth_hint, const uint32_t* level_start,
                     const uint32_t* sys_of, const SysParams* sysp, const Info* info, NodeTables nt, bool quad,
                     cudaStream_t s);
 void launch_group_marks(int64_t cap_m, const Info* info, const NodeTables nt, int gmax, int64_t n,

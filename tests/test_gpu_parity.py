@@ -498,3 +498,27 @@ def test_size_class_modes_agree(tc, gmax):
         assert np.array_equal(lists[0][k], lists[1][k]), k
     assert lists[0]["interactions"] == lists[1]["interactions"]
     assert np.array_equal(accs[0][0], accs[1][0]) and np.array_equal(accs[0][1], accs[1][1])
+
+
+def test_step_builds_a_deeper_tree_than_the_last_synchronised_one(tc):
+    """A captured step knows the tree depth only from an earlier build; its
+    moment reduction gives each level down to that depth + 2 a launch and
+    any deeper level one block.  The drift of one step moves 40 bodies into
+    a cube of side 1e-6, so the step's tree is 15+ levels deeper than the
+    last synchronised one: its moments and structure still equal the
+    oracle's on the new positions."""
+    p, _, m = _bodies("uniform", 4096, 31)
+    ctx = _ctx(tc, gmax=64)
+    ctx.build(_dev(p), _dev(m), 8)
+    ctx.forces(0.5, 0.01)
+    ctx.sizes()  # synchronise: the depth hint is this shallow tree's
+    dt = 1e-6
+    target = 0.9 + 1e-6 * np.random.default_rng(5).random((40, 3))
+    v = np.zeros_like(p)
+    v[:40] = ((target - p[:40]) / dt).astype(np.float32)
+    ctx.set_velocity(_dev(v))
+    ctx.step(dt)  # kick, drift into the cluster, rebuild inside the captured step, walk, kick
+    pos, _ = ctx.get_state()
+    t = oracle.Tree(pos, m, 8, 64)
+    assert t.level.max() >= 15
+    _compare_tree(ctx, t, 64)
