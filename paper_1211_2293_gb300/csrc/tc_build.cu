@@ -278,11 +278,17 @@ __global__ void k_node_counts(const uint64_t* __restrict__ keys, const uint32_t*
         top[s] = (int8_t)t;
         nstart[s] = (uint32_t)max(0, t - d);
     }
-    // deepest level of the forest: a warp maximum (every lane of the launch's
-    // full warps takes part), then one atomic per warp
+    // deepest level of the forest: a block maximum, then one atomic per
+    // block (blocks of 256)
+    __shared__ int wmax[8];
 #pragma unroll
     for (int o = 16; o; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(depth, t);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) t = max(t, wmax[k]);
+        atomicMax(depth, t);
+    }
 }
 
 // The same two steps in one kernel for leaf_max <= kTileWindow: a block of
@@ -335,9 +341,17 @@ __global__ void __launch_bounds__(kCountThreads) k_node_counts_tiled(const uint6
         top[s] = (int8_t)t;
         nstart[s] = (uint32_t)max(0, t - d);
     }
+    // deepest level: a block maximum, then one atomic per block (one per
+    // warp made the atomics on the single word the kernel's bottleneck)
+    __shared__ int wmax[kCountThreads / 32];
 #pragma unroll
     for (int o = 16; o; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(depth, t);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kCountThreads / 32; k++) t = max(t, wmax[k]);
+        atomicMax(depth, t);
+    }
 }
 
 __global__ void k_check_capacity(const uint32_t* __restrict__ m_total, Info* info)
