@@ -181,8 +181,10 @@ template <typename K>
 constexpr size_t onesweep_smem() { return (size_t)kSortTile * (sizeof(K) + sizeof(uint32_t)); }
 
 // SYS: the digit is taken from the system of the value's body, sys_of[val]
+// Three tiles per SM (80 registers): the build at 2^22 takes 3 % less time
+// than with two, at 2^20 the same.
 template <typename K, bool SYS>
-__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n_host, const int64_t* __restrict__ n_dev,
                                                            int shift, const uint32_t* __restrict__ goff,
