@@ -86,10 +86,24 @@ __global__ void k_scan_top(uint32_t* __restrict__ bsum, int64_t nb, uint32_t* __
     if (threadIdx.x == 0 && total) *total = carry;
 }
 
+// PREFIX: the block's offset is the sum of the raw partials of the blocks
+// before it (no k_scan_top; the last block writes the total) -- for up to
+// kScanFusedBlocks blocks, where that sum is cheaper than another launch
+constexpr int64_t kScanFusedBlocks = 1024;
+
+template <bool PREFIX>
 __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
-                            const uint32_t* __restrict__ bsum)
+                            const uint32_t* __restrict__ bsum, uint32_t* __restrict__ total)
 {
     __shared__ uint32_t sm[33];
+    uint32_t off = 0;
+    if (PREFIX) {
+        uint32_t t = 0;
+        for (int64_t j = threadIdx.x; j < (int64_t)blockIdx.x; j += kScanThreads) t += bsum[j];
+        block_excl_scan<kScanThreads>(t, off, sm);  // off = the block-wide sum
+    } else {
+        off = bsum[blockIdx.x];
+    }
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
@@ -100,7 +114,8 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restric
         s += v[i];
     }
     uint32_t tot;
-    uint32_t e = block_excl_scan<kScanThreads>(s, tot, sm) + bsum[blockIdx.x];
+    uint32_t e = block_excl_scan<kScanThreads>(s, tot, sm) + off;
+    if (PREFIX && total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = off + tot;
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
         int64_t k = base + i;
@@ -336,8 +351,13 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
     }
     int64_t nb = (n + kScanTile - 1) / kScanTile;
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, blocksum);
+    if (nb <= kScanFusedBlocks) {
+        k_scan_down<true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, blocksum, total_dev);
+        count_launches(2);
+        return;
+    }
     k_scan_top<<<1, 1024, 0, s>>>(blocksum, nb, total_dev);
-    k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, blocksum);
+    k_scan_down<false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, blocksum, nullptr);
     count_launches(3);
 }
 
