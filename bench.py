@@ -113,10 +113,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile():
-    """dram bytes of one force phase (both size-class launches of the walk)
-    from the committed ncu summary, or None if the walk kernel's source
-    changed since it was captured."""
+def _traffic_from_profile(shape=None):
+    """dram bytes of one force phase (every launch of the walk) from the
+    committed ncu summary, or None if the walk kernel's source changed since
+    it was captured or the summary's walk shape is not the one measured."""
     try:
         txt = open(PROFILE_TRAFFIC).read()
         cur = hashlib.sha256(open(WALK_SRC, "rb").read()).hexdigest()[:16]
@@ -126,6 +126,8 @@ def _traffic_from_profile():
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
         if kv.get("walk_source_sha256_16") != cur:
+            return None
+        if shape is not None and kv.get("walk_shape") != "%d,%d,%d" % (shape["gmax"], shape["tile"], shape["warps"]):
             return None
         return float(kv["dram_bytes_per_phase"])
     except Exception:
@@ -225,6 +227,19 @@ def aggregate_over_ranks(ms, n_per_rank, world, dist=None, device="cpu"):
     return ms, n_per_rank * world / (ms / 1e3)
 
 
+def walk_shape(ctx, args, theta):
+    """The walk's group size, list tile and warps per block: the autotuner's
+    choice for this workload and opening angle (it times the walk kernel for
+    every shape on the current bodies and keeps the fastest), or --shape."""
+    if args.shape:
+        g, t, w = (int(x) for x in args.shape.split(","))
+        ctx.set_config(gmax=g, tile=t, warps=w)
+        return {"gmax": g, "tile": t, "warps": w, "chosen_by": "--shape"}
+    best, ms = ctx.autotune(theta, EPS, reps=3)
+    return {"gmax": best["gmax"], "tile": best["tile"], "warps": best["warps"], "chosen_by": "autotuner",
+            "walk_ms_when_tuned": ms}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -244,6 +259,7 @@ def run_ours(args, rank, world, local_rank):
     ctx = tc.Context(want_pot=0, verify=0)
     ctx.build(P, Mm, LEAF)
     ctx.set_velocity(V)
+    shape = walk_shape(ctx, args, args.theta)
     ctx.forces(args.theta, EPS)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -299,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
     inter_avg = statistics.mean(inter)
     achieved = inter_avg * FLOPS_PER_INTERACTION / (walk_ms / 1e3) / 1e12
     peak = fp32_peak_tflops()
-    traffic = _traffic_from_profile()
+    traffic = _traffic_from_profile(shape)
     probe = {"scalar_fma": tc.probe_fp32(False), "paired_fma": tc.probe_fp32(True)}
     force_probe = tc.probe_force()
 
@@ -315,6 +331,7 @@ def run_ours(args, rank, world, local_rank):
     # few timed steps (L2 flushed between them) and the accuracy
     alt = None
     if args.theta != THETA_ALT:
+        alt_shape = walk_shape(ctx, args, THETA_ALT)
         ctx.forces(THETA_ALT, EPS)
         for _ in range(2):
             ctx.step(DT)
@@ -340,7 +357,7 @@ def run_ours(args, rank, world, local_rank):
         a7 = ctx.get_acc()[idx].astype(np.float64)
         ad7, _ = ctx.direct(idx, EPS)
         a_walk = atim["walk_ms"] / len(alt_ms)
-        alt = {"theta": THETA_ALT, "ms_per_step": statistics.mean(alt_ms),
+        alt = {"theta": THETA_ALT, "walk_shape": alt_shape, "ms_per_step": statistics.mean(alt_ms),
                "bodies_per_s": n / (statistics.mean(alt_ms) / 1e3), "walk_ms": a_walk,
                "interactions_per_step": statistics.mean(alt_inter),
                "fp32_tflops": statistics.mean(alt_inter) * FLOPS_PER_INTERACTION / (a_walk / 1e3) / 1e12,
@@ -351,7 +368,7 @@ def run_ours(args, rank, world, local_rank):
     hp = torch.from_numpy(p).pin_memory()
     hm = torch.from_numpy(m).pin_memory()
     hacc = torch.empty((n, 3), dtype=torch.float32).pin_memory()
-    e2e_ctx = tc.Context(want_pot=0, verify=0)
+    e2e_ctx = tc.Context(want_pot=0, verify=0, gmax=shape["gmax"], tile=shape["tile"], warps=shape["warps"])
     for _ in range(2):
         e2e_ctx.build(hp, hm, LEAF)
         e2e_ctx.forces(args.theta, EPS)
@@ -385,6 +402,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(n, args.theta),
+            "walk_shape": shape,
             "rms_force_err": rms,
             "at_theta_0.7": alt,
             "interactions_per_step": inter_avg,
@@ -393,7 +411,8 @@ def run_ours(args, rank, world, local_rank):
                                   "update": tim["update_ms"] / args.steps},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_walk (walk + force; one force phase = one launch per group-size class)",
+                         "kernel": "k_walk (walk + force; one force phase = one launch, or one per group-size "
+                                   "class for gmax 64 and 128)",
                          "peak_basis": "2 flops x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)",
                          "frac_at_measured_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])
                                                     if clk.get("sm_mhz") else None),
@@ -745,6 +764,8 @@ def main():
     ap.add_argument("--cpu-frac", type=int, default=8, help="oracle walks 1/cpu_frac of the groups")
     ap.add_argument("--ref-frac", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="uniform: walk shape 'gmax,tile,warps' instead of the autotuner's choice")
     ap.add_argument("--workload", choices=["uniform", "batch", "precision", "learned"], default="uniform",
                     help="uniform: the benchmark line; batch: 512 Plummer systems in one forest; "
                          "precision: cell-relative vs plain float32 on two colliding Plummer spheres; "
