@@ -199,7 +199,7 @@ int tc_diag(tc_ctx *ctx, double *out8);
 
 /* Direct O(N * ns) summation for bodies idx[0..ns) (original indices) over
  * all n bodies of the current state: acc (ns x 3) and pot (ns, nullable),
- * FP32 terms, FP64 accumulation.  The accuracy judge of the treecode. */
+ * FP32 terms, FP64 accumulation.  The accuracy reference of the treecode. */
 int tc_direct(tc_ctx *ctx, const int64_t *idx, int64_t ns, float eps, float G, double *acc,
               double *pot);
 

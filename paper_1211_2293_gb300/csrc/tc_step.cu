@@ -1,5 +1,5 @@
 // tc_step.cu -- moving the bodies (kick-drift-kick leapfrog), FP64
-// diagnostics and the direct-summation judge.
+// diagnostics and the direct-summation reference.
 //
 // Paper, Sec. 3.1: after the force summation each body updates its position
 // and velocity.  The integrator is not named; the kick-drift-kick leapfrog

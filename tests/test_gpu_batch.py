@@ -67,7 +67,7 @@ def test_batch_matches_per_system_oracle(tc, gmax, theta):
             _check_forces(acc[a:b], pot[a:b], w, t, body_ok)
         else:
             assert np.all(acc[a:b] == 0)
-        # the direct-sum judge sums within the system only
+        # the direct-sum reference sums within the system only
         idx = np.arange(a, b, max(1, (b - a) // 50))
         ad, _ = ctx.direct(idx, 0.01)
         ao, _ = oracle.direct(p, m, 0.01, idx=idx - a)
