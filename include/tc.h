@@ -107,8 +107,9 @@ int tc_set_stream(tc_ctx *ctx, void *cuda_stream);
  * leaf_max (a cube is divided while it holds more than leaf_max bodies,
  * down to level 21), the cells' masses and centres of mass (FP64 reduction)
  * and the body groups.  1 <= n < 2^31, 1 <= leaf_max <= 4096, masses > 0.
- * Velocities are reset to zero when n changes.  Synchronises once (to size
- * the node table). */
+ * Velocities are reset to zero when n changes.  Synchronises with the
+ * device part-way (to report invalid input and size the node table); the
+ * rest is enqueued. */
 int tc_ctx_build(tc_ctx *ctx, const float *pos, const float *mass, int64_t n, int leaf_max);
 
 /* A batch of nsys independent systems in one context (bodies of system s are
