@@ -225,15 +225,21 @@ int tc_get_timings(tc_ctx *ctx, double *out6);
  * the inputs are read where they are, the outputs written where they are,
  * and the only scratch (per-slice partial sums) lives in a fixed 4 MiB
  * array that every GPU loading libtc holds until the process exits.
- *   pos (n x 3), mass (n), idx (ns, original indices in [0, n)), acc
- *   (ns x 3), pot (ns, nullable): all device-accessible memory (device,
- *   managed or mapped host); host pageable memory is rejected (TC_EINVAL)
- *   because it would need staging.  An index outside [0, n) yields NaN
- *   for that target.
+ *   pos (n x 3 float32), mass (n float32), idx (ns int64, original
+ *   indices in [0, n)), acc (ns x 3 float64), pot (ns float64, nullable):
+ *   memory the current device reaches in place -- its own device memory,
+ *   managed memory or mapped pinned host memory.  Host pageable memory and
+ *   another device's memory are rejected (TC_EINVAL): the first would need
+ *   staging, the second may not be peer-mapped.  The C ABI cannot see
+ *   element types or array lengths: buffers shorter than stated, or of
+ *   other types, are read or written out of bounds.  An index outside
+ *   [0, n) yields NaN for that target (it is never dereferenced).
  *   1 <= ns <= 8192 (the scratch's capacity; more is rejected with
  *   TC_EINVAL), 1 <= n < 2^31, eps > 0.
- *   stream: cudaStream_t for the two kernels (NULL = legacy default);
- *   the call only enqueues.
+ *   stream: cudaStream_t of the current device for the two kernels
+ *   (NULL = legacy default); the call only enqueues.  A CUDA error already
+ *   pending when the call starts is returned as TC_ECUDA (and left
+ *   pending) before anything is launched.
  * The first call on a device looks up the device address of the scratch
  * array (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls on a device share the scratch: calls whose work

@@ -131,6 +131,30 @@ std::atomic<long long> g_launches{0};
 }
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+constexpr int kSmCacheDevices = 64;
+std::atomic<int> g_sm_count[kSmCacheDevices] = {};
+}
+int sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev >= 0 && dev < kSmCacheDevices) {
+        const int c = g_sm_count[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev >= 0 && dev < kSmCacheDevices) g_sm_count[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
 }  // namespace tc
 
 namespace {

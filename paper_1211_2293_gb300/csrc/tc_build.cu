@@ -775,7 +775,8 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 inline unsigned gsgrid(int64_t cap, int t)
 {
     int64_t g = (cap + t - 1) / t;
-    if (g > 16 * 152) g = 16 * 152;
+    const int64_t gmax = 16 * (int64_t)sm_count();
+    if (g > gmax) g = gmax;
     return (unsigned)(g < 1 ? 1 : g);
 }
 
@@ -863,10 +864,11 @@ void launch_moments(const float4* body, int64_t cap_m, int depth, int depth_hint
     if (quad) k_leaf_moments<true><<<g, 128, 0, s>>>(body, sysp, info, nt);
     else k_leaf_moments<false><<<g, 128, 0, s>>>(body, sysp, info, nt);
     count_launches(1);
-    // the level launches take a small grid (4 blocks per SM of a 152-SM
-    // part): most levels hold few internal cells, the launches past the
-    // tree's depth none, and a large grid costs more to start than they work
-    const unsigned gl = g < 608u ? g : 608u;
+    // the level launches take a small grid (4 blocks per SM): most levels
+    // hold few internal cells, the launches past the tree's depth none, and a
+    // large grid costs more to start than they work
+    const unsigned glim = 4u * (unsigned)sm_count();
+    const unsigned gl = g < glim ? g : glim;
     int top = depth < 0 ? kMaxLevel : depth;
     if (depth < 0 && depth_hint >= 0 && depth_hint + 3 < kMaxLevel) {
         // depth unknown on the host (a captured step): the levels from the

@@ -90,6 +90,9 @@ constexpr int kSortMaxPasses = 10;   // 8 key passes + up to 2 system passes
 // of kernels it launched to a process-wide counter (count_launches).
 void count_launches(int k);
 long long launches_total();
+// streaming multiprocessors of the current device (cached per device; a
+// host query, allowed while a stream is being captured)
+int sm_count();
 // records the reason of a failure outside any context (tc_last_error(NULL))
 void set_thread_error(const char* msg);
 

@@ -40,7 +40,8 @@ static __device__ __align__(256) double g_direct_scratch[kStaticNsMax * kSlicesM
 static_assert(sizeof(g_direct_scratch) == kDirectScratchBytes, "scratch size");
 
 std::mutex g_setup_mu;
-double* g_scratch_dev[kMaxDevices] = {};
+double* g_scratch_dev[kMaxDevices] = {};  // device address of the scratch, per device
+int g_sms[kMaxDevices] = {};              // streaming multiprocessors, per device
 
 // Block (bx, s) sums targets [bx * 256, +256) over source slice s: FP32 terms
 // per 256-source tile, tiles added in FP64.
@@ -115,15 +116,18 @@ __global__ void k_direct_reduce(const double* __restrict__ scratch, const float*
     if (pot) pot[t] = (double)G * (s[3] + (double)(mass[i] * rsqrtf(eps2)));
 }
 
-bool device_reachable(const void* p)
+// memory a kernel on device `dev` can read and write in place: device memory
+// of that device (another device's memory may not be peer-mapped), managed
+// memory, or mapped pinned host memory
+bool device_reachable(const void* p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
-           (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr);
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+    return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr);
 }
 
 }  // namespace
@@ -145,19 +149,21 @@ extern "C" int tc_direct_static(const float* pos, const float* mass, int64_t n, 
     if (ns < 1 || ns > kStaticNsMax) return bad(TC_EINVAL, "ns must be in [1, 8192] (the fixed scratch holds 8192 targets)");
     if (!(eps > 0.f) || !std::isfinite(eps) || !std::isfinite(G))
         return bad(TC_EINVAL, "eps must be > 0 and finite, G finite");
-    if (!device_reachable(pos) || !device_reachable(mass) || !device_reachable(idx) || !device_reachable(acc) ||
-        (pot && !device_reachable(pot)))
-        return bad(TC_EINVAL, "every pointer must be device-accessible memory (nothing is staged)");
-
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return bad(TC_ECUDA, "no usable current device");
     }
+    if (!device_reachable(pos, dev) || !device_reachable(mass, dev) || !device_reachable(idx, dev) ||
+        !device_reachable(acc, dev) || (pot && !device_reachable(pot, dev)))
+        return bad(TC_EINVAL,
+                   "every pointer must be memory the current device reaches in place (its own device memory, "
+                   "managed or mapped host memory; nothing is staged)");
     double* scratch = nullptr;
+    int sms = 0;
     {
         // once per device, with that device current: the device address of
-        // the static scratch array
+        // the static scratch array and the device's SM count
         std::lock_guard<std::mutex> lk(g_setup_mu);
         if (!g_scratch_dev[dev]) {
             void* p = nullptr;
@@ -168,14 +174,33 @@ extern "C" int tc_direct_static(const float* pos, const float* mass, int64_t n, 
                 set_thread_error(msg);
                 return TC_ECUDA;
             }
+            int c = 0;
+            e = cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess || c < 1) {
+                cudaGetLastError();
+                return bad(TC_ECUDA, "cudaDeviceGetAttribute(MultiProcessorCount) failed");
+            }
+            g_sms[dev] = c;
             g_scratch_dev[dev] = (double*)p;
         }
         scratch = g_scratch_dev[dev];
+        sms = g_sms[dev];
+    }
+    // an error left pending by earlier, unrelated work is reported as such
+    // (and not cleared) instead of being taken for this call's launch failure
+    {
+        const cudaError_t pe = cudaPeekAtLastError();
+        if (pe != cudaSuccess) {
+            snprintf(msg, sizeof(msg), "tc_direct_static: a CUDA error was already pending before the launch: %s",
+                     cudaGetErrorString(pe));
+            set_thread_error(msg);
+            return TC_ECUDA;
+        }
     }
 
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nbx = (ns + kThreads - 1) / kThreads;
-    int S = (int)((4 * 152 + nbx - 1) / nbx);
+    int S = (int)((4 * (int64_t)sms + nbx - 1) / nbx);
     if (S > kSlicesMax) S = kSlicesMax;
     if (S > n) S = (int)n;
     if (S < 1) S = 1;

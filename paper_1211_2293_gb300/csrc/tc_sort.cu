@@ -377,7 +377,7 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
     cudaMemsetAsync(b.status, 0, (size_t)npass * nt * 256 * sizeof(unsigned long long), s);
     cudaMemsetAsync(b.tiles, 0, kSortMaxPasses * sizeof(uint32_t), s);
     int hb = (int)((n + kSortThreads * 16 - 1) / (kSortThreads * 16));
-    if (hb > 4 * 152) hb = 4 * 152;
+    if (hb > 4 * sm_count()) hb = 4 * sm_count();
     k_sort_hist_all<K><<<hb, kSortThreads, 0, s>>>(keys, n, n_dev, nkey, b.ghist);
     count_launches(1);
     if (nsys) {

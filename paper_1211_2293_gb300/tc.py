@@ -426,10 +426,53 @@ def tc_step(dt: float):
     _check(lib.tc_step(float(dt)))
 
 
+def _check_static_args(pos, mass, idx, acc, pot):
+    """Shapes, element types and devices of tc_direct_static's arguments,
+    checked before anything reaches the C ABI (which sees bare pointers and
+    would read or write past a buffer that is too short or of another
+    type).  Returns the common CUDA device."""
+    import torch
+
+    def need(name, x, dtype, shape):
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+        if x.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+        if tuple(x.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}, got {tuple(x.shape)}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+
+    if not isinstance(mass, torch.Tensor) or mass.dim() != 1:
+        raise ValueError("mass must be a 1-D torch.Tensor")
+    if not isinstance(idx, torch.Tensor) or idx.dim() != 1:
+        raise ValueError("idx must be a 1-D torch.Tensor")
+    n, ns = int(mass.shape[0]), int(idx.shape[0])
+    need("pos", pos, torch.float32, (n, 3))
+    need("mass", mass, torch.float32, (n,))
+    need("idx", idx, torch.int64, (ns,))
+    need("acc", acc, torch.float64, (ns, 3))
+    if pot is not None:
+        need("pot", pot, torch.float64, (ns,))
+    devs = {x.device for x in (pos, mass, idx, acc, pot) if x is not None}
+    if len(devs) != 1 or next(iter(devs)).type != "cuda":
+        raise ValueError(f"all arrays must be CUDA tensors on one device, got {sorted(str(d) for d in devs)}")
+    return next(iter(devs))
+
+
 def tc_direct_static(pos, mass, idx, eps: float, G: float, acc, pot=None, stream=None):
     """Direct summation into caller-owned device buffers; allocates nothing
-    on the device (see include/tc.h).  All arrays must be CUDA tensors."""
+    on the device (see include/tc.h).  pos (n, 3) float32, mass (n,)
+    float32, idx (ns,) int64, acc (ns, 3) float64, pot (ns,) float64 or
+    None: contiguous CUDA tensors on one device.  The call runs on that
+    device, on `stream` (a CUDA stream of that device) or its current torch
+    stream."""
+    import torch
+
+    dev = _check_static_args(pos, mass, idx, acc, pot)
     lib = load()
-    s = _current_stream() if stream is None else ctypes.c_void_p(int(stream))
-    _check(lib.tc_direct_static(_ptr(pos), _ptr(mass), int(mass.shape[0]), _ptr(idx), int(idx.shape[0]),
-                                float(eps), float(G), _ptr(acc), _ptr(pot), s))
+    with torch.cuda.device(dev):
+        s = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream) if stream is None else \
+            ctypes.c_void_p(int(stream))
+        _check(lib.tc_direct_static(_ptr(pos), _ptr(mass), int(mass.shape[0]), _ptr(idx), int(idx.shape[0]),
+                                    float(eps), float(G), _ptr(acc), _ptr(pot), s))

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -55,3 +56,41 @@ def test_no_oracle_in_product_path():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "tc_oracle" not in txt, f
+
+
+def test_direct_static_binding_rejects_bad_arguments_before_the_call(monkeypatch):
+    """The binding checks element types, shapes and devices before the C ABI
+    sees a pointer: a float32 acc, short outputs, an int32 idx or CPU
+    tensors would otherwise make the kernels read or write outside the
+    caller's buffers.  The library is never loaded for a rejected call."""
+    import torch
+
+    from paper_1211_2293_gb300 import tc
+
+    def no_load(*a, **k):
+        raise AssertionError("the library was reached")
+
+    monkeypatch.setattr(tc, "load", no_load)
+    n, ns = 10, 4
+    good = dict(pos=torch.zeros((n, 3)), mass=torch.ones(n), idx=torch.zeros(ns, dtype=torch.int64),
+                acc=torch.zeros((ns, 3), dtype=torch.float64), pot=torch.zeros(ns, dtype=torch.float64))
+    cases = [
+        ("acc", torch.zeros((ns, 3), dtype=torch.float32), TypeError),
+        ("acc", torch.zeros((ns - 1, 3), dtype=torch.float64), ValueError),
+        ("pot", torch.zeros(ns - 1, dtype=torch.float64), ValueError),
+        ("pot", torch.zeros(ns, dtype=torch.float32), TypeError),
+        ("idx", torch.zeros(ns, dtype=torch.int32), TypeError),
+        ("pos", torch.zeros((n, 4)), ValueError),
+        ("pos", torch.zeros((n, 3), dtype=torch.float64), TypeError),
+        ("mass", torch.ones((n, 1)), ValueError),
+        ("acc", torch.zeros((3, ns), dtype=torch.float64).t(), ValueError),  # not contiguous
+        ("pos", np.zeros((n, 3), np.float32), TypeError),
+    ]
+    for name, bad, exc in cases:
+        kw = dict(good)
+        kw[name] = bad
+        with pytest.raises(exc):
+            tc.tc_direct_static(kw["pos"], kw["mass"], kw["idx"], 0.01, 1.0, kw["acc"], kw["pot"])
+    # right types and shapes, but host tensors: refused as not on a CUDA device
+    with pytest.raises(ValueError, match="CUDA"):
+        tc.tc_direct_static(good["pos"], good["mass"], good["idx"], 0.01, 1.0, good["acc"], good["pot"])
