@@ -649,7 +649,7 @@ def run_learned(args, rank, world, local_rank):
     X, T, F, _, _ = ctx.mlp_pairs(theta_tr, eps, band, prob, 2, target)
     pairs_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    losses = ctx.mlp_train(X, T, ctx.mlp_weights(F), epochs=args.epochs, batch=1024, lr=2e-3, seed=3,
+    losses = ctx.mlp_train(X, T, F, epochs=args.epochs, batch=1024, lr=2e-3, seed=3, factors=True,
                            band=band)
     train_s = time.perf_counter() - t0
     model, _ = ctx.mlp_get()

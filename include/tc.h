@@ -293,16 +293,21 @@ int tc_mlp_forward(tc_ctx *ctx, const float *X, int64_t n, float *Y);
 int tc_mlp_loss_grad(tc_ctx *ctx, const float *X, const float *T, const float *W, int64_t n, float *grad,
                      float *loss);
 /* Train a fresh model (weights and biases uniform in +-1/sqrt(fan-in), from
- * seed; feature means/scales
- * and output RMS from the data) on n >= 16 pairs (X n x 13 features, T n x 3
- * labels, W n loss weights or NULL) with Adam, learning rate lr decayed
- * along a cosine over all steps, shuffled mini-batches of `batch` (>= 16),
+ * a counter-based generator keyed by seed; feature means/scales and output
+ * RMS from the data) on n >= 16 pairs (X n x 13 features, T n x 3 labels)
+ * with Adam, learning rate lr decayed along a cosine over all steps,
+ * mini-batches of `batch` (>= 16) in a fresh seeded order each pass,
  * `epochs` passes; sets it as the context's model with the given band.
- * losses[epochs] (nullable) gets the mean mini-batch loss of each pass.
- * With W = F^2 (F from tc_mlp_pairs) the loss is the mean squared error of
- * the corrected acceleration. */
-int tc_mlp_train(tc_ctx *ctx, const float *X, const float *T, const float *W, int64_t n, int epochs, int batch,
-                 float lr, uint64_t seed, float band, float *losses);
+ * Loss weights: weight_mode TC_MLP_WEIGHTS takes W (n, >= 0; NULL for all
+ * 1) as the weights; TC_MLP_FACTORS takes W as the pairs' label factors F
+ * (tc_mlp_pairs) and weights each pair by F^2 / mean(F^2), which makes the
+ * loss the mean squared error of the corrected acceleration.  Everything,
+ * the data's statistics included, is computed on the device.  losses[epochs]
+ * (nullable) gets the mean mini-batch loss of each pass. */
+#define TC_MLP_WEIGHTS 0
+#define TC_MLP_FACTORS 1
+int tc_mlp_train(tc_ctx *ctx, const float *X, const float *T, const float *W, int32_t weight_mode, int64_t n,
+                 int epochs, int batch, float lr, uint64_t seed, float band, float *losses);
 /* Training pairs generated by the method itself: a walk at theta over the
  * current bodies emits, with probability prob (seeded), every accepted cell
  * holding two or more bodies with s >= band * d, paired with a body of the

@@ -101,6 +101,14 @@ def _load():
     lib.or_tree_group_list.restype = None
     lib.or_tree_learned.argtypes = [P, D, D, D, D, P, P, I64, I64, P, P]
     lib.or_tree_learned.restype = I64
+    lib.or_tree_learned_bf16.argtypes = [P, D, D, D, D, P, P, I64, I64, P, P, P]
+    lib.or_tree_learned_bf16.restype = I64
+    lib.or_bf16.argtypes = [D]
+    lib.or_bf16.restype = D
+    lib.or_mlp_forward_bf16.argtypes = [P, P, P, I64, P, P]
+    lib.or_mlp_forward_bf16.restype = None
+    lib.or_mlp_grad_bf16.argtypes = [P, P, P, P, P, I64, P, P, P]
+    lib.or_mlp_grad_bf16.restype = D
     _lib = lib
     return lib
 
@@ -265,6 +273,23 @@ class Tree:
                                        int(g0), int(g1), _ptr(corr), _ptr(flag))
         return corr, flag, int(ev)
 
+    def learned_bf16(self, theta, eps, band, params, maps, G=1.0, groups=None):
+        """The band sum of ``learned`` with the network's BF16 rounding model:
+        (corr, radius of an FP32 implementation (n x 3), flag, evaluations);
+        NaN outside the walked groups."""
+        if self.G == 0:
+            raise RuntimeError("make_groups first")
+        g0, g1 = (0, self.G) if groups is None else groups
+        corr = np.full((self.n, 3), np.nan)
+        crad = np.full((self.n, 3), np.nan)
+        flag = np.full(self.G, -1, dtype=np.int32)
+        p = _f64(params)
+        m = _f64(maps)
+        assert p.size == MLP_NPARAM and m.size == 29
+        ev = self._lib.or_tree_learned_bf16(self._h, float(theta), float(eps), float(G), float(band), _ptr(p),
+                                            _ptr(m), int(g0), int(g1), _ptr(corr), _ptr(crad), _ptr(flag))
+        return corr, crad, flag, int(ev)
+
     def mlp_factor(self, node: int, x, G: float = 1.0):
         """G M s^2 / r^4 of cell node at point x (the acceleration unit of a label)."""
         return float(self._lib.or_mlp_factor(self._h, int(node), _ptr(_f64(x)), float(G)))
@@ -365,3 +390,42 @@ def mlp_grad(params, X, T, w=None):
     g = np.zeros(MLP_NPARAM)
     loss = lib.or_mlp_grad(_ptr(params), _ptr(X), _ptr(T), _ptr(w), X.shape[0], _ptr(g))
     return float(loss), g
+
+
+def bf16(x):
+    """Nearest bfloat16 value (8-bit significand, ties to even), FP64."""
+    lib = _load()
+    a = np.asarray(x, np.float64)
+    return np.vectorize(lib.or_bf16, otypes=[np.float64])(a) if a.ndim else lib.or_bf16(float(a))
+
+
+def mlp_forward_bf16(params, X, Xr=None):
+    """BF16 rounding model of the network (inputs, weights and hidden
+    activations rounded to bfloat16, sums exact): (Y[n,3], R[n,3]) with R
+    the radius within which an implementation making the same roundings on
+    FP32 sums lands, for inputs within Xr (n x 13, None: exact) of X."""
+    lib = _load()
+    params = _f64(params)
+    X = _f64(X).reshape(-1, 13)
+    Xr = None if Xr is None else _f64(np.broadcast_to(Xr, X.shape))
+    Y = np.zeros((X.shape[0], 3))
+    R = np.zeros((X.shape[0], 3))
+    lib.or_mlp_forward_bf16(_ptr(params), _ptr(X), _ptr(Xr), X.shape[0], _ptr(Y), _ptr(R))
+    return Y, R
+
+
+def mlp_grad_bf16(params, X, T, w=None, Xr=None):
+    """(loss, loss radius, gradient, gradient radius) of the BF16 rounding
+    model (the backward's product operands dY, dH2, dH1 rounded as well)."""
+    lib = _load()
+    params = _f64(params)
+    X = _f64(X).reshape(-1, 13)
+    T = _f64(T).reshape(-1, 3)
+    w = None if w is None else _f64(w).reshape(-1)
+    Xr = None if Xr is None else _f64(np.broadcast_to(Xr, X.shape))
+    g = np.zeros(MLP_NPARAM)
+    gr = np.zeros(MLP_NPARAM)
+    lrad = ctypes.c_double()
+    loss = lib.or_mlp_grad_bf16(_ptr(params), _ptr(X), _ptr(Xr), _ptr(T), _ptr(w), X.shape[0], _ptr(g), _ptr(gr),
+                                ctypes.byref(lrad))
+    return float(loss), lrad.value, g, gr

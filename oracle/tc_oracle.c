@@ -915,16 +915,264 @@ double or_mlp_grad(const double *p, const double *X, const double *T, const doub
 }
 #undef H
 
+/* ------------------------------------------------------------------ */
+/* BF16 rounding model of the network.                                  */
+/* The network above is exact (FP64).  A tensor-core implementation    */
+/* rounds some operands to bfloat16 (an 8-bit significand) and adds in */
+/* FP32.  The model below rounds the same operands at the same points  */
+/* -- the normalised inputs, the weights, the hidden activations after */
+/* the ReLU and, in the backward pass, the operands of the products    */
+/* that form the gradients -- and keeps every sum exact.  Beside each  */
+/* value it carries a radius: how far an implementation that performs */
+/* the same roundings on FP32 sums (each addition off by at most one   */
+/* FP32 ulp of the largest partial magnitude) can land from the model  */
+/* value.  Rounding to nearest is monotone, so a value known to lie in */
+/* [v - r, v + r] before a rounding lies in [bf16(v - r), bf16(v + r)] */
+/* after it; most hidden units are far from a rounding boundary and    */
+/* keep radius 0 there.  The model is a reading of the precision the   */
+/* learned correction runs at, not a copy of any kernel's structure.   */
+/* ------------------------------------------------------------------ */
+#define RM_U32 (1.0 / 8388608.0) /* 2^-23: one FP32 ulp at 1 */
+
+/* nearest number with an 8-bit significand, ties to even (the bfloat16
+ * value of x, for x in the normal range of float) */
+double or_bf16(double x)
+{
+    if (x == 0.0 || !isfinite(x))
+        return x;
+    int e;
+    double m = frexp(x, &e);         /* x = m 2^e, 0.5 <= |m| < 1 */
+    double t = ldexp(m, 8);          /* 128 <= |t| < 256: 8 significant bits */
+    double r = nearbyint(t);         /* round half to even (default mode) */
+    return ldexp(r, e - 8);
+}
+
+/* model value of bf16(relu?(v)) and the largest distance to the values an
+ * implementation reaches from [v - r, v + r] */
+static double bf16_iv(double v, double r, int relu, double *rad)
+{
+    double lo = v - r, hi = v + r;
+    if (relu) {
+        v = v > 0.0 ? v : 0.0;
+        lo = lo > 0.0 ? lo : 0.0;
+        hi = hi > 0.0 ? hi : 0.0;
+    }
+    double m = or_bf16(v), a = or_bf16(lo), b = or_bf16(hi);
+    *rad = (b - m > m - a) ? b - m : m - a;
+    return m;
+}
+
+/* z_j = b_j + sum_i a_i bf16(W[i][j]) exactly, and the radius of an FP32
+ * accumulation (kacc additions) of inputs known within da_i of a_i */
+static void layer_iv(const double *W, const double *b, int nin, int nout, int kacc, const double *a,
+                     const double *da, double *z, double *dz)
+{
+    for (int j = 0; j < nout; j++) {
+        double s = b[j], mag = fabs(b[j]), prop = 0.0;
+        for (int i = 0; i < nin; i++) {
+            double w = or_bf16(W[i * nout + j]);
+            s += a[i] * w;
+            mag += (fabs(a[i]) + da[i]) * fabs(w);
+            prop += da[i] * fabs(w);
+        }
+        z[j] = s;
+        dz[j] = prop + (double)(kacc + 1) * RM_U32 * mag;
+    }
+}
+
+#define RH 64
+typedef struct {
+    double x[13], dx[13];
+    double z1[RH], dz1[RH], h1[RH], dh1[RH];
+    double z2[RH], dz2[RH], h2[RH], dh2[RH];
+    double y[3], dy[3];
+} rm_fwd_t;
+
+static void rm_forward(const double *p, const double *x, const double *xr, rm_fwd_t *f)
+{
+    const double *W1 = p, *b1 = W1 + 13 * RH, *W2 = b1 + RH, *b2 = W2 + RH * RH, *W3 = b2 + RH, *b3 = W3 + RH * 3;
+    for (int i = 0; i < 13; i++)
+        f->x[i] = bf16_iv(x[i], xr ? xr[i] : 0.0, 0, &f->dx[i]);
+    layer_iv(W1, b1, 13, RH, 16, f->x, f->dx, f->z1, f->dz1);
+    for (int j = 0; j < RH; j++)
+        f->h1[j] = bf16_iv(f->z1[j], f->dz1[j], 1, &f->dh1[j]);
+    layer_iv(W2, b2, RH, RH, RH, f->h1, f->dh1, f->z2, f->dz2);
+    for (int j = 0; j < RH; j++)
+        f->h2[j] = bf16_iv(f->z2[j], f->dz2[j], 1, &f->dh2[j]);
+    layer_iv(W3, b3, RH, 3, RH, f->h2, f->dh2, f->y, f->dy);
+}
+
+void or_mlp_forward_bf16(const double *p, const double *X, const double *Xr, int64_t n, double *Y, double *R)
+{
+    rm_fwd_t f;
+    for (int64_t i = 0; i < n; i++) {
+        rm_forward(p, &X[13 * i], Xr ? &Xr[13 * i] : NULL, &f);
+        for (int k = 0; k < 3; k++) {
+            Y[3 * i + k] = f.y[k];
+            if (R)
+                R[3 * i + k] = f.dy[k];
+        }
+    }
+}
+
+/* a masked product z * [h > 0] where the implementation's z lies within r
+ * and its pre-activation (model zh) within rh: value and radius (an
+ * uncertain mask allows 0 as well) */
+static double mask_iv(double z, double r, double zh, double rh, double *rad)
+{
+    if (zh - rh > 0.0) {
+        *rad = r;
+        return z;
+    }
+    if (zh + rh <= 0.0) {
+        *rad = 0.0;
+        return 0.0;
+    }
+    *rad = fabs(z) + r;
+    return zh > 0.0 ? z : 0.0;
+}
+
+/* Loss and gradient of the rounding model (layout as or_mlp_grad).  Per
+ * row: e = y - T, dY = 2 w e / n; the products dW3 = H2^T dY,
+ * dH2 = dY W3^T, dW2 = H1^T dH2, dH1 = dH2 W2^T, dW1 = X^T dH1 take BF16
+ * operands (dY, dH2, dH1 rounded before use); the bias gradients sum the
+ * unrounded dY, dH2, dH1.  grad_rad (nullable) receives the radius of an
+ * implementation that accumulates every sum -- over k and over the n rows
+ * -- in FP32; *loss_rad (nullable) that of the loss. */
+double or_mlp_grad_bf16(const double *p, const double *X, const double *Xr, const double *T, const double *w,
+                        int64_t n, double *g, double *grad_rad, double *loss_rad)
+{
+    const double *W2 = p + 13 * RH + RH, *W3 = W2 + RH * RH + RH;
+    double *gW1 = g, *gb1 = gW1 + 13 * RH, *gW2 = gb1 + RH, *gb2 = gW2 + RH * RH, *gW3 = gb2 + RH,
+           *gb3 = gW3 + RH * 3;
+    /* per element: sum of term radii and sum of |terms| (for the FP32
+     * accumulation over rows) */
+    double *er = (double *)calloc(OR_MLP_NPARAM, sizeof(double));
+    double *em = (double *)calloc(OR_MLP_NPARAM, sizeof(double));
+    memset(g, 0, OR_MLP_NPARAM * sizeof(double));
+    double loss = 0.0, lr = 0.0, lmag = 0.0;
+    rm_fwd_t f;
+    double dyv[3], ddy[3], dyb[3], ddyb[3];
+    double dh2[RH], rdh2[RH], dh2b[RH], rdh2b[RH], dh1[RH], rdh1[RH], dh1b[RH], rdh1b[RH];
+    for (int64_t i = 0; i < n; i++) {
+        rm_forward(p, &X[13 * i], Xr ? &Xr[13 * i] : NULL, &f);
+        double wi = w ? w[i] : 1.0;
+        for (int k = 0; k < 3; k++) {
+            double e = f.y[k] - T[3 * i + k];
+            double re = f.dy[k] + RM_U32 * (fabs(e) + f.dy[k]);
+            loss += wi * e * e;
+            lr += wi * (2.0 * fabs(e) * re + re * re);
+            lmag += wi * (fabs(e) + re) * (fabs(e) + re);
+            dyv[k] = 2.0 * wi * e / (double)n;
+            /* 2 w e / n formed in FP32: a few roundings */
+            ddy[k] = 2.0 * wi * re / (double)n + 4.0 * RM_U32 * fabs(dyv[k]);
+            dyb[k] = bf16_iv(dyv[k], ddy[k], 0, &ddyb[k]);
+        }
+        /* output layer */
+        for (int k = 0; k < 3; k++) {
+            gb3[k] += dyv[k];
+            er[13 * RH + RH + RH * RH + RH + RH * 3 + k] += ddy[k];
+            em[13 * RH + RH + RH * RH + RH + RH * 3 + k] += fabs(dyv[k]) + ddy[k];
+            for (int j = 0; j < RH; j++) {
+                int o = 13 * RH + RH + RH * RH + RH + j * 3 + k;
+                gW3[j * 3 + k] += f.h2[j] * dyb[k];
+                er[o] += fabs(f.h2[j]) * ddyb[k] + fabs(dyb[k]) * f.dh2[j] + f.dh2[j] * ddyb[k];
+                em[o] += (fabs(f.h2[j]) + f.dh2[j]) * (fabs(dyb[k]) + ddyb[k]);
+            }
+        }
+        for (int j = 0; j < RH; j++) {
+            double z = 0.0, mag = 0.0, pr = 0.0;
+            for (int k = 0; k < 3; k++) {
+                double w3 = or_bf16(W3[j * 3 + k]);
+                z += w3 * dyb[k];
+                mag += fabs(w3) * (fabs(dyb[k]) + ddyb[k]);
+                pr += fabs(w3) * ddyb[k];
+            }
+            dh2[j] = mask_iv(z, pr + 17.0 * RM_U32 * mag, f.z2[j], f.dz2[j], &rdh2[j]);
+            dh2b[j] = bf16_iv(dh2[j], rdh2[j], 0, &rdh2b[j]);
+        }
+        /* second hidden layer */
+        for (int j = 0; j < RH; j++) {
+            int ob = 13 * RH + RH + RH * RH + j;
+            gb2[j] += dh2[j];
+            er[ob] += rdh2[j];
+            em[ob] += fabs(dh2[j]) + rdh2[j];
+            for (int i2 = 0; i2 < RH; i2++) {
+                int o = 13 * RH + RH + i2 * RH + j;
+                gW2[i2 * RH + j] += f.h1[i2] * dh2b[j];
+                er[o] += fabs(f.h1[i2]) * rdh2b[j] + fabs(dh2b[j]) * f.dh1[i2] + f.dh1[i2] * rdh2b[j];
+                em[o] += (fabs(f.h1[i2]) + f.dh1[i2]) * (fabs(dh2b[j]) + rdh2b[j]);
+            }
+        }
+        for (int i2 = 0; i2 < RH; i2++) {
+            double z = 0.0, mag = 0.0, pr = 0.0;
+            for (int j = 0; j < RH; j++) {
+                double w2 = or_bf16(W2[i2 * RH + j]);
+                z += w2 * dh2b[j];
+                mag += fabs(w2) * (fabs(dh2b[j]) + rdh2b[j]);
+                pr += fabs(w2) * rdh2b[j];
+            }
+            dh1[i2] = mask_iv(z, pr + (RH + 1) * RM_U32 * mag, f.z1[i2], f.dz1[i2], &rdh1[i2]);
+            dh1b[i2] = bf16_iv(dh1[i2], rdh1[i2], 0, &rdh1b[i2]);
+        }
+        /* first hidden layer */
+        for (int j = 0; j < RH; j++) {
+            int ob = 13 * RH + j;
+            gb1[j] += dh1[j];
+            er[ob] += rdh1[j];
+            em[ob] += fabs(dh1[j]) + rdh1[j];
+            for (int i1 = 0; i1 < 13; i1++) {
+                int o = i1 * RH + j;
+                gW1[o] += f.x[i1] * dh1b[j];
+                er[o] += fabs(f.x[i1]) * rdh1b[j] + fabs(dh1b[j]) * f.dx[i1] + f.dx[i1] * rdh1b[j];
+                em[o] += (fabs(f.x[i1]) + f.dx[i1]) * (fabs(dh1b[j]) + rdh1b[j]);
+            }
+        }
+    }
+    if (grad_rad)
+        for (int k = 0; k < OR_MLP_NPARAM; k++)
+            grad_rad[k] = er[k] + (double)(n + 17) * RM_U32 * em[k];
+    if (loss_rad)
+        *loss_rad = (lr + (double)(n + 17) * RM_U32 * lmag) / (double)n;
+    free(er);
+    free(em);
+    return loss / (double)n;
+}
+#undef RH
+
+/* Radius of a feature an FP32 implementation computes at the same point
+ * (an error analysis of FP32 evaluation of the definitions in
+ * or_mlp_features, with a margin of 4): offsets d/s carry the rounding of
+ * the cell's centre of mass and of the group's centre relative to its
+ * reference cube (side sref); s/r those of r and of one reciprocal square
+ * root (2 ulps); log2(count) a fast logarithm (2^-21 absolute); the moment
+ * ratios two roundings of the inputs and one approximate division. */
+static void feature_radius(const double *f, double s, double sref, double r, double *fr)
+{
+    const double u = RM_U32, off = 4.0 * (2.0 * u * (fabs(f[0]) + fabs(f[1]) + fabs(f[2])) + u + 4.0 * u * sref / s);
+    for (int a = 0; a < 3; a++)
+        fr[a] = off;
+    fr[3] = 4.0 * f[3] * (2.0 * u + off * s / r);
+    fr[4] = 4.0 * u * f[4];
+    fr[5] = 4.0 * (4.0 * u * (1.0 + f[5]));
+    fr[6] = 4.0 * (4.0 * u * f[6]);
+    for (int k = 7; k < 13; k++)
+        fr[k] = 4.0 * (4.0 * u * fabs(f[k]));
+}
+
 /* Learned correction of the group walk.  For each group: the accepted cells
  * v of its walk holding two or more bodies with s >= band * d (d = distance
  * from v's centre of mass to the group's box) are evaluated at the centre
- * x_g of the group's box, and (G M_v / r^2) y is added to every body of the
- * group (r = |com_v - x_g|).  y = network((f - mean) * scale) * yscale with
- * maps = 13 means, 13 scales, 3 output scales; with params NULL, y is the
- * exact label at x_g instead (what a perfect model would give). */
-int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, double band,
-                        const double *params, const double *maps, int64_t g_begin, int64_t g_end,
-                        double *corr, int32_t *flag)
+ * x_g of the group's box, and F y is added to every body of the group, with
+ * F = G M_v s^2 / r^4 (r = |com_v - x_g|, s the cell side: the scale of the
+ * quadrupole term).  y = network((f - mean) * scale) * yscale with maps =
+ * 13 means, 13 scales, 3 output scales; with params NULL, y is the exact
+ * label at x_g instead (what a perfect model would give); with rm the
+ * network is its BF16 rounding model and crad gets the radius of an FP32
+ * implementation. */
+static int64_t learned_walk(const or_tree *t, double theta, double eps, double G, double band,
+                            const double *params, const double *maps, int64_t g_begin, int64_t g_end, int rm,
+                            double *corr, double *crad, int32_t *flag)
 {
     int64_t evals = 0;
     walk_t w;
@@ -948,9 +1196,11 @@ int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, do
                     w.hi[a] = t->xs[3 * j + a];
             }
         open_cube(t, &w, 0);
-        double xg[3], cg[3] = {0, 0, 0};
+        double xg[3], cg[3] = {0, 0, 0}, cr[3] = {0, 0, 0}, cm[3] = {0, 0, 0};
         for (int a = 0; a < 3; a++)
             xg[a] = 0.5 * (w.lo[a] + w.hi[a]);
+        double sref = cube_side(t, t->gref[g]);
+        int64_t nev = 0;
         for (int64_t k = 0; k < w.ncells; k++) {
             int64_t v = w.cells[k];
             if (t->count[v] < 2)
@@ -961,27 +1211,65 @@ int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, do
                 w.flagged = 1;
             if (s < bd)
                 continue;
-            double y[3];
+            double y[3], yr[3] = {0, 0, 0};
             if (params) {
                 double f[13], h1[64], h2[64];
                 or_mlp_features(t, v, xg, eps, msys, f);
-                for (int i = 0; i < 13; i++)
-                    f[i] = (f[i] - maps[i]) * maps[13 + i];
-                mlp_layers(params, f, h1, h2, y);
-                for (int a = 0; a < 3; a++)
-                    y[a] *= maps[26 + a];
+                if (rm) {
+                    /* normalised inputs and their radius: the feature's own,
+                     * scaled, plus the two FP32 roundings of (f - mean) scale */
+                    double fr[13], xr[13];
+                    double r2 = 0.0;
+                    for (int a = 0; a < 3; a++)
+                        r2 += (t->com[3 * v + a] - xg[a]) * (t->com[3 * v + a] - xg[a]);
+                    feature_radius(f, s, sref, sqrt(r2), fr);
+                    for (int i = 0; i < 13; i++) {
+                        double xn = (f[i] - maps[i]) * maps[13 + i];
+                        xr[i] = fabs(maps[13 + i]) * fr[i] + 2.0 * RM_U32 * (fabs(maps[i] * maps[13 + i]) + fabs(xn));
+                        f[i] = xn;
+                    }
+                    rm_fwd_t fw;
+                    rm_forward(params, f, xr, &fw);
+                    for (int a = 0; a < 3; a++) {
+                        y[a] = fw.y[a] * maps[26 + a];
+                        yr[a] = fabs(maps[26 + a]) * fw.dy[a] + RM_U32 * fabs(y[a]);
+                    }
+                } else {
+                    for (int i = 0; i < 13; i++)
+                        f[i] = (f[i] - maps[i]) * maps[13 + i];
+                    mlp_layers(params, f, h1, h2, y);
+                    for (int a = 0; a < 3; a++)
+                        y[a] *= maps[26 + a];
+                }
             } else {
                 or_mlp_label(t, v, xg, eps, G, y);
             }
             double fac = or_mlp_factor(t, v, xg, G);
-            for (int a = 0; a < 3; a++)
+            for (int a = 0; a < 3; a++) {
                 cg[a] += fac * y[a];
+                if (rm) {
+                    /* the factor G M s^2 / r^4 in FP32: a few roundings and
+                     * the reciprocal square root, plus r's own radius */
+                    double r2 = 0.0;
+                    for (int b = 0; b < 3; b++)
+                        r2 += (t->com[3 * v + b] - xg[b]) * (t->com[3 * v + b] - xg[b]);
+                    double dr = 4.0 * (2.0 * RM_U32 * sqrt(r2) + 4.0 * RM_U32 * (s + sref));
+                    double frel = 16.0 * RM_U32 + 4.0 * dr / sqrt(r2);
+                    cr[a] += fabs(fac) * yr[a] + frel * fabs(fac * y[a]);
+                    cm[a] += fabs(fac) * (fabs(y[a]) + yr[a]);
+                }
+            }
             evals++;
+            nev++;
         }
         for (int64_t i = w.gfirst; i < w.gfirst + w.gcount; i++) {
             int64_t o = (int64_t)t->perm[i];
-            for (int a = 0; a < 3; a++)
+            for (int a = 0; a < 3; a++) {
                 corr[3 * o + a] = cg[a];
+                /* FP32 sums over the group's cells: one ulp per addition */
+                if (crad)
+                    crad[3 * o + a] = cr[a] + (double)(nev + 6) * RM_U32 * cm[a];
+            }
         }
         if (flag)
             flag[g] = w.flagged;
@@ -989,6 +1277,22 @@ int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, do
     free(w.cells);
     free(w.leaves);
     return evals;
+}
+
+int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, double band,
+                        const double *params, const double *maps, int64_t g_begin, int64_t g_end,
+                        double *corr, int32_t *flag)
+{
+    return learned_walk(t, theta, eps, G, band, params, maps, g_begin, g_end, 0, corr, NULL, flag);
+}
+
+int64_t or_tree_learned_bf16(const or_tree *t, double theta, double eps, double G, double band,
+                             const double *params, const double *maps, int64_t g_begin, int64_t g_end,
+                             double *corr, double *crad, int32_t *flag)
+{
+    if (!params)
+        return -1;
+    return learned_walk(t, theta, eps, G, band, params, maps, g_begin, g_end, 1, corr, crad, flag);
 }
 
 /* The interaction list of one group at theta: accepted cells and opened

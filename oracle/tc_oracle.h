@@ -138,6 +138,20 @@ void or_mlp_forward(const double *params, const double *X, int64_t n, double *Y)
 double or_mlp_grad(const double *params, const double *X, const double *T, const double *w, int64_t n,
                    double *grad);
 
+/* BF16 rounding model of the network: the normalised inputs, the weights
+ * and the hidden activations after the ReLU rounded to bfloat16 (nearest,
+ * ties to even), sums exact; in the backward pass the operands of the
+ * gradient products (dY, dH2, dH1) rounded too, the bias gradients from the
+ * unrounded values.  R / grad_rad / loss_rad (nullable) get the radius
+ * around each model value within which an implementation performing the
+ * same roundings on FP32 sums must land, given inputs within Xr (nullable:
+ * exact) of X before their rounding. */
+double or_bf16(double x);
+void or_mlp_forward_bf16(const double *params, const double *X, const double *Xr, int64_t n, double *Y,
+                         double *R);
+double or_mlp_grad_bf16(const double *params, const double *X, const double *Xr, const double *T,
+                        const double *w, int64_t n, double *grad, double *grad_rad, double *loss_rad);
+
 /* Learned correction of the group walk for groups [g_begin, g_end): every
  * accepted cell of a group's walk with two or more bodies and s >= band * d
  * (d = distance from its centre of mass to the group's box) is evaluated at
@@ -150,6 +164,15 @@ double or_mlp_grad(const double *params, const double *X, const double *T, const
 int64_t or_tree_learned(const or_tree *t, double theta, double eps, double G, double band,
                         const double *params, const double *maps, int64_t g_begin, int64_t g_end,
                         double *corr, int32_t *flag);
+/* The same band sum with the network's BF16 rounding model (or_mlp_forward_bf16;
+ * params required): crad (n x 3) gets the radius within which an FP32
+ * implementation lands -- its features computed in FP32 at the same point
+ * (radii from an error analysis of that evaluation), normalised, run
+ * through the rounding model, scaled by factors computed in FP32 and summed
+ * over the group's cells in FP32. */
+int64_t or_tree_learned_bf16(const or_tree *t, double theta, double eps, double G, double band,
+                             const double *params, const double *maps, int64_t g_begin, int64_t g_end,
+                             double *corr, double *crad, int32_t *flag);
 
 #ifdef __cplusplus
 }

@@ -107,10 +107,13 @@ struct tc_ctx {
     float* mlp_t = nullptr;
     float* mlp_w = nullptr;       // per-pair loss weights / label factors
     int32_t* mlp_idx = nullptr;
+    float* mlp_raw = nullptr;     // scratch: raw features as given (n x 13)
+    double* mlp_sums = nullptr;   // FP64 sums of the training data (kMlpSums)
+    float* mlp_wscale = nullptr;  // n / sum F^2 (factor weights)
+    int32_t* mlp_bad = nullptr;   // a given loss weight was negative or not finite
     int64_t mlp_cap = 0;
     bool have_mlp = false;
     float mlp_band = 0.5f;
-    std::vector<float> mlp_maps_h;  // host copy of the feature / output maps
     int32_t* list_buf = nullptr;    // list export scratch: cells, then leaves
     int64_t list_cap = 0;
     int64_t* list_n = nullptr;
@@ -681,7 +684,8 @@ void tc_destroy(tc_ctx* c)
                     c->pre_level, c->pre_first, c->iota, c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c,
                     c->nt.d, c->nt.quad, c->nt.mass64, c->nt.com64, c->nt.quad64, c->info, c->mlp_params,
                     c->mlp_maps, c->mlp_dev, c->mlp_m, c->mlp_v, c->mlp_grad, c->mlp_loss, c->mlp_evals, c->mlp_x,
-                    c->mlp_t, c->mlp_idx, c->pair_b, c->pair_v, c->pair_n};
+                    c->mlp_t, c->mlp_idx, c->mlp_raw, c->mlp_sums, c->mlp_wscale, c->mlp_bad,
+                    c->pair_b, c->pair_v, c->pair_n};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->info_h) cudaFreeHost(c->info_h);
@@ -1045,14 +1049,7 @@ namespace {
 
 constexpr int kMlpNModel = kMlpNParamHost + 2 * 13 + 3;  // parameters + feature means, scales + output scales
 
-uint64_t smix(uint64_t& st)
-{
-    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-double sunif(uint64_t& st) { return (double)(smix(st) >> 11) * (1.0 / 9007199254740992.0); }
+
 
 int mlp_alloc(tc_ctx* c)
 {
@@ -1065,6 +1062,9 @@ int mlp_alloc(tc_ctx* c)
     TC_GROW(c, c->mlp_grad, kMlpNParamHost);
     TC_GROW(c, c->mlp_loss, 4);
     TC_GROW(c, c->mlp_evals, 1);
+    TC_GROW(c, c->mlp_sums, kMlpSums);
+    TC_GROW(c, c->mlp_wscale, 1);
+    TC_GROW(c, c->mlp_bad, 1);
     TC_CUDA(c, cudaMemsetAsync(c->mlp_evals, 0, sizeof(*c->mlp_evals), c->stream));
     return TC_OK;
 }
@@ -1076,42 +1076,41 @@ int mlp_scratch(tc_ctx* c, int64_t n)
     TC_GROW(c, c->mlp_t, n * 3);
     TC_GROW(c, c->mlp_w, n);
     TC_GROW(c, c->mlp_idx, n);
+    TC_GROW(c, c->mlp_raw, n * 13);
     c->mlp_cap = n;
     return TC_OK;
 }
 
-// raw features (n x 13, host or device) -> normalised padded rows on the host
-int mlp_rows_host(tc_ctx* c, const float* X, int64_t n, std::vector<float>& rows)
+// raw features X (n x 13) and targets T (n x 3, nullable), host or device
+// memory, -> normalised padded rows in mlp_x and scaled targets in mlp_t
+// (kernels; the inputs are first copied as they are)
+int mlp_rows(tc_ctx* c, const float* X, const float* T, int64_t n)
 {
-    std::vector<float> raw(n * 13);
-    TC_COPY(c, raw.data(), X, n * 13 * sizeof(float));
-    rows.assign(n * 16, 0.f);
-    for (int64_t i = 0; i < n; i++)
-        for (int k = 0; k < 13; k++)
-            rows[i * 16 + k] = (raw[i * 13 + k] - c->mlp_maps_h[k]) * c->mlp_maps_h[13 + k];
+    TC_CUDA(c, cudaMemcpyAsync(c->mlp_raw, X, n * 13 * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (T) TC_CUDA(c, cudaMemcpyAsync(c->mlp_t, T, n * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    // the scaled targets are written in place of the raw ones
+    launch_mlp_rows(c->mlp_raw, T ? c->mlp_t : nullptr, n, c->mlp_maps, c->mlp_x, c->mlp_t, c->stream);
+    TC_CUDA(c, cudaGetLastError());
     return TC_OK;
 }
 
-int mlp_targets_host(tc_ctx* c, const float* T, int64_t n, std::vector<float>& t)
-{
-    t.resize(n * 3);
-    TC_COPY(c, t.data(), T, n * 3 * sizeof(float));
-    for (int64_t i = 0; i < n; i++)
-        for (int k = 0; k < 3; k++) t[i * 3 + k] /= c->mlp_maps_h[26 + k];
-    return TC_OK;
-}
-
-// per-pair weights (n, host or device; nullable) -> c->mlp_w; *wdev = the
-// device pointer to pass to the training kernel (null without weights)
-int mlp_weights(tc_ctx* c, const float* W, int64_t n, const float** wdev)
+// per-pair loss weights (n, host or device; nullable) -> c->mlp_w: mode 0
+// the given weights (checked: finite, >= 0), mode 1 W holds the pairs' label
+// factors F and the weights become F^2 / mean(F^2) (needs mlp_wscale from
+// the training data's sums); *wdev = the device pointer to pass to the
+// training kernel (null without weights)
+int mlp_weights(tc_ctx* c, const float* W, int mode, int64_t n, const float** wdev)
 {
     *wdev = nullptr;
     if (!W) return TC_OK;
-    std::vector<float> w(n);
-    TC_COPY(c, w.data(), W, n * sizeof(float));
-    for (float v : w)
-        if (!std::isfinite(v) || v < 0.f) return fail(c, TC_EINVAL, "mlp weights must be finite and >= 0");
-    TC_COPY(c, c->mlp_w, w.data(), n * sizeof(float));
+    TC_CUDA(c, cudaMemcpyAsync(c->mlp_w, W, n * sizeof(float), cudaMemcpyDefault, c->stream));
+    TC_CUDA(c, cudaMemsetAsync(c->mlp_bad, 0, sizeof(int32_t), c->stream));
+    launch_mlp_weights(c->mlp_w, n, mode, c->mlp_wscale, c->mlp_bad, c->stream);
+    TC_CUDA(c, cudaGetLastError());
+    int32_t bad = 0;
+    TC_COPY(c, &bad, c->mlp_bad, sizeof(int32_t));
+    if (bad)
+        return fail(c, TC_EINVAL, mode ? "mlp label factors must be finite" : "mlp weights must be finite and >= 0");
     *wdev = c->mlp_w;
     return TC_OK;
 }
@@ -1124,9 +1123,8 @@ int mlp_upload(tc_ctx* c, const float* model)
     TC_COPY(c, h.data(), model, kMlpNModel * sizeof(float));
     for (float v : h)
         if (!std::isfinite(v)) return fail(c, TC_EINVAL, "tc_mlp_set: non-finite model value");
-    c->mlp_maps_h.assign(h.begin() + kMlpNParamHost, h.end());
     TC_COPY(c, c->mlp_params, h.data(), kMlpNParamHost * sizeof(float));
-    TC_COPY(c, c->mlp_maps, c->mlp_maps_h.data(), 29 * sizeof(float));
+    TC_COPY(c, c->mlp_maps, h.data() + kMlpNParamHost, 29 * sizeof(float));
     launch_mlp_pack(c->mlp_params, c->mlp_maps, c->mlp_dev, c->stream);
     TC_CUDA(c, cudaGetLastError());
     c->have_mlp = true;
@@ -1153,7 +1151,7 @@ int tc_mlp_get(tc_ctx* c, float* model, float* band)
     if (!c->have_mlp) return fail(c, TC_ESTATE, "tc_mlp_get: no model");
     if (model) {
         TC_COPY(c, model, c->mlp_params, kMlpNParamHost * sizeof(float));
-        TC_COPY(c, model + kMlpNParamHost, c->mlp_maps_h.data(), 29 * sizeof(float));
+        TC_COPY(c, model + kMlpNParamHost, c->mlp_maps, 29 * sizeof(float));
     }
     if (band) *band = c->mlp_band;
     return TC_OK;
@@ -1166,10 +1164,7 @@ int tc_mlp_forward(tc_ctx* c, const float* X, int64_t n, float* Y)
     if (n < 1) return fail(c, TC_EINVAL, "tc_mlp_forward: n must be >= 1");
     int r = mlp_scratch(c, n);
     if (r) return r;
-    std::vector<float> rows;
-    r = mlp_rows_host(c, X, n, rows);
-    if (r) return r;
-    TC_CUDA(c, cudaMemcpyAsync(c->mlp_x, rows.data(), n * 16 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    if ((r = mlp_rows(c, X, nullptr, n))) return r;
     launch_mlp_infer(c->mlp_x, n, c->mlp_dev, c->mlp_t, c->stream);
     TC_CUDA(c, cudaGetLastError());
     TC_CUDA(c, cudaMemcpyAsync(Y, c->mlp_t, n * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
@@ -1183,15 +1178,10 @@ int tc_mlp_loss_grad(tc_ctx* c, const float* X, const float* T, const float* W, 
     if (n < 1 || n >= (int64_t)1 << 31) return fail(c, TC_EINVAL, "tc_mlp_loss_grad: bad n");
     int r = mlp_scratch(c, n);
     if (r) return r;
-    std::vector<float> rows, t;
-    if ((r = mlp_rows_host(c, X, n, rows)) || (r = mlp_targets_host(c, T, n, t))) return r;
-    std::vector<int32_t> idx(n);
-    for (int64_t i = 0; i < n; i++) idx[i] = (int32_t)i;
-    TC_COPY(c, c->mlp_x, rows.data(), n * 16 * sizeof(float));
-    TC_COPY(c, c->mlp_t, t.data(), n * 3 * sizeof(float));
-    TC_COPY(c, c->mlp_idx, idx.data(), n * sizeof(int32_t));
+    if ((r = mlp_rows(c, X, T, n))) return r;
+    launch_mlp_shuffle(n, 0, c->mlp_idx, c->stream);  // key 0: the rows in order
     const float* wdev = nullptr;
-    if ((r = mlp_weights(c, W, n, &wdev))) return r;
+    if ((r = mlp_weights(c, W, 0, n, &wdev))) return r;
     TC_CUDA(c, cudaMemsetAsync(c->mlp_grad, 0, kMlpNParamHost * sizeof(float), c->stream));
     TC_CUDA(c, cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), c->stream));
     int64_t blocks = (n + 63) / 64;
@@ -1204,65 +1194,59 @@ int tc_mlp_loss_grad(tc_ctx* c, const float* X, const float* T, const float* W, 
     return check_device(c);
 }
 
-int tc_mlp_train(tc_ctx* c, const float* X, const float* T, const float* W, int64_t n, int epochs, int batch,
-                 float lr, uint64_t seed, float band, float* losses)
+int tc_mlp_train(tc_ctx* c, const float* X, const float* T, const float* W, int32_t weight_mode, int64_t n,
+                 int epochs, int batch, float lr, uint64_t seed, float band, float* losses)
 {
     if (!c || !X || !T) return fail(c, TC_EINVAL, "tc_mlp_train: null argument");
     if (n < 16 || n >= (int64_t)1 << 31) return fail(c, TC_EINVAL, "tc_mlp_train: need 16 <= n < 2^31 pairs");
     if (epochs < 1 || batch < 16 || !finite(lr) || lr <= 0.f || !finite(band) || band < 0.f)
         return fail(c, TC_EINVAL, "tc_mlp_train: epochs >= 1, batch >= 16, lr > 0, band >= 0 required");
-    // normalisation: feature means and inverse standard deviations, output RMS
-    std::vector<float> raw(n * 13), tt(n * 3);
-    TC_COPY(c, raw.data(), X, n * 13 * sizeof(float));
-    TC_COPY(c, tt.data(), T, n * 3 * sizeof(float));
-    std::vector<float> model(kMlpNModel, 0.f);
-    for (int k = 0; k < 13; k++) {
-        double s1 = 0, s2 = 0;
-        for (int64_t i = 0; i < n; i++) {
-            s1 += raw[i * 13 + k];
-            s2 += (double)raw[i * 13 + k] * raw[i * 13 + k];
-        }
-        const double mean = s1 / n, var = std::max(0.0, s2 / n - mean * mean);
-        model[kMlpNParamHost + k] = (float)mean;
-        model[kMlpNParamHost + 13 + k] = var > 1e-30 ? (float)(1.0 / std::sqrt(var)) : 0.f;
-    }
-    for (int k = 0; k < 3; k++) {
-        double s2 = 0;
-        for (int64_t i = 0; i < n; i++) s2 += (double)tt[i * 3 + k] * tt[i * 3 + k];
-        const double rms = std::sqrt(s2 / n);
-        model[kMlpNParamHost + 26 + k] = rms > 1e-30 ? (float)rms : 1.f;
-    }
-    // weights and biases uniform in +-1/sqrt(fan-in)
-    uint64_t st = seed;
-    float* p = model.data();
-    const int fan[3] = {13, 64, 64}, outs[3] = {64, 64, 3};
-    for (int l = 0; l < 3; l++) {
-        const double bound = 1.0 / std::sqrt((double)fan[l]);
-        for (int i = 0; i < fan[l] * outs[l] + outs[l]; i++) *p++ = (float)((2.0 * sunif(st) - 1.0) * bound);
-    }
+    if (weight_mode != TC_MLP_WEIGHTS && weight_mode != TC_MLP_FACTORS)
+        return fail(c, TC_EINVAL, "tc_mlp_train: weight_mode must be TC_MLP_WEIGHTS or TC_MLP_FACTORS");
+    if (weight_mode == TC_MLP_FACTORS && !W) return fail(c, TC_EINVAL, "tc_mlp_train: TC_MLP_FACTORS needs W");
+    int r = mlp_alloc(c);
+    if (r) return r;
+    if ((r = mlp_scratch(c, n))) return r;
+    // the data as given, then (kernels) its sums, the model's maps (feature
+    // means and scales, output RMS), fresh parameters, normalised rows and
+    // scaled targets, loss weights
+    TC_CUDA(c, cudaMemcpyAsync(c->mlp_raw, X, n * 13 * sizeof(float), cudaMemcpyDefault, c->stream));
+    TC_CUDA(c, cudaMemcpyAsync(c->mlp_t, T, n * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (W) TC_CUDA(c, cudaMemcpyAsync(c->mlp_w, W, n * sizeof(float), cudaMemcpyDefault, c->stream));
+    launch_mlp_sums(c->mlp_raw, c->mlp_t, weight_mode == TC_MLP_FACTORS ? c->mlp_w : nullptr, n, c->mlp_sums,
+                    c->stream);
+    launch_mlp_maps(c->mlp_sums, n, c->mlp_maps, c->mlp_wscale, c->stream);
+    launch_mlp_init(c->mlp_params, seed, c->stream);
+    launch_mlp_pack(c->mlp_params, c->mlp_maps, c->mlp_dev, c->stream);
+    launch_mlp_rows(c->mlp_raw, c->mlp_t, n, c->mlp_maps, c->mlp_x, c->mlp_t, c->stream);
+    TC_CUDA(c, cudaGetLastError());
     c->mlp_band = band;
-    int r = mlp_upload(c, model.data());
-    if (r) return r;
-    r = mlp_scratch(c, n);
-    if (r) return r;
-    std::vector<float> rows, t;
-    if ((r = mlp_rows_host(c, X, n, rows)) || (r = mlp_targets_host(c, T, n, t))) return r;
-    TC_COPY(c, c->mlp_x, rows.data(), n * 16 * sizeof(float));
-    TC_COPY(c, c->mlp_t, t.data(), n * 3 * sizeof(float));
+    c->have_mlp = true;
+    c->walk_ready = false;
+    drop_graph(c);
     const float* wdev = nullptr;
-    if ((r = mlp_weights(c, W, n, &wdev))) return r;
+    if (W) {
+        TC_CUDA(c, cudaMemsetAsync(c->mlp_bad, 0, sizeof(int32_t), c->stream));
+        launch_mlp_weights(c->mlp_w, n, weight_mode == TC_MLP_FACTORS ? 1 : 0, c->mlp_wscale, c->mlp_bad, c->stream);
+        TC_CUDA(c, cudaGetLastError());
+        int32_t bad = 0;
+        TC_COPY(c, &bad, c->mlp_bad, sizeof(int32_t));
+        if (bad) {
+            c->have_mlp = false;
+            return fail(c, TC_EINVAL, weight_mode == TC_MLP_FACTORS ? "tc_mlp_train: label factors must be finite"
+                                                                    : "tc_mlp_train: weights must be finite and >= 0");
+        }
+        wdev = c->mlp_w;
+    }
     TC_CUDA(c, cudaMemsetAsync(c->mlp_m, 0, kMlpNParamHost * sizeof(float), c->stream));
     TC_CUDA(c, cudaMemsetAsync(c->mlp_v, 0, kMlpNParamHost * sizeof(float), c->stream));
-    std::vector<int32_t> idx(n);
-    for (int64_t i = 0; i < n; i++) idx[i] = (int32_t)i;
     int step = 0;
     const int64_t total_steps = (int64_t)epochs * ((n + batch - 1) / batch);
+    uint64_t key = seed;
     for (int ep = 0; ep < epochs; ep++) {
-        for (int64_t i = n - 1; i > 0; i--) {  // Fisher-Yates
-            const int64_t j = (int64_t)(smix(st) % (uint64_t)(i + 1));
-            std::swap(idx[i], idx[j]);
-        }
-        TC_CUDA(c, cudaMemcpyAsync(c->mlp_idx, idx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        // a fresh seeded permutation of the pairs each pass (on the device)
+        key = key * 6364136223846793005ull + 1442695040888963407ull;
+        launch_mlp_shuffle(n, key, c->mlp_idx, c->stream);
         TC_CUDA(c, cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), c->stream));
         int nb = 0;
         for (int64_t b0 = 0; b0 < n; b0 += batch) {
@@ -1279,8 +1263,6 @@ int tc_mlp_train(tc_ctx* c, const float* X, const float* T, const float* W, int6
             launch_mlp_pack(c->mlp_params, c->mlp_maps, c->mlp_dev, c->stream);
             nb++;
         }
-        // the host index buffer of this epoch must stay intact until it is copied
-        TC_CUDA(c, cudaStreamSynchronize(c->stream));
         if (losses) {
             float l = 0.f;
             TC_COPY(c, &l, c->mlp_loss, sizeof(float));

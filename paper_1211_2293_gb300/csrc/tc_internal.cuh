@@ -243,6 +243,19 @@ void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const 
                         const SysParams* sysp, NodeTables nt, float eps, float G, float* feat, float* lab,
                         float* fac, cudaStream_t s);
 void launch_sys_mass(SysParams* sysp, int nsys, const NodeTables nt, const Info* info, cudaStream_t s);
+// training data on the device: FP64 sums of x, x^2, t^2 (and F^2) over the
+// pairs (kMlpSums doubles), the model's maps from them (and the factor-weight
+// scale), normalised rows and scaled targets, loss weights (mode 0: check
+// the given ones, mode 1: F^2 n / sum F^2; *bad = 1 for a non-finite or
+// negative weight), fresh parameters, and a seeded permutation of [0, n)
+constexpr int kMlpSums = 13 + 13 + 3 + 1;
+void launch_mlp_sums(const float* X, const float* T, const float* F, int64_t n, double* sums, cudaStream_t s);
+void launch_mlp_maps(const double* sums, int64_t n, float* maps, float* wscale, cudaStream_t s);
+void launch_mlp_rows(const float* X, const float* T, int64_t n, const float* maps, float* rows, float* tout,
+                     cudaStream_t s);
+void launch_mlp_weights(float* w, int64_t n, int mode, const float* wscale, int32_t* bad, cudaStream_t s);
+void launch_mlp_init(float* params, uint64_t seed, cudaStream_t s);
+void launch_mlp_shuffle(int64_t n, uint64_t key, int32_t* idx, cudaStream_t s);
 
 // FP32 throughput probe (8 independent FMA chains per thread, scalar or
 // paired f32x2 instructions)

@@ -432,6 +432,140 @@ __global__ void k_pair_labels(const int32_t* __restrict__ pb, const int32_t* __r
     if (fac) fac[k] = (float)F;
 }
 
+// ---------------------------------------------------------------- training data
+// Sums over the n training pairs, in FP64: column c of blockIdx.y takes
+//   c < 13: x_c,  13 <= c < 26: x_(c-13)^2,  26 <= c < 29: t_(c-26)^2,
+//   c = 29: F^2 (the pairs' label factors; F null: skipped)
+__global__ void k_mlp_sums(const float* __restrict__ X, const float* __restrict__ T, const float* __restrict__ F,
+                           int64_t n, double* __restrict__ sums)
+{
+    const int c = blockIdx.y;
+    if (c == kMlpSums - 1 && !F) return;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v;
+        if (c < kMlpIn) v = X[i * kMlpIn + c];
+        else if (c < 2 * kMlpIn) { v = X[i * kMlpIn + c - kMlpIn]; v *= v; }
+        else if (c < 2 * kMlpIn + kMlpOut) { v = T[i * kMlpOut + c - 2 * kMlpIn]; v *= v; }
+        else { v = F[i]; v *= v; }
+        s += v;
+    }
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(&sums[c], s);
+    }
+}
+
+// the model's maps from the sums: feature means and inverse standard
+// deviations (0 for a constant feature), output RMS (1 for an all-zero
+// output); and the factor-weight scale n / sum F^2
+__global__ void k_mlp_maps(const double* __restrict__ sums, int64_t n, float* __restrict__ maps,
+                           float* __restrict__ wscale)
+{
+    const int k = threadIdx.x;
+    const double inv_n = 1.0 / (double)n;
+    if (k < kMlpIn) {
+        const double mean = sums[k] * inv_n;
+        const double var = fmax(0.0, sums[kMlpIn + k] * inv_n - mean * mean);
+        maps[k] = (float)mean;
+        maps[kMlpIn + k] = var > 1e-30 ? (float)(1.0 / sqrt(var)) : 0.f;
+    } else if (k < kMlpIn + kMlpOut) {
+        const double rms = sqrt(sums[2 * kMlpIn + k - kMlpIn] * inv_n);
+        maps[2 * kMlpIn + k - kMlpIn] = rms > 1e-30 ? (float)rms : 1.f;
+    } else if (k == kMlpIn + kMlpOut) {
+        const double s2 = sums[kMlpSums - 1];
+        *wscale = s2 > 0.0 ? (float)((double)n / s2) : 0.f;
+    }
+}
+
+// normalised padded rows (x - mean) * scale, each operation rounded on its
+// own (no contraction), zero padding; targets t / yscale
+__global__ void k_mlp_rows(const float* __restrict__ X, const float* __restrict__ T, int64_t n,
+                           const float* __restrict__ maps, float* __restrict__ rows, float* __restrict__ tout)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * kMlpInPad;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / kMlpInPad;
+        const int k = (int)(e % kMlpInPad);
+        rows[e] = k < kMlpIn ? __fmul_rn(__fsub_rn(X[i * kMlpIn + k], maps[k]), maps[kMlpIn + k]) : 0.f;
+        if (T && k < kMlpOut) tout[i * kMlpOut + k] = __fdiv_rn(T[i * kMlpOut + k], maps[2 * kMlpIn + k]);
+    }
+}
+
+// loss weights in place: mode 0 checks the given weights (finite, >= 0;
+// *bad = 1 otherwise), mode 1 turns label factors F into F^2 n / sum F^2
+__global__ void k_mlp_weights(float* __restrict__ w, int64_t n, int mode, const float* __restrict__ wscale,
+                              int32_t* __restrict__ bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = w[i];
+        if (!isfinite(v) || (mode == 0 && v < 0.f)) {
+            *bad = 1;
+            continue;
+        }
+        if (mode == 1) w[i] = __fmul_rn(__fmul_rn(v, v), *wscale);
+    }
+}
+
+// Fresh parameters: weights and biases of layer l uniform in +-1/sqrt(fan-in)
+// from a counter-based generator (SplitMix64 of seed and index)
+__device__ __forceinline__ uint64_t splitmix(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_mlp_init(float* __restrict__ p, uint64_t seed)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpNParam) return;
+    const int l1 = kMlpIn * kMlpHid + kMlpHid;
+    const double fan = i < l1 ? (double)kMlpIn : (double)kMlpHid;
+    const double u = (double)(splitmix(seed * 0x100000001B3ull + (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+    p[i] = (float)((2.0 * u - 1.0) / sqrt(fan));
+}
+
+// A random permutation of [0, n) without sorting: a 4-round Feistel network
+// is a bijection on [0, 4^h) (4^h >= n, h the half width in bits); walking
+// its cycle from i until the value falls below n gives a bijection on
+// [0, n) (the walk ends: the cycle through i < n returns to i).  Key 0
+// gives the identity.
+__device__ __forceinline__ uint32_t feistel(uint32_t x, int h, uint64_t key)
+{
+    const uint32_t mask = (1u << h) - 1u;
+    uint32_t L = x >> h, R = x & mask;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const uint32_t f = (uint32_t)splitmix(key + 0x632BE59BD9B4E019ull * (uint64_t)r + R) & mask;
+        const uint32_t t = L ^ f;
+        L = R;
+        R = t;
+    }
+    return (L << h) | R;
+}
+
+__global__ void k_mlp_shuffle(int64_t n, int h, uint64_t key, int32_t* __restrict__ idx)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)i;
+        if (key != 0) {
+            do {
+                x = feistel(x, h, key);
+            } while ((int64_t)x >= n);
+        }
+        idx[i] = (int32_t)x;
+    }
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -476,6 +610,54 @@ void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const 
                         float* fac, cudaStream_t s)
 {
     k_pair_labels<<<nblk(np, 128), 128, 0, s>>>(pb, pv, np, body, sys_of, sysp, nt, eps, G, feat, lab, fac);
+    count_launches(1);
+}
+
+void launch_mlp_sums(const float* X, const float* T, const float* F, int64_t n, double* sums, cudaStream_t s)
+{
+    cudaMemsetAsync(sums, 0, kMlpSums * sizeof(double), s);
+    int64_t g = (n + 255) / 256;
+    if (g > 2 * sm_count()) g = 2 * sm_count();
+    k_mlp_sums<<<dim3((unsigned)(g < 1 ? 1 : g), kMlpSums), 256, 0, s>>>(X, T, F, n, sums);
+    count_launches(1);
+}
+
+void launch_mlp_maps(const double* sums, int64_t n, float* maps, float* wscale, cudaStream_t s)
+{
+    k_mlp_maps<<<1, 32, 0, s>>>(sums, n, maps, wscale);
+    count_launches(1);
+}
+
+void launch_mlp_rows(const float* X, const float* T, int64_t n, const float* maps, float* rows, float* tout,
+                     cudaStream_t s)
+{
+    int64_t g = (n * kMlpInPad + 255) / 256;
+    if (g > 16 * sm_count()) g = 16 * sm_count();
+    k_mlp_rows<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(X, T, n, maps, rows, tout);
+    count_launches(1);
+}
+
+void launch_mlp_weights(float* w, int64_t n, int mode, const float* wscale, int32_t* bad, cudaStream_t s)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > 16 * sm_count()) g = 16 * sm_count();
+    k_mlp_weights<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(w, n, mode, wscale, bad);
+    count_launches(1);
+}
+
+void launch_mlp_init(float* params, uint64_t seed, cudaStream_t s)
+{
+    k_mlp_init<<<nblk(kMlpNParam, 256), 256, 0, s>>>(params, seed);
+    count_launches(1);
+}
+
+void launch_mlp_shuffle(int64_t n, uint64_t key, int32_t* idx, cudaStream_t s)
+{
+    int h = 1;
+    while (((int64_t)1 << (2 * h)) < n) h++;
+    int64_t g = (n + 255) / 256;
+    if (g > 16 * sm_count()) g = 16 * sm_count();
+    k_mlp_shuffle<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(n, h, key, idx);
     count_launches(1);
 }
 

@@ -37,6 +37,7 @@ EXPORTS = [
 ]
 
 MLP_NPARAM = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
+TC_MLP_WEIGHTS, TC_MLP_FACTORS = 0, 1
 MLP_NMODEL = MLP_NPARAM + 13 + 13 + 3
 
 
@@ -104,7 +105,7 @@ def load(path: str | None = None):
         "tc_mlp_get": ([P, P, P], I32),
         "tc_mlp_forward": ([P, P, I64, P], I32),
         "tc_mlp_loss_grad": ([P, P, P, P, I64, P, P], I32),
-        "tc_mlp_train": ([P, P, P, P, I64, I32, I32, F, ctypes.c_uint64, F, P], I32),
+        "tc_mlp_train": ([P, P, P, P, I32, I64, I32, I32, F, ctypes.c_uint64, F, P], I32),
         "tc_mlp_pairs": ([P, F, F, F, F, ctypes.c_uint64, I64, P, P, P, P, P, P], I32),
         "tc_mlp_evals": ([P, P], I32),
         "tc_get_group_list": ([P, I64, F, P, P, I64, P, P], I32),
@@ -269,13 +270,16 @@ class Context:
                                            ctypes.byref(loss)))
         return loss.value, g
 
-    def mlp_train(self, X, T, W=None, epochs=40, batch=1024, lr=2e-3, seed=0, band=0.5):
-        """Train a fresh model on pairs (X, T) with loss weights W (None: 1)."""
+    def mlp_train(self, X, T, W=None, epochs=40, batch=1024, lr=2e-3, seed=0, band=0.5, factors=False):
+        """Train a fresh model on pairs (X, T).  W: loss weights (None: 1), or
+        with factors=True the pairs' label factors F (weights F^2 / mean F^2,
+        formed by the library)."""
         X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 13)
         T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1, 3)
         W = None if W is None else np.ascontiguousarray(W, dtype=np.float32).reshape(-1)
         losses = np.zeros(int(epochs), np.float32)
-        self._c(self._lib.tc_mlp_train(self._h, _ptr(X), _ptr(T), _ptr(W), X.shape[0], int(epochs), int(batch),
+        mode = TC_MLP_FACTORS if factors else TC_MLP_WEIGHTS
+        self._c(self._lib.tc_mlp_train(self._h, _ptr(X), _ptr(T), _ptr(W), mode, X.shape[0], int(epochs), int(batch),
                                        float(lr), int(seed), float(band), _ptr(losses)))
         return losses
 
@@ -292,13 +296,6 @@ class Context:
                                        ctypes.byref(npairs)))
         k = npairs.value
         return X[:k], T[:k], F[:k], b[:k], v[:k]
-
-    @staticmethod
-    def mlp_weights(F):
-        """Loss weights that make the training loss the mean squared error of
-        the corrected acceleration: F^2, normalised to mean 1."""
-        w = np.asarray(F, np.float64) ** 2
-        return (w / w.mean()).astype(np.float32)
 
     def mlp_evals(self):
         v = ctypes.c_int64()

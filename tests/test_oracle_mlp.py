@@ -259,3 +259,183 @@ def test_learned_oracle_band_and_zero_model():
     _, _, e1 = t.learned(0.9, 0.01, 0.0, zero, maps)
     _, _, e2 = t.learned(0.9, 0.01, 0.5, zero, maps)
     assert e1 > e2 > 0
+
+
+# ---------------------------------------------------------------- BF16 rounding model
+def _bf16_bits(x):
+    """bfloat16 rounding of float32 values by their bit pattern (round half
+    to even on the 16 dropped bits): an independent statement of the format"""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def test_bf16_rounding_values():
+    """8-bit significand, ties to even: 1 + 2^-8 lies halfway between 1 and
+    1 + 2^-7 and goes to 1; 1 + 3 2^-8 lies halfway between 1 + 2^-7 and
+    1 + 2^-6 and goes to 1 + 2^-6; anything above a midpoint goes up."""
+    cases = [(1 + 2.0 ** -8, 1.0), (1 + 3 * 2.0 ** -8, 1 + 2.0 ** -6), (1 + 2.0 ** -8 + 2.0 ** -20, 1 + 2.0 ** -7),
+             (-(1 + 2.0 ** -8 + 2.0 ** -20), -(1 + 2.0 ** -7)), (255.0, 255.0), (257.0, 256.0), (259.0, 260.0),
+             (0.0, 0.0), (3.0 * 2.0 ** -100, 3.0 * 2.0 ** -100)]
+    for x, want in cases:
+        assert oracle.bf16(x) == want, x
+    # the same as rounding the float32 bit pattern, on random floats
+    v = (np.random.default_rng(7).standard_normal(20000) * 10.0 ** np.random.default_rng(8).uniform(-6, 6, 20000))
+    v32 = v.astype(np.float32)
+    assert np.array_equal(oracle.bf16(v32.astype(np.float64)), _bf16_bits(v32).astype(np.float64))
+
+
+def test_rounding_model_hand_wired():
+    """One path through the network, with a hidden value on each side of a
+    BF16 rounding boundary: z1 = 1 + 2^-8 (a tie, rounds to 1) and
+    z1' = 1 + 2^-8 + 2^-12 (rounds up to 1 + 2^-7); layer 2 doubles, layer 3
+    sums, so y = 2 (1) + 2 (1 + 2^-7) exactly, while the exact network gives
+    2 (1 + 2^-8) + 2 (1 + 2^-8 + 2^-12)."""
+    W1 = np.zeros((13, H)); W1[0, 0] = 1.0; W1[0, 1] = 1.0
+    b1 = np.zeros(H); b1[0] = 2.0 ** -8; b1[1] = 2.0 ** -8 + 2.0 ** -12
+    W2 = np.zeros((H, H)); W2[0, 0] = 2.0; W2[1, 1] = 2.0
+    W3 = np.zeros((H, 3)); W3[0, 0] = 1.0; W3[1, 0] = 1.0; W3[1, 2] = -3.0
+    p = _pack(W1, b1, W2, np.zeros(H), W3, np.array([0.0, 0.25, 0.0]))
+    X = np.zeros((1, 13)); X[0, 0] = 1.0
+    Y, R = oracle.mlp_forward_bf16(p, X)
+    assert Y[0, 0] == 2.0 + 2.0 * (1 + 2.0 ** -7)
+    assert Y[0, 1] == 0.25
+    assert Y[0, 2] == -6.0 * (1 + 2.0 ** -7)
+    exact = oracle.mlp_forward(p, X)
+    assert exact[0, 0] == 4.0 + 4.0 * 2.0 ** -8 + 2.0 * 2.0 ** -12
+    # an FP32 sum can move z1 = 1 + 2^-8 off the tie: the radius admits
+    # both neighbours there; exactly representable values keep a radius of
+    # a few FP32 ulps only
+    assert R[0, 0] >= 2.0 * 2.0 ** -7 - 1e-12
+    assert R[0, 1] <= 65 * 2.0 ** -23 * 0.25
+    # inputs away from any boundary: the model equals the exact network
+    p2 = _pack(W1, np.zeros(H), W2, np.zeros(H), W3, np.zeros(3))
+    X2 = np.zeros((1, 13)); X2[0, 0] = 1.5
+    Y2, R2 = oracle.mlp_forward_bf16(p2, X2)
+    assert np.array_equal(Y2, oracle.mlp_forward(p2, X2))
+    assert np.all(R2 <= 65 * 2.0 ** -23 * np.abs(Y2) * (1 + 1e-12))
+
+
+def _emulate_fp32(p, X):
+    """An FP32-accumulating implementation of the rounding model, written
+    independently in numpy: BF16 operands (bit rounding of float32), products
+    exact in float32, sums added one by one in float32."""
+    W1, b1, W2, b2, W3, b3 = (a.astype(np.float32) for a in _split(p))
+    W1, W2, W3 = _bf16_bits(W1), _bf16_bits(W2), _bf16_bits(W3)
+
+    def dense(a, W, b):
+        z = np.broadcast_to(b, (a.shape[0], W.shape[1])).astype(np.float32).copy()
+        for i in range(W.shape[0]):
+            z = (z + a[:, i:i + 1] * W[i][None, :]).astype(np.float32)
+        return z
+
+    x = _bf16_bits(X.astype(np.float32))
+    h1 = _bf16_bits(np.maximum(dense(x, W1, b1), 0))
+    h2 = _bf16_bits(np.maximum(dense(h1, W2, b2), 0))
+    return dense(h2, W3, b3).astype(np.float64), (x, h1, h2)
+
+
+def test_rounding_model_radius_holds_an_fp32_implementation():
+    """The FP32 emulation lands inside the model's radius on every output of
+    1000 random rows, and the radius is small: a BF16 flip of a hidden unit
+    is rare, so the radius is a few FP32 ulps of the output for most rows."""
+    rng = np.random.default_rng(21)
+    W1 = rng.standard_normal((13, H)) * np.sqrt(2 / 13)
+    W2 = rng.standard_normal((H, H)) * np.sqrt(2 / H)
+    W3 = rng.standard_normal((H, 3)) * np.sqrt(1 / H)
+    p = _pack(W1, rng.standard_normal(H) * 0.1, W2, rng.standard_normal(H) * 0.1, W3, rng.standard_normal(3) * 0.1)
+    p = p.astype(np.float32).astype(np.float64)
+    X = (rng.standard_normal((1000, 13)) * 1.5).astype(np.float32).astype(np.float64)
+    Y, R = oracle.mlp_forward_bf16(p, X)
+    Ye, _ = _emulate_fp32(p, X)
+    assert np.all(np.abs(Ye - Y) <= R)
+    scale = np.sqrt(np.mean(Y ** 2))
+    assert np.median(R) <= 1e-4 * scale
+    # the rounding is visible: the model is not the exact network
+    Yx = oracle.mlp_forward(p, X)
+    d = np.abs(Yx - Y)
+    assert d.max() > 10 * np.median(R) and np.sqrt(np.mean(d ** 2)) <= 2e-2 * scale
+
+
+def test_rounding_model_gradient():
+    """The rounding model's gradient stays within BF16 rounding of the exact
+    gradient (pinned by finite differences above), every parameter block
+    included; the loss matches its own forward; an FP32 emulation of the
+    backward (dY, dH2, dH1 rounded to BF16 before their products, biases
+    from the unrounded values) lands inside the radius."""
+    rng = np.random.default_rng(22)
+    p = (rng.standard_normal(oracle.MLP_NPARAM) * 0.3).astype(np.float32).astype(np.float64)
+    n = 40
+    X = rng.standard_normal((n, 13)).astype(np.float32).astype(np.float64)
+    T = rng.standard_normal((n, 3)).astype(np.float32).astype(np.float64)
+    w = rng.uniform(0.2, 3.0, n).astype(np.float32).astype(np.float64)
+    L, Lr, g, gr = oracle.mlp_grad_bf16(p, X, T, w)
+    Y, _ = oracle.mlp_forward_bf16(p, X)
+    assert L == pytest.approx(np.mean(w * np.sum((Y - T) ** 2, 1)), rel=1e-13)
+    Lx, gx = oracle.mlp_grad(p, X, T, w)
+    o = 0
+    for k in (13 * H, H, H * H, H, H * 3, 3):
+        blk = slice(o, o + k)
+        assert np.linalg.norm(g[blk] - gx[blk]) <= 2e-2 * np.linalg.norm(gx[blk]), k
+        o += k
+    # FP32 emulation of the backward
+    W1, b1, W2, b2, W3, b3 = (a.astype(np.float32) for a in _split(p))
+    W2b, W3b = _bf16_bits(W2), _bf16_bits(W3)
+    ye, (xb, h1, h2) = _emulate_fp32(p, X)
+    dy = (np.float32(2) * w[:, None].astype(np.float32) * (ye.astype(np.float32) - T.astype(np.float32))
+          * np.float32(1.0 / n)).astype(np.float32)
+    dyb = _bf16_bits(dy)
+    dh2 = np.zeros((n, H), np.float32)
+    for k in range(3):
+        dh2 = (dh2 + dyb[:, k:k + 1] * W3b[:, k][None, :]).astype(np.float32)
+    dh2 = np.where(h2 > 0, dh2, 0).astype(np.float32)
+    dh2b = _bf16_bits(dh2)
+    dh1 = np.zeros((n, H), np.float32)
+    for j in range(H):
+        dh1 = (dh1 + dh2b[:, j:j + 1] * W2b[:, j][None, :]).astype(np.float32)
+    dh1 = np.where(h1 > 0, dh1, 0).astype(np.float32)
+    dh1b = _bf16_bits(dh1)
+
+    def rowsum(a):
+        s = np.zeros(a.shape[1:], np.float32)
+        for r in range(a.shape[0]):
+            s = (s + a[r]).astype(np.float32)
+        return s
+
+    ge = np.concatenate([rowsum(xb[:, :, None] * dh1b[:, None, :]).ravel(), rowsum(dh1).ravel(),
+                         rowsum(h1[:, :, None] * dh2b[:, None, :]).ravel(), rowsum(dh2).ravel(),
+                         rowsum(h2[:, :, None] * dyb[:, None, :]).ravel(), rowsum(dy).ravel()]).astype(np.float64)
+    assert np.all(np.abs(ge - g) <= gr)
+    # the radius is a worst case over every BF16 flip an FP32 sum can cause
+    # (each flip propagates through the later roundings), yet still small
+    assert np.linalg.norm(gr) <= 2e-2 * np.linalg.norm(g)
+
+
+def test_rounding_model_band_sum():
+    """The band sum through the rounding model selects the same cells as the
+    exact network's (same evaluations and flags), stays within BF16 rounding
+    of it, and with a constant network (no hidden unit reaches the output)
+    equals it up to the factor's rounding."""
+    n = 3000
+    p, _, m = inputs.plummer(n, 31)
+    t = oracle.Tree(p, m, 8, 32)
+    rng = np.random.default_rng(32)
+    W1 = rng.standard_normal((13, H)) * np.sqrt(2 / 13)
+    W2 = rng.standard_normal((H, H)) * np.sqrt(2 / H)
+    W3 = rng.standard_normal((H, 3)) * np.sqrt(1 / H)
+    params = _pack(W1, rng.standard_normal(H) * 0.1, W2, rng.standard_normal(H) * 0.1, W3,
+                   rng.standard_normal(3) * 0.1).astype(np.float32).astype(np.float64)
+    maps = np.concatenate([np.zeros(13), np.full(13, 0.5), np.full(3, 0.01)])
+    ce, fe, ee = t.learned(0.9, 1e-2, 0.5, params, maps)
+    cb, rb, fb, eb = t.learned_bf16(0.9, 1e-2, 0.5, params, maps)
+    assert ee == eb > 100 and np.array_equal(fe, fb)
+    assert np.all(rb >= 0)
+    scale = np.sqrt(np.mean(ce ** 2))
+    assert np.sqrt(np.mean((cb - ce) ** 2)) <= 2e-2 * scale
+    assert np.median(rb) <= 1e-3 * scale
+    const = np.zeros(oracle.MLP_NPARAM)
+    const[-3:] = [1.0, -2.0, 0.5]
+    c1, _, _ = t.learned(0.9, 1e-2, 0.5, const, maps)
+    c2, r2, _, _ = t.learned_bf16(0.9, 1e-2, 0.5, const, maps)
+    assert np.allclose(c2, c1, rtol=1e-15, atol=0)
+    assert np.all(r2 <= 1e-4 * np.abs(c1) + 1e-300)
