@@ -1,22 +1,36 @@
 #!/usr/bin/env python
 """Benchmark of the treecode force phase on one GB300 (or N replicas).
 
-Workload (default): uniform random cube [-1, 1]^3, N = 2^20 equal masses,
-leaf threshold 16, Plummer softening eps = 1e-3, opening angle theta = 0.5,
-kick-drift-kick leapfrog with dt = 1e-4.  One timed step is one pass of the
-whole hot path: kick + drift, tree build (bounding box, Morton keys, radix
-sort, node table, FP64 moments, groups), the walk + force kernel, kick.
+Default line (the metric's own comparison): the learned far-field correction
+against the plain monopole walk on a fresh Plummer sphere of N = 2^22 bodies
+(eps 1e-3, leaf 16, gmax 64), each path at the opening angle where its RMS
+force error against direct summation (4096 sampled bodies) is 1e-3.  The
+network is trained first on the GPU, on up to 2M body-cell pairs that the
+walk of another Plummer sphere (2^20 bodies) generates; its band is chosen on
+that training sphere, never on the evaluation timings.  One timed step is one
+pass of the whole hot path: kick + drift, tree build (bounding box, Morton
+keys, radix sort, node table, FP64 moments, groups), the walk + force kernel
+(with the network inside the walk for the learned path), kick -- one replay
+of the captured step graph.  The two paths are timed interleaved, step by
+step, L2 flushed (a 256 MiB write) before each; medians and spreads are
+reported, and the walk alone beside the step.
+
+Sub-keys carry the other workloads: ``uniform_1m`` (uniform cube, 2^20
+bodies, theta 0.5, the build/walk roofline and the phase split),
+``precision_16m`` (two Plummer spheres, 2^24 bodies: precise vs plain float32
+against the FP64 oracle) and ``batch_512`` (512 Plummer systems in one
+forest).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints ONE JSON line (rank 0).  ``value`` is bodies/s summed over ranks
-(each rank runs an independent replica: the force phase needs no exchange
-on one GPU), timed with CUDA events around each step, L2 flushed (a 256 MiB
-write) between steps.  ``roofline`` is the walk + force kernel against the
-FP32 CUDA-core peak (20 flops per body-source interaction), timed with the
-library's CUDA events on its own stream.  ``--impl reference`` times the CPU
-oracle (plain FP64 C; tree build on one thread, the walk over the host's
-cores) on a bounded sample of the same workload.
+Prints ONE JSON line (rank 0).  ``value`` is bodies/s of the learned path
+summed over ranks (each rank runs an independent replica: the force phase
+needs no exchange on one GPU).  ``roofline`` is the plain walk + force kernel
+on the same sphere against the FP32 CUDA-core peak (20 flops per body-source
+interaction), timed with the library's CUDA events on its own stream.
+``--impl reference`` times the CPU oracle (plain FP64 C; tree build on one
+thread, the walk over the host's cores) on a bounded sample of the same
+workload, at the opening angle where the oracle's own RMS error is 1e-3.
 """
 from __future__ import annotations
 
@@ -43,8 +57,13 @@ LEAF, EPS, DT, THETA, SEED = 16, 1e-3, 1e-4, 0.5, 0
 THETA_ALT = 0.7  # the uniform workload's second opening angle
 FLOPS_PER_INTERACTION = 20
 QUAD_FLOPS_PER_CELL = 55  # monopole + quadrupole term of one cell (FMA = 2)
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+MLP_FLOPS_PER_EVAL = 2 * (16 * 64 + 64 * 64 + 64 * 8)  # one network row on the tensor cores, padded shapes
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0
+# learned workload: training sphere, evaluation sphere, accuracy goal
+N_TRAIN, N_EVAL, SEED_TRAIN, SEED_EVAL = 1 << 20, 1 << 22, 100, 101
+THETA_TRAIN, BAND_TRAIN, BANDS, GOAL = 0.7, 0.4, (0.5, 0.55, 0.6, 0.65), 1e-3
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "walk_uniform_1m.txt")
+PROFILE_TRAFFIC_PLUMMER = os.path.join(ROOT, "profiles", "walk_plummer_4m.txt")
 WALK_SRC = os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", "tc_walk.cuh")
 
 
@@ -58,8 +77,34 @@ def workload_config(n, theta):
     }
 
 
-def fp32_peak_tflops(mhz=SM_MAX_MHZ):
-    return 2.0 * FP32_LANES * SMS * mhz * 1e6 / 1e12
+def learned_config(n_eval=N_EVAL):
+    return {
+        "workload": f"learned far-field correction vs plain monopole walk: fresh Plummer sphere N={n_eval} "
+                    f"(a=1, cutoff 10, masses 1/N, seed {SEED_EVAL}), eps 1e-3, leaf 16, gmax 64, each path at "
+                    f"the theta where its RMS force error vs direct sum (4096 sampled bodies) is 1e-3; network "
+                    f"13->64->64->3 trained on the GPU on <= 2M body-cell pairs of a {N_TRAIN}-body Plummer sphere "
+                    f"(seed {SEED_TRAIN}); KDK leapfrog dt 1e-4 per step (build + walk/force + update)",
+        "n_bodies": n_eval, "eps": EPS, "leaf": LEAF, "gmax": 64, "dt": DT, "rms_goal": GOAL,
+        "l2": "flushed before every timed step (256 MiB write)",
+        "timing": "plain and learned steps interleaved, one captured-graph replay each, CUDA events",
+    }
+
+
+_SMS = None
+
+
+def device_sms():
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    global _SMS
+    if _SMS is None:
+        import torch
+
+        _SMS = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return _SMS
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ, sms=None):
+    return 2.0 * FP32_LANES * (sms or device_sms()) * mhz * 1e6 / 1e12
 
 
 # ------------------------------------------------------------------ clocks
@@ -113,12 +158,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile(shape=None):
+def _traffic_from_profile(shape=None, path=None):
     """dram bytes of one force phase (every launch of the walk) from the
     committed ncu summary, or None if the walk kernel's source changed since
     it was captured or the summary's walk shape is not the one measured."""
     try:
-        txt = open(PROFILE_TRAFFIC).read()
+        txt = open(path or PROFILE_TRAFFIC).read()
         cur = hashlib.sha256(open(WALK_SRC, "rb").read()).hexdigest()[:16]
         kv = {}
         for line in txt.splitlines():
@@ -135,20 +180,23 @@ def _traffic_from_profile(shape=None):
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(p, m, v, theta, frac_groups=8, gmax=64, threads=1, tree=None):
-    """One sampled oracle step: full tree build (one thread), the walk for
-    1/frac_groups of the groups (evenly spread; over `threads` host threads,
-    each walking its own chunks of groups -- the oracle's C walk runs
-    outside Python's lock), the leapfrog update; returns the extrapolated
-    seconds of a whole step, what was sampled and the wall time."""
+def oracle_sample(p, m, v, theta, frac_groups=8, gmax=64, threads=1, tree=None, tree_build_s=None, leaf=LEAF,
+                  eps=EPS):
+    """One sampled oracle step: full tree build (one thread; or a tree built
+    earlier, with the seconds its build took), the walk for 1/frac_groups of
+    the groups (evenly spread; over `threads` host threads, each walking its
+    own chunks of groups -- the oracle's C walk runs outside Python's lock),
+    the leapfrog update; returns the extrapolated seconds of a whole step,
+    what was sampled and the wall time."""
     import concurrent.futures as cf
 
     import oracle
 
     n = p.shape[0]
     t0 = time.perf_counter()
-    t = oracle.Tree(p, m, LEAF, gmax)
+    t = tree if tree is not None else oracle.Tree(p, m, leaf, gmax)
     t1 = time.perf_counter()
+    build_s = tree_build_s if tree is not None else (t1 - t0)
     nchunks = max(16, 4 * threads)
     per = max(1, t.G // (frac_groups * nchunks))
     starts = [int(g0) for g0 in np.linspace(0, t.G - per, nchunks).astype(int)]
@@ -156,7 +204,7 @@ def oracle_sample(p, m, v, theta, frac_groups=8, gmax=64, threads=1, tree=None):
     acc_all = np.zeros((n, 3))  # groups own disjoint bodies: one shared output
 
     def walk(g0):
-        t._lib.or_tree_walk(t._h, float(theta), float(EPS), 1.0, g0, g0 + per,
+        t._lib.or_tree_walk(t._h, float(theta), float(eps), 1.0, g0, g0 + per,
                             acc_all.ctypes.data_as(ctypes.c_void_p), None, None, None, None, None, None)
         return per
 
@@ -172,10 +220,53 @@ def oracle_sample(p, m, v, theta, frac_groups=8, gmax=64, threads=1, tree=None):
     oracle.kick(vv, acc, DT / 2)
     t3 = time.perf_counter()
     scale = t.G / walked
-    est = (t1 - t0) + (t2 - t1) * scale + (t3 - t2)
+    est = build_s + (t2 - t1) * scale + (t3 - t2)
     sample = (f"oracle tree build of all {n} bodies (1 thread) + walk/force of {walked} of {t.G} groups "
               f"on {threads} thread(s) (x{scale:.1f} extrapolated) + leapfrog update")
     return est, sample, (t3 - t0)
+
+
+def oracle_iso_theta(t, p, m, lo=0.4, hi=0.9, it=7, nsample=512, eps=EPS, goal=GOAL):
+    """The largest theta in [lo, hi] at which the oracle's own walk has an
+    RMS force error <= goal against its FP64 direct sum, on the groups of
+    nsample sampled bodies (bisection)."""
+    import oracle
+
+    n = p.shape[0]
+    idx = inputs_sample(n, nsample, seed=1)
+    ad, _ = oracle.direct(p, m, eps, 1.0, idx=idx, want_pot=False)
+    inv = np.empty(n, np.int64)
+    inv[t.perm] = np.arange(n)
+    groups = np.unique(np.searchsorted(t.gfirst, inv[idx], side="right") - 1)
+
+    acc_all = np.zeros((n, 3))  # groups own disjoint bodies: one shared output
+    import concurrent.futures as cf
+
+    def rms(theta):
+        def walk(g):
+            t._lib.or_tree_walk(t._h, float(theta), float(eps), 1.0, int(g), int(g) + 1,
+                                acc_all.ctypes.data_as(ctypes.c_void_p), None, None, None, None, None, None)
+
+        with cf.ThreadPoolExecutor(max_workers=host_cores()) as ex:
+            list(ex.map(walk, groups))
+        a = acc_all[idx]
+        return float(np.sqrt(np.mean(np.sum((a - ad) ** 2, 1) / np.sum(ad ** 2, 1))))
+
+    if rms(lo) > goal:
+        return lo
+    for _ in range(it):
+        mid = 0.5 * (lo + hi)
+        if rms(mid) <= goal:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def inputs_sample(n, k, seed):
+    from paper_1211_2293_gb300 import inputs
+
+    return inputs.sample_indices(n, k, seed=seed)
 
 
 def host_cores():
@@ -186,26 +277,41 @@ def host_cores():
 
 
 def run_reference(args, rank, world):
+    """The CPU oracle as it stands on the default workload's evaluation
+    sphere (2^22-body Plummer, eps 1e-3, leaf 16, gmax 64), at the opening
+    angle where the oracle's own RMS force error against its FP64 direct
+    sum is 1e-3 (bisection on 512 sampled bodies): the tree built once on
+    one thread, then every step walks a bounded sample of the groups over the
+    host's cores, extrapolated to all groups, plus the leapfrog update.  The
+    oracle has no learned correction: this is the method it implements, at
+    the same accuracy."""
     if rank != 0:
         return 0
+    import oracle
     from paper_1211_2293_gb300 import inputs
 
-    n = args.n
-    p, v, m = inputs.uniform_cube(n, SEED)
+    n = args.n if args.n != N_DEFAULT else N_EVAL
+    p, v, m = inputs.plummer(n, SEED_EVAL)
     cores = host_cores()
+    t0 = time.perf_counter()
+    t = oracle.Tree(p, m, LEAF, 64)
+    build_s = time.perf_counter() - t0
+    theta = oracle_iso_theta(t, p, m)
     times = []
     sample = ""
     for k in range(args.warmup + args.steps):
-        est, sample, _ = oracle_sample(p, m, v, args.theta, frac_groups=args.ref_frac, threads=cores)
+        est, sample, _ = oracle_sample(p, m, v, theta, frac_groups=args.ref_frac, threads=cores, tree=t,
+                                       tree_build_s=build_s)
         if k >= args.warmup:
             times.append(est)
     sec = statistics.mean(times)
     value = n / sec
+    sample = sample + f"; theta {theta:.4f} (the oracle's RMS error 1e-3 on 512 sampled bodies)"
     line = {
         "metric": METRIC, "value": value, "unit": "bodies/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": workload_config(n, args.theta),
+        "config": learned_config(n),
         "cpu_baseline": {"value": value, "unit": "bodies/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "bodies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -267,7 +373,7 @@ def walk_shape(ctx, args, theta):
             "walk_ms_when_chosen": ms_tuned}
 
 
-def run_ours(args, rank, world, local_rank):
+def run_uniform(args, rank, world, local_rank, cpu_baseline=True):
     import torch
 
     from paper_1211_2293_gb300 import inputs, tc
@@ -418,7 +524,7 @@ def run_ours(args, rank, world, local_rank):
     line = None
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and cpu_baseline and not args.no_cpu_baseline:
             cores = host_cores()
             est, sample, _ = oracle_sample(p, m, v, args.theta, frac_groups=args.cpu_frac, threads=cores)
             est1, sample1, _ = oracle_sample(p, m, v, args.theta, frac_groups=4 * args.cpu_frac, threads=1)
@@ -440,7 +546,7 @@ def run_ours(args, rank, world, local_rank):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_walk (walk + force; one force phase = one launch, or one per group-size "
                                    "class for gmax 64 and 128)",
-                         "peak_basis": "2 flops x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)",
+                         "peak_basis": f"2 flops x 128 FP32 lanes x {device_sms()} SMs x 2070 MHz (max SM clock)",
                          "frac_at_measured_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])
                                                     if clk.get("sm_mhz") else None),
                          "fp32_probe_tflops": probe,
@@ -462,7 +568,336 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-def run_batch(args, rank, world, local_rank):
+def _spread(xs):
+    q = np.percentile(np.asarray(xs, np.float64), [0, 25, 50, 75, 100])
+    return {"min": float(q[0]), "p25": float(q[1]), "median": float(q[2]), "p75": float(q[3]), "max": float(q[4])}
+
+
+def _rms_vs_direct(a, ad):
+    a = np.asarray(a, np.float64)
+    return float(np.sqrt(np.mean(np.sum((a - ad) ** 2, 1) / np.sum(ad ** 2, 1))))
+
+
+def _iso_theta(ctx, idx, ad, lo, hi, it=9, goal=GOAL):
+    """The largest theta in [lo, hi] whose RMS force error against the direct
+    sums ad (bodies idx) is <= goal (bisection), with that error; None if
+    even lo misses it."""
+    def err(theta):
+        ctx.forces(theta, EPS)
+        return _rms_vs_direct(ctx.get_acc()[idx], ad)
+
+    e_lo = err(lo)
+    if e_lo > goal:
+        return None, e_lo
+    for _ in range(it):
+        mid = 0.5 * (lo + hi)
+        e = err(mid)
+        if e <= goal:
+            lo, e_lo = mid, e
+        else:
+            hi = mid
+    return lo, e_lo
+
+
+def _walk_median(ctx, theta, reps=5):
+    ts = []
+    ctx.forces(theta, EPS)
+    ctx.sync()
+    for _ in range(reps):
+        ctx.set_timing(True)
+        ctx.forces(theta, EPS)
+        ts.append(ctx.timings()["walk_ms"])
+        ctx.set_timing(False)
+    return statistics.median(ts)
+
+
+def _oracle_group_errors(t, p_gpu_acc, theta, sample, extra=None, kappa_max=50.0, eps=EPS):
+    """Max / RMS relative error of GPU accelerations against the FP64
+    oracle's walk (plus an extra per-body term, e.g. the learned correction)
+    for the bodies of the groups holding the sampled bodies, groups whose
+    opening or band tests lay within 1e-6 of their bound left out; bodies
+    whose sum is dominated by cancellation (kappa > kappa_max) counted
+    apart."""
+    import concurrent.futures as cf
+
+    n = t.n
+    inv = np.empty(n, np.int64)
+    inv[t.perm] = np.arange(n)
+    groups = np.unique(np.searchsorted(t.gfirst, inv[sample], side="right") - 1)
+    acc = np.zeros((n, 3))
+    amag = np.zeros(n)
+    flag = np.zeros(t.G, np.int32)
+
+    def walk(g):
+        t._lib.or_tree_walk(t._h, float(theta), float(eps), 1.0, int(g), int(g) + 1,
+                            acc.ctypes.data_as(ctypes.c_void_p), None, amag.ctypes.data_as(ctypes.c_void_p),
+                            None, None, None, flag.ctypes.data_as(ctypes.c_void_p))
+
+    with cf.ThreadPoolExecutor(max_workers=host_cores()) as ex:
+        list(ex.map(walk, groups))
+    rel, kap, skipped = [], [], 0
+    for g in groups:
+        if flag[g] or (extra is not None and extra[1][g]):
+            skipped += 1
+            continue
+        bi = t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]
+        ref = acc[bi] + (extra[0][bi] if extra is not None else 0.0)
+        err = np.linalg.norm(p_gpu_acc[bi].astype(np.float64) - ref, axis=1)
+        nrm = np.linalg.norm(ref, axis=1)
+        rel.append(err / nrm)
+        kap.append(amag[bi] / nrm)
+    rel = np.concatenate(rel)
+    kap = np.concatenate(kap)
+    well = kap <= kappa_max
+    return {"max_rel_err": float(rel[well].max()), "rms_rel_err": float(np.sqrt(np.mean(rel[well] ** 2))),
+            "bodies": int(rel.size), "groups": int(groups.size - skipped), "flagged_groups_skipped": int(skipped),
+            "kappa_gt_50_bodies": int((~well).sum()),
+            "max_rel_err_incl_kappa_gt_50": float(rel.max())}
+
+
+def run_learned_default(args, rank, world, local_rank, dist=None):
+    """The metric's comparison (see the module docstring).  Returns the JSON
+    line (rank 0) or None."""
+    import torch
+
+    import oracle
+    from paper_1211_2293_gb300 import inputs, tc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    tc.load()
+    n_ev = args.n if args.n != N_DEFAULT else N_EVAL
+    # ---- training: pairs generated by the walk itself, trained on the GPU
+    p_tr, _, m_tr = inputs.plummer(N_TRAIN, seed=SEED_TRAIN + 1000 * rank)
+    ctx_tr = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
+    ctx_tr.build(torch.from_numpy(p_tr).to(dev), torch.from_numpy(m_tr).to(dev), LEAF)
+    target = 2_000_000
+    n_all = len(ctx_tr.mlp_pairs(THETA_TRAIN, EPS, BAND_TRAIN, 0.05, 1, target)[0])
+    prob = min(1.0, 0.05 * target / max(1, n_all))
+    t0 = time.perf_counter()
+    X, T, F, _, _ = ctx_tr.mlp_pairs(THETA_TRAIN, EPS, BAND_TRAIN, prob, 2, target)
+    pairs_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = ctx_tr.mlp_train(X, T, F, epochs=args.epochs, batch=1024, lr=2e-3, seed=3, band=BAND_TRAIN,
+                              factors=True)
+    train_s = time.perf_counter() - t0
+    model, _ = ctx_tr.mlp_get()
+    npairs = int(len(X))
+    # ---- the band (the correction's one free parameter) chosen on the
+    # training sphere: each candidate at its own theta of RMS error 1e-3
+    # there, the fastest walk kept
+    idx_tr = inputs.sample_indices(N_TRAIN, 4096, seed=1)
+    ad_tr, _ = ctx_tr.direct(idx_tr, EPS)
+    ctx_tr.set_config(learned=1)
+    bands = []
+    for b in BANDS:
+        ctx_tr.mlp_set(model, b)
+        th, e = _iso_theta(ctx_tr, idx_tr, ad_tr, 0.4, 1.2)
+        if th is not None:
+            bands.append({"band": b, "theta": th, "rms_err": e, "walk_ms": _walk_median(ctx_tr, th)})
+    ctx_tr.set_config(learned=0)
+    th_tr_plain, e_tr_plain = _iso_theta(ctx_tr, idx_tr, ad_tr, 0.4, 1.0)
+    plain_tr_ms = _walk_median(ctx_tr, th_tr_plain) if th_tr_plain is not None else None
+    band = min(bands, key=lambda r: r["walk_ms"])["band"] if bands else BANDS[0]
+    ctx_tr.close()
+    del X, T, F
+
+    # ---- evaluation sphere: each path at its own theta of RMS error 1e-3
+    p, v, m = inputs.plummer(n_ev, seed=SEED_EVAL + 1000 * rank)
+    P, M, V = (torch.from_numpy(a).to(dev) for a in (p, m, v))
+    ctxP = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
+    ctxL = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
+    ctxP.build(P, M, LEAF)
+    ctxL.build(P, M, LEAF)
+    ctxL.mlp_set(model, band)
+    ctxL.set_config(learned=1)
+    idx = inputs.sample_indices(n_ev, 4096, seed=1)
+    ad, _ = ctxP.direct(idx, EPS)
+    thP, eP = _iso_theta(ctxP, idx, ad, 0.4, 1.0)
+    thL, eL = _iso_theta(ctxL, idx, ad, 0.4, 1.2)
+    if thL is None:  # the correction cannot reach the goal at any theta >= 0.4: time it at the plain theta
+        thL = thP
+    ctxP.forces(thP, EPS)
+    accP0 = ctxP.get_acc().copy()
+    ctxL.mlp_evals()
+    ctxL.forces(thL, EPS)
+    accL0 = ctxL.get_acc().copy()
+    evals = ctxL.mlp_evals()
+    rmsP, rmsL = _rms_vs_direct(accP0[idx], ad), _rms_vs_direct(accL0[idx], ad)
+    statP, statL = ctxP.lists(per_group=False), ctxL.lists(per_group=False)
+
+    # ---- interleaved timing: one captured step graph per path per rep
+    for c, th in ((ctxP, thP), (ctxL, thL)):
+        c.set_velocity(V)
+        c.forces(th, EPS)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for c in (ctxP, ctxL):
+            flush.zero_()
+            c.step(DT)
+    ctxP.sync()
+    ctxL.sync()
+    clocks = ClockSampler(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else None)
+    clocks.start()
+    t_load = time.perf_counter()
+    while time.perf_counter() - t_load < 1.0:
+        for c in (ctxP, ctxL):
+            c.step(DT)
+        ctxL.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    reps = max(10, args.steps)
+    ctxP.timings()  # the launch count of the timed region starts here
+    msP, msL = [], []
+    wall0 = time.perf_counter()
+    for _ in range(reps):
+        for c, out in ((ctxP, msP), (ctxL, msL)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.step(DT)
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ctxP.timings()["launches"]
+    # the walk alone (the library's events around the walk kernel), interleaved
+    wP, wL, bP, bL = [], [], [], []
+    for _ in range(reps):
+        for c, th, wo, bo in ((ctxP, thP, wP, bP), (ctxL, thL, wL, bL)):
+            flush.zero_()
+            c.set_timing(True)
+            c.step(DT)
+            tm = c.timings()
+            wo.append(tm["walk_ms"])
+            bo.append(tm["build_ms"])
+            c.set_timing(False)
+    interP = ctxP.lists(per_group=False)["interactions"]
+    interL = ctxL.lists(per_group=False)["interactions"]
+    medP, medL = statistics.median(msP), statistics.median(msL)
+    ms_agg, value = aggregate_over_ranks(medL, n_ev, world, dist, dev)
+    _, value_plain = aggregate_over_ranks(medP, n_ev, world, dist, dev)
+    ratios = [a / b for a, b in zip(msP, msL)]
+
+    # ---- end to end through the C ABI from pinned host buffers (learned)
+    hp = torch.from_numpy(p).pin_memory()
+    hm = torch.from_numpy(m).pin_memory()
+    hacc = torch.empty((n_ev, 3), dtype=torch.float32).pin_memory()
+    ctxE = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
+    ctxE.build(hp, hm, LEAF)
+    ctxE.mlp_set(model, band)
+    ctxE.set_config(learned=1)
+    for _ in range(2):
+        ctxE.build(hp, hm, LEAF)
+        ctxE.forces(thL, EPS)
+        ctxE.get_acc(hacc)
+    e2e_ms = []
+    for _ in range(max(3, reps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctxE.build(hp, hm, LEAF)
+        ctxE.forces(thL, EPS)
+        ctxE.get_acc(hacc)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    _, e2e_val = aggregate_over_ranks(statistics.median(e2e_ms), n_ev, world, dist, dev)
+    ctxE.close()
+    probe = {"scalar_fma": tc.probe_fp32(False), "paired_fma": tc.probe_fp32(True)}
+    force_probe = tc.probe_force()
+    if rank != 0:
+        return None
+
+    # ---- against the FP64 oracle: the same bodies, tree and lists; the
+    # learned path adds the oracle's band sum of the same network (exact
+    # FP64 evaluation), so BF16 rounding counts as error
+    t0 = time.perf_counter()
+    t = oracle.Tree(p, m, LEAF, 64)
+    tree_s = time.perf_counter() - t0
+    sample = inputs.sample_indices(n_ev, 64, seed=5)
+    errP = _oracle_group_errors(t, accP0, thP, sample)
+    inv = np.empty(n_ev, np.int64)
+    inv[t.perm] = np.arange(n_ev)
+    groups = np.unique(np.searchsorted(t.gfirst, inv[sample], side="right") - 1)
+    corr = np.zeros((n_ev, 3))
+    lflag = np.zeros(t.G, np.int32)
+    prm = np.ascontiguousarray(model[:tc.MLP_NPARAM], dtype=np.float64)
+    mps = np.ascontiguousarray(model[tc.MLP_NPARAM:], dtype=np.float64)
+    for g in groups:  # each call writes its own group's bodies and flag
+        t._lib.or_tree_learned(t._h, float(thL), float(EPS), 1.0, float(band), prm.ctypes.data_as(ctypes.c_void_p),
+                               mps.ctypes.data_as(ctypes.c_void_p), int(g), int(g) + 1,
+                               corr.ctypes.data_as(ctypes.c_void_p), lflag.ctypes.data_as(ctypes.c_void_p))
+    errL = _oracle_group_errors(t, accL0, thL, sample, extra=(corr, lflag))
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        est, csample, _ = oracle_sample(p, m, v, thP, frac_groups=64, threads=cores, tree=t, tree_build_s=tree_s)
+        cpu = {"value": n_ev / est, "unit": "bodies/s", "cores": cores, "kind": "oracle",
+               "sample": csample + f" at the plain walk's theta {thP:.4f} (the oracle has no learned correction)"}
+
+    achieved = interP * FLOPS_PER_INTERACTION / (statistics.median(wP) / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    achievedL = interL * FLOPS_PER_INTERACTION / (statistics.median(wL) / 1e3) / 1e12
+    shape = {"gmax": 64, "tile": 128, "warps": 4}
+    line = {
+        "metric": METRIC, "value": value, "unit": "bodies/s", "n_gpus": world, "steps": reps, "warmup": args.warmup,
+        "ms_per_step": ms_agg, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 forces (FP64 build reductions), bf16 tensor-core MLP with fp32 accumulation",
+        "data": "synthetic", "config": learned_config(n_ev),
+        "value_is": "learned path, bodies/s per step (median of the interleaved timed steps), at the theta where "
+                    "its RMS force error vs direct summation is 1e-3",
+        "plain": {"theta": thP, "rms_force_err": rmsP, "ms_per_step": _spread(msP), "bodies_per_s": value_plain,
+                  "walk_ms": _spread(wP), "build_ms": statistics.median(bP),
+                  "interactions_per_body": statP["interactions"] / n_ev, "fp32_tflops_walk": achieved,
+                  "vs_fp64_oracle": errP},
+        "learned": {"theta": thL, "band": band, "rms_force_err": rmsL, "ms_per_step": _spread(msL),
+                    "bodies_per_s": value, "walk_ms": _spread(wL), "build_ms": statistics.median(bL),
+                    "interactions_per_body": statL["interactions"] / n_ev, "mlp_evals_per_body": evals / n_ev,
+                    "fp32_tflops_walk": achievedL,
+                    "mlp_tflops_walk": evals * MLP_FLOPS_PER_EVAL / (statistics.median(wL) / 1e3) / 1e12,
+                    "vs_fp64_oracle": errL},
+        "learned_over_plain": {"step": medP / medL, "step_per_rep_ratio": _spread(ratios),
+                               "walk": statistics.median(wP) / statistics.median(wL)},
+        "band_selection_on_training_sphere": {"candidates": bands, "chosen": band,
+                                              "plain": {"theta": th_tr_plain, "rms_err": e_tr_plain,
+                                                        "walk_ms": plain_tr_ms}},
+        "training": {"pairs": npairs, "pair_prob": prob, "pairs_s": pairs_s,
+                     "epochs": args.epochs, "batch": 1024, "lr": "2e-3, cosine decay",
+                     "loss_weights": "F^2 / mean F^2 (acceleration error), formed in the library", "train_s": train_s,
+                     "loss_first": float(losses[0]), "loss_last": float(losses[-1])},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": _traffic_from_profile(shape, PROFILE_TRAFFIC_PLUMMER),
+                     "kernel": "k_walk, plain precise walk of the evaluation sphere at its 1e-3 theta (one force "
+                               "phase = one launch per group-size class)",
+                     "peak_basis": f"2 flops x 128 FP32 lanes x {device_sms()} SMs x 2070 MHz (max SM clock); "
+                                   "MEASURED_PEAKS.json has no FP32 figure",
+                     "frac_at_measured_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"]) if clk.get("sm_mhz")
+                                                else None),
+                     "fp32_probe_tflops": probe, "force_loop_alone_tflops": force_probe,
+                     "force_loop_alone_frac": force_probe / peak},
+        "e2e": {"value": e2e_val, "unit": "bodies/s", "h2d_bytes_per_step": int(16 * n_ev),
+                "d2h_bytes_per_step": int(12 * n_ev),
+                "what": "learned force evaluation from pinned host pos/mass: upload, build, walk/force with the "
+                        "network, download of accelerations"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed": wall,
+        "cpu_baseline": cpu,
+    }
+    return line
+
+
+def batch_line(args, rank, world, local_rank):
     """512 independent Plummer systems (N log-uniform in [1024, 65536],
     theta 0.6, leaf 8, eps 0.01, KDK dt 1e-3) in one forest: one walk launch
     and one step graph per step; launch shape from the autotuner."""
@@ -543,28 +978,32 @@ def run_batch(args, rank, world, local_rank):
         "graph_kernels_per_step": tim["graph_kernels"],
         "clocks": clk,
     }
+    ctx.close()
+    return line
+
+
+def run_batch(args, rank, world, local_rank):
+    line = batch_line(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
 
 
-def run_precision(args, rank, world, local_rank):
+def precision_summary(args, local_rank, nsample=2048):
     """Two Plummer spheres of 2^23 bodies each, 6 scale radii apart and
     approaching at 0.5 (N = 2^24, theta 0.75, leaf 16, eps 5e-4): forces of
     the precise mode (cell-relative coordinates, compensated tile sums) and of
     the plain float32 mode against the FP64 oracle's forces on the same tree
-    and lists for the groups holding 8192 sampled bodies; and the cost."""
+    and lists for the groups holding nsample sampled bodies; and the cost."""
     import torch
 
     import oracle
     from paper_1211_2293_gb300 import inputs, tc
 
-    if rank != 0:
-        return 0
     torch.cuda.set_device(local_rank)
     tc.load()
     theta, eps, leaf = 0.75, 5e-4, 16
-    n = args.n if args.n != N_DEFAULT else 1 << 24
+    n = args.n if (args.n != N_DEFAULT and args.workload == "precision") else 1 << 24
     p, v, m = inputs.two_plummer(n, seed=0)
     P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
     res = {}
@@ -573,44 +1012,41 @@ def run_precision(args, rank, world, local_rank):
         ctx.build(P, M, leaf)
         ctx.forces(theta, eps)
         ctx.sync()
-        ctx.set_timing(True)
-        for _ in range(3):
+        ts = []
+        for _ in range(5):
+            ctx.set_timing(True)
             ctx.forces(theta, eps)
-        walk_ms = ctx.timings()["walk_ms"] / 3
-        ctx.set_timing(False)
-        res[mode] = dict(acc=ctx.get_acc(), walk_ms=walk_ms)
+            ts.append(ctx.timings()["walk_ms"])
+            ctx.set_timing(False)
+        res[mode] = dict(acc=ctx.get_acc(), walk_ms=statistics.median(ts))
         gmax = ctx.config()["gmax"]
+        ctx.close()
+    del P, M
     t0 = time.perf_counter()
     t = oracle.Tree(p, m, leaf, gmax)
-    sample = inputs.sample_indices(n, 8192, seed=3)
-    inv = np.empty(n, np.int64)
-    inv[t.perm] = np.arange(n)
-    gid = np.searchsorted(t.gfirst, inv[sample], side="right") - 1
-    groups = np.unique(gid)
-    acc_or = np.full((n, 3), np.nan)
-    flagged = 0
-    for g in groups:
-        w = t.walk(theta, eps, groups=(int(g), int(g) + 1), want_pot=False)
-        flagged += int(w["flag"][g] == 1)
-        idx = t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]
-        acc_or[idx] = w["acc"][idx]
-    oracle_s = time.perf_counter() - t0
-    ao = acc_or[sample]
+    sample = inputs.sample_indices(n, nsample, seed=3)
     out = {}
     for mode, name in ((1, "precise"), (0, "plain")):
-        a = res[mode]["acc"][sample].astype(np.float64)
-        rel = np.linalg.norm(a - ao, axis=1) / np.linalg.norm(ao, axis=1)
-        out[name] = {"max_rel_err": float(rel.max()), "rms_rel_err": float(np.sqrt(np.mean(rel ** 2))),
-                     "p99_rel_err": float(np.percentile(rel, 99)), "walk_ms": res[mode]["walk_ms"],
+        e = _oracle_group_errors(t, res[mode]["acc"], theta, sample, eps=eps)
+        out[name] = {"max_rel_err": e["max_rel_err"], "rms_rel_err": e["rms_rel_err"],
+                     "max_rel_err_incl_kappa_gt_50": e["max_rel_err_incl_kappa_gt_50"],
+                     "kappa_gt_50_bodies": e["kappa_gt_50_bodies"], "bodies": e["bodies"],
+                     "flagged_groups_skipped": e["flagged_groups_skipped"], "walk_ms": res[mode]["walk_ms"],
                      "bodies_per_s_walk": n / (res[mode]["walk_ms"] / 1e3)}
-    line = {"metric": "force error vs FP64 oracle (8192 sampled bodies) and walk throughput: precise vs plain",
-            "value": out["precise"]["max_rel_err"], "unit": "max relative error", "higher_is_better": False,
-            "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"two Plummer spheres, N={n}, 6 scale radii apart, approaching at 0.5, "
-                                   f"theta 0.75, leaf 16, eps 5e-4", "n_bodies": n},
+    return {"workload": f"two Plummer spheres, N={n}, 6 scale radii apart, approaching at 0.5, theta 0.75, "
+                        f"leaf 16, eps 5e-4; errors vs the FP64 oracle on the groups of {nsample} sampled bodies",
             "precise": out["precise"], "plain": out["plain"],
-            "precise_cost": res[1]["walk_ms"] / res[0]["walk_ms"],
-            "sampled_groups": int(groups.size), "flagged_groups": flagged, "oracle_seconds": oracle_s}
+            "precise_cost": res[1]["walk_ms"] / res[0]["walk_ms"], "oracle_seconds": time.perf_counter() - t0}
+
+
+def run_precision(args, rank, world, local_rank):
+    if rank != 0:
+        return 0
+    r = precision_summary(args, local_rank, nsample=8192)
+    line = {"metric": "force error vs FP64 oracle (8192 sampled bodies) and walk throughput: precise vs plain",
+            "value": r["precise"]["max_rel_err"], "unit": "max relative error", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic", "config": {"workload": r["workload"]}}
+    line.update(r)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -789,14 +1225,17 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--theta", type=float, default=THETA)
     ap.add_argument("--cpu-frac", type=int, default=8, help="oracle walks 1/cpu_frac of the groups")
-    ap.add_argument("--ref-frac", type=int, default=16)
+    ap.add_argument("--ref-frac", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default=None,
                     help="uniform: walk shape 'gmax,tile,warps' instead of the autotuner's choice")
-    ap.add_argument("--workload", choices=["uniform", "batch", "precision", "learned"], default="uniform",
-                    help="uniform: the benchmark line; batch: 512 Plummer systems in one forest; "
-                         "precision: cell-relative vs plain float32 on two colliding Plummer spheres; "
-                         "learned: the learned far-field correction against the plain walk")
+    ap.add_argument("--workload", choices=["default", "uniform", "batch", "precision", "learned"],
+                    default="default",
+                    help="default: the benchmark line (learned vs plain at RMS 1e-3 on a 2^22 Plummer sphere, "
+                         "with the other workloads as sub-keys); uniform: the uniform cube alone; batch: 512 "
+                         "Plummer systems in one forest; precision: cell-relative vs plain float32 on two colliding "
+                         "Plummer spheres; learned: the learned correction's sweep (bands, quadrupole, fixed theta)")
+    ap.add_argument("--headline-only", action="store_true", help="default workload without the sub-keys")
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")
     ap.add_argument("--band-train", type=float, default=0.4, help="learned: band of the training pairs")
@@ -820,18 +1259,30 @@ def main():
         return run_precision(args, rank, world, local_rank)
     if args.workload == "learned":
         return run_learned(args, rank, world, local_rank)
+    dist = None
     if world > 1:
         import torch
         import torch.distributed as dist
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    line = run_ours(args, rank, world, local_rank)
-    if line is not None:
+    if args.workload == "uniform":
+        line = run_uniform(args, rank, world, local_rank)
+    else:
+        line = run_learned_default(args, rank, world, local_rank, dist)
+        if not args.headline_only:
+            # the other workloads, as sub-keys (every rank runs the uniform
+            # replica; the precision and batch summaries run on rank 0)
+            sub_args = argparse.Namespace(**vars(args))
+            sub_args.n = N_DEFAULT
+            uni = run_uniform(sub_args, rank, world, local_rank, cpu_baseline=False)
+            if rank == 0:
+                line["uniform_1m"] = uni
+                line["precision_16m"] = precision_summary(sub_args, local_rank)
+                line["batch_512"] = batch_line(sub_args, rank, 1, local_rank)
+    if line is not None and rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
-        import torch.distributed as dist
-
         dist.destroy_process_group()
     return 0
 
