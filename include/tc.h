@@ -76,7 +76,13 @@ typedef struct tc_ctx tc_ctx;
  *             summed one body per lane, one of at most 64 two per lane, a
  *             larger one four (the default); 0: one launch, gmax / 32
  *             bodies per lane for every group.  Lists and forces are the
- *             same in both.                                               */
+ *             same in both.
+ *   split     1: the monopole walks (learned = 0, quadrupole = 0) run with
+ *             the tree walk and the force loop on different warps: a
+ *             producer warp walks and fills a ring of list tiles in shared
+ *             memory, a consumer warp sums them (the default); 0: every
+ *             warp walks and sums its own groups.  Same lists; the sums
+ *             take the tiles in another order (rounding-level differences). */
 typedef struct {
     int32_t gmax;
     int32_t warps;
@@ -91,6 +97,7 @@ typedef struct {
     int32_t learned;
     int32_t quadrupole;
     int32_t classes;
+    int32_t split;
 } tc_config;
 
 /* Create a context on the current CUDA device.  `cuda_stream` is a

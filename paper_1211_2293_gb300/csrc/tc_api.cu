@@ -471,6 +471,7 @@ int prepare_forces(tc_ctx* c)
     wc.learned = c->cfg.learned && c->have_mlp;
     wc.quadw = c->cfg.quadrupole;
     wc.classes = c->cfg.gmax > 32 ? c->cfg.classes : 0;
+    wc.split = (c->cfg.split && !wc.learned && !wc.quadw) ? 1 : 0;
     int64_t st = c->cfg.stack;
     if (c->cap_m < st) st = c->cap_m < 32 ? 32 : c->cap_m;  // a stack of M entries cannot overflow
     st = (st + 3) & ~(int64_t)3;                            // keeps every warp's tiles 16-byte aligned
@@ -667,6 +668,7 @@ int tc_create(tc_ctx** out, void* stream)
     c->cfg.learned = 0;
     c->cfg.quadrupole = 0;
     c->cfg.classes = 1;
+    c->cfg.split = 1;
     *out = c;
     return TC_OK;
 }
@@ -709,6 +711,7 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
     if (cfg->quadrupole && (!cfg->precise || !cfg->quad))
         return fail(c, TC_EINVAL, "quadrupole = 1 needs precise = 1 and quad = 1");
     if (cfg->classes < 0 || cfg->classes > 1) return fail(c, TC_EINVAL, "classes must be 0 or 1 (got %d)", cfg->classes);
+    if (cfg->split < 0 || cfg->split > 1) return fail(c, TC_EINVAL, "split must be 0 or 1 (got %d)", cfg->split);
     bool rebuild = c->built && (cfg->gmax != c->cfg.gmax || (cfg->quad != 0) != (c->cfg.quad != 0));
     c->cfg = *cfg;
     c->cfg.precise = cfg->precise ? 1 : 0;
@@ -1293,6 +1296,7 @@ int tc_mlp_pairs(tc_ctx* c, float theta, float eps, float band, float prob, uint
     tc_config keep = c->cfg;
     c->cfg.learned = 0;
     c->cfg.quadrupole = 0;
+    c->cfg.split = 0;  // list export and pair emission live in k_walk
     c->walk_ready = false;
     r = prepare_forces(c);
     c->cfg = keep;
@@ -1398,6 +1402,7 @@ int tc_get_group_list(tc_ctx* c, int64_t group, float theta, int32_t* cells, int
     tc_config keep = c->cfg;
     c->cfg.learned = 0;
     c->cfg.quadrupole = 0;
+    c->cfg.split = 0;  // list export and pair emission live in k_walk
     c->walk_ready = false;
     r = prepare_forces(c);
     c->cfg = keep;

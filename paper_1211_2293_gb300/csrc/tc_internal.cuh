@@ -215,6 +215,7 @@ struct WalkConfig {
     int learned;      // 1: learned far-field correction (precise mode, no potential)
     int quadw;        // 1: accepted cells add their quadrupole term (precise mode)
     int classes;      // 1: one launch per group size class, largest first; 0: one launch
+    int split;        // 1: monopole walks on producer/consumer warp pairs (k_walk_ws)
 };
 // host-side preparation of the walk kernel's launch (attributes, occupancy);
 // call before a stream capture

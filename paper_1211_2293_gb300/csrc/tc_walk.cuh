@@ -798,6 +798,14 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
     }
 }
 
+}  // namespace
+}  // namespace tc
+
+#include "tc_walk_ws.cuh"
+
+namespace tc {
+namespace {
+
 template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED, bool QUADW>
 cudaError_t prepare_t(const WalkConfig& c, int num_sms, int* grid, size_t* smem_out)
 {
@@ -843,10 +851,15 @@ cudaError_t dispatch_modes(const WalkConfig& c, Args... args)
     return F<B, TT, false, false, false, false>::run(args...);
 }
 
+// split = 1 runs the monopole walks (precise or plain, with or without the
+// potential) on k_walk_ws, producer and consumer warps apart
 template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED, bool QUADW>
 struct PrepareF {
     static cudaError_t run(const WalkConfig* c, int num_sms, int* grid, size_t* smem)
     {
+        if constexpr (!LEARNED && !QUADW) {
+            if (c->split) return prepare_ws_t<B, TILE, PRECISE, POT>(*c, num_sms, grid, smem);
+        }
         return prepare_t<B, TILE, PRECISE, POT, LEARNED, QUADW>(*c, num_sms, grid, smem);
     }
 };
@@ -854,6 +867,9 @@ template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED, bool QUADW>
 struct LaunchF {
     static cudaError_t run(const WalkArgs* a, const WalkConfig* c, int grid, size_t smem, cudaStream_t s)
     {
+        if constexpr (!LEARNED && !QUADW) {
+            if (c->split) return launch_ws_t<B, TILE, PRECISE, POT>(*a, *c, grid, smem, s);
+        }
         return launch_t<B, TILE, PRECISE, POT, LEARNED, QUADW>(*a, *c, grid, smem, s);
     }
 };

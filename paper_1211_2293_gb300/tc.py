@@ -52,7 +52,7 @@ class tc_config(ctypes.Structure):
                 ("want_pot", ctypes.c_int32), ("verify", ctypes.c_int32), ("stack", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("quad", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("learned", ctypes.c_int32), ("quadrupole", ctypes.c_int32),
-                ("classes", ctypes.c_int32)]
+                ("classes", ctypes.c_int32), ("split", ctypes.c_int32)]
 
 
 _lib = None

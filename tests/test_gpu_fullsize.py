@@ -91,7 +91,7 @@ def test_learned_workload_full_size_sampled(tc):
 
     n = 1 << 22
     p, _, m = inputs.plummer(n, seed=101)
-    ctx = tc.Context(precise=1, quad=1, want_pot=0, verify=1)
+    ctx = tc.Context(precise=1, quad=1, want_pot=0, verify=1, split=0)
     ctx.build(_dev(p), _dev(m), 16)
     X, T, _, _, _ = ctx.mlp_pairs(0.9, 1e-3, 0.5, 0.01, 3, 200000)
     mean, sd = X.mean(0), X.std(0)

@@ -150,7 +150,9 @@ def test_loss_and_gradient_match_oracle(tc):
 
 def _built(tc, n, seed, leaf=16, gmax=64):
     p, _, m = inputs.plummer(n, seed)
-    ctx = tc.Context(gmax=gmax, precise=1, quad=1, want_pot=0, verify=1)
+    # split = 0: the plain walk the learned one is compared with runs on the
+    # same kernel, so the two sums agree bit for bit
+    ctx = tc.Context(gmax=gmax, precise=1, quad=1, want_pot=0, verify=1, split=0)
     ctx.build(p, m, leaf)
     return ctx, p, m
 

@@ -532,3 +532,56 @@ def test_step_builds_a_deeper_tree_than_the_last_synchronised_one(tc):
     t = oracle.Tree(pos, m, 8, 64)
     assert t.level.max() >= 15
     _compare_tree(ctx, t, 64)
+
+
+@pytest.mark.parametrize("kind,n,leaf,gmax,theta,eps,precise,pot,tile,warps", [
+    ("plummer", 20000, 8, 64, 0.6, 0.01, 1, 1, 128, 4),
+    ("uniform", 50000, 16, 64, 0.5, 1e-3, 1, 0, 128, 4),
+    ("plummer", 20000, 8, 128, 0.9, 0.01, 0, 1, 256, 2),
+    ("plummer", 7000, 8, 32, 0.7, 0.01, 1, 0, 64, 1),
+    ("random", 3000, 1, 17, 0.6, 0.05, 1, 1, 128, 3),
+])
+def test_split_walk_matches_one_warp_walk_and_oracle(tc, kind, n, leaf, gmax, theta, eps, precise, pot, tile, warps):
+    """The producer/consumer walk (split = 1) builds the same lists as the
+    one-warp walk (split = 0) -- lengths and set hashes of every group
+    bit-exact -- and its forces meet the oracle bar; the two sums differ only
+    in the order the tiles are added (within 2e-5 relative of each other)."""
+    p, _, m = _bodies(kind, n, 11)
+    out = {}
+    for split in (0, 1):
+        ctx = _ctx(tc, gmax=gmax, precise=precise, want_pot=pot, tile=tile, warps=warps, split=split)
+        ctx.build(_dev(p), _dev(m), leaf)
+        ctx.forces(theta, eps)
+        if pot:
+            acc, pt = ctx.get_acc(with_pot=True)
+        else:
+            acc, pt = ctx.get_acc(), None
+        out[split] = (acc.copy(), None if pt is None else pt.copy(), ctx.lists())
+    L0, L1 = out[0][2], out[1][2]
+    for k in ("ncell", "nbody", "hash"):
+        assert np.array_equal(L0[k], L1[k]), k
+    assert L0["interactions"] == L1["interactions"]
+    a0, a1 = out[0][0].astype(np.float64), out[1][0].astype(np.float64)
+    assert np.all(np.linalg.norm(a1 - a0, axis=1) <= 2e-5 * np.linalg.norm(a0, axis=1) + 1e-30)
+    t = oracle.Tree(p, m, leaf, gmax)
+    w = t.walk(theta, eps)
+    ok = np.zeros(n, bool)
+    for g in np.where(w["flag"] == 0)[0]:
+        ok[t.perm[t.gfirst[g]:t.gfirst[g] + t.gcount[g]]] = True
+    _check_forces(out[1][0], out[1][1], w, t, ok, tol=2e-5 if precise else 1e-4)
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_walk_stack_overflow_reported_both_walks(tc, split):
+    """A stack too small for theta = 0 stops the affected groups of either
+    walk with TC_EDEVICE; the context stays usable."""
+    p, _, m = _bodies("plummer", 20000, 3)
+    ctx = _ctx(tc, stack=64, split=split)
+    ctx.build(_dev(p), _dev(m), 4)
+    ctx.forces(0.0, 0.01)
+    with pytest.raises(tc.TcError) as e:
+        ctx.sync()
+    assert e.value.code == tc.TC_EDEVICE
+    ctx.set_config(stack=4096)
+    ctx.forces(0.5, 0.01)
+    ctx.sync()
