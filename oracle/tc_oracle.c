@@ -1146,8 +1146,11 @@ double or_mlp_grad_bf16(const double *p, const double *X, const double *Xr, cons
  * the cell's centre of mass and of the group's centre relative to its
  * reference cube (side sref); s/r those of r and of one reciprocal square
  * root (2 ulps); log2(count) a fast logarithm (2^-21 absolute); the moment
- * ratios two roundings of the inputs and one approximate division. */
-static void feature_radius(const double *f, double s, double sref, double r, double *fr)
+ * ratios two roundings of the inputs and one approximate division, plus the
+ * error of second moments accumulated in FP32 (a few roundings per body of
+ * a leaf of at most leaf_max bodies and per child above it, each at most
+ * half an FP32 ulp of a term no larger than M s^2). */
+static void feature_radius(const double *f, double s, double sref, double r, int leaf_max, double *fr)
 {
     const double u = RM_U32, off = 4.0 * (2.0 * u * (fabs(f[0]) + fabs(f[1]) + fabs(f[2])) + u + 4.0 * u * sref / s);
     for (int a = 0; a < 3; a++)
@@ -1156,8 +1159,10 @@ static void feature_radius(const double *f, double s, double sref, double r, dou
     fr[4] = 4.0 * u * f[4];
     fr[5] = 4.0 * (4.0 * u * (1.0 + f[5]));
     fr[6] = 4.0 * (4.0 * u * f[6]);
+    /* the moment ratios also carry the FP32 second moments' error:
+     * (leaf_max + 96) 2^-26 in units of M s^2, taken twice */
     for (int k = 7; k < 13; k++)
-        fr[k] = 4.0 * (4.0 * u * fabs(f[k]));
+        fr[k] = 4.0 * (4.0 * u * fabs(f[k])) + (double)(leaf_max + 96) * u / 4.0;
 }
 
 /* Learned correction of the group walk.  For each group: the accepted cells
@@ -1222,7 +1227,7 @@ static int64_t learned_walk(const or_tree *t, double theta, double eps, double G
                     double r2 = 0.0;
                     for (int a = 0; a < 3; a++)
                         r2 += (t->com[3 * v + a] - xg[a]) * (t->com[3 * v + a] - xg[a]);
-                    feature_radius(f, s, sref, sqrt(r2), fr);
+                    feature_radius(f, s, sref, sqrt(r2), t->leaf_max, fr);
                     for (int i = 0; i < 13; i++) {
                         double xn = (f[i] - maps[i]) * maps[13 + i];
                         xr[i] = fabs(maps[13 + i]) * fr[i] + 2.0 * RM_U32 * (fabs(maps[i] * maps[13 + i]) + fabs(xn));

@@ -308,7 +308,6 @@ int ensure_nodes(tc_ctx* c, int64_t M)
     TC_GROW(c, c->nt.quad, 6 * cap);
     TC_GROW(c, c->nt.mass64, cap);
     TC_GROW(c, c->nt.com64, 3 * cap);
-    TC_GROW(c, c->nt.quad64, 6 * cap);
     // the level sort reuses the body sort's value ping-pong buffer and status words
     if (cap > c->cap_n) TC_GROW(c, c->sb.vals_alt, cap);
     if (radix_tiles(cap) > (int64_t)kSortMaxPasses * radix_tiles(c->cap_n))
@@ -684,7 +683,7 @@ void tc_destroy(tc_ctx* c)
                     c->sb.blocksum, c->w, c->delta, c->top, c->nstart, c->prepos, c->gflag, c->gscan, c->gref_at,
                     c->gfirst, c->gref, c->ncell, c->nbody, c->hash, c->totals, c->idx_dev, c->dir_out,
                     c->pre_level, c->pre_first, c->iota, c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c,
-                    c->nt.d, c->nt.quad, c->nt.mass64, c->nt.com64, c->nt.quad64, c->info, c->mlp_params,
+                    c->nt.d, c->nt.quad, c->nt.mass64, c->nt.com64, c->info, c->mlp_params,
                     c->mlp_maps, c->mlp_dev, c->mlp_m, c->mlp_v, c->mlp_grad, c->mlp_loss, c->mlp_evals, c->mlp_x,
                     c->mlp_t, c->mlp_idx, c->mlp_raw, c->mlp_sums, c->mlp_wscale, c->mlp_bad,
                     c->pair_b, c->pair_v, c->pair_n};
@@ -924,7 +923,12 @@ int tc_get_nodes(tc_ctx* c, int32_t* level, uint64_t* prefix, int32_t* first, in
     }
     if (mass) TC_CUDA(c, cudaMemcpy(mass, c->nt.mass64, M * sizeof(double), cudaMemcpyDefault));
     if (com) TC_CUDA(c, cudaMemcpy(com, c->nt.com64, 3 * M * sizeof(double), cudaMemcpyDefault));
-    if (quad) TC_CUDA(c, cudaMemcpy(quad, c->nt.quad64, 6 * M * sizeof(double), cudaMemcpyDefault));
+    if (quad) {
+        std::vector<float> qf((size_t)6 * M);
+        TC_CUDA(c, cudaMemcpy(qf.data(), c->nt.quad, 6 * M * sizeof(float), cudaMemcpyDeviceToHost));
+        std::vector<double> qd(qf.begin(), qf.end());
+        TC_CUDA(c, cudaMemcpy(quad, qd.data(), 6 * M * sizeof(double), cudaMemcpyDefault));
+    }
     return TC_OK;
 }
 

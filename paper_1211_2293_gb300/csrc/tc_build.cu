@@ -450,19 +450,25 @@ __device__ __forceinline__ void cube_centre(const SysParams& P, int4 c, double* 
 }
 
 template <bool QUAD>
-__device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const double* Q,
-                           const double* C)
+__device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const float* Q, const double* C)
 {
     nt.mass64[v] = M;
     for (int a = 0; a < 3; a++) nt.com64[3 * v + a] = com[a];
     nt.a[v] = make_float4((float)(com[0] - C[0]), (float)(com[1] - C[1]), (float)(com[2] - C[2]), (float)M);
     nt.d[v] = make_float4((float)com[0], (float)com[1], (float)com[2], (float)M);
     if (QUAD) {
-        for (int a = 0; a < 6; a++) nt.quad64[6 * v + a] = Q[a];
-        for (int a = 0; a < 6; a++) nt.quad[6 * v + a] = (float)Q[a];
+        for (int a = 0; a < 6; a++) nt.quad[6 * v + a] = Q[a];
     }
 }
 
+// Mass and centre of mass in FP64; second moments in FP32.  The second
+// moments only feed the learned correction's BF16 features and the
+// quadrupole terms, small corrections to the monopole, so FP32 serves them
+// (their error stays a few hundred FP32 ulps of M s^2); the FP64 pipe, a
+// small fraction of the FP32 rate on GB300, is left to the mass and the
+// centre of mass.  Per leaf: Q about the cube centre C from the bodies'
+// offsets x - C (formed in FP64, rounded once), then moved to the centre of
+// mass by the parallel-axis rule Q_com = Q_C - M (com - C)(com - C)^T.
 template <bool QUAD>
 __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams* __restrict__ sysp,
                                const Info* info, NodeTables nt)
@@ -476,39 +482,49 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
         double C[3];
         cube_centre(sysp[c.w], c, C);
         // m and sum m x in absolute coordinates (the product of two floats is
-        // exact in FP64, so each term is one fused multiply-add): GB300 runs
-        // FP64 at a small fraction of its FP32 rate and this kernel is bound
-        // by it
+        // exact in FP64, so each term is one fused multiply-add); Q about C
+        // in FP32 alongside
         double m = 0.0, S[3] = {0, 0, 0};
+        float QC[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int j = b.x; j < b.x + b.y; j++) {
             const float4 q = body[j];
             const double w = (double)q.w;
+            const double x = (double)q.x, y = (double)q.y, z = (double)q.z;
             m += w;
-            S[0] = fma(w, (double)q.x, S[0]);
-            S[1] = fma(w, (double)q.y, S[1]);
-            S[2] = fma(w, (double)q.z, S[2]);
+            S[0] = fma(w, x, S[0]);
+            S[1] = fma(w, y, S[1]);
+            S[2] = fma(w, z, S[2]);
+            if (QUAD) {
+                const float dx = (float)(x - C[0]), dy = (float)(y - C[1]), dz = (float)(z - C[2]);
+                const float wx = q.w * dx, wy = q.w * dy, wz = q.w * dz;
+                QC[0] = fmaf(wx, dx, QC[0]);
+                QC[1] = fmaf(wx, dy, QC[1]);
+                QC[2] = fmaf(wx, dz, QC[2]);
+                QC[3] = fmaf(wy, dy, QC[3]);
+                QC[4] = fmaf(wy, dz, QC[4]);
+                QC[5] = fmaf(wz, dz, QC[5]);
+            }
         }
         const double inv = 1.0 / m;
         const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
-        double Q[6] = {0, 0, 0, 0, 0, 0};
-        for (int j = b.x; QUAD && j < b.x + b.y; j++) {
-            const float4 q = body[j];
-            const double dx = (double)q.x - com[0];
-            const double dy = (double)q.y - com[1];
-            const double dz = (double)q.z - com[2];
-            const double mj = (double)q.w;
-            Q[0] += mj * dx * dx;
-            Q[1] += mj * dx * dy;
-            Q[2] += mj * dx * dz;
-            Q[3] += mj * dy * dy;
-            Q[4] += mj * dy * dz;
-            Q[5] += mj * dz * dz;
+        float Q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (QUAD) {
+            const float ex = (float)(com[0] - C[0]), ey = (float)(com[1] - C[1]), ez = (float)(com[2] - C[2]);
+            const float mf = (float)m;
+            Q[0] = fmaf(-mf * ex, ex, QC[0]);
+            Q[1] = fmaf(-mf * ex, ey, QC[1]);
+            Q[2] = fmaf(-mf * ex, ez, QC[2]);
+            Q[3] = fmaf(-mf * ey, ey, QC[3]);
+            Q[4] = fmaf(-mf * ey, ez, QC[4]);
+            Q[5] = fmaf(-mf * ez, ez, QC[5]);
         }
         store_node<QUAD>(nt, v, m, com, Q, C);
     }
 }
 
-// one internal cell v from its children (a leaf returns at once)
+// one internal cell v from its children (a leaf returns at once): mass and
+// centre of mass in FP64, second moments in FP32 by the parallel-axis rule
+// from the children's, Q_v = sum_c Q_c + m_c d_c d_c^T, d_c = com_c - com_v
 template <bool QUAD>
 __device__ __forceinline__ void level_node(int64_t v, const SysParams* __restrict__ sysp, NodeTables& nt)
 {
@@ -524,18 +540,19 @@ __device__ __forceinline__ void level_node(int64_t v, const SysParams* __restric
     }
     const double inv = 1.0 / m;
     const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
-    double Q[6] = {0, 0, 0, 0, 0, 0};
+    float Q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = 0; QUAD && k < nch; k++) {
         const int64_t c = pb.z + k;
-        const double mc = nt.mass64[c];
-        double d[3];
-        for (int a = 0; a < 3; a++) d[a] = nt.com64[3 * c + a] - com[a];
-        Q[0] += nt.quad64[6 * c + 0] + mc * d[0] * d[0];
-        Q[1] += nt.quad64[6 * c + 1] + mc * d[0] * d[1];
-        Q[2] += nt.quad64[6 * c + 2] + mc * d[0] * d[2];
-        Q[3] += nt.quad64[6 * c + 3] + mc * d[1] * d[1];
-        Q[4] += nt.quad64[6 * c + 4] + mc * d[1] * d[2];
-        Q[5] += nt.quad64[6 * c + 5] + mc * d[2] * d[2];
+        const float mc = (float)nt.mass64[c];
+        float d[3];
+        for (int a = 0; a < 3; a++) d[a] = (float)(nt.com64[3 * c + a] - com[a]);
+        const float* qc = nt.quad + 6 * c;
+        Q[0] += fmaf(mc * d[0], d[0], qc[0]);
+        Q[1] += fmaf(mc * d[0], d[1], qc[1]);
+        Q[2] += fmaf(mc * d[0], d[2], qc[2]);
+        Q[3] += fmaf(mc * d[1], d[1], qc[3]);
+        Q[4] += fmaf(mc * d[1], d[2], qc[4]);
+        Q[5] += fmaf(mc * d[2], d[2], qc[5]);
     }
     const int4 cc = nt.c[v];
     double C[3];

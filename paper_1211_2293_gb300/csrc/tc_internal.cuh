@@ -67,10 +67,9 @@ struct NodeTables {
     int4* b;
     int4* c;
     float4* d;
-    float* quad;     // 6 per node, second moments about the COM (float)
+    float* quad;     // 6 per node, second moments about the COM (FP32)
     double* mass64;  // FP64 bottom-up reduction results
     double* com64;   // 3 per node
-    double* quad64;  // 6 per node
 };
 
 // scratch of the radix sort / scans

@@ -412,7 +412,7 @@ __global__ void k_pair_labels(const int32_t* __restrict__ pb, const int32_t* __r
     f[4] = (float)(eps / s);
     f[5] = (float)log2((double)b.y);
     f[6] = (float)(M / nt.mass64[cc.w]);  // the system's root is node cc.w
-    for (int q = 0; q < 6; q++) f[7 + q] = (float)(nt.quad64[6 * v + q] / (M * s * s));
+    for (int q = 0; q < 6; q++) f[7 + q] = (float)((double)nt.quad[6 * v + q] / (M * s * s));
     const double e2 = (double)eps * (double)eps;
     double ae[3] = {0, 0, 0};
     for (int j = b.x; j < b.x + b.y; j++) {

