@@ -80,9 +80,13 @@ typedef struct tc_ctx tc_ctx;
  *   split     1: the monopole walks (learned = 0, quadrupole = 0) run with
  *             the tree walk and the force loop on different warps: a
  *             producer warp walks and fills a ring of list tiles in shared
- *             memory, a consumer warp sums them (the default); 0: every
- *             warp walks and sums its own groups.  Same lists; the sums
- *             take the tiles in another order (rounding-level differences). */
+ *             memory, a consumer warp sums them (the default); the learned
+ *             walk stays on one warp per group with the network evaluated
+ *             inside the walk.  2: the learned walk also splits, its band
+ *             cells recorded by the producers and the network run on all of
+ *             them after the walk.  0: every warp walks and sums its own
+ *             groups.  Same lists; the sums take the tiles in another order
+ *             (rounding-level differences). */
 typedef struct {
     int32_t gmax;
     int32_t warps;

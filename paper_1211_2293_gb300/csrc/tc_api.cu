@@ -111,6 +111,14 @@ struct tc_ctx {
     double* mlp_sums = nullptr;   // FP64 sums of the training data (kMlpSums)
     float* mlp_wscale = nullptr;  // n / sum F^2 (factor weights)
     int32_t* mlp_bad = nullptr;   // a given loss weight was negative or not finite
+    // learned correction evaluated after the split walk: the band-cell
+    // record, its length, each group's box centre and correction
+    int2* band = nullptr;
+    unsigned long long* band_n = nullptr;
+    float* gcentre = nullptr;
+    float* gcorr = nullptr;
+    int64_t band_cap = 0;
+    int64_t band_gcap = 0;
     int64_t mlp_cap = 0;
     bool have_mlp = false;
     float mlp_band = 0.5f;
@@ -306,6 +314,7 @@ int ensure_nodes(tc_ctx* c, int64_t M)
     TC_GROW(c, c->nt.c, cap);
     TC_GROW(c, c->nt.d, cap);
     TC_GROW(c, c->nt.quad, 6 * cap);
+    TC_GROW(c, c->nt.feat, 2 * cap);
     TC_GROW(c, c->nt.mass64, cap);
     TC_GROW(c, c->nt.com64, 3 * cap);
     // the level sort reuses the body sort's value ping-pong buffer and status words
@@ -334,6 +343,10 @@ int check_device(tc_ctx* c)
                         "drift -- call tc_ctx_build or tc_set_state to resize");
         if (e & kErrStack) return fail(c, TC_EDEVICE, "walk stack overflow (raise tc_config.stack)");
         if (e & kErrWorkLoop) return fail(c, TC_EDEVICE, "a bounded device wait gave up");
+        if (e & kErrBand)
+            return fail(c, TC_EDEVICE,
+                        "the learned walk recorded more band cells than its buffer holds (12 per body); its "
+                        "correction is incomplete -- narrow the band or use split = 0");
         return fail(c, TC_EDEVICE, "device error word 0x%x", e);
     }
     return TC_OK;
@@ -470,11 +483,39 @@ int prepare_forces(tc_ctx* c)
     wc.learned = c->cfg.learned && c->have_mlp;
     wc.quadw = c->cfg.quadrupole;
     wc.classes = c->cfg.gmax > 32 ? c->cfg.classes : 0;
-    wc.split = (c->cfg.split && !wc.learned && !wc.quadw) ? 1 : 0;
+    // split 1: producer/consumer walks for the monopole walks, the learned
+    // walk keeps the network inside the one-warp walk; 2: the learned walk
+    // too, the network then evaluated after the walk
+    wc.split = (!wc.quadw && (c->cfg.split == 2 || (c->cfg.split == 1 && !wc.learned))) ? 1 : 0;
     int64_t st = c->cfg.stack;
     if (c->cap_m < st) st = c->cap_m < 32 ? 32 : c->cap_m;  // a stack of M entries cannot overflow
     st = (st + 3) & ~(int64_t)3;                            // keeps every warp's tiles 16-byte aligned
     wc.stack = (int)st;
+    if (wc.learned && wc.split) {
+        // the band-cell record: 12 cells per body (the learned workloads
+        // record 2 to 7) plus a chunk per producer warp of every size-class
+        // launch (each keeps a partly filled chunk); a walk that records
+        // more stops with an error (TC_EDEVICE) instead of writing past it.
+        // TC_BAND_CAP (entries) overrides the size, to exercise that error.
+        int64_t want = 12 * c->cap_n + (int64_t)3 * c->num_sms * 2 * 4 * kBandChunk + 65536;
+        if (const char* env = getenv("TC_BAND_CAP")) {
+            const long long v = atoll(env);
+            if (v > 0) want = v;
+        }
+        if (want != c->band_cap) {
+            if (want > c->band_cap) TC_GROW(c, c->band, want);
+            c->band_cap = want;
+            c->walk_ready = false;
+            drop_graph(c);
+        }
+        if (!c->band_n) TC_GROW(c, c->band_n, 1);
+        if (c->cap_n + 1 > c->band_gcap) {
+            TC_GROW(c, c->gcentre, 3 * (c->cap_n + 1));
+            TC_GROW(c, c->gcorr, 3 * (c->cap_n + 1));
+            c->band_gcap = c->cap_n + 1;
+            drop_graph(c);
+        }
+    }
     if (c->walk_ready && memcmp(&wc, &c->walk_cfg, sizeof(wc)) == 0) return TC_OK;
     cudaError_t e = prepare_walk(wc, c->num_sms, &c->walk_grid, &c->walk_smem);
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk kernel set-up: %s", cudaGetErrorString(e));
@@ -514,13 +555,25 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
     a.G = G;
     a.inv_eps = 1.0f / eps;
     a.eps = eps;
+    const bool deferred = c->walk_cfg.learned && c->walk_cfg.split;
     if (c->walk_cfg.learned) {
         a.mlp = c->mlp_dev;
         a.band2 = c->mlp_band * c->mlp_band;
         a.mlp_evals = c->mlp_evals;
     }
+    if (deferred) {
+        a.band = c->band;
+        a.band_n = c->band_n;
+        a.band_cap = c->band_cap;
+        a.gcentre = c->gcentre;
+    }
     cudaEvent_t t0 = phase_begin(c, s, 1);
     cudaError_t e = cudaSuccess;
+    if (c->walk_cfg.learned) launch_node_features(c->info, c->cap_m, c->sysp, c->nt, eps, c->mlp_dev, s);
+    if (deferred) {
+        cudaMemsetAsync(c->band_n, 0, sizeof(unsigned long long), s);
+        cudaMemsetAsync(c->gcorr, 0, 3 * c->band_gcap * sizeof(float), s);
+    }
     if (c->walk_ncls == 0) {
         e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, s);
     } else {
@@ -531,6 +584,11 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
             e = launch_walk(a, c->walk_cls[k], c->walk_cls_grid[k], c->walk_cls_smem[k], s,
                             k == c->walk_ncls - 1);
         }
+    }
+    if (e == cudaSuccess && deferred) {
+        launch_band_eval(a, c->mlp_dev, c->gcorr, c->mlp_evals, s);
+        launch_band_apply(c->info, c->band_gcap - 1, c->gfirst, c->perm, c->gcorr, c->acc, s);
+        e = cudaGetLastError();
     }
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk launch: %s", cudaGetErrorString(e));
     phase_end(c, 1, t0, s);
@@ -683,9 +741,10 @@ void tc_destroy(tc_ctx* c)
                     c->sb.blocksum, c->w, c->delta, c->top, c->nstart, c->prepos, c->gflag, c->gscan, c->gref_at,
                     c->gfirst, c->gref, c->ncell, c->nbody, c->hash, c->totals, c->idx_dev, c->dir_out,
                     c->pre_level, c->pre_first, c->iota, c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c,
-                    c->nt.d, c->nt.quad, c->nt.mass64, c->nt.com64, c->info, c->mlp_params,
+                    c->nt.d, c->nt.quad, c->nt.feat, c->nt.mass64, c->nt.com64, c->info, c->mlp_params,
                     c->mlp_maps, c->mlp_dev, c->mlp_m, c->mlp_v, c->mlp_grad, c->mlp_loss, c->mlp_evals, c->mlp_x,
-                    c->mlp_t, c->mlp_idx, c->mlp_raw, c->mlp_sums, c->mlp_wscale, c->mlp_bad,
+                    c->mlp_t, c->mlp_idx, c->mlp_raw, c->mlp_sums, c->mlp_wscale, c->mlp_bad, c->band, c->band_n,
+                    c->gcentre, c->gcorr,
                     c->pair_b, c->pair_v, c->pair_n};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -710,7 +769,7 @@ int tc_set_config(tc_ctx* c, const tc_config* cfg)
     if (cfg->quadrupole && (!cfg->precise || !cfg->quad))
         return fail(c, TC_EINVAL, "quadrupole = 1 needs precise = 1 and quad = 1");
     if (cfg->classes < 0 || cfg->classes > 1) return fail(c, TC_EINVAL, "classes must be 0 or 1 (got %d)", cfg->classes);
-    if (cfg->split < 0 || cfg->split > 1) return fail(c, TC_EINVAL, "split must be 0 or 1 (got %d)", cfg->split);
+    if (cfg->split < 0 || cfg->split > 2) return fail(c, TC_EINVAL, "split must be 0, 1 or 2 (got %d)", cfg->split);
     bool rebuild = c->built && (cfg->gmax != c->cfg.gmax || (cfg->quad != 0) != (c->cfg.quad != 0));
     c->cfg = *cfg;
     c->cfg.precise = cfg->precise ? 1 : 0;

@@ -23,6 +23,7 @@ enum : int32_t {
     kErrStack = 2,        // walk stack overflow
     kErrCapacity = 4,     // the node table outgrew its allocation
     kErrWorkLoop = 8,     // a bounded wait gave up
+    kErrBand = 16,        // the learned walk's band-cell record outgrew its buffer
 };
 
 // Per-system root cube (written by the bounding-box kernels).
@@ -68,6 +69,8 @@ struct NodeTables {
     int4* c;
     float4* d;
     float* quad;     // 6 per node, second moments about the COM (FP32)
+    uint4* feat;     // 2 per node: the learned correction's cell-only features (eps/s, log2 count,
+                     // M / M_sys, 6 moment ratios), normalised, as BF16 pairs (words 2..7 of a row)
     double* mass64;  // FP64 bottom-up reduction results
     double* com64;   // 3 per node
 };
@@ -201,7 +204,17 @@ struct WalkArgs {
     const int32_t* glist;
     const int32_t* glist_n;
     int work_slot;  // this launch's work-queue counter, info->work[work_slot]
+    // learned correction evaluated after the walk (split walk): the band
+    // cells of every group recorded as (node, group) pairs in chunks of
+    // kBandChunk entries taken from *band_n (unused tails hold node -1),
+    // at most band_cap entries; gcentre[3 g ..] the group's box centre in its
+    // reference cube's frame
+    int2* band;
+    unsigned long long* band_n;
+    int64_t band_cap;
+    float* gcentre;
 };
+constexpr int kBandChunk = 256;
 struct WalkConfig {
     int gmax;         // 32, 64 or 128
     int warps;        // warps per block
@@ -239,6 +252,18 @@ cudaError_t launch_mlp_train(const float* X, const float* T, const float* W, con
 void launch_mlp_pack(const float* params, const float* maps, void* model, cudaStream_t s);
 void launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, int t, cudaStream_t s);
 void launch_mlp_infer(const float* X, int64_t n, const void* model, float* Y, cudaStream_t s);
+// the learned correction evaluated after a split walk: every recorded band
+// cell's row at its group's centre through the network on the tensor cores,
+// F label summed per group into gcorr (G x 3, zeroed by the caller); then
+// each body's acceleration gains its group's sum
+void launch_band_eval(const WalkArgs& a, const void* model, float* gcorr, unsigned long long* evals,
+                      cudaStream_t s);
+void launch_band_apply(const Info* info, int64_t cap_g, const int32_t* gfirst, const uint32_t* perm,
+                       const float* gcorr, float* acc, cudaStream_t s);
+// the learned correction's per-cell features of every node for softening
+// eps under the model (run before a learned walk)
+void launch_node_features(const Info* info, int64_t cap_m, const SysParams* sysp, NodeTables nt, float eps,
+                          const void* model, cudaStream_t s);
 void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const float4* body, const uint32_t* sys_of,
                         const SysParams* sysp, NodeTables nt, float eps, float G, float* feat, float* lab,
                         float* fac, cudaStream_t s);

@@ -432,6 +432,45 @@ __global__ void k_pair_labels(const int32_t* __restrict__ pb, const int32_t* __r
     if (fac) fac[k] = (float)F;
 }
 
+// ---------------------------------------------------------------- node features
+// The nine features of a cell that do not depend on the point it is
+// evaluated at -- eps/s, log2(count), M / M_sys and the six moment ratios
+// Q_ab / (M s^2) -- normalised with the model's maps and packed as BF16
+// pairs in the order of a network row (words 2..7: features 4..12, then the
+// zero padding), once per node and force phase, so a walk that evaluates a
+// cell forms only d/s and s/r itself.
+__global__ void k_node_features(const Info* info, const SysParams* __restrict__ sysp, NodeTables nt, float eps,
+                                const MlpDev* __restrict__ model)
+{
+    if ((*(volatile const int32_t*)&info->err & kErrCapacity) != 0) return;
+    const int64_t M = info->M;
+    const MlpFrag& m = model->frag;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (int64_t)gridDim.x * blockDim.x) {
+        const int4 nb = nt.b[v];
+        const float4 na = nt.a[v];
+        const int4 cc = nt.c[v];
+        const SysParams& P = sysp[cc.w];
+        const int level = nb.w & 255;
+        const float inv_s = scalbnf(1.0f / P.Lf, level);  // exact: sides are powers of two
+        const float Mc = na.w;
+        const float iq = __fdividef(inv_s * inv_s, Mc);
+        const float* qd = nt.quad + 6 * v;
+        float f[kMlpInPad];
+#pragma unroll
+        for (int k = 0; k < kMlpInPad; k++) f[k] = 0.f;
+        f[4] = eps * inv_s;
+        f[5] = __log2f((float)nb.y);
+        f[6] = Mc * (1.0f / P.msys);
+#pragma unroll
+        for (int k = 0; k < 6; k++) f[7 + k] = qd[k] * iq;
+#pragma unroll
+        for (int k = 4; k < kMlpIn; k++) f[k] = fmaf(f[k], m.xscale[k], m.xoff[k]);
+        nt.feat[2 * v] = make_uint4(pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]), pack_bf16(f[8], f[9]),
+                                    pack_bf16(f[10], f[11]));
+        nt.feat[2 * v + 1] = make_uint4(pack_bf16(f[12], 0.f), 0u, 0u, 0u);
+    }
+}
+
 // ---------------------------------------------------------------- training data
 // Sums over the n training pairs, in FP64: column c of blockIdx.y takes
 //   c < 13: x_c,  13 <= c < 26: x_(c-13)^2,  26 <= c < 29: t_(c-26)^2,
@@ -658,6 +697,15 @@ void launch_mlp_shuffle(int64_t n, uint64_t key, int32_t* idx, cudaStream_t s)
     int64_t g = (n + 255) / 256;
     if (g > 16 * sm_count()) g = 16 * sm_count();
     k_mlp_shuffle<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(n, h, key, idx);
+    count_launches(1);
+}
+
+void launch_node_features(const Info* info, int64_t cap_m, const SysParams* sysp, NodeTables nt, float eps,
+                          const void* model, cudaStream_t s)
+{
+    int64_t g = (cap_m + 255) / 256;
+    if (g > 16 * sm_count()) g = 16 * sm_count();
+    k_node_features<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(info, sysp, nt, eps, (const MlpDev*)model);
     count_launches(1);
 }
 

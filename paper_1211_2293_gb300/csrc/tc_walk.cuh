@@ -359,50 +359,56 @@ constexpr int kPend = 64;   // < 32 left over + 32 added by a step
 constexpr int kRowW = 9;    // words per row
 __host__ __device__ constexpr size_t mlp_frag_bytes() { return (sizeof(MlpFrag) + 15) & ~(size_t)15; }
 
+// The network row of cell v seen from the group's box centre xgc (in the
+// frame of the group's reference cube rc): d/s and s/r formed here, the
+// other nine features from the node's record (k_node_features), and the
+// factor G M s^2 / r^4 that turns a label into an acceleration
+__device__ __forceinline__ void band_row(const MlpFrag& m, int v, const NodeTables& nt, int4 rc, float uf, float Lf,
+                                         float inv_L, const float (&xgc)[3], float G, uint32_t (&w)[8], float& fac)
+{
+    const int4 nb = __ldg(&nt.b[v]);
+    const float4 na = __ldg(&nt.a[v]);
+    const int4 cc = __ldg(&nt.c[v]);
+    const uint4 c0 = __ldg(&nt.feat[2 * v]);
+    const uint4 c1 = __ldg(&nt.feat[2 * v + 1]);
+    // centre of mass in the group's reference frame, as in the walk
+    const float dx = fmaf((float)(cc.x - rc.x), uf, na.x) - xgc[0];
+    const float dy = fmaf((float)(cc.y - rc.y), uf, na.y) - xgc[1];
+    const float dz = fmaf((float)(cc.z - rc.z), uf, na.z) - xgc[2];
+    const float sz = scalbnf(Lf, -(nb.w & 255));
+    const float inv_s = scalbnf(inv_L, nb.w & 255);  // exact: sides are powers of two
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float ri = rsqrtf(r2);
+    const float Mc = na.w;
+    const float f0 = fmaf(dx * inv_s, m.xscale[0], m.xoff[0]);
+    const float f1 = fmaf(dy * inv_s, m.xscale[1], m.xoff[1]);
+    const float f2 = fmaf(dz * inv_s, m.xscale[2], m.xoff[2]);
+    const float f3 = fmaf(ri * sz, m.xscale[3], m.xoff[3]);
+    w[0] = pack_bf16(f0, f1);
+    w[1] = pack_bf16(f2, f3);
+    w[2] = c0.x;
+    w[3] = c0.y;
+    w[4] = c0.z;
+    w[5] = c0.w;
+    w[6] = c1.x;
+    w[7] = c1.y;
+    const float ri2 = ri * ri;
+    fac = G * Mc * (sz * sz) * (ri2 * ri2);  // G M s^2 / r^4
+}
+
 // rows of the n <= 32 cells pend[0, n) evaluated, label x yscale x factor
-// added to corr (lanes of q = 0 hold x, y; of q = 1 hold z)
+// added to corr (lanes of q = 0 hold x, y; of q = 1 hold z).  Lane j builds
+// the row of cell j.
 __device__ __noinline__ void learned_rows(const MlpFrag& m, const uint32_t* pend, int n, uint32_t* rows,
                                           const NodeTables& nt, int4 rc, float uf, float Lf, float inv_L,
                                           const float (&xgc)[3], float eps, float inv_msys, float G,
                                           float (&corr)[3], int lane)
 {
+    (void)eps;
+    (void)inv_msys;
     uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     float fac = 0.f;
-    if (lane < n) {
-        const int v = (int)pend[lane];
-        const int4 nb = __ldg(&nt.b[v]);
-        const float4 na = __ldg(&nt.a[v]);
-        const int4 cc = __ldg(&nt.c[v]);
-        // centre of mass in the group's reference frame, as in the walk
-        const float dx = fmaf((float)(cc.x - rc.x), uf, na.x) - xgc[0];
-        const float dy = fmaf((float)(cc.y - rc.y), uf, na.y) - xgc[1];
-        const float dz = fmaf((float)(cc.z - rc.z), uf, na.z) - xgc[2];
-        const float sz = scalbnf(Lf, -(nb.w & 255));
-        const float inv_s = scalbnf(inv_L, nb.w & 255);  // exact: sides are powers of two
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float ri = rsqrtf(r2);
-        const float Mc = na.w;
-        const float* qd = nt.quad + 6 * (int64_t)v;
-        const float iq = __fdividef(inv_s * inv_s, Mc);
-        float f[kMlpInPad];
-        f[0] = dx * inv_s;
-        f[1] = dy * inv_s;
-        f[2] = dz * inv_s;
-        f[3] = ri * sz;
-        f[4] = eps * inv_s;
-        f[5] = __log2f((float)nb.y);
-        f[6] = Mc * inv_msys;
-#pragma unroll
-        for (int k = 0; k < 6; k++) f[7 + k] = __ldg(qd + k) * iq;
-#pragma unroll
-        for (int k = 0; k < kMlpIn; k++) f[k] = fmaf(f[k], m.xscale[k], m.xoff[k]);
-#pragma unroll
-        for (int k = kMlpIn; k < kMlpInPad; k++) f[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; k++) w[k] = pack_bf16(f[2 * k], f[2 * k + 1]);
-        const float ri2 = ri * ri;
-        fac = G * Mc * (sz * sz) * (ri2 * ri2);  // G M s^2 / r^4
-    }
+    if (lane < n) band_row(m, (int)pend[lane], nt, rc, uf, Lf, inv_L, xgc, G, w, fac);
     uint32_t* r = rows + lane * kRowW;
 #pragma unroll
     for (int k = 0; k < 8; k++) r[k] = w[k];
@@ -852,13 +858,15 @@ cudaError_t dispatch_modes(const WalkConfig& c, Args... args)
 }
 
 // split = 1 runs the monopole walks (precise or plain, with or without the
-// potential) on k_walk_ws, producer and consumer warps apart
+// potential) on k_walk_ws, producer and consumer warps apart; the learned
+// walk there records its band cells for k_band_eval instead of evaluating
+// the network inside the walk
 template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED, bool QUADW>
 struct PrepareF {
     static cudaError_t run(const WalkConfig* c, int num_sms, int* grid, size_t* smem)
     {
-        if constexpr (!LEARNED && !QUADW) {
-            if (c->split) return prepare_ws_t<B, TILE, PRECISE, POT>(*c, num_sms, grid, smem);
+        if constexpr (!QUADW) {
+            if (c->split) return prepare_ws_t<B, TILE, PRECISE, POT, LEARNED>(*c, num_sms, grid, smem);
         }
         return prepare_t<B, TILE, PRECISE, POT, LEARNED, QUADW>(*c, num_sms, grid, smem);
     }
@@ -867,8 +875,8 @@ template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED, bool QUADW>
 struct LaunchF {
     static cudaError_t run(const WalkArgs* a, const WalkConfig* c, int grid, size_t smem, cudaStream_t s)
     {
-        if constexpr (!LEARNED && !QUADW) {
-            if (c->split) return launch_ws_t<B, TILE, PRECISE, POT>(*a, *c, grid, smem, s);
+        if constexpr (!QUADW) {
+            if (c->split) return launch_ws_t<B, TILE, PRECISE, POT, LEARNED>(*a, *c, grid, smem, s);
         }
         return launch_t<B, TILE, PRECISE, POT, LEARNED, QUADW>(*a, *c, grid, smem, s);
     }

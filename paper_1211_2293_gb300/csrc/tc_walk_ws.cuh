@@ -92,7 +92,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
     return __all_sync(0xffffffffu, ok);
 }
 
-template <int B, int TILE, bool PRECISE, bool POT>
+// LEARNED: the producer also records the group's band cells (accepted, two
+// bodies or more, s >= band d) for the network, which runs after the walk
+// (k_band_eval), and the group's box centre
+template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_ws(WalkArgs a, int stack_cap)
 {
     constexpr int kTile = TILE;
@@ -153,6 +156,41 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
             mbar_arrive(&full[k % kWsSlots]);
             k++;
         };
+        // band cells: this warp's chunk of the record (cbase < 0: none yet)
+        int64_t cbase = -1;
+        int cused = kBandChunk;
+        const int64_t band_lim = (a.band_cap / kBandChunk) * kBandChunk;
+        auto band_append = [&](bool band, int v, int g) {
+            const unsigned bm = __ballot_sync(0xffffffffu, band);
+            const int c = __popc(bm);
+            if (c == 0) return;
+            const int rank = __popc(bm & lt);
+            const int room = kBandChunk - cused;
+            int64_t nbase = -1;
+            if (c > room) {  // a new chunk for the cells that do not fit
+                long long x = -1;
+                if (lane == 0) {
+                    x = (long long)atomicAdd(a.band_n, (unsigned long long)kBandChunk);
+                    if (x + kBandChunk > band_lim) {
+                        atomicOr(&a.info->err, kErrBand);
+                        x = -1;
+                    }
+                }
+                nbase = __shfl_sync(0xffffffffu, x, 0);
+            }
+            if (band) {
+                int64_t pos = -1;
+                if (rank < room) pos = cbase + cused + rank;
+                else if (nbase >= 0) pos = nbase + (rank - room);
+                if (pos >= 0) a.band[pos] = make_int2(v, g);
+            }
+            if (c > room) {
+                cbase = nbase;
+                cused = nbase >= 0 ? c - room : kBandChunk;
+            } else {
+                cused += c;
+            }
+        };
         auto open_slot = [&](int flags, int g) {
             WsHdr* h = slot_hdr(k);
             if (lane == 0) {
@@ -169,6 +207,9 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
                     open_slot(kWsDone, 0);
                     hand_over(0, 0, 0);
                 }
+                // the unused tail of the chunk: no cell
+                if (LEARNED && cbase >= 0)
+                    for (int j = cused + lane; j < kBandChunk; j += 32) a.band[cbase + j] = make_int2(-1, 0);
                 break;
             }
             if (a.glist) g = __ldg(a.glist + g);
@@ -223,6 +264,12 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
                 flo[kk] = __shfl_sync(0xffffffffu, fb, kk);
                 fhi[kk] = __shfl_sync(0xffffffffu, fb, kk + 3);
             }
+            if (LEARNED && lane == 0) {
+                // the group's box centre, reference-relative (as k_walk forms it)
+#pragma unroll
+                for (int kk = 0; kk < 3; kk++)
+                    a.gcentre[3 * (int64_t)g + kk] = 0.5f * (fmaf(klof[kk], uf, flo[kk]) + fmaf(khif[kk], uf, fhi[kk]));
+            }
             if (!take()) {
                 alive = false;
                 break;
@@ -254,6 +301,7 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
                 int4 nb = make_int4(0, 0, 0, 0);
                 bool acc = false, oleaf = false, oint = false;
                 float4 src = make_float4(0.f, 0.f, 0.f, 0.f);
+                float band_e2 = 0.f;
                 if (v >= 0) {
                     nb = __ldg(&nt.b[v]);
                     const float4 na = __ldg(&nt.a[v]);
@@ -273,6 +321,7 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
                         }
                         const float sz = pow2_down(Lf, nb.w & 255, fast_side);
                         acc = (sz * sz) < a.theta2 * e2;
+                        band_e2 = e2;
                         if (acc) {
                             if (PRECISE) {
                                 src = make_float4(fmaf(D[0], uf, off[0]), fmaf(D[1], uf, off[1]),
@@ -305,6 +354,14 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
                 }
                 cn += __popc(am);
                 Lc += __popc(am);
+                if (LEARNED) {
+                    bool band = false;
+                    if (acc && nb.y >= 2) {
+                        const float sz = pow2_down(Lf, nb.w & 255, fast_side);
+                        band = sz * sz >= a.band2 * band_e2;
+                    }
+                    band_append(band, v, g);
+                }
                 // opened leaves -> the slot's body part, 32 bodies at a time
                 const unsigned lm = __ballot_sync(0xffffffffu, oleaf);
                 if (lm) {
@@ -454,12 +511,12 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
     }
 }
 
-template <int B, int TILE, bool PRECISE, bool POT>
+template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 cudaError_t prepare_ws_t(const WalkConfig& c, int num_sms, int* grid, size_t* smem_out)
 {
     const int pairs = c.warps < 1 ? 1 : (c.warps > kWsMaxPairs ? kWsMaxPairs : c.warps);
     const size_t smem = ws_pair_bytes(TILE, c.stack) * pairs;
-    auto kern = k_walk_ws<B, TILE, PRECISE, POT>;
+    auto kern = k_walk_ws<B, TILE, PRECISE, POT, LEARNED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -472,14 +529,15 @@ cudaError_t prepare_ws_t(const WalkConfig& c, int num_sms, int* grid, size_t* sm
     return cudaSuccess;
 }
 
-template <int B, int TILE, bool PRECISE, bool POT>
+template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 cudaError_t launch_ws_t(const WalkArgs& a, const WalkConfig& c, int grid, size_t smem, cudaStream_t s)
 {
-    // the split walk has no list export, training pairs, learned or
-    // quadrupole terms: those run on k_walk
-    if (a.list_cells || a.pair_body || a.mlp) return cudaErrorInvalidValue;
+    // the split walk has no list export, training pairs or quadrupole
+    // terms (those run on k_walk); its learned walk records band cells
+    if (a.list_cells || a.pair_body) return cudaErrorInvalidValue;
+    if (LEARNED && (!a.band || !a.band_n || !a.gcentre)) return cudaErrorInvalidValue;
     const int pairs = c.warps < 1 ? 1 : (c.warps > kWsMaxPairs ? kWsMaxPairs : c.warps);
-    k_walk_ws<B, TILE, PRECISE, POT><<<grid, pairs * 64, smem, s>>>(a, c.stack);
+    k_walk_ws<B, TILE, PRECISE, POT, LEARNED><<<grid, pairs * 64, smem, s>>>(a, c.stack);
     count_launches(1);
     return cudaGetLastError();
 }

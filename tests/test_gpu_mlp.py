@@ -148,17 +148,20 @@ def test_loss_and_gradient_match_oracle(tc):
               f"radius {np.linalg.norm(gr) / np.linalg.norm(go):.2e}")
 
 
-def _built(tc, n, seed, leaf=16, gmax=64):
+def _built(tc, n, seed, leaf=16, gmax=64, split=0):
     p, _, m = inputs.plummer(n, seed)
-    # split = 0: the plain walk the learned one is compared with runs on the
-    # same kernel, so the two sums agree bit for bit
-    ctx = tc.Context(gmax=gmax, precise=1, quad=1, want_pot=0, verify=1, split=0)
+    # the plain walk the learned one is compared with runs on the same kernel
+    # (split 0: one warp per group, the network inside the walk; 2: producer
+    # and consumer warps, the network after the walk), so the walk's own sums
+    # agree bit for bit
+    ctx = tc.Context(gmax=gmax, precise=1, quad=1, want_pot=0, verify=1, split=split)
     ctx.build(p, m, leaf)
     return ctx, p, m
 
 
-def test_zero_model_leaves_forces_bit_identical(tc):
-    ctx, p, m = _built(tc, 20000, 6)
+@pytest.mark.parametrize("split", [0, 2])
+def test_zero_model_leaves_forces_bit_identical(tc, split):
+    ctx, p, m = _built(tc, 20000, 6, split=split)
     ctx.forces(0.9, 1e-3)
     a0 = ctx.get_acc().copy()
     ctx.mlp_set(np.zeros(tc.MLP_NMODEL, np.float32), band=0.3)
@@ -205,8 +208,9 @@ def _compare_band_sum(ctx, p, m, theta, eps, G, band, params, maps, rel=None, le
     return d, c, bound
 
 
-def test_constant_model_matches_oracle_band_sum(tc):
-    ctx, p, m = _built(tc, 20000, 7)
+@pytest.mark.parametrize("split", [0, 2])
+def test_constant_model_matches_oracle_band_sum(tc, split):
+    ctx, p, m = _built(tc, 20000, 7, split=split)
     cvec = np.array([1.0, -0.5, 2.0], np.float32)
     params = np.zeros(NP, np.float32)
     params[-3:] = cvec
@@ -215,8 +219,9 @@ def test_constant_model_matches_oracle_band_sum(tc):
     _compare_band_sum(ctx, p, m, 0.9, 1e-3, 1.3, 0.5, params, maps, rel=1e-4)
 
 
-def test_random_model_matches_oracle_band_sum(tc):
-    ctx, p, m = _built(tc, 16384, 8)
+@pytest.mark.parametrize("split", [0, 2])
+def test_random_model_matches_oracle_band_sum(tc, split):
+    ctx, p, m = _built(tc, 16384, 8, split=split)
     # maps from real features of the same system
     X, T, _, _, _ = ctx.mlp_pairs(0.9, 1e-3, 0.4, 0.2, 11, 50000)
     assert len(X) > 1000
@@ -330,3 +335,25 @@ def test_learned_step_and_config_errors(tc):
         ctx.mlp_set(bad, 0.5)
     with pytest.raises(tc.TcError):
         ctx.mlp_set(np.zeros(tc.MLP_NMODEL, np.float32), -1.0)
+
+
+def test_deferred_band_record_overflow_is_reported(tc, monkeypatch):
+    """A learned split walk that records more band cells than its buffer
+    holds stops with TC_EDEVICE instead of writing past it (the buffer cut
+    to 4096 entries through TC_BAND_CAP); with the buffer restored the same
+    context runs the learned walk again."""
+    ctx, p, m = _built(tc, 20000, 40, split=2)
+    rng = np.random.default_rng(41)
+    params = (rng.standard_normal(tc.MLP_NPARAM) * 0.1).astype(np.float32)
+    model = np.concatenate([params, np.zeros(13), np.ones(13), np.full(3, 1e-3)]).astype(np.float32)
+    ctx.mlp_set(model, band=0.3)
+    ctx.set_config(learned=1)
+    monkeypatch.setenv("TC_BAND_CAP", "4096")
+    ctx.forces(0.9, 1e-3)
+    with pytest.raises(tc.TcError) as e:
+        ctx.sync()
+    assert e.value.code == tc.TC_EDEVICE and "band" in str(e.value)
+    monkeypatch.delenv("TC_BAND_CAP")
+    ctx.forces(0.9, 1e-3)
+    ctx.sync()
+    assert ctx.mlp_evals() > 4096
