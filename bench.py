@@ -64,7 +64,20 @@ N_TRAIN, N_EVAL, SEED_TRAIN, SEED_EVAL = 1 << 20, 1 << 22, 100, 101
 THETA_TRAIN, BAND_TRAIN, BANDS, GOAL = 0.7, 0.4, (0.5, 0.55, 0.6, 0.65), 1e-3
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "walk_uniform_1m.txt")
 PROFILE_TRAFFIC_PLUMMER = os.path.join(ROOT, "profiles", "walk_plummer_4m.txt")
-WALK_SRC = os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", "tc_walk.cuh")
+WALK_SRC = [os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", f) for f in ("tc_walk.cuh", "tc_walk_ws.cuh")]
+
+
+def walk_source_hash(paths=None):
+    """First 16 hex digits of the SHA-256 of the walk kernels' sources (the
+    one-warp and the split walk), in order: the key a committed ncu summary
+    records, so that its DRAM bytes are used only for the same kernels."""
+    paths = paths if paths is not None else WALK_SRC
+    if isinstance(paths, str):
+        paths = [paths]
+    h = hashlib.sha256()
+    for q in paths:
+        h.update(open(q, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def workload_config(n, theta):
@@ -164,7 +177,7 @@ def _traffic_from_profile(shape=None, path=None):
     it was captured or the summary's walk shape is not the one measured."""
     try:
         txt = open(path or PROFILE_TRAFFIC).read()
-        cur = hashlib.sha256(open(WALK_SRC, "rb").read()).hexdigest()[:16]
+        cur = walk_source_hash()
         kv = {}
         for line in txt.splitlines():
             if ":" in line:
