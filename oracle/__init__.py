@@ -103,6 +103,8 @@ def _load():
     lib.or_tree_learned.restype = I64
     lib.or_tree_learned_bf16.argtypes = [P, D, D, D, D, P, P, I64, I64, P, P, P]
     lib.or_tree_learned_bf16.restype = I64
+    lib.or_fmm.argtypes = [P, D, D, D, P, P]
+    lib.or_fmm.restype = None
     lib.or_bf16.argtypes = [D]
     lib.or_bf16.restype = D
     lib.or_mlp_forward_bf16.argtypes = [P, P, P, I64, P, P]
@@ -289,6 +291,15 @@ class Tree:
         ev = self._lib.or_tree_learned_bf16(self._h, float(theta), float(eps), float(G), float(band), _ptr(p),
                                             _ptr(m), int(g0), int(g1), _ptr(corr), _ptr(crad), _ptr(flag))
         return corr, crad, flag, int(ev)
+
+    def fmm(self, theta, eps, G=1.0):
+        """Fast multipole accelerations (n x 3, original order) and the
+        traversal's statistics: dict(m2l, p2p, ties, m2l_hash, p2p_hash)."""
+        acc = np.zeros((self.n, 3))
+        st = np.zeros(5, np.int64)
+        self._lib.or_fmm(self._h, float(theta), float(eps), float(G), _ptr(acc), _ptr(st))
+        return acc, dict(m2l=int(st[0]), p2p=int(st[1]), ties=int(st[2]), m2l_hash=int(st[3]) & (2**64 - 1),
+                         p2p_hash=int(st[4]) & (2**64 - 1))
 
     def mlp_factor(self, node: int, x, G: float = 1.0):
         """G M s^2 / r^4 of cell node at point x (the acceleration unit of a label)."""

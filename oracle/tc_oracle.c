@@ -1332,3 +1332,181 @@ void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cell
     free(w.cells);
     free(w.leaves);
 }
+
+/* ------------------------------------------------------------------ */
+/* Fast multipole method (Sec. 5 names it as the treecode's O(N)       */
+/* successor; the paper gives no formulation, so this is a reading,    */
+/* stated in full).  Same tree as the treecode.                        */
+/*   Expansion centres: every cell's centre of mass c_X.               */
+/*   Multipoles: the monopole, mass M_X at c_X.                        */
+/*   Local expansions, first order about c_B: the field at x near B is  */
+/*     a(x) = L0_B + L1_B (x - c_B), L0 a vector, L1 the field's 3x3    */
+/*     Jacobian.                                                        */
+/*   Acceptance of a pair of disjoint cells: s_A + s_B < theta |c_A - c_B|*/
+/*     (s the cube side); a pair of cells lying within 1e-6 relative of */
+/*     the bound is counted (ties).                                    */
+/*   Dual traversal from (root, root):                                  */
+/*     (X, X): a leaf -> P2P within it; otherwise every (child, child).  */
+/*     (A, B), A != B: accepted -> M2L(A -> B); both leaves -> P2P(A ->  */
+/*     B); otherwise split B if it is internal and (A is a leaf or      */
+/*     s_B >= s_A), else split A.                                       */
+/*   M2L(A -> B): d = c_A - c_B, rho^2 = |d|^2 + eps^2,                 */
+/*     L0_B += G M_A d / rho^3, L1_B += G M_A (3 d d^T / rho^5 - I/rho^3).*/
+/*   L2L, parents before children: L0_c += L0_p + L1_p (c_c - c_p),     */
+/*     L1_c += L1_p.                                                     */
+/*   L2P: a_i += L0_leaf + L1_leaf (x_i - c_leaf) for a leaf's bodies.   */
+/*   P2P(A -> B): a_i += G m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^1.5,*/
+/*     i in B, j in A, j != i.                                           */
+/* Every ordered pair of bodies is reached through exactly one M2L or    */
+/* P2P: the traversal splits pairs down to disjoint cells or leaves.     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const or_tree *t;
+    double theta, eps2, G;
+    double *L0, *L1; /* M x 3, M x 9 */
+    double *acc;     /* sorted order, n x 3 */
+    int64_t n_m2l, n_p2p, ties;
+    uint64_t h_m2l, h_p2p; /* order-independent hashes of the pair sets */
+} fmm_t;
+
+static uint64_t fmm_mix(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static void fmm_p2p(fmm_t *f, int64_t A, int64_t B)
+{
+    const or_tree *t = f->t;
+    f->n_p2p++;
+    f->h_p2p += fmm_mix(((uint64_t)A << 32) ^ (uint64_t)B);
+    double phi = 0.0, mag = 0.0;
+    for (int64_t i = t->first[B]; i < t->first[B] + t->count[B]; i++)
+        for (int64_t j = t->first[A]; j < t->first[A] + t->count[A]; j++) {
+            if (j == i)
+                continue;
+            add_force(&t->xs[3 * i], &t->xs[3 * j], t->ms[j], f->eps2, f->G, &f->acc[3 * i], &phi, &mag);
+        }
+}
+
+static void fmm_m2l(fmm_t *f, int64_t A, int64_t B)
+{
+    const or_tree *t = f->t;
+    f->n_m2l++;
+    f->h_m2l += fmm_mix(((uint64_t)A << 32) ^ (uint64_t)B);
+    double d[3];
+    for (int a = 0; a < 3; a++)
+        d[a] = t->com[3 * A + a] - t->com[3 * B + a];
+    double rho2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + f->eps2;
+    double ri = 1.0 / sqrt(rho2);
+    double ri3 = ri * ri * ri, ri5 = ri3 * ri * ri;
+    double gm = f->G * t->mass[A];
+    for (int a = 0; a < 3; a++) {
+        f->L0[3 * B + a] += gm * d[a] * ri3;
+        for (int b = 0; b < 3; b++)
+            f->L1[9 * B + 3 * a + b] += gm * (3.0 * d[a] * d[b] * ri5 - (a == b ? ri3 : 0.0));
+    }
+}
+
+static void fmm_pair(fmm_t *f, int64_t A, int64_t B)
+{
+    const or_tree *t = f->t;
+    const int leafA = t->nchild[A] == 0, leafB = t->nchild[B] == 0;
+    if (A == B) {
+        if (leafA) {
+            fmm_p2p(f, A, A);
+            return;
+        }
+        for (int64_t ca = t->child_first[A]; ca < t->child_first[A] + t->nchild[A]; ca++)
+            for (int64_t cb = t->child_first[A]; cb < t->child_first[A] + t->nchild[A]; cb++)
+                fmm_pair(f, ca, cb);
+        return;
+    }
+    const double sA = cube_side(t, A), sB = cube_side(t, B);
+    double d2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double e = t->com[3 * A + a] - t->com[3 * B + a];
+        d2 += e * e;
+    }
+    const double lhs = sA + sB, rhs = f->theta * sqrt(d2);
+    if (fabs(lhs - rhs) <= 1e-6 * rhs)
+        f->ties++;
+    if (lhs < rhs) {
+        fmm_m2l(f, A, B);
+        return;
+    }
+    if (leafA && leafB) {
+        fmm_p2p(f, A, B);
+        return;
+    }
+    if (!leafB && (leafA || sB >= sA)) {
+        for (int64_t cb = t->child_first[B]; cb < t->child_first[B] + t->nchild[B]; cb++)
+            fmm_pair(f, A, cb);
+    } else {
+        for (int64_t ca = t->child_first[A]; ca < t->child_first[A] + t->nchild[A]; ca++)
+            fmm_pair(f, ca, B);
+    }
+}
+
+/* Accelerations (n x 3, ORIGINAL order) of the FMM at opening parameter
+ * theta; stats[0..4] (nullable) = M2L pairs, P2P pairs, ties, and the two
+ * pair-set hashes (as int64 bit patterns). */
+void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc_out, int64_t *stats)
+{
+    fmm_t f;
+    memset(&f, 0, sizeof(f));
+    f.t = t;
+    f.theta = theta;
+    f.eps2 = eps * eps;
+    f.G = G;
+    f.L0 = (double *)calloc((size_t)t->M * 3, sizeof(double));
+    f.L1 = (double *)calloc((size_t)t->M * 9, sizeof(double));
+    f.acc = (double *)calloc((size_t)t->n * 3, sizeof(double));
+    fmm_pair(&f, 0, 0);
+    /* L2L: breadth-first order puts every parent before its children */
+    for (int64_t v = 1; v < t->M; v++) {
+        int64_t p = t->parent[v];
+        double dc[3];
+        for (int a = 0; a < 3; a++)
+            dc[a] = t->com[3 * v + a] - t->com[3 * p + a];
+        for (int a = 0; a < 3; a++) {
+            double s = f.L0[3 * p + a];
+            for (int b = 0; b < 3; b++)
+                s += f.L1[9 * p + 3 * a + b] * dc[b];
+            f.L0[3 * v + a] += s;
+            for (int b = 0; b < 3; b++)
+                f.L1[9 * v + 3 * a + b] += f.L1[9 * p + 3 * a + b];
+        }
+    }
+    /* L2P */
+    for (int64_t v = 0; v < t->M; v++) {
+        if (t->nchild[v] != 0)
+            continue;
+        for (int64_t i = t->first[v]; i < t->first[v] + t->count[v]; i++) {
+            double dx[3];
+            for (int a = 0; a < 3; a++)
+                dx[a] = t->xs[3 * i + a] - t->com[3 * v + a];
+            for (int a = 0; a < 3; a++) {
+                double s = f.L0[3 * v + a];
+                for (int b = 0; b < 3; b++)
+                    s += f.L1[9 * v + 3 * a + b] * dx[b];
+                f.acc[3 * i + a] += s;
+            }
+        }
+    }
+    for (int64_t i = 0; i < t->n; i++)
+        for (int a = 0; a < 3; a++)
+            acc_out[3 * (int64_t)t->perm[i] + a] = f.acc[3 * i + a];
+    if (stats) {
+        stats[0] = f.n_m2l;
+        stats[1] = f.n_p2p;
+        stats[2] = f.ties;
+        stats[3] = (int64_t)f.h_m2l;
+        stats[4] = (int64_t)f.h_p2p;
+    }
+    free(f.L0);
+    free(f.L1);
+    free(f.acc);
+}

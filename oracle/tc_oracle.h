@@ -174,6 +174,14 @@ int64_t or_tree_learned_bf16(const or_tree *t, double theta, double eps, double 
                              const double *params, const double *maps, int64_t g_begin, int64_t g_end,
                              double *corr, double *crad, int32_t *flag);
 
+/* Fast multipole method on the same tree (a reading of Sec. 5, stated in
+ * tc_oracle.c): monopoles at the cells' centres of mass, first-order local
+ * expansions, pair acceptance s_A + s_B < theta |c_A - c_B|, dual traversal,
+ * M2L / L2L / L2P and P2P between leaves.  acc (n x 3, original order);
+ * stats (nullable, 5): M2L pairs, P2P pairs, ties, M2L and P2P pair-set
+ * hashes. */
+void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc, int64_t *stats);
+
 #ifdef __cplusplus
 }
 #endif

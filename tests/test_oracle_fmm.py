@@ -1,0 +1,91 @@
+"""Pins of the oracle's fast multipole method (a reading of the paper's
+Sec. 5, stated in oracle/tc_oracle.c): monopoles at cell centres of mass,
+first-order local expansions (field and its Jacobian), pair acceptance
+s_A + s_B < theta |c_A - c_B|, dual traversal, M2L / L2L / L2P and P2P.
+
+* theta = 0 accepts no pair: every interaction is P2P, the direct sum.
+* Two bodies far apart: a monopole of one body is exact, and the local
+  expansion evaluated at its own centre (the other body) is exact.
+* Softening much larger than the system makes every field linear in the
+  positions, where monopoles and first-order local expansions are exact: the
+  FMM then equals the direct sum at any theta, which fails if the traversal
+  drops or repeats a pair of bodies.
+* A far source acting on a small cluster: the local expansion's error falls
+  like (cluster size)^2 / distance^4, a second-order remainder of a field
+  falling like distance^-2 (the Jacobian is right); without it, or with a
+  wrong one, the error would fall like distance^-3.
+"""
+import numpy as np
+
+import oracle
+from paper_1211_2293_gb300 import inputs
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def test_theta_zero_is_the_direct_sum():
+    p, _, m = inputs.plummer(2000, 3)
+    t = oracle.Tree(p, m, 8, 64)
+    a, st = t.fmm(0.0, 0.01)
+    ad, _ = oracle.direct(p, m, 0.01, want_pot=False)
+    assert st["m2l"] == 0 and st["p2p"] > 0
+    assert _rel(a, ad).max() <= 1e-13
+
+
+def test_two_bodies_exact():
+    p = np.array([[-0.9, -0.8, -0.85], [0.9, 0.8, 0.95]], np.float32)
+    m = np.array([0.3, 1.7], np.float32)
+    t = oracle.Tree(p, m, 1, 1)
+    a, st = t.fmm(1.5, 1e-3)
+    ad, _ = oracle.direct(p, m, 1e-3, want_pot=False)
+    # the two leaves meet each other through M2L; each meets itself in a
+    # (bodiless) P2P
+    assert st["m2l"] == 2 and st["p2p"] == 2
+    assert _rel(a, ad).max() <= 1e-14
+
+
+def test_every_pair_once_linear_field_limit():
+    p, _, m = inputs.plummer(1500, 4)
+    t = oracle.Tree(p, m, 4, 64)
+    eps = 1e4  # >> system size (cutoff 10): fields linear to (size / eps)^2 = 1e-6
+    ad, _ = oracle.direct(p, m, eps, want_pot=False)
+    for theta in (0.3, 0.7, 1.2):
+        a, st = t.fmm(theta, eps)
+        assert st["m2l"] > 0
+        assert _rel(a, ad).max() <= 1e-5, theta
+
+
+def test_local_expansion_second_order():
+    rng = np.random.default_rng(5)
+    cluster = (rng.standard_normal((8, 3)) * 0.02).astype(np.float32)
+    direction = np.array([1.0, 0.3, 0.2]) / np.linalg.norm([1.0, 0.3, 0.2])
+    errs = []
+    for D in (2.0, 4.0, 8.0):
+        src = (direction * D).astype(np.float32)[None, :]
+        p = np.concatenate([cluster, src]).astype(np.float32)
+        m = np.concatenate([np.full(8, 1e-3), [1.0]]).astype(np.float32)
+        t = oracle.Tree(p, m, 8, 1)
+        a, st = t.fmm(1.5, 1e-4)
+        assert st["m2l"] > 0
+        # the source's field on the cluster: the cluster's own pairs are P2P
+        # (exact), so the FMM error is the local expansion's
+        ad, _ = oracle.direct(p, m, 1e-4, want_pot=False)
+        errs.append(np.abs(a[:8] - ad[:8]).max())
+    # the far field is G M / D^2; the first term a first-order expansion
+    # drops is (cluster size)^2 G M / D^4, so each doubling of D divides the
+    # error by 16 -- by 8 if the Jacobian were missing or wrong
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 12.0 < r1 < 20.0 and 12.0 < r2 < 20.0, errs
+
+
+def test_error_shrinks_with_theta():
+    p, _, m = inputs.plummer(4000, 6)
+    t = oracle.Tree(p, m, 8, 64)
+    ad, _ = oracle.direct(p, m, 0.01, want_pot=False)
+    rms = []
+    for theta in (0.6, 0.3, 0.2):
+        a, _ = t.fmm(theta, 0.01)
+        rms.append(float(np.sqrt(np.mean(_rel(a, ad) ** 2))))
+    assert rms[1] < rms[0] / 3 and rms[2] < rms[1] and rms[2] < 1e-3, rms
