@@ -449,6 +449,20 @@ __device__ __forceinline__ void cube_centre(const SysParams& P, int4 c, double* 
     C[2] = P.c0[2] + (double)c.z * u;
 }
 
+// The exact FP64 value of a float, formed on the integer pipe from the
+// IEEE-754 fields (sign, exponent rebased from 127 to 1023, the 23 mantissa
+// bits moved to the top of the 52): GB300's FP64 pipe, which the leaf
+// moments saturate, then only adds and multiplies.  Zero, subnormal and
+// non-finite values take the conversion instruction.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint64_t d = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 template <bool QUAD>
 __device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const float* Q, const double* C)
 {
@@ -488,8 +502,8 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
         float QC[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int j = b.x; j < b.x + b.y; j++) {
             const float4 q = body[j];
-            const double w = (double)q.w;
-            const double x = (double)q.x, y = (double)q.y, z = (double)q.z;
+            const double w = widen(q.w);
+            const double x = widen(q.x), y = widen(q.y), z = widen(q.z);
             m += w;
             S[0] = fma(w, x, S[0]);
             S[1] = fma(w, y, S[1]);
