@@ -1339,22 +1339,31 @@ void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cell
 /* stated in full).  Same tree as the treecode.                        */
 /*   Expansion centres: every cell's centre of mass c_X.               */
 /*   Multipoles: the monopole, mass M_X at c_X.                        */
-/*   Local expansions, first order about c_B: the field at x near B is  */
-/*     a(x) = L0_B + L1_B (x - c_B), L0 a vector, L1 the field's 3x3    */
-/*     Jacobian.                                                        */
+/*   Local expansions, second order about c_B: the field at x near B is */
+/*     a(x) = L0 + L1 dx + (1/2) L2 dx dx, dx = x - c_B; L0 a vector,   */
+/*     L1 the field's Jacobian (symmetric), L2 its second derivatives   */
+/*     (a symmetric 3-index tensor).                                    */
 /*   Acceptance of a pair of disjoint cells: s_A + s_B < theta |c_A - c_B|*/
-/*     (s the cube side); a pair of cells lying within 1e-6 relative of */
-/*     the bound is counted (ties).                                    */
+/*     (s the cube side); a pair lying within 1e-6 relative of the bound */
+/*     is counted (ties).                                               */
 /*   Dual traversal from (root, root):                                  */
 /*     (X, X): a leaf -> P2P within it; otherwise every (child, child).  */
 /*     (A, B), A != B: accepted -> M2L(A -> B); both leaves -> P2P(A ->  */
 /*     B); otherwise split B if it is internal and (A is a leaf or      */
-/*     s_B >= s_A), else split A.                                       */
-/*   M2L(A -> B): d = c_A - c_B, rho^2 = |d|^2 + eps^2,                 */
-/*     L0_B += G M_A d / rho^3, L1_B += G M_A (3 d d^T / rho^5 - I/rho^3).*/
-/*   L2L, parents before children: L0_c += L0_p + L1_p (c_c - c_p),     */
-/*     L1_c += L1_p.                                                     */
-/*   L2P: a_i += L0_leaf + L1_leaf (x_i - c_leaf) for a leaf's bodies.   */
+/*     s_B >= s_A), else split A.  Per target cell this is a walk: a    */
+/*     target B refines each candidate source larger than itself until  */
+/*     it is accepted, a leaf or no larger, and hands the unresolved     */
+/*     ones, with its own children, to its children as their candidates.*/
+/*   M2L(A -> B): d = c_A - c_B, rho^2 = |d|^2 + eps^2, the softened     */
+/*     field G M_A d / rho^3 and its derivatives at c_B:                 */
+/*     L0_i += G M d_i / rho^3                                           */
+/*     L1_ij += G M (3 d_i d_j / rho^5 - delta_ij / rho^3)               */
+/*     L2_ijk += G M (15 d_i d_j d_k / rho^7                             */
+/*               - 3 (delta_ij d_k + delta_ik d_j + delta_jk d_i) / rho^5)*/
+/*   L2L, parents before children, t = c_c - c_p:                        */
+/*     L0_c += L0_p + L1_p t + (1/2) L2_p t t, L1_c += L1_p + L2_p t,    */
+/*     L2_c += L2_p.                                                     */
+/*   L2P: a_i += L0 + L1 dx + (1/2) L2 dx dx over a leaf's bodies.        */
 /*   P2P(A -> B): a_i += G m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^1.5,*/
 /*     i in B, j in A, j != i.                                           */
 /* Every ordered pair of bodies is reached through exactly one M2L or    */
@@ -1363,7 +1372,7 @@ void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cell
 typedef struct {
     const or_tree *t;
     double theta, eps2, G;
-    double *L0, *L1; /* M x 3, M x 9 */
+    double *L0, *L1, *L2; /* M x 3, M x 9, M x 27 (full index ranges) */
     double *acc;     /* sorted order, n x 3 */
     int64_t n_m2l, n_p2p, ties;
     uint64_t h_m2l, h_p2p; /* order-independent hashes of the pair sets */
@@ -1403,10 +1412,16 @@ static void fmm_m2l(fmm_t *f, int64_t A, int64_t B)
     double ri = 1.0 / sqrt(rho2);
     double ri3 = ri * ri * ri, ri5 = ri3 * ri * ri;
     double gm = f->G * t->mass[A];
+    double ri7 = ri5 * ri * ri;
     for (int a = 0; a < 3; a++) {
         f->L0[3 * B + a] += gm * d[a] * ri3;
-        for (int b = 0; b < 3; b++)
+        for (int b = 0; b < 3; b++) {
             f->L1[9 * B + 3 * a + b] += gm * (3.0 * d[a] * d[b] * ri5 - (a == b ? ri3 : 0.0));
+            for (int c = 0; c < 3; c++)
+                f->L2[27 * B + 9 * a + 3 * b + c] +=
+                    gm * (15.0 * d[a] * d[b] * d[c] * ri7 -
+                          3.0 * ((a == b ? d[c] : 0.0) + (a == c ? d[b] : 0.0) + (b == c ? d[a] : 0.0)) * ri5);
+        }
     }
 }
 
@@ -1463,6 +1478,7 @@ void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc_ou
     f.G = G;
     f.L0 = (double *)calloc((size_t)t->M * 3, sizeof(double));
     f.L1 = (double *)calloc((size_t)t->M * 9, sizeof(double));
+    f.L2 = (double *)calloc((size_t)t->M * 27, sizeof(double));
     f.acc = (double *)calloc((size_t)t->n * 3, sizeof(double));
     fmm_pair(&f, 0, 0);
     /* L2L: breadth-first order puts every parent before its children */
@@ -1473,11 +1489,20 @@ void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc_ou
             dc[a] = t->com[3 * v + a] - t->com[3 * p + a];
         for (int a = 0; a < 3; a++) {
             double s = f.L0[3 * p + a];
-            for (int b = 0; b < 3; b++)
+            for (int b = 0; b < 3; b++) {
                 s += f.L1[9 * p + 3 * a + b] * dc[b];
+                for (int c = 0; c < 3; c++)
+                    s += 0.5 * f.L2[27 * p + 9 * a + 3 * b + c] * dc[b] * dc[c];
+            }
             f.L0[3 * v + a] += s;
-            for (int b = 0; b < 3; b++)
-                f.L1[9 * v + 3 * a + b] += f.L1[9 * p + 3 * a + b];
+            for (int b = 0; b < 3; b++) {
+                double u = f.L1[9 * p + 3 * a + b];
+                for (int c = 0; c < 3; c++)
+                    u += f.L2[27 * p + 9 * a + 3 * b + c] * dc[c];
+                f.L1[9 * v + 3 * a + b] += u;
+                for (int c = 0; c < 3; c++)
+                    f.L2[27 * v + 9 * a + 3 * b + c] += f.L2[27 * p + 9 * a + 3 * b + c];
+            }
         }
     }
     /* L2P */
@@ -1490,8 +1515,11 @@ void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc_ou
                 dx[a] = t->xs[3 * i + a] - t->com[3 * v + a];
             for (int a = 0; a < 3; a++) {
                 double s = f.L0[3 * v + a];
-                for (int b = 0; b < 3; b++)
+                for (int b = 0; b < 3; b++) {
                     s += f.L1[9 * v + 3 * a + b] * dx[b];
+                    for (int c = 0; c < 3; c++)
+                        s += 0.5 * f.L2[27 * v + 9 * a + 3 * b + c] * dx[b] * dx[c];
+                }
                 f.acc[3 * i + a] += s;
             }
         }
@@ -1508,5 +1536,6 @@ void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc_ou
     }
     free(f.L0);
     free(f.L1);
+    free(f.L2);
     free(f.acc);
 }

@@ -1,19 +1,21 @@
 """Pins of the oracle's fast multipole method (a reading of the paper's
 Sec. 5, stated in oracle/tc_oracle.c): monopoles at cell centres of mass,
-first-order local expansions (field and its Jacobian), pair acceptance
+second-order local expansions (the field, its Jacobian and its second
+derivatives), pair acceptance
 s_A + s_B < theta |c_A - c_B|, dual traversal, M2L / L2L / L2P and P2P.
 
 * theta = 0 accepts no pair: every interaction is P2P, the direct sum.
 * Two bodies far apart: a monopole of one body is exact, and the local
   expansion evaluated at its own centre (the other body) is exact.
 * Softening much larger than the system makes every field linear in the
-  positions, where monopoles and first-order local expansions are exact: the
-  FMM then equals the direct sum at any theta, which fails if the traversal
+  positions, where monopoles and the local expansions are exact: the FMM
+  then equals the direct sum at any theta, which fails if the traversal
   drops or repeats a pair of bodies.
 * A far source acting on a small cluster: the local expansion's error falls
-  like (cluster size)^2 / distance^4, a second-order remainder of a field
-  falling like distance^-2 (the Jacobian is right); without it, or with a
-  wrong one, the error would fall like distance^-3.
+  like (cluster size)^3 / distance^5, a third-order remainder of a field
+  falling like distance^-2 (Jacobian and second derivatives right); a
+  missing or wrong second-derivative term would leave distance^-4, a
+  missing or wrong Jacobian distance^-3.
 """
 import numpy as np
 
@@ -73,11 +75,12 @@ def test_local_expansion_second_order():
         # (exact), so the FMM error is the local expansion's
         ad, _ = oracle.direct(p, m, 1e-4, want_pot=False)
         errs.append(np.abs(a[:8] - ad[:8]).max())
-    # the far field is G M / D^2; the first term a first-order expansion
-    # drops is (cluster size)^2 G M / D^4, so each doubling of D divides the
-    # error by 16 -- by 8 if the Jacobian were missing or wrong
+    # the far field is G M / D^2; the first term a second-order expansion
+    # drops is (cluster size)^3 G M / D^5, so each doubling of D divides the
+    # error by 32 -- by 16 if the second derivatives were missing or wrong,
+    # by 8 without the Jacobian
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
-    assert 12.0 < r1 < 20.0 and 12.0 < r2 < 20.0, errs
+    assert 24.0 < r1 < 40.0 and 24.0 < r2 < 40.0, errs
 
 
 def test_error_shrinks_with_theta():
