@@ -105,6 +105,8 @@ def _load():
     lib.or_tree_learned_bf16.restype = I64
     lib.or_fmm.argtypes = [P, D, D, D, P, P]
     lib.or_fmm.restype = None
+    lib.or_fmm_nodes.argtypes = [P, D, D, D, P, P, P, P, P, P, P]
+    lib.or_fmm_nodes.restype = None
     lib.or_bf16.argtypes = [D]
     lib.or_bf16.restype = D
     lib.or_mlp_forward_bf16.argtypes = [P, P, P, I64, P, P]
@@ -292,14 +294,27 @@ class Tree:
                                             _ptr(m), int(g0), int(g1), _ptr(corr), _ptr(crad), _ptr(flag))
         return corr, crad, flag, int(ev)
 
-    def fmm(self, theta, eps, G=1.0):
+    def fmm(self, theta, eps, G=1.0, per_node=False):
         """Fast multipole accelerations (n x 3, original order) and the
-        traversal's statistics: dict(m2l, p2p, ties, m2l_hash, p2p_hash)."""
+        traversal's statistics: dict(m2l, p2p, ties, m2l_hash, p2p_hash);
+        with per_node, also per target cell (M each): nm2l, np2p, hm2l, hp2p
+        and flag (a tie in the cell's walk or an ancestor's)."""
         acc = np.zeros((self.n, 3))
         st = np.zeros(5, np.int64)
-        self._lib.or_fmm(self._h, float(theta), float(eps), float(G), _ptr(acc), _ptr(st))
-        return acc, dict(m2l=int(st[0]), p2p=int(st[1]), ties=int(st[2]), m2l_hash=int(st[3]) & (2**64 - 1),
-                         p2p_hash=int(st[4]) & (2**64 - 1))
+        if not per_node:
+            self._lib.or_fmm(self._h, float(theta), float(eps), float(G), _ptr(acc), _ptr(st))
+        else:
+            M = self.M
+            rec = dict(nm2l=np.zeros(M, np.int64), np2p=np.zeros(M, np.int64), hm2l=np.zeros(M, np.uint64),
+                       hp2p=np.zeros(M, np.uint64), flag=np.zeros(M, np.int32))
+            self._lib.or_fmm_nodes(self._h, float(theta), float(eps), float(G), _ptr(acc), _ptr(st),
+                                   _ptr(rec["nm2l"]), _ptr(rec["np2p"]), _ptr(rec["hm2l"]), _ptr(rec["hp2p"]),
+                                   _ptr(rec["flag"]))
+        out = dict(m2l=int(st[0]), p2p=int(st[1]), ties=int(st[2]), m2l_hash=int(st[3]) & (2**64 - 1),
+                   p2p_hash=int(st[4]) & (2**64 - 1))
+        if per_node:
+            out.update(rec)
+        return acc, out
 
     def mlp_factor(self, node: int, x, G: float = 1.0):
         """G M s^2 / r^4 of cell node at point x (the acceleration unit of a label)."""

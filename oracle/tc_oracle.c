@@ -1376,6 +1376,10 @@ typedef struct {
     double *acc;     /* sorted order, n x 3 */
     int64_t n_m2l, n_p2p, ties;
     uint64_t h_m2l, h_p2p; /* order-independent hashes of the pair sets */
+    /* per target cell (nullable) */
+    int64_t *nm2l, *np2p;
+    uint64_t *hm2l, *hp2p;
+    int32_t *flag;
 } fmm_t;
 
 static uint64_t fmm_mix(uint64_t z)
@@ -1389,8 +1393,13 @@ static uint64_t fmm_mix(uint64_t z)
 static void fmm_p2p(fmm_t *f, int64_t A, int64_t B)
 {
     const or_tree *t = f->t;
+    const uint64_t h = fmm_mix(((uint64_t)A << 32) ^ (uint64_t)B);
     f->n_p2p++;
-    f->h_p2p += fmm_mix(((uint64_t)A << 32) ^ (uint64_t)B);
+    f->h_p2p += h;
+    if (f->np2p) {
+        f->np2p[B]++;
+        f->hp2p[B] += h;
+    }
     double phi = 0.0, mag = 0.0;
     for (int64_t i = t->first[B]; i < t->first[B] + t->count[B]; i++)
         for (int64_t j = t->first[A]; j < t->first[A] + t->count[A]; j++) {
@@ -1403,8 +1412,13 @@ static void fmm_p2p(fmm_t *f, int64_t A, int64_t B)
 static void fmm_m2l(fmm_t *f, int64_t A, int64_t B)
 {
     const or_tree *t = f->t;
+    const uint64_t h = fmm_mix(((uint64_t)A << 32) ^ (uint64_t)B);
     f->n_m2l++;
-    f->h_m2l += fmm_mix(((uint64_t)A << 32) ^ (uint64_t)B);
+    f->h_m2l += h;
+    if (f->nm2l) {
+        f->nm2l[B]++;
+        f->hm2l[B] += h;
+    }
     double d[3];
     for (int a = 0; a < 3; a++)
         d[a] = t->com[3 * A + a] - t->com[3 * B + a];
@@ -1446,8 +1460,11 @@ static void fmm_pair(fmm_t *f, int64_t A, int64_t B)
         d2 += e * e;
     }
     const double lhs = sA + sB, rhs = f->theta * sqrt(d2);
-    if (fabs(lhs - rhs) <= 1e-6 * rhs)
+    if (fabs(lhs - rhs) <= 1e-6 * rhs) {
         f->ties++;
+        if (f->flag)
+            f->flag[B] = 1;
+    }
     if (lhs < rhs) {
         fmm_m2l(f, A, B);
         return;
@@ -1470,8 +1487,33 @@ static void fmm_pair(fmm_t *f, int64_t A, int64_t B)
  * pair-set hashes (as int64 bit patterns). */
 void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc_out, int64_t *stats)
 {
+    or_fmm_nodes(t, theta, eps, G, acc_out, stats, NULL, NULL, NULL, NULL, NULL);
+}
+
+void or_fmm_nodes(const or_tree *t, double theta, double eps, double G, double *acc_out, int64_t *stats,
+                  int64_t *nm2l, int64_t *np2p, uint64_t *hm2l, uint64_t *hp2p, int32_t *flag)
+{
     fmm_t f;
     memset(&f, 0, sizeof(f));
+    int64_t *own_n = NULL;
+    uint64_t *own_h = NULL;
+    int32_t *own_f = NULL;
+    if (nm2l || np2p || hm2l || hp2p || flag) {
+        /* the records are kept together; absent ones go to scratch */
+        own_n = (int64_t *)calloc((size_t)t->M * 2, sizeof(int64_t));
+        own_h = (uint64_t *)calloc((size_t)t->M * 2, sizeof(uint64_t));
+        own_f = (int32_t *)calloc((size_t)t->M, sizeof(int32_t));
+        f.nm2l = nm2l ? nm2l : own_n;
+        f.np2p = np2p ? np2p : own_n + t->M;
+        f.hm2l = hm2l ? hm2l : own_h;
+        f.hp2p = hp2p ? hp2p : own_h + t->M;
+        f.flag = flag ? flag : own_f;
+        memset(f.nm2l, 0, (size_t)t->M * sizeof(int64_t));
+        memset(f.np2p, 0, (size_t)t->M * sizeof(int64_t));
+        memset(f.hm2l, 0, (size_t)t->M * sizeof(uint64_t));
+        memset(f.hp2p, 0, (size_t)t->M * sizeof(uint64_t));
+        memset(f.flag, 0, (size_t)t->M * sizeof(int32_t));
+    }
     f.t = t;
     f.theta = theta;
     f.eps2 = eps * eps;
@@ -1534,6 +1576,14 @@ void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc_ou
         stats[3] = (int64_t)f.h_m2l;
         stats[4] = (int64_t)f.h_p2p;
     }
+    /* a flagged cell hands its (possibly flipped) pairs to its subtree */
+    if (f.flag)
+        for (int64_t v = 1; v < t->M; v++)
+            if (f.flag[t->parent[v]])
+                f.flag[v] = 1;
+    free(own_n);
+    free(own_h);
+    free(own_f);
     free(f.L0);
     free(f.L1);
     free(f.L2);

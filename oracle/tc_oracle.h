@@ -181,6 +181,13 @@ int64_t or_tree_learned_bf16(const or_tree *t, double theta, double eps, double 
  * stats (nullable, 5): M2L pairs, P2P pairs, ties, M2L and P2P pair-set
  * hashes. */
 void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc, int64_t *stats);
+/* The same with per-target-cell records (each nullable, M entries): M2L and
+ * P2P pairs whose target is the cell, their pair-set hashes, and a flag set
+ * when the cell or one of its ancestors tested a pair within 1e-6 relative
+ * of the acceptance bound (a decision that rounding may flip, and with it
+ * every pair its subtree is handed). */
+void or_fmm_nodes(const or_tree *t, double theta, double eps, double G, double *acc, int64_t *stats,
+                  int64_t *nm2l, int64_t *np2p, uint64_t *hm2l, uint64_t *hp2p, int32_t *flag);
 
 #ifdef __cplusplus
 }

@@ -92,3 +92,21 @@ def test_error_shrinks_with_theta():
         a, _ = t.fmm(theta, 0.01)
         rms.append(float(np.sqrt(np.mean(_rel(a, ad) ** 2))))
     assert rms[1] < rms[0] / 3 and rms[2] < rms[1] and rms[2] < 1e-3, rms
+
+
+def test_per_target_records_sum_to_the_totals_and_flags_reach_the_subtree():
+    p, _, m = inputs.plummer(6000, 8)
+    t = oracle.Tree(p, m, 8, 64)
+    a0, st0 = t.fmm(0.5, 0.01)
+    a, st = t.fmm(0.5, 0.01, per_node=True)
+    assert np.array_equal(a, a0)
+    assert st["nm2l"].sum() == st0["m2l"] and st["np2p"].sum() == st0["p2p"]
+    assert int(st["hm2l"].sum(dtype=np.uint64)) == st0["m2l_hash"]
+    assert int(st["hp2p"].sum(dtype=np.uint64)) == st0["p2p_hash"]
+    # a leaf's self pair is a P2P with itself as target
+    leaves = np.where(t.nchild == 0)[0]
+    assert np.all(st["np2p"][leaves] >= 1)
+    # flags: a flagged parent flags all its children
+    par = t.parent[1:]
+    assert np.all(st["flag"][1:][st["flag"][par] == 1] == 1)
+    assert (st0["ties"] == 0) == (st["flag"].sum() == 0)
