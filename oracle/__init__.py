@@ -107,6 +107,8 @@ def _load():
     lib.or_fmm.restype = None
     lib.or_fmm_nodes.argtypes = [P, D, D, D, P, P, P, P, P, P, P]
     lib.or_fmm_nodes.restype = None
+    lib.or_fmm_radii.argtypes = [P, P]
+    lib.or_fmm_radii.restype = None
     lib.or_bf16.argtypes = [D]
     lib.or_bf16.restype = D
     lib.or_mlp_forward_bf16.argtypes = [P, P, P, I64, P, P]
@@ -293,6 +295,12 @@ class Tree:
         ev = self._lib.or_tree_learned_bf16(self._h, float(theta), float(eps), float(G), float(band), _ptr(p),
                                             _ptr(m), int(g0), int(g1), _ptr(corr), _ptr(crad), _ptr(flag))
         return corr, crad, flag, int(ev)
+
+    def fmm_radii(self):
+        """r_X of every cell (the FMM's acceptance radii), FP64."""
+        r = np.zeros(self.M)
+        self._lib.or_fmm_radii(self._h, _ptr(r))
+        return r
 
     def fmm(self, theta, eps, G=1.0, per_node=False):
         """Fast multipole accelerations (n x 3, original order) and the

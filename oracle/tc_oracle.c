@@ -1339,20 +1339,23 @@ void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cell
 /* stated in full).  Same tree as the treecode.                        */
 /*   Expansion centres: every cell's centre of mass c_X.               */
 /*   Multipoles: the monopole, mass M_X at c_X.                        */
+/*   Radii: r_X bounds the distance of X's bodies from c_X: a leaf's    */
+/*     farthest body; above, the farthest child sphere,                 */
+/*     max over children (|c_child - c_X| + r_child).                   */
 /*   Local expansions, second order about c_B: the field at x near B is */
 /*     a(x) = L0 + L1 dx + (1/2) L2 dx dx, dx = x - c_B; L0 a vector,   */
 /*     L1 the field's Jacobian (symmetric), L2 its second derivatives   */
 /*     (a symmetric 3-index tensor).                                    */
-/*   Acceptance of a pair of disjoint cells: s_A + s_B < theta |c_A - c_B|*/
-/*     (s the cube side); a pair lying within 1e-6 relative of the bound */
-/*     is counted (ties).                                               */
+/*   Acceptance of a pair of disjoint cells: r_A + r_B < theta |c_A - c_B|*/
+/*     (the spheres about the centres, shrunk by theta, are disjoint);  */
+/*     a pair within 1e-6 relative of the bound is counted (ties).      */
 /*   Dual traversal from (root, root):                                  */
 /*     (X, X): a leaf -> P2P within it; otherwise every (child, child).  */
 /*     (A, B), A != B: accepted -> M2L(A -> B); both leaves -> P2P(A ->  */
 /*     B); otherwise split B if it is internal and (A is a leaf or      */
-/*     s_B >= s_A), else split A.  Per target cell this is a walk: a    */
-/*     target B refines each candidate source larger than itself until  */
-/*     it is accepted, a leaf or no larger, and hands the unresolved     */
+/*     r_B >= r_A), else split A.  Per target cell this is a walk: a    */
+/*     target B refines each candidate source wider than itself until   */
+/*     it is accepted, a leaf or no wider, and hands the unresolved     */
 /*     ones, with its own children, to its children as their candidates.*/
 /*   M2L(A -> B): d = c_A - c_B, rho^2 = |d|^2 + eps^2, the softened     */
 /*     field G M_A d / rho^3 and its derivatives at c_B:                 */
@@ -1373,6 +1376,7 @@ typedef struct {
     const or_tree *t;
     double theta, eps2, G;
     double *L0, *L1, *L2; /* M x 3, M x 9, M x 27 (full index ranges) */
+    double *rad;     /* M: radius about the centre of mass */
     double *acc;     /* sorted order, n x 3 */
     int64_t n_m2l, n_p2p, ties;
     uint64_t h_m2l, h_p2p; /* order-independent hashes of the pair sets */
@@ -1453,14 +1457,15 @@ static void fmm_pair(fmm_t *f, int64_t A, int64_t B)
                 fmm_pair(f, ca, cb);
         return;
     }
-    const double sA = cube_side(t, A), sB = cube_side(t, B);
+    const double rA = f->rad[A], rB = f->rad[B];
     double d2 = 0.0;
     for (int a = 0; a < 3; a++) {
         double e = t->com[3 * A + a] - t->com[3 * B + a];
         d2 += e * e;
     }
-    const double lhs = sA + sB, rhs = f->theta * sqrt(d2);
-    if (fabs(lhs - rhs) <= 1e-6 * rhs) {
+    const double lhs = rA + rB, rhs = f->theta * sqrt(d2);
+    /* rhs = 0 (theta = 0, or coincident centres) rejects exactly */
+    if (rhs > 0.0 && fabs(lhs - rhs) <= 1e-6 * rhs) {
         f->ties++;
         if (f->flag)
             f->flag[B] = 1;
@@ -1473,12 +1478,40 @@ static void fmm_pair(fmm_t *f, int64_t A, int64_t B)
         fmm_p2p(f, A, B);
         return;
     }
-    if (!leafB && (leafA || sB >= sA)) {
+    if (!leafB && (leafA || rB >= rA)) {
         for (int64_t cb = t->child_first[B]; cb < t->child_first[B] + t->nchild[B]; cb++)
             fmm_pair(f, A, cb);
     } else {
         for (int64_t ca = t->child_first[A]; ca < t->child_first[A] + t->nchild[A]; ca++)
             fmm_pair(f, ca, B);
+    }
+}
+
+/* r_X of every cell: children come after their parent in breadth-first
+ * order, so one backward sweep sees every child before its parent. */
+void or_fmm_radii(const or_tree *t, double *rad)
+{
+    for (int64_t v = t->M - 1; v >= 0; v--) {
+        const double *c = &t->com[3 * v];
+        double r = 0.0;
+        if (t->nchild[v] == 0) {
+            for (int64_t i = t->first[v]; i < t->first[v] + t->count[v]; i++) {
+                const double *x = &t->xs[3 * i];
+                double e = sqrt((x[0] - c[0]) * (x[0] - c[0]) + (x[1] - c[1]) * (x[1] - c[1]) +
+                                (x[2] - c[2]) * (x[2] - c[2]));
+                if (e > r)
+                    r = e;
+            }
+        } else {
+            for (int64_t k = t->child_first[v]; k < t->child_first[v] + t->nchild[v]; k++) {
+                const double *q = &t->com[3 * k];
+                double e = sqrt((q[0] - c[0]) * (q[0] - c[0]) + (q[1] - c[1]) * (q[1] - c[1]) +
+                                (q[2] - c[2]) * (q[2] - c[2])) + rad[k];
+                if (e > r)
+                    r = e;
+            }
+        }
+        rad[v] = r;
     }
 }
 
@@ -1522,6 +1555,8 @@ void or_fmm_nodes(const or_tree *t, double theta, double eps, double G, double *
     f.L1 = (double *)calloc((size_t)t->M * 9, sizeof(double));
     f.L2 = (double *)calloc((size_t)t->M * 27, sizeof(double));
     f.acc = (double *)calloc((size_t)t->n * 3, sizeof(double));
+    f.rad = (double *)calloc((size_t)t->M, sizeof(double));
+    or_fmm_radii(t, f.rad);
     fmm_pair(&f, 0, 0);
     /* L2L: breadth-first order puts every parent before its children */
     for (int64_t v = 1; v < t->M; v++) {
@@ -1584,6 +1619,7 @@ void or_fmm_nodes(const or_tree *t, double theta, double eps, double G, double *
     free(own_n);
     free(own_h);
     free(own_f);
+    free(f.rad);
     free(f.L0);
     free(f.L1);
     free(f.L2);

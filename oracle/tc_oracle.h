@@ -176,11 +176,15 @@ int64_t or_tree_learned_bf16(const or_tree *t, double theta, double eps, double 
 
 /* Fast multipole method on the same tree (a reading of Sec. 5, stated in
  * tc_oracle.c): monopoles at the cells' centres of mass, second-order local
- * expansions, pair acceptance s_A + s_B < theta |c_A - c_B|, dual traversal,
+ * expansions, pair acceptance r_A + r_B < theta |c_A - c_B| (r_X: the
+ * cell's radius about its centre of mass, or_fmm_radii), dual traversal,
  * M2L / L2L / L2P and P2P between leaves.  acc (n x 3, original order);
  * stats (nullable, 5): M2L pairs, P2P pairs, ties, M2L and P2P pair-set
  * hashes. */
 void or_fmm(const or_tree *t, double theta, double eps, double G, double *acc, int64_t *stats);
+/* r_X (M): a leaf's farthest body from its centre of mass; above, the
+ * farthest child sphere, max over children (|c_child - c_X| + r_child). */
+void or_fmm_radii(const or_tree *t, double *rad);
 /* The same with per-target-cell records (each nullable, M entries): M2L and
  * P2P pairs whose target is the cell, their pair-set hashes, and a flag set
  * when the cell or one of its ancestors tested a pair within 1e-6 relative

@@ -1,8 +1,12 @@
 """Pins of the oracle's fast multipole method (a reading of the paper's
 Sec. 5, stated in oracle/tc_oracle.c): monopoles at cell centres of mass,
 second-order local expansions (the field, its Jacobian and its second
-derivatives), pair acceptance
-s_A + s_B < theta |c_A - c_B|, dual traversal, M2L / L2L / L2P and P2P.
+derivatives), pair acceptance r_A + r_B < theta |c_A - c_B| with r_X the
+cell's radius about its centre of mass, dual traversal, M2L / L2L / L2P and
+P2P.
+
+* Radii: every body lies within r_X of c_X for every cell X holding it, a
+  leaf's radius is its farthest body (brute force).
 
 * theta = 0 accepts no pair: every interaction is P2P, the direct sum.
 * Two bodies far apart: a monopole of one body is exact, and the local
@@ -40,12 +44,31 @@ def test_two_bodies_exact():
     p = np.array([[-0.9, -0.8, -0.85], [0.9, 0.8, 0.95]], np.float32)
     m = np.array([0.3, 1.7], np.float32)
     t = oracle.Tree(p, m, 1, 1)
-    a, st = t.fmm(1.5, 1e-3)
     ad, _ = oracle.direct(p, m, 1e-3, want_pot=False)
-    # the two leaves meet each other through M2L; each meets itself in a
+    # one-body leaves have radius 0, so any theta > 0 accepts them (cube
+    # sides, about 2 here against a distance of 2.5, would not at 0.3): the
+    # two leaves meet each other through M2L, each meets itself in a
     # (bodiless) P2P
-    assert st["m2l"] == 2 and st["p2p"] == 2
-    assert _rel(a, ad).max() <= 1e-14
+    for theta in (0.3, 1.5):
+        a, st = t.fmm(theta, 1e-3)
+        assert st["m2l"] == 2 and st["p2p"] == 2
+        assert _rel(a, ad).max() <= 1e-14
+
+
+def test_radii_bound_every_body():
+    p, _, m = inputs.plummer(3000, 9)
+    t = oracle.Tree(p, m, 8, 64)
+    r = t.fmm_radii()
+    xs = p.astype(np.float64)
+    for v in range(t.M):
+        idx = t.perm[t.first[v]:t.first[v] + t.count[v]]
+        far = np.sqrt(np.sum((xs[idx] - t.com[v]) ** 2, axis=1)).max()
+        if t.nchild[v] == 0:
+            assert abs(r[v] - far) <= 1e-12 * max(far, 1e-300), v
+        else:
+            assert far <= r[v] * (1 + 1e-12), v
+            kids = range(t.child_first[v], t.child_first[v] + t.nchild[v])
+            assert r[v] >= max(r[k] for k in kids), v
 
 
 def test_every_pair_once_linear_field_limit():
