@@ -260,6 +260,49 @@ int tc_get_timings(tc_ctx *ctx, double *out6);
 int tc_direct_static(const float *pos, const float *mass, int64_t n, const int64_t *idx, int64_t ns,
                      float eps, float G, double *acc, double *pot, void *cuda_stream);
 
+/* Fast multipole method on the current tree (Sec. 5 names the FMM as the
+ * treecode's O(N) successor and gives no formulation; this is the reading
+ * implemented):
+ *   expansion centres  every cell's centre of mass c_X (the build's FP64
+ *                      reduction); its multipole is the monopole M_X;
+ *   local expansions   second order about c_B: near B the field is
+ *                      a(x) = L0 + L1 dx + (1/2) L2 dx dx, dx = x - c_B,
+ *                      with L1 the field's Jacobian and L2 its second
+ *                      derivatives (FP32, symmetric storage);
+ *   acceptance         distinct cells A, B with s_A + s_B < theta |c_A - c_B|
+ *                      (s the cube side), tested in FP32;
+ *   traversal          dual, from (root, root): a cell paired with itself
+ *                      splits into every (child, child) pair (a leaf: P2P
+ *                      within it); an accepted pair is an M2L from A to B;
+ *                      two leaves are a P2P; otherwise B is split when it is
+ *                      internal and (A is a leaf or s_B >= s_A), else A;
+ *   M2L (A -> B)       the Plummer-softened field G M_A d / rho^3 of A's
+ *                      monopole, d = c_A - c_B, rho^2 = |d|^2 + eps^2, and
+ *                      its first two derivatives, added to L(B);
+ *   L2L                parents before children: L(child) += L(parent)
+ *                      moved to the child's centre (exact for a quadratic);
+ *   L2P, P2P           every body of a leaf gets its leaf's expansion and
+ *                      the softened direct sum over the bodies of every leaf
+ *                      P2P-paired with it (compensated FP32 summation).
+ * Every ordered pair of bodies is counted exactly once, through one M2L or
+ * one P2P.  theta >= 0 (0: every pair is P2P, the direct sum), eps > 0.
+ * The accelerations replace the context's (tc_get_acc; no potential), and
+ * tc_ctx_step refuses them (TC_ESTATE): a step integrates with the treecode.
+ * Synchronises (it reads the tree's level ranges and checks its scratch).
+ * Scratch is kept in the context and grows as needed: a pass whose lists
+ * outgrew it is rerun.  TC_EDEVICE when a cell's refinement stack overflows
+ * (2048 sources; theta far below 0.2 on strongly clustered bodies). */
+int tc_ctx_fmm(tc_ctx *ctx, float theta, float eps, float G);
+/* Pair counts of the last tc_ctx_fmm (M2L, P2P, self pairs of leaves
+ * included) and two order-independent hashes of the pair sets: the sums
+ * over pairs of splitmix64((A << 32) ^ B), A source and B target
+ * breadth-first node indices (tc_get_nodes).  Any pointer may be NULL;
+ * hash2 receives {M2L hash, P2P hash}. */
+int tc_get_fmm_stats(tc_ctx *ctx, int64_t *m2l, int64_t *p2p, uint64_t *hash2);
+/* The same per target cell (nnodes entries each, host memory, any may be
+ * NULL): M2L and P2P pairs whose target is the cell, and their hashes. */
+int tc_get_fmm_pairs(tc_ctx *ctx, int64_t *nm2l, int64_t *np2p, uint64_t *hm2l, uint64_t *hp2p);
+
 /* Autotuner: times the walk + force kernel for every group size (32, 64,
  * 128), list tile (64, 128, 256) and warps per block (2, 4) on the current
  * bodies (reps timed runs each, the fastest kept), sets the best and returns

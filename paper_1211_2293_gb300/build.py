@@ -27,7 +27,7 @@ INCLUDE = os.path.join(ROOT, "include")
 WALK_UNITS = [(f"tc_walk_b{b}_t{t}", "tc_walk_unit.cu", [f"-DTC_WALK_B={b}", f"-DTC_WALK_TILE={t}"])
               for b in (4, 2, 1) for t in (128, 64, 256)]
 UNITS = WALK_UNITS + [(s[:-3], s, []) for s in ["tc_api.cu", "tc_walk.cu", "tc_sort.cu", "tc_build.cu", "tc_step.cu",
-                                               "tc_noalloc.cu", "tc_mlp.cu", "tc_band.cu",
+                                               "tc_noalloc.cu", "tc_mlp.cu", "tc_band.cu", "tc_fmm.cu",
                                                "tc_force_probe.cu"]]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

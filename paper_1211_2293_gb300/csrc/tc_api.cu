@@ -130,6 +130,27 @@ struct tc_ctx {
     unsigned long long* pair_n = nullptr;
     int64_t pair_cap = 0;
 
+    // fast multipole method: parent table, local expansions, unresolved
+    // source lists (per node: offset and count into the pool of its level's
+    // parity), per-warp slabs, counters, level starts
+    bool forces_fmm = false;
+    int32_t* fmm_parent = nullptr;
+    float* fmm_loc = nullptr;
+    int64_t* fmm_off = nullptr;
+    int32_t* fmm_cnt = nullptr;
+    unsigned long long* fmm_rec = nullptr;  // 4 per node
+    double* fmm_rad = nullptr;               // acceptance radii (FP64, FP32)
+    float* fmm_radf = nullptr;
+    int64_t fmm_cap_m = 0;
+    int32_t* fmm_pool[2] = {nullptr, nullptr};
+    int64_t fmm_pool_cap = 0;
+    int32_t* fmm_slab = nullptr;
+    int64_t fmm_slab_cap = 0;
+    int64_t fmm_slab_warps = 0;
+    unsigned long long* fmm_ctr = nullptr;
+    int64_t* fmm_lstart = nullptr;
+    unsigned long long fmm_stats[4] = {0, 0, 0, 0};
+
     // the captured leapfrog step
     cudaGraphExec_t gexec = nullptr;
     std::string gkey;
@@ -343,6 +364,10 @@ int check_device(tc_ctx* c)
                         "drift -- call tc_ctx_build or tc_set_state to resize");
         if (e & kErrStack) return fail(c, TC_EDEVICE, "walk stack overflow (raise tc_config.stack)");
         if (e & kErrWorkLoop) return fail(c, TC_EDEVICE, "a bounded device wait gave up");
+        if (e & kErrFmmStack)
+            return fail(c, TC_EDEVICE, "the FMM's refinement stack (2048 sources per cell) overflowed; raise theta");
+        if (e & (kErrFmmPool | kErrFmmSlab))
+            return fail(c, TC_EDEVICE, "the FMM's unresolved-source lists still overflowed after regrowing");
         if (e & kErrBand)
             return fail(c, TC_EDEVICE,
                         "the learned walk recorded more band cells than its buffer holds (12 per body); its "
@@ -593,6 +618,7 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "walk launch: %s", cudaGetErrorString(e));
     phase_end(c, 1, t0, s);
     c->have_forces = true;
+    c->forces_fmm = false;
     c->forces_pot = c->cfg.want_pot != 0;
     c->theta = theta;
     c->eps = eps;
@@ -736,18 +762,10 @@ void tc_destroy(tc_ctx* c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     drop_graph(c);
-    void* bufs[] = {c->pos, c->vel, c->acc, c->pot, c->mass, c->sys_of, c->sysp, c->off_dev, c->chunks, c->keys,
-                    c->perm, c->body, c->sb.keys_alt, c->sb.vals_alt, c->sb.ghist, c->sb.status, c->sb.tiles,
-                    c->sb.blocksum, c->w, c->delta, c->top, c->nstart, c->prepos, c->gflag, c->gscan, c->gref_at,
-                    c->gfirst, c->gref, c->ncell, c->nbody, c->hash, c->totals, c->idx_dev, c->dir_out,
-                    c->pre_level, c->pre_first, c->iota, c->bfs_of_pre, c->lvl_alt, c->nt.a, c->nt.b, c->nt.c,
-                    c->nt.d, c->nt.quad, c->nt.feat, c->nt.mass64, c->nt.com64, c->info, c->mlp_params,
-                    c->mlp_maps, c->mlp_dev, c->mlp_m, c->mlp_v, c->mlp_grad, c->mlp_loss, c->mlp_evals, c->mlp_x,
-                    c->mlp_t, c->mlp_idx, c->mlp_raw, c->mlp_sums, c->mlp_wscale, c->mlp_bad, c->band, c->band_n,
-                    c->gcentre, c->gcorr,
-                    c->pair_b, c->pair_v, c->pair_n};
-    for (void* p : bufs)
-        if (p) cudaFree(p);
+    // every device buffer but the Info word was made by grow(), which records it
+    for (auto& kv : c->sizes) cudaFree(kv.first);
+    c->sizes.clear();
+    if (c->info) cudaFree(c->info);
     if (c->info_h) cudaFreeHost(c->info_h);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -863,6 +881,8 @@ int tc_ctx_step(tc_ctx* c, float dt)
     if (!c) return fail(c, TC_EINVAL, "tc_step: null context");
     if (!finite(dt)) return fail(c, TC_EINVAL, "tc_step: dt must be finite");
     if (!c->have_forces) return fail(c, TC_ESTATE, "tc_step: compute forces on the current positions first");
+    if (c->forces_fmm)
+        return fail(c, TC_ESTATE, "tc_step: the step integrates with the treecode; call tc_ctx_forces first");
     if (c->cfg.graph) return step_graph(c, dt);
     return step_eager(c, dt);
 }
@@ -1038,6 +1058,148 @@ int tc_diag(tc_ctx* c, double* out8)
     if (r) return r;
     for (int k = 0; k < 8; k++) out8[k] = c->info_h->diag[k];
     if (!pot) out8[1] = NAN;
+    return TC_OK;
+}
+
+int tc_ctx_fmm(tc_ctx* c, float theta, float eps, float G)
+{
+    if (!c) return fail(c, TC_EINVAL, "tc_fmm: null context");
+    if (!c->built) return fail(c, TC_ESTATE, "tc_fmm: build the tree first");
+    if (!finite(theta) || theta < 0.f) return fail(c, TC_EINVAL, "tc_fmm: theta must be finite and >= 0");
+    if (!finite(eps) || eps <= 0.f) return fail(c, TC_EINVAL, "tc_fmm: eps must be finite and > 0");
+    if (!finite(G)) return fail(c, TC_EINVAL, "tc_fmm: G must be finite");
+    int r = check_device(c);  // synchronises: the last build's node count, no pending error
+    if (r) return r;
+    const int64_t M = c->info_h->M;
+    cudaStream_t s = c->stream;
+    if (c->fmm_cap_m < c->cap_m) {
+        TC_GROW(c, c->fmm_parent, c->cap_m);
+        TC_GROW(c, c->fmm_loc, c->cap_m * fmm_loc_width());
+        TC_GROW(c, c->fmm_off, c->cap_m);
+        TC_GROW(c, c->fmm_cnt, c->cap_m);
+        TC_GROW(c, c->fmm_rec, 4 * c->cap_m);
+        TC_GROW(c, c->fmm_rad, c->cap_m);
+        TC_GROW(c, c->fmm_radf, c->cap_m);
+        c->fmm_cap_m = c->cap_m;
+    }
+    if (!c->fmm_ctr) TC_GROW(c, c->fmm_ctr, 8);
+    if (!c->fmm_lstart) TC_GROW(c, c->fmm_lstart, kFmmLevelSlots);
+    launch_fmm_level_starts(c->info, c->cap_m, c->nt, c->fmm_lstart, s);
+    TC_CUDA(c, cudaGetLastError());
+    int64_t ls[kFmmLevelSlots];
+    TC_CUDA(c, cudaMemcpyAsync(ls, c->fmm_lstart, sizeof(ls), cudaMemcpyDeviceToHost, s));
+    TC_CUDA(c, cudaStreamSynchronize(s));
+    int depth = 0;
+    while (depth < kMaxLevel && ls[depth + 1] < M) depth++;
+    // the pools and slabs start at an estimate and grow to what an attempt
+    // that overflowed them counted; the overflowing attempt is discarded
+    // (TC_FMM_POOL / TC_FMM_SLAB, in entries, override the first estimate
+    // of a context, to exercise the regrowth)
+    int64_t want_pool = std::max<int64_t>(c->fmm_pool_cap, 32 * c->cap_m + 65536);
+    int64_t want_slab = std::max<int64_t>(c->fmm_slab_cap, 4096);
+    if (c->fmm_pool_cap == 0)
+        if (const char* env = getenv("TC_FMM_POOL")) want_pool = std::max<long long>(1, atoll(env));
+    if (c->fmm_slab_cap == 0)
+        if (const char* env = getenv("TC_FMM_SLAB")) want_slab = std::max<long long>(1, atoll(env));
+    cudaEvent_t t0 = phase_begin(c, s, 1);
+    unsigned long long ctr[8];
+    for (int attempt = 0;; attempt++) {
+        if (want_pool > c->fmm_pool_cap) {
+            TC_GROW(c, c->fmm_pool[0], want_pool);
+            TC_GROW(c, c->fmm_pool[1], want_pool);
+            c->fmm_pool_cap = want_pool;
+        }
+        const int64_t warps = fmm_slab_warps();
+        if (want_slab > c->fmm_slab_cap || warps != c->fmm_slab_warps) {
+            TC_GROW(c, c->fmm_slab, want_slab * warps);
+            c->fmm_slab_cap = want_slab;
+            c->fmm_slab_warps = warps;
+        }
+        TC_CUDA(c, cudaMemsetAsync(c->fmm_ctr, 0, 8 * sizeof(unsigned long long), s));
+        TC_CUDA(c, cudaMemsetAsync(c->fmm_cnt, 0, c->cap_m * sizeof(int32_t), s));
+        TC_CUDA(c, cudaMemsetAsync(c->fmm_off, 0, c->cap_m * sizeof(int64_t), s));
+        FmmLaunch p{};
+        p.body = c->body;
+        p.perm = c->perm;
+        p.sysp = c->sysp;
+        p.nt = c->nt;
+        p.info = c->info;
+        p.err = &c->info->err;
+        p.cap_m = c->cap_m;
+        p.parent = c->fmm_parent;
+        p.loc = c->fmm_loc;
+        p.pool[0] = c->fmm_pool[0];
+        p.pool[1] = c->fmm_pool[1];
+        p.pool_cap = c->fmm_pool_cap;
+        p.slab = c->fmm_slab;
+        p.slab_cap = c->fmm_slab_cap;
+        p.near_off = c->fmm_off;
+        p.near_cnt = c->fmm_cnt;
+        p.ctr = c->fmm_ctr;
+        p.rec = c->fmm_rec;
+        p.rad = c->fmm_rad;
+        p.radf = c->fmm_radf;
+        p.acc = c->acc;
+        p.theta = theta;
+        p.eps = eps;
+        p.G = G;
+        cudaError_t e = launch_fmm(p, ls, depth, s);
+        if (e != cudaSuccess) return fail(c, TC_ECUDA, "fmm launch: %s", cudaGetErrorString(e));
+        TC_CUDA(c, cudaMemcpyAsync(ctr, c->fmm_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s));
+        TC_CUDA(c, cudaStreamSynchronize(s));
+        TC_CUDA(c, cudaMemcpy(c->info_h, c->info, sizeof(Info), cudaMemcpyDeviceToHost));
+        const int32_t err = c->info_h->err;
+        const int32_t grow_bits = kErrFmmPool | kErrFmmSlab;
+        // a level that overflowed handed its children short lists, so deeper
+        // levels may need more than this pass counted: grow at least 2x
+        if ((err & grow_bits) && !(err & ~grow_bits) && attempt < 16) {
+            TC_CUDA(c, cudaMemsetAsync(&c->info->err, 0, sizeof(int32_t), s));
+            if (err & kErrFmmPool)
+                want_pool = std::max<int64_t>((int64_t)(ctr[2] + ctr[2] / 4 + 4096), 2 * c->fmm_pool_cap);
+            if (err & kErrFmmSlab)
+                want_slab = std::max<int64_t>((int64_t)(ctr[3] + ctr[3] / 4 + 256), 2 * c->fmm_slab_cap);
+            continue;
+        }
+        if (err) {
+            c->have_forces = false;
+            return check_device(c);  // reports and clears the error word
+        }
+        break;
+    }
+    phase_end(c, 1, t0, s);
+    for (int k = 0; k < 4; k++) c->fmm_stats[k] = ctr[4 + k];
+    c->have_forces = true;
+    c->forces_fmm = true;
+    c->forces_pot = false;
+    return TC_OK;
+}
+
+int tc_get_fmm_pairs(tc_ctx* c, int64_t* nm2l, int64_t* np2p, uint64_t* hm2l, uint64_t* hp2p)
+{
+    if (!c) return fail(c, TC_EINVAL, "tc_get_fmm_pairs: null context");
+    if (!c->have_forces || !c->forces_fmm) return fail(c, TC_ESTATE, "tc_get_fmm_pairs: the last forces were not tc_ctx_fmm's");
+    const int64_t M = c->info_h->M;
+    std::vector<unsigned long long> rec(4 * M);
+    TC_CUDA(c, cudaMemcpy(rec.data(), c->fmm_rec, rec.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    for (int64_t v = 0; v < M; v++) {
+        if (nm2l) nm2l[v] = (int64_t)rec[4 * v];
+        if (np2p) np2p[v] = (int64_t)rec[4 * v + 1];
+        if (hm2l) hm2l[v] = rec[4 * v + 2];
+        if (hp2p) hp2p[v] = rec[4 * v + 3];
+    }
+    return TC_OK;
+}
+
+int tc_get_fmm_stats(tc_ctx* c, int64_t* m2l, int64_t* p2p, uint64_t* hash2)
+{
+    if (!c) return fail(c, TC_EINVAL, "tc_get_fmm_stats: null context");
+    if (!c->have_forces || !c->forces_fmm) return fail(c, TC_ESTATE, "tc_get_fmm_stats: the last forces were not tc_ctx_fmm's");
+    if (m2l) *m2l = (int64_t)c->fmm_stats[0];
+    if (p2p) *p2p = (int64_t)c->fmm_stats[1];
+    if (hash2) {
+        hash2[0] = c->fmm_stats[2];
+        hash2[1] = c->fmm_stats[3];
+    }
     return TC_OK;
 }
 

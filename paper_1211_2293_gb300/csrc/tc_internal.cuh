@@ -24,6 +24,9 @@ enum : int32_t {
     kErrCapacity = 4,     // the node table outgrew its allocation
     kErrWorkLoop = 8,     // a bounded wait gave up
     kErrBand = 16,        // the learned walk's band-cell record outgrew its buffer
+    kErrFmmPool = 32,     // the FMM's unresolved-source pool outgrew its allocation (regrown, rerun)
+    kErrFmmSlab = 64,     // one cell's unresolved-source list outgrew its slab (regrown, rerun)
+    kErrFmmStack = 128,   // the FMM's refinement stack overflowed
 };
 
 // Per-system root cube (written by the bounding-box kernels).
@@ -295,5 +298,43 @@ void launch_diag(const float* pos, const float* vel, const float* mass, const fl
 void launch_direct(const float* pos, const float* mass, const uint32_t* sys_of, const SysParams* sysp,
                    const int64_t* idx, int64_t ns, float eps2, float G, double* acc, double* pot,
                    cudaStream_t s);
+
+// fast multipole method (tc_fmm.cu).  Level starts: lstart[l] is the first
+// breadth-first index of level l, lstart[l] = M past the deepest level
+// (kFmmLevelSlots entries).  launch_fmm launches the parent table and one
+// kernel per level 0..depth; its scratch: loc (cap_m x fmm_loc_width()
+// floats), near_off / near_cnt (cap_m), two pools of pool_cap entries, a slab
+// of slab_cap entries for each of fmm_slab_warps() warps, ctr (8 counters:
+// pool fill per level parity, pool need, slab need, M2L pairs, P2P pairs and
+// their two hashes; zero the last six before the launch); rec: per node its
+// M2L and P2P pairs as target and their hashes.
+constexpr int kFmmLevelSlots = kMaxLevel + 3;
+struct FmmLaunch {
+    const float4* body;
+    const uint32_t* perm;
+    const SysParams* sysp;
+    NodeTables nt;
+    const Info* info;
+    int32_t* err;
+    int64_t cap_m;
+    int32_t* parent;
+    float* loc;
+    int32_t* pool[2];
+    int64_t pool_cap;
+    int32_t* slab;
+    int64_t slab_cap;
+    int64_t* near_off;
+    int32_t* near_cnt;
+    unsigned long long* ctr;
+    unsigned long long* rec;  // 4 per node (M2L pairs, P2P pairs, their hashes), 32-byte aligned
+    double* rad;              // per node: r_X (FP64), and rounded to FP32
+    float* radf;
+    float* acc;
+    float theta, eps, G;
+};
+int64_t fmm_slab_warps();
+int fmm_loc_width();
+void launch_fmm_level_starts(const Info* info, int64_t cap_m, NodeTables nt, int64_t* lstart, cudaStream_t s);
+cudaError_t launch_fmm(const FmmLaunch& p, const int64_t* lstart_h, int depth, cudaStream_t s);
 
 }  // namespace tc

@@ -34,6 +34,7 @@ EXPORTS = [
     "tc_mlp_pairs", "tc_mlp_evals", "tc_get_group_list", "tc_selftest_bounded_wait",
     "tc_probe_fp32",
     "tc_probe_force",
+    "tc_ctx_fmm", "tc_get_fmm_stats", "tc_get_fmm_pairs",
 ]
 
 MLP_NPARAM = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
@@ -112,6 +113,9 @@ def load(path: str | None = None):
         "tc_selftest_bounded_wait": ([P, P], I32),
         "tc_probe_fp32": ([I32, P], I32),
         "tc_probe_force": ([P], I32),
+        "tc_ctx_fmm": ([P, F, F, F], I32),
+        "tc_get_fmm_stats": ([P, P, P, P], I32),
+        "tc_get_fmm_pairs": ([P, P, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -307,6 +311,26 @@ class Context:
 
     def forces(self, theta: float, eps: float, G: float = 1.0):
         self._c(self._lib.tc_ctx_forces(self._h, float(theta), float(eps), float(G)))
+
+    def fmm(self, theta: float, eps: float, G: float = 1.0):
+        """Fast multipole accelerations on the current tree (read with get_acc)."""
+        self._c(self._lib.tc_ctx_fmm(self._h, float(theta), float(eps), float(G)))
+
+    def fmm_stats(self) -> dict:
+        """M2L and P2P pair counts of the last fmm() and the pair-set hashes."""
+        m, p = ctypes.c_int64(), ctypes.c_int64()
+        h = np.zeros(2, np.uint64)
+        self._c(self._lib.tc_get_fmm_stats(self._h, ctypes.byref(m), ctypes.byref(p), _ptr(h)))
+        return dict(m2l=m.value, p2p=p.value, m2l_hash=int(h[0]), p2p_hash=int(h[1]))
+
+    def fmm_pairs(self) -> dict:
+        """Per target cell of the last fmm(): nm2l, np2p, hm2l, hp2p."""
+        M = self.sizes()[1]
+        rec = dict(nm2l=np.zeros(M, np.int64), np2p=np.zeros(M, np.int64), hm2l=np.zeros(M, np.uint64),
+                   hp2p=np.zeros(M, np.uint64))
+        self._c(self._lib.tc_get_fmm_pairs(self._h, _ptr(rec["nm2l"]), _ptr(rec["np2p"]), _ptr(rec["hm2l"]),
+                                           _ptr(rec["hp2p"])))
+        return rec
 
     def step(self, dt: float):
         self._c(self._lib.tc_ctx_step(self._h, float(dt)))

@@ -35,3 +35,18 @@ def rel_err_rms(a, b):
     num = np.sum((a - b) ** 2, axis=1)
     den = np.sum(b ** 2, axis=1)
     return float(np.sqrt(np.mean(num / den)))
+
+
+def abs_field(pos, mass, idx, eps, rows=64):
+    """sum_j m_j |x_j - x_i| / (|x_j - x_i|^2 + eps^2)^(3/2) for i in idx
+    (FP64): the sum of the magnitudes of the softened pair fields, the scale
+    of the float32 rounding of a sum of those terms however they cancel."""
+    p = np.asarray(pos, np.float64)
+    m = np.asarray(mass, np.float64)
+    idx = np.asarray(idx, np.int64)
+    out = np.zeros(idx.shape[0])
+    for k0 in range(0, idx.shape[0], rows):
+        d = p[None, :, :] - p[idx[k0:k0 + rows]][:, None, :]
+        r2 = np.einsum("ijk,ijk->ij", d, d)
+        out[k0:k0 + rows] = (np.sqrt(r2) * (r2 + eps * eps) ** -1.5) @ m
+    return out
