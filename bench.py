@@ -19,7 +19,8 @@ Sub-keys carry the other workloads: ``uniform_1m`` (uniform cube, 2^20
 bodies, theta 0.5, the build/walk roofline and the phase split),
 ``precision_16m`` (two Plummer spheres, 2^24 bodies: precise vs plain float32
 against the FP64 oracle) and ``batch_512`` (512 Plummer systems in one
-forest).
+forest) and ``fmm_4m`` (the fast multipole method beside the treecode walk
+on the evaluation sphere, each at its own 1e-3 opening angle, force phase).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -1052,6 +1053,65 @@ def precision_summary(args, local_rank, nsample=2048):
             "precise_cost": res[1]["walk_ms"] / res[0]["walk_ms"], "oracle_seconds": time.perf_counter() - t0}
 
 
+def fmm_summary(args, local_rank, nsample=4096, reps=7):
+    """The fast multipole method (tc_ctx_fmm) beside the treecode walk on the
+    evaluation sphere (Plummer, 2^22 bodies, eps 1e-3, leaf 16), each at the
+    opening angle where its RMS force error against direct summation is 1e-3;
+    force phase only (the tree is built once), interleaved, L2 flushed."""
+    import torch
+
+    from paper_1211_2293_gb300 import inputs, tc
+
+    dev = torch.device("cuda", local_rank)
+    n = N_EVAL
+    p, _, m = inputs.plummer(n, seed=SEED_EVAL)
+    ctx = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
+    ctx.build(torch.from_numpy(p).to(dev), torch.from_numpy(m).to(dev), LEAF)
+    idx = inputs.sample_indices(n, nsample, seed=1)
+    ad, _ = ctx.direct(idx, EPS)
+
+    def fmm_err(theta):
+        ctx.fmm(theta, EPS)
+        return _rms_vs_direct(ctx.get_acc()[idx], ad)
+
+    lo, hi = 0.2, 0.7
+    e_lo = fmm_err(lo)
+    for _ in range(9):
+        mid = 0.5 * (lo + hi)
+        e = fmm_err(mid)
+        if e <= GOAL:
+            lo, e_lo = mid, e
+        else:
+            hi = mid
+    thF, eF = lo, e_lo
+    thP, eP = _iso_theta(ctx, idx, ad, 0.4, 1.0)
+    ctx.fmm(thF, EPS)
+    st = ctx.fmm_stats()
+    ctx.set_config(verify=1)  # the walk's interaction count (timed below without it)
+    ctx.forces(thP, EPS)
+    inter = ctx.lists(per_group=False)["interactions"]
+    ctx.set_config(verify=0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tf, tp = [], []
+    for _ in range(reps):
+        for fn, out in ((lambda: ctx.fmm(thF, EPS), tf), (lambda: ctx.forces(thP, EPS), tp)):
+            flush.zero_()
+            ctx.sync()
+            ctx.set_timing(True)
+            fn()
+            out.append(ctx.timings()["walk_ms"])
+            ctx.set_timing(False)
+    ctx.close()
+    mf, mp = statistics.median(tf), statistics.median(tp)
+    return {"n": n, "theta": thF, "rms_force_err": eF, "force_ms": _spread(tf), "bodies_per_s": n / (mf / 1e3),
+            "m2l_per_body": st["m2l"] / n, "p2p_pairs_per_body": st["p2p"] / n,
+            "treecode": {"theta": thP, "rms_force_err": eP, "force_ms": _spread(tp),
+                         "bodies_per_s": n / (mp / 1e3), "interactions_per_body": inter / n},
+            "fmm_over_treecode": mp / mf,
+            "what": "force phase alone (library events around the FMM passes / the walk + force kernel), tree built "
+                    "once; acceptance r_A + r_B < theta |c_A - c_B|, monopole sources, second-order local expansions"}
+
+
 def run_precision(args, rank, world, local_rank):
     if rank != 0:
         return 0
@@ -1189,7 +1249,7 @@ def run_profile_case(args):
     build: a uniform cube built twice (eager builds; capture the second);
     learned: one learned walk (seeded random network, band 0.5, theta 0.9)
     on a 2^20-body Plummer sphere; quadrupole: one quadrupole walk (theta
-    0.7) on the same sphere."""
+    0.7) on the same sphere; fmm: two FMM passes (theta 0.4) on it."""
     import torch
 
     from paper_1211_2293_gb300 import inputs, tc
@@ -1209,6 +1269,14 @@ def run_profile_case(args):
     n = 1 << 20
     p, _, m = inputs.plummer(n, seed=101)
     P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
+    if case == "fmm":
+        ctx = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
+        ctx.build(P, M, 16)
+        ctx.fmm(0.4, 1e-3)
+        ctx.fmm(0.4, 1e-3)
+        print(f"fmm: Plummer N={n}, theta 0.4, {ctx.fmm_stats()}")
+        ctx.close()
+        return 0
     if case == "learned":
         ctx = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
         ctx.build(P, M, 16)
@@ -1242,7 +1310,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default=None,
                     help="uniform: walk shape 'gmax,tile,warps' instead of the autotuner's choice")
-    ap.add_argument("--workload", choices=["default", "uniform", "batch", "precision", "learned"],
+    ap.add_argument("--workload", choices=["default", "uniform", "batch", "precision", "learned", "fmm"],
                     default="default",
                     help="default: the benchmark line (learned vs plain at RMS 1e-3 on a 2^22 Plummer sphere, "
                          "with the other workloads as sub-keys); uniform: the uniform cube alone; batch: 512 "
@@ -1253,7 +1321,7 @@ def main():
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")
     ap.add_argument("--band-train", type=float, default=0.4, help="learned: band of the training pairs")
     ap.add_argument("--nsys", type=int, default=512)
-    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole"], default=None,
+    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole", "fmm"], default=None,
                     help="run one small case of a kernel family for an ncu capture and exit")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1281,6 +1349,11 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "uniform":
         line = run_uniform(args, rank, world, local_rank)
+    elif args.workload == "fmm":
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        line = {"workload": "fmm", **fmm_summary(args, local_rank)} if rank == 0 else None
     else:
         line = run_learned_default(args, rank, world, local_rank, dist)
         if not args.headline_only:
@@ -1293,6 +1366,7 @@ def main():
                 line["uniform_1m"] = uni
                 line["precision_16m"] = precision_summary(sub_args, local_rank)
                 line["batch_512"] = batch_line(sub_args, rank, 1, local_rank)
+                line["fmm_4m"] = fmm_summary(sub_args, local_rank)
     if line is not None and rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -297,10 +297,12 @@ int tc_ctx_fmm(tc_ctx *ctx, float theta, float eps, float G);
  * included) and two order-independent hashes of the pair sets: the sums
  * over pairs of splitmix64((A << 32) ^ B), A source and B target
  * breadth-first node indices (tc_get_nodes).  Any pointer may be NULL;
- * hash2 receives {M2L hash, P2P hash}. */
+ * hash2 receives {M2L hash, P2P hash} and needs verify = 1 in the
+ * configuration of that pass (else TC_ESTATE). */
 int tc_get_fmm_stats(tc_ctx *ctx, int64_t *m2l, int64_t *p2p, uint64_t *hash2);
 /* The same per target cell (nnodes entries each, host memory, any may be
- * NULL): M2L and P2P pairs whose target is the cell, and their hashes. */
+ * NULL): M2L and P2P pairs whose target is the cell, and their hashes
+ * (verify = 1 in the configuration of that pass, else TC_ESTATE). */
 int tc_get_fmm_pairs(tc_ctx *ctx, int64_t *nm2l, int64_t *np2p, uint64_t *hm2l, uint64_t *hp2p);
 
 /* Autotuner: times the walk + force kernel for every group size (32, 64,

@@ -150,6 +150,7 @@ struct tc_ctx {
     unsigned long long* fmm_ctr = nullptr;
     int64_t* fmm_lstart = nullptr;
     unsigned long long fmm_stats[4] = {0, 0, 0, 0};
+    bool fmm_records = false;  // the last pass kept hashes and per-node records
 
     // the captured leapfrog step
     cudaGraphExec_t gexec = nullptr;
@@ -1139,6 +1140,7 @@ int tc_ctx_fmm(tc_ctx* c, float theta, float eps, float G)
         p.rec = c->fmm_rec;
         p.rad = c->fmm_rad;
         p.radf = c->fmm_radf;
+        p.records = c->cfg.verify;
         p.acc = c->acc;
         p.theta = theta;
         p.eps = eps;
@@ -1168,6 +1170,7 @@ int tc_ctx_fmm(tc_ctx* c, float theta, float eps, float G)
     }
     phase_end(c, 1, t0, s);
     for (int k = 0; k < 4; k++) c->fmm_stats[k] = ctr[4 + k];
+    c->fmm_records = c->cfg.verify != 0;
     c->have_forces = true;
     c->forces_fmm = true;
     c->forces_pot = false;
@@ -1178,6 +1181,7 @@ int tc_get_fmm_pairs(tc_ctx* c, int64_t* nm2l, int64_t* np2p, uint64_t* hm2l, ui
 {
     if (!c) return fail(c, TC_EINVAL, "tc_get_fmm_pairs: null context");
     if (!c->have_forces || !c->forces_fmm) return fail(c, TC_ESTATE, "tc_get_fmm_pairs: the last forces were not tc_ctx_fmm's");
+    if (!c->fmm_records) return fail(c, TC_ESTATE, "tc_get_fmm_pairs: per-cell records need verify = 1");
     const int64_t M = c->info_h->M;
     std::vector<unsigned long long> rec(4 * M);
     TC_CUDA(c, cudaMemcpy(rec.data(), c->fmm_rec, rec.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
@@ -1194,6 +1198,7 @@ int tc_get_fmm_stats(tc_ctx* c, int64_t* m2l, int64_t* p2p, uint64_t* hash2)
 {
     if (!c) return fail(c, TC_EINVAL, "tc_get_fmm_stats: null context");
     if (!c->have_forces || !c->forces_fmm) return fail(c, TC_ESTATE, "tc_get_fmm_stats: the last forces were not tc_ctx_fmm's");
+    if (hash2 && !c->fmm_records) return fail(c, TC_ESTATE, "tc_get_fmm_stats: pair-set hashes need verify = 1");
     if (m2l) *m2l = (int64_t)c->fmm_stats[0];
     if (p2p) *p2p = (int64_t)c->fmm_stats[1];
     if (hash2) {

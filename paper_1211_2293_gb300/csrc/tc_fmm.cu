@@ -41,7 +41,7 @@ namespace {
 constexpr int kFmmWarps = 4;
 constexpr int kFmmStack = 2048;  // refinement stack per warp (shared memory)
 constexpr int kFmmTile = 128;
-constexpr int kFmmBlocksPerSm = 4;
+constexpr int kFmmBlocksPerSm = 5;
 constexpr int kLocW = 20;        // floats per local expansion: L0 3, L1 6, L2 10, one spare
 
 // Symmetric storage: L1 as (00 01 02 11 12 22), L2 as
@@ -143,6 +143,7 @@ struct FmmArgs {
     float* acc;              // n x 3, original order
     unsigned long long* rec; // per node: M2L pairs, P2P pairs, their hashes (target = the node)
     const float* radf;       // per node: r_X rounded to FP32
+    int records;             // keep the pair-set hashes and the per-node records
     float theta2, eps2, G;
 };
 
@@ -235,7 +236,7 @@ __global__ void k_fmm_parent(const Info* info, NodeTables nt, int32_t* __restric
 }
 
 // one warp per cell of [start, end): the target walk described above
-__global__ void __launch_bounds__(kFmmWarps * 32) k_fmm_level(FmmArgs a, int64_t start, int64_t end)
+__global__ void __launch_bounds__(kFmmWarps * 32, kFmmBlocksPerSm) k_fmm_level(FmmArgs a, int64_t start, int64_t end)
 {
     __shared__ uint32_t stk_s[kFmmWarps][kFmmStack];
     __shared__ __align__(16) float tile_s[kFmmWarps][4 * tile_cap(kFmmTile)];
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(kFmmWarps * 32) k_fmm_level(FmmArgs a, int64_t
                     }
                     if (r == 0 && (m2l || p2p)) {
                         const unsigned long long hh =
-                            mix64(((unsigned long long)(unsigned)A << 32) ^ (unsigned long long)B);
+                            a.records ? mix64(((unsigned long long)(unsigned)A << 32) ^ (unsigned long long)B) : 0ull;
                         if (m2l) {
                             n_m2l++;
                             h_m2l += hh;
@@ -426,8 +427,10 @@ __global__ void __launch_bounds__(kFmmWarps * 32) k_fmm_level(FmmArgs a, int64_t
                     h_p2p += __shfl_xor_sync(0xffffffffu, h_p2p, o);
                 }
                 if (lane == 0) {
-                    ulonglong4_32a* rec = reinterpret_cast<ulonglong4_32a*>(a.rec) + B;
-                    *rec = make_ulonglong4_32a(n_m2l, n_p2p, h_m2l, h_p2p);
+                    if (a.records) {
+                        ulonglong4_32a* rec = reinterpret_cast<ulonglong4_32a*>(a.rec) + B;
+                        *rec = make_ulonglong4_32a(n_m2l, n_p2p, h_m2l, h_p2p);
+                    }
                     t_m2l += n_m2l;
                     t_p2p += n_p2p;
                     th_m2l += h_m2l;
@@ -581,6 +584,7 @@ cudaError_t launch_fmm(const FmmLaunch& p, const int64_t* lstart_h, int depth, c
     a.acc = p.acc;
     a.rec = p.rec;
     a.radf = p.radf;
+    a.records = p.records;
     a.theta2 = p.theta * p.theta;
     a.eps2 = p.eps * p.eps;
     a.G = p.G;

@@ -329,6 +329,7 @@ struct FmmLaunch {
     unsigned long long* rec;  // 4 per node (M2L pairs, P2P pairs, their hashes), 32-byte aligned
     double* rad;              // per node: r_X (FP64), and rounded to FP32
     float* radf;
+    int records;              // pair-set hashes and per-node records (else counts only)
     float* acc;
     float theta, eps, G;
 };

@@ -317,11 +317,13 @@ class Context:
         self._c(self._lib.tc_ctx_fmm(self._h, float(theta), float(eps), float(G)))
 
     def fmm_stats(self) -> dict:
-        """M2L and P2P pair counts of the last fmm() and the pair-set hashes."""
+        """M2L and P2P pair counts of the last fmm() and the pair-set hashes
+        (None unless verify is set)."""
         m, p = ctypes.c_int64(), ctypes.c_int64()
-        h = np.zeros(2, np.uint64)
+        h = np.zeros(2, np.uint64) if self.config()["verify"] else None
         self._c(self._lib.tc_get_fmm_stats(self._h, ctypes.byref(m), ctypes.byref(p), _ptr(h)))
-        return dict(m2l=m.value, p2p=p.value, m2l_hash=int(h[0]), p2p_hash=int(h[1]))
+        return dict(m2l=m.value, p2p=p.value, m2l_hash=None if h is None else int(h[0]),
+                    p2p_hash=None if h is None else int(h[1]))
 
     def fmm_pairs(self) -> dict:
         """Per target cell of the last fmm(): nm2l, np2p, hm2l, hp2p."""

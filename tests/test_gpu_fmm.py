@@ -39,7 +39,7 @@ def _dev(x):
 
 
 def _run(tc, p, m, leaf, theta, eps, G):
-    ctx = tc.Context()
+    ctx = tc.Context(verify=1)
     ctx.build(_dev(p), _dev(m), leaf)
     ctx.fmm(theta, eps, G)
     return ctx, ctx.get_acc().astype(np.float64)
@@ -116,7 +116,7 @@ def test_fmm_single_leaf_and_two_bodies(tc):
 
 def test_fmm_is_deterministic_and_repeatable(tc):
     p, _, m = inputs.plummer(50000, 26)
-    ctx = tc.Context()
+    ctx = tc.Context(verify=1)
     ctx.build(_dev(p), _dev(m), 16)
     ctx.fmm(0.5, 0.01, 1.0)
     a1 = ctx.get_acc().copy()
@@ -129,14 +129,14 @@ def test_fmm_regrows_its_lists(tc, monkeypatch):
     # initial pool and slab far too small: every pass that overflows is
     # discarded and rerun with the counted sizes; the result is the same
     p, _, m = inputs.plummer(50000, 27)
-    ctx = tc.Context()
+    ctx = tc.Context(verify=1)
     ctx.build(_dev(p), _dev(m), 16)
     ctx.fmm(0.4, 0.01, 1.0)
     ref = ctx.get_acc().copy()
     ref_st = ctx.fmm_stats()
     monkeypatch.setenv("TC_FMM_POOL", "64")
     monkeypatch.setenv("TC_FMM_SLAB", "8")
-    ctx2 = tc.Context()
+    ctx2 = tc.Context(verify=1)
     ctx2.build(_dev(p), _dev(m), 16)
     ctx2.fmm(0.4, 0.01, 1.0)
     assert np.array_equal(ctx2.get_acc(), ref) and ctx2.fmm_stats() == ref_st
@@ -149,7 +149,7 @@ def test_fmm_batch_of_systems(tc):
     p = np.concatenate([q[0] for q in parts])
     m = np.concatenate([q[2] for q in parts])
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    ctx = tc.Context()
+    ctx = tc.Context(verify=1)
     ctx.build_batch(_dev(p), _dev(m), off, 16)
     ctx.fmm(0.5, 0.01, 1.0)
     a = ctx.get_acc().astype(np.float64)
@@ -179,6 +179,17 @@ def test_fmm_step_refuses_fmm_forces_and_stats_need_fmm(tc):
         ctx.fmm_stats()
     assert e.value.code == tc.TC_ESTATE
     ctx.fmm(0.5, 0.01, 1.0)
+    # counts without verify, records and hashes only with it; the counts
+    # do not depend on it
+    st = ctx.fmm_stats()
+    assert st["m2l_hash"] is None and st["m2l"] > 0
+    with pytest.raises(tc.TcError) as e:
+        ctx.fmm_pairs()
+    assert e.value.code == tc.TC_ESTATE
+    ctx.set_config(verify=1)
+    ctx.fmm(0.5, 0.01, 1.0)
+    st1 = ctx.fmm_stats()
+    assert (st1["m2l"], st1["p2p"]) == (st["m2l"], st["p2p"]) and st1["m2l_hash"] is not None
     with pytest.raises(tc.TcError) as e:
         ctx.step(1e-3)
     assert e.value.code == tc.TC_ESTATE
