@@ -68,6 +68,34 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b)
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_addr(b)) : "memory");
 }
 
+// the opened leaves' bodies reach a slot by cp.async (4-byte copies into the
+// pair-interleaved tile, global -> shared without passing through registers);
+// before its arrival on the slot's full barrier every producer lane makes the
+// barrier track its copies (cp.async.mbarrier.arrive without .noinc: the
+// pending count rises now and falls when the lane's copies have landed), so
+// the phase completes only once the bodies are in the tile
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void put_entry_async(float* tile, int k, const float4* src)
+{
+    float* t = tile + 8 * (k >> 1) + (k & 1);
+    const float* s = reinterpret_cast<const float*>(src);
+    cp_async4(t, s);
+    cp_async4(t + 2, s + 1);
+    cp_async4(t + 4, s + 2);
+    cp_async4(t + 6, s + 3);
+}
+
+__device__ __forceinline__ void mbar_track_copies(uint64_t* b)
+{
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
 {
     uint32_t ok;
@@ -153,6 +181,7 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
                 h->bn = bn;
             }
             __syncwarp();
+            mbar_track_copies(&full[k % kWsSlots]);
             mbar_arrive(&full[k % kWsSlots]);
             k++;
         };
@@ -381,7 +410,7 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
                         }
                         const int f = __shfl_sync(0xffffffffu, nb.x, pos);
                         const int e0 = __shfl_sync(0xffffffffu, excl_c, pos);
-                        if (o + lane < T) put_entry(btile, bn + lane, __ldg(&a.body[f + (t - e0)]));
+                        if (o + lane < T) put_entry_async(btile, bn + lane, &a.body[f + (t - e0)]);
                         bn += min(32, T - o);
                         if (bn >= kTile) {
                             hand_over(0, cn, bn);
@@ -433,6 +462,7 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
             __syncwarp();
         }
         (void)alive;
+        cp_async_wait_all();  // (a warp that gave up may still have copies in flight)
         return;
     }
 
