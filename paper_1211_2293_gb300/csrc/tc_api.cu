@@ -115,7 +115,7 @@ struct tc_ctx {
     // record, its length, each group's box centre and correction
     int2* band = nullptr;
     unsigned long long* band_n = nullptr;
-    float* gcentre = nullptr;
+    float4* grec = nullptr;  // 2 per group: the rows' frame
     float* gcorr = nullptr;
     int64_t band_cap = 0;
     int64_t band_gcap = 0;
@@ -536,7 +536,7 @@ int prepare_forces(tc_ctx* c)
         }
         if (!c->band_n) TC_GROW(c, c->band_n, 1);
         if (c->cap_n + 1 > c->band_gcap) {
-            TC_GROW(c, c->gcentre, 3 * (c->cap_n + 1));
+            TC_GROW(c, c->grec, 2 * (c->cap_n + 1));
             TC_GROW(c, c->gcorr, 3 * (c->cap_n + 1));
             c->band_gcap = c->cap_n + 1;
             drop_graph(c);
@@ -591,7 +591,7 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
         a.band = c->band;
         a.band_n = c->band_n;
         a.band_cap = c->band_cap;
-        a.gcentre = c->gcentre;
+        a.grec = c->grec;
     }
     cudaEvent_t t0 = phase_begin(c, s, 1);
     cudaError_t e = cudaSuccess;

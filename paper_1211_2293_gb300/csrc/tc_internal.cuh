@@ -209,13 +209,14 @@ struct WalkArgs {
     int work_slot;  // this launch's work-queue counter, info->work[work_slot]
     // learned correction evaluated after the walk (split walk): the band
     // cells of every group recorded as (node, group) pairs in chunks of
-    // kBandChunk entries taken from *band_n (unused tails hold node -1),
-    // at most band_cap entries; gcentre[3 g ..] the group's box centre in its
-    // reference cube's frame
+    // kBandChunk entries taken from *band_n (unused tails hold node -1), at
+    // most band_cap entries; grec[2 g], grec[2 g + 1] the group's record for
+    // the rows: {box centre in its reference cube's frame, h/2} and
+    // {reference cube centre (integer units of h/2, as int bits), root side}
     int2* band;
     unsigned long long* band_n;
     int64_t band_cap;
-    float* gcentre;
+    float4* grec;
 };
 constexpr int kBandChunk = 256;
 struct WalkConfig {

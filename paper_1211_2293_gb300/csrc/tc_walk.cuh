@@ -363,37 +363,60 @@ __host__ __device__ constexpr size_t mlp_frag_bytes() { return (sizeof(MlpFrag) 
 // frame of the group's reference cube rc): d/s and s/r formed here, the
 // other nine features from the node's record (k_node_features), and the
 // factor G M s^2 / r^4 that turns a label into an acceleration
+// what a row needs of its node: the walk record (b, a, c) and the packed
+// cell-only features
+struct BandNode {
+    int4 nb;
+    float4 na;
+    int4 cc;
+    uint4 c0;
+    uint2 c1;
+};
+
+__device__ __forceinline__ BandNode band_node_load(const NodeTables& nt, int v)
+{
+    BandNode q;
+    q.nb = __ldg(&nt.b[v]);
+    q.na = __ldg(&nt.a[v]);
+    q.cc = __ldg(&nt.c[v]);
+    q.c0 = __ldg(&nt.feat[2 * v]);
+    q.c1 = __ldg(reinterpret_cast<const uint2*>(&nt.feat[2 * v + 1]));
+    return q;
+}
+
+__device__ __forceinline__ void band_row_from(const float* __restrict__ xscale, const float* __restrict__ xoff,
+                                              const BandNode& q, int4 rc, float uf, float Lf, float inv_L,
+                                              const float (&xgc)[3], float G, uint32_t (&w)[8], float& fac)
+{
+    // centre of mass in the group's reference frame, as in the walk
+    const float dx = fmaf((float)(q.cc.x - rc.x), uf, q.na.x) - xgc[0];
+    const float dy = fmaf((float)(q.cc.y - rc.y), uf, q.na.y) - xgc[1];
+    const float dz = fmaf((float)(q.cc.z - rc.z), uf, q.na.z) - xgc[2];
+    const float sz = scalbnf(Lf, -(q.nb.w & 255));
+    const float inv_s = scalbnf(inv_L, q.nb.w & 255);  // exact: sides are powers of two
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float ri = rsqrtf(r2);
+    const float Mc = q.na.w;
+    const float f0 = fmaf(dx * inv_s, xscale[0], xoff[0]);
+    const float f1 = fmaf(dy * inv_s, xscale[1], xoff[1]);
+    const float f2 = fmaf(dz * inv_s, xscale[2], xoff[2]);
+    const float f3 = fmaf(ri * sz, xscale[3], xoff[3]);
+    w[0] = pack_bf16(f0, f1);
+    w[1] = pack_bf16(f2, f3);
+    w[2] = q.c0.x;
+    w[3] = q.c0.y;
+    w[4] = q.c0.z;
+    w[5] = q.c0.w;
+    w[6] = q.c1.x;
+    w[7] = q.c1.y;
+    const float ri2 = ri * ri;
+    fac = G * Mc * (sz * sz) * (ri2 * ri2);  // G M s^2 / r^4
+}
+
 __device__ __forceinline__ void band_row(const MlpFrag& m, int v, const NodeTables& nt, int4 rc, float uf, float Lf,
                                          float inv_L, const float (&xgc)[3], float G, uint32_t (&w)[8], float& fac)
 {
-    const int4 nb = __ldg(&nt.b[v]);
-    const float4 na = __ldg(&nt.a[v]);
-    const int4 cc = __ldg(&nt.c[v]);
-    const uint4 c0 = __ldg(&nt.feat[2 * v]);
-    const uint4 c1 = __ldg(&nt.feat[2 * v + 1]);
-    // centre of mass in the group's reference frame, as in the walk
-    const float dx = fmaf((float)(cc.x - rc.x), uf, na.x) - xgc[0];
-    const float dy = fmaf((float)(cc.y - rc.y), uf, na.y) - xgc[1];
-    const float dz = fmaf((float)(cc.z - rc.z), uf, na.z) - xgc[2];
-    const float sz = scalbnf(Lf, -(nb.w & 255));
-    const float inv_s = scalbnf(inv_L, nb.w & 255);  // exact: sides are powers of two
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    const float ri = rsqrtf(r2);
-    const float Mc = na.w;
-    const float f0 = fmaf(dx * inv_s, m.xscale[0], m.xoff[0]);
-    const float f1 = fmaf(dy * inv_s, m.xscale[1], m.xoff[1]);
-    const float f2 = fmaf(dz * inv_s, m.xscale[2], m.xoff[2]);
-    const float f3 = fmaf(ri * sz, m.xscale[3], m.xoff[3]);
-    w[0] = pack_bf16(f0, f1);
-    w[1] = pack_bf16(f2, f3);
-    w[2] = c0.x;
-    w[3] = c0.y;
-    w[4] = c0.z;
-    w[5] = c0.w;
-    w[6] = c1.x;
-    w[7] = c1.y;
-    const float ri2 = ri * ri;
-    fac = G * Mc * (sz * sz) * (ri2 * ri2);  // G M s^2 / r^4
+    band_row_from(m.xscale, m.xoff, band_node_load(nt, v), rc, uf, Lf, inv_L, xgc, G, w, fac);
 }
 
 // rows of the n <= 32 cells pend[0, n) evaluated, label x yscale x factor

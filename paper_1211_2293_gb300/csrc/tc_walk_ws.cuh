@@ -122,7 +122,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
 
 // LEARNED: the producer also records the group's band cells (accepted, two
 // bodies or more, s >= band d) for the network, which runs after the walk
-// (k_band_eval), and the group's box centre
+// (k_band_eval) as (node, group) pairs, and each group's record (box centre
+// and frame)
 template <int B, int TILE, bool PRECISE, bool POT, bool LEARNED>
 __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_ws(WalkArgs a, int stack_cap)
 {
@@ -294,10 +295,14 @@ __global__ void __launch_bounds__(2 * 32 * kWsMaxPairs, B >= 4 ? 1 : 2) k_walk_w
                 fhi[kk] = __shfl_sync(0xffffffffu, fb, kk + 3);
             }
             if (LEARNED && lane == 0) {
-                // the group's box centre, reference-relative (as k_walk forms it)
+                // the group's record: box centre, reference-relative (as
+                // k_walk forms it), and the frame the network's rows need
+                float xc[3];
 #pragma unroll
-                for (int kk = 0; kk < 3; kk++)
-                    a.gcentre[3 * (int64_t)g + kk] = 0.5f * (fmaf(klof[kk], uf, flo[kk]) + fmaf(khif[kk], uf, fhi[kk]));
+                for (int kk = 0; kk < 3; kk++) xc[kk] = 0.5f * (fmaf(klof[kk], uf, flo[kk]) + fmaf(khif[kk], uf, fhi[kk]));
+                a.grec[2 * (int64_t)g] = make_float4(xc[0], xc[1], xc[2], uf);
+                a.grec[2 * (int64_t)g + 1] =
+                    make_float4(__int_as_float(rc.x), __int_as_float(rc.y), __int_as_float(rc.z), Lf);
             }
             if (!take()) {
                 alive = false;
@@ -565,7 +570,7 @@ cudaError_t launch_ws_t(const WalkArgs& a, const WalkConfig& c, int grid, size_t
     // the split walk has no list export, training pairs or quadrupole
     // terms (those run on k_walk); its learned walk records band cells
     if (a.list_cells || a.pair_body) return cudaErrorInvalidValue;
-    if (LEARNED && (!a.band || !a.band_n || !a.gcentre)) return cudaErrorInvalidValue;
+    if (LEARNED && (!a.band || !a.band_n || !a.grec)) return cudaErrorInvalidValue;
     const int pairs = c.warps < 1 ? 1 : (c.warps > kWsMaxPairs ? kWsMaxPairs : c.warps);
     k_walk_ws<B, TILE, PRECISE, POT, LEARNED><<<grid, pairs * 64, smem, s>>>(a, c.stack);
     count_launches(1);
