@@ -1249,7 +1249,12 @@ def run_profile_case(args):
     build: a uniform cube built twice (eager builds; capture the second);
     learned: one learned walk (seeded random network, band 0.5, theta 0.9)
     on a 2^20-body Plummer sphere; quadrupole: one quadrupole walk (theta
-    0.7) on the same sphere; fmm: two FMM passes (theta 0.4) on it."""
+    0.7) on the same sphere; fmm: two FMM passes (theta 0.4) on a Plummer
+    sphere of --n bodies (default 2^20); band: two learned force phases with
+    the network after the walk (split 2: k_band_eval, the same random network,
+    band 0.55, theta 0.667) on a 2^21-body sphere; walk_plummer: two plain
+    force phases of the default line's plain path (2^22, theta 0.62);
+    walk_uniform: two force phases on the uniform cube (2^20, theta 0.5)."""
     import torch
 
     from paper_1211_2293_gb300 import inputs, tc
@@ -1269,6 +1274,37 @@ def run_profile_case(args):
     n = 1 << 20
     p, _, m = inputs.plummer(n, seed=101)
     P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
+    if case in ("walk_plummer", "walk_uniform", "band") or (case == "fmm" and args.n != N_DEFAULT):
+        if case == "walk_uniform":
+            p, _, m = inputs.uniform_cube(1 << 20, SEED)
+        else:
+            p, _, m = inputs.plummer({"fmm": args.n, "band": 1 << 21}.get(case, N_EVAL), seed=101)
+        P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
+        n = p.shape[0]
+    if case in ("walk_plummer", "walk_uniform"):
+        ctx = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
+        ctx.build(P, M, LEAF)
+        th = 0.62 if case == "walk_plummer" else THETA
+        for _ in range(2):
+            ctx.forces(th, EPS)
+        ctx.sync()
+        print(f"{case}: N={n}, theta {th}")
+        ctx.close()
+        return 0
+    if case == "band":
+        ctx = tc.Context(precise=1, quad=1, want_pot=0, verify=0, split=2)
+        ctx.build(P, M, LEAF)
+        rng = np.random.default_rng(0)
+        params = (rng.standard_normal(tc.MLP_NPARAM) * 0.1).astype(np.float32)
+        model = np.concatenate([params, np.zeros(13), np.ones(13), np.full(3, 1e-3)]).astype(np.float32)
+        ctx.mlp_set(model, 0.55)
+        ctx.set_config(learned=1)
+        for _ in range(2):
+            ctx.forces(0.667, EPS)
+        ctx.sync()
+        print(f"band: Plummer N={n}, evaluations {ctx.mlp_evals()}")
+        ctx.close()
+        return 0
     if case == "fmm":
         ctx = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
         ctx.build(P, M, 16)
@@ -1321,7 +1357,8 @@ def main():
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")
     ap.add_argument("--band-train", type=float, default=0.4, help="learned: band of the training pairs")
     ap.add_argument("--nsys", type=int, default=512)
-    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole", "fmm"], default=None,
+    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole", "fmm", "band", "walk_plummer",
+                                               "walk_uniform"], default=None,
                     help="run one small case of a kernel family for an ncu capture and exit")
     args = ap.parse_args()
     if args.warmup < 3:
