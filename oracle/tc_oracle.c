@@ -1342,10 +1342,10 @@ void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cell
 /*   Radii: r_X bounds the distance of X's bodies from c_X: a leaf's    */
 /*     farthest body; above, the farthest child sphere,                 */
 /*     max over children (|c_child - c_X| + r_child).                   */
-/*   Local expansions, second order about c_B: the field at x near B is */
-/*     a(x) = L0 + L1 dx + (1/2) L2 dx dx, dx = x - c_B; L0 a vector,   */
-/*     L1 the field's Jacobian (symmetric), L2 its second derivatives   */
-/*     (a symmetric 3-index tensor).                                    */
+/*   Local expansions, third order about c_B: the field at x near B is  */
+/*     a(x) = L0 + L1 dx + (1/2) L2 dx dx + (1/6) L3 dx dx dx,           */
+/*     dx = x - c_B; L0 a vector, L1 the field's Jacobian (symmetric),   */
+/*     L2 and L3 its second and third derivatives (symmetric tensors).   */
 /*   Acceptance of a pair of disjoint cells: r_A + r_B < theta |c_A - c_B|*/
 /*     (the spheres about the centres, shrunk by theta, are disjoint);  */
 /*     a pair within 1e-6 relative of the bound is counted (ties).      */
@@ -1363,10 +1363,16 @@ void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cell
 /*     L1_ij += G M (3 d_i d_j / rho^5 - delta_ij / rho^3)               */
 /*     L2_ijk += G M (15 d_i d_j d_k / rho^7                             */
 /*               - 3 (delta_ij d_k + delta_ik d_j + delta_jk d_i) / rho^5)*/
-/*   L2L, parents before children, t = c_c - c_p:                        */
-/*     L0_c += L0_p + L1_p t + (1/2) L2_p t t, L1_c += L1_p + L2_p t,    */
-/*     L2_c += L2_p.                                                     */
-/*   L2P: a_i += L0 + L1 dx + (1/2) L2 dx dx over a leaf's bodies.        */
+/*     L3_ijkl += G M (105 d_i d_j d_k d_l / rho^9                       */
+/*               - 15 (the 6 terms delta_ab d_c d_e) / rho^7             */
+/*               + 3 (the 3 terms delta_ab delta_ce) / rho^5)            */
+/*   L2L, parents before children, t = c_c - c_p: each coefficient       */
+/*     gains its parent's Taylor series moved by t:                      */
+/*     L0_c += L0_p + L1_p t + (1/2) L2_p t t + (1/6) L3_p t t t,        */
+/*     L1_c += L1_p + L2_p t + (1/2) L3_p t t, L2_c += L2_p + L3_p t,    */
+/*     L3_c += L3_p.                                                     */
+/*   L2P: a_i += L0 + L1 dx + (1/2) L2 dx dx + (1/6) L3 dx dx dx over a   */
+/*     leaf's bodies.                                                    */
 /*   P2P(A -> B): a_i += G m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^1.5,*/
 /*     i in B, j in A, j != i.                                           */
 /* Every ordered pair of bodies is reached through exactly one M2L or    */
@@ -1375,7 +1381,7 @@ void or_tree_group_list(const or_tree *t, double theta, int64_t g, int64_t *cell
 typedef struct {
     const or_tree *t;
     double theta, eps2, G;
-    double *L0, *L1, *L2; /* M x 3, M x 9, M x 27 (full index ranges) */
+    double *L0, *L1, *L2, *L3; /* M x 3, M x 9, M x 27, M x 81 (full index ranges) */
     double *rad;     /* M: radius about the centre of mass */
     double *acc;     /* sorted order, n x 3 */
     int64_t n_m2l, n_p2p, ties;
@@ -1431,6 +1437,19 @@ static void fmm_m2l(fmm_t *f, int64_t A, int64_t B)
     double ri3 = ri * ri * ri, ri5 = ri3 * ri * ri;
     double gm = f->G * t->mass[A];
     double ri7 = ri5 * ri * ri;
+    double ri9 = ri7 * ri * ri;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            for (int c = 0; c < 3; c++)
+                for (int e = 0; e < 3; e++) {
+                    const double dd = (a == b ? d[c] * d[e] : 0.0) + (a == c ? d[b] * d[e] : 0.0) +
+                                      (a == e ? d[b] * d[c] : 0.0) + (b == c ? d[a] * d[e] : 0.0) +
+                                      (b == e ? d[a] * d[c] : 0.0) + (c == e ? d[a] * d[b] : 0.0);
+                    const double d2 = (a == b && c == e ? 1.0 : 0.0) + (a == c && b == e ? 1.0 : 0.0) +
+                                      (a == e && b == c ? 1.0 : 0.0);
+                    f->L3[81 * B + 27 * a + 9 * b + 3 * c + e] +=
+                        gm * (105.0 * d[a] * d[b] * d[c] * d[e] * ri9 - 15.0 * dd * ri7 + 3.0 * d2 * ri5);
+                }
     for (int a = 0; a < 3; a++) {
         f->L0[3 * B + a] += gm * d[a] * ri3;
         for (int b = 0; b < 3; b++) {
@@ -1554,6 +1573,7 @@ void or_fmm_nodes(const or_tree *t, double theta, double eps, double G, double *
     f.L0 = (double *)calloc((size_t)t->M * 3, sizeof(double));
     f.L1 = (double *)calloc((size_t)t->M * 9, sizeof(double));
     f.L2 = (double *)calloc((size_t)t->M * 27, sizeof(double));
+    f.L3 = (double *)calloc((size_t)t->M * 81, sizeof(double));
     f.acc = (double *)calloc((size_t)t->n * 3, sizeof(double));
     f.rad = (double *)calloc((size_t)t->M, sizeof(double));
     or_fmm_radii(t, f.rad);
@@ -1568,17 +1588,29 @@ void or_fmm_nodes(const or_tree *t, double theta, double eps, double G, double *
             double s = f.L0[3 * p + a];
             for (int b = 0; b < 3; b++) {
                 s += f.L1[9 * p + 3 * a + b] * dc[b];
-                for (int c = 0; c < 3; c++)
+                for (int c = 0; c < 3; c++) {
                     s += 0.5 * f.L2[27 * p + 9 * a + 3 * b + c] * dc[b] * dc[c];
+                    for (int e = 0; e < 3; e++)
+                        s += f.L3[81 * p + 27 * a + 9 * b + 3 * c + e] * dc[b] * dc[c] * dc[e] / 6.0;
+                }
             }
             f.L0[3 * v + a] += s;
             for (int b = 0; b < 3; b++) {
                 double u = f.L1[9 * p + 3 * a + b];
-                for (int c = 0; c < 3; c++)
+                for (int c = 0; c < 3; c++) {
                     u += f.L2[27 * p + 9 * a + 3 * b + c] * dc[c];
+                    for (int e = 0; e < 3; e++)
+                        u += 0.5 * f.L3[81 * p + 27 * a + 9 * b + 3 * c + e] * dc[c] * dc[e];
+                }
                 f.L1[9 * v + 3 * a + b] += u;
-                for (int c = 0; c < 3; c++)
-                    f.L2[27 * v + 9 * a + 3 * b + c] += f.L2[27 * p + 9 * a + 3 * b + c];
+                for (int c = 0; c < 3; c++) {
+                    double w = f.L2[27 * p + 9 * a + 3 * b + c];
+                    for (int e = 0; e < 3; e++)
+                        w += f.L3[81 * p + 27 * a + 9 * b + 3 * c + e] * dc[e];
+                    f.L2[27 * v + 9 * a + 3 * b + c] += w;
+                    for (int e = 0; e < 3; e++)
+                        f.L3[81 * v + 27 * a + 9 * b + 3 * c + e] += f.L3[81 * p + 27 * a + 9 * b + 3 * c + e];
+                }
             }
         }
     }
@@ -1594,8 +1626,11 @@ void or_fmm_nodes(const or_tree *t, double theta, double eps, double G, double *
                 double s = f.L0[3 * v + a];
                 for (int b = 0; b < 3; b++) {
                     s += f.L1[9 * v + 3 * a + b] * dx[b];
-                    for (int c = 0; c < 3; c++)
+                    for (int c = 0; c < 3; c++) {
                         s += 0.5 * f.L2[27 * v + 9 * a + 3 * b + c] * dx[b] * dx[c];
+                        for (int e = 0; e < 3; e++)
+                            s += f.L3[81 * v + 27 * a + 9 * b + 3 * c + e] * dx[b] * dx[c] * dx[e] / 6.0;
+                    }
                 }
                 f.acc[3 * i + a] += s;
             }
@@ -1623,5 +1658,6 @@ void or_fmm_nodes(const or_tree *t, double theta, double eps, double G, double *
     free(f.L0);
     free(f.L1);
     free(f.L2);
+    free(f.L3);
     free(f.acc);
 }

@@ -175,7 +175,7 @@ int64_t or_tree_learned_bf16(const or_tree *t, double theta, double eps, double 
                              double *corr, double *crad, int32_t *flag);
 
 /* Fast multipole method on the same tree (a reading of Sec. 5, stated in
- * tc_oracle.c): monopoles at the cells' centres of mass, second-order local
+ * tc_oracle.c): monopoles at the cells' centres of mass, third-order local
  * expansions, pair acceptance r_A + r_B < theta |c_A - c_B| (r_X: the
  * cell's radius about its centre of mass, or_fmm_radii), dual traversal,
  * M2L / L2L / L2P and P2P between leaves.  acc (n x 3, original order);

@@ -1,6 +1,6 @@
 """Pins of the oracle's fast multipole method (a reading of the paper's
 Sec. 5, stated in oracle/tc_oracle.c): monopoles at cell centres of mass,
-second-order local expansions (the field, its Jacobian and its second
+third-order local expansions (the field, its Jacobian, its second and third
 derivatives), pair acceptance r_A + r_B < theta |c_A - c_B| with r_X the
 cell's radius about its centre of mass, dual traversal, M2L / L2L / L2P and
 P2P.
@@ -16,10 +16,10 @@ P2P.
   then equals the direct sum at any theta, which fails if the traversal
   drops or repeats a pair of bodies.
 * A far source acting on a small cluster: the local expansion's error falls
-  like (cluster size)^3 / distance^5, a third-order remainder of a field
-  falling like distance^-2 (Jacobian and second derivatives right); a
-  missing or wrong second-derivative term would leave distance^-4, a
-  missing or wrong Jacobian distance^-3.
+  like (cluster size)^4 / distance^6, a fourth-order remainder of a field
+  falling like distance^-2 (every derivative term right); a missing or
+  wrong third-derivative term would leave distance^-5, a second-derivative
+  one distance^-4, the Jacobian distance^-3.
 """
 import numpy as np
 
@@ -82,7 +82,7 @@ def test_every_pair_once_linear_field_limit():
         assert _rel(a, ad).max() <= 1e-5, theta
 
 
-def test_local_expansion_second_order():
+def test_local_expansion_third_order():
     rng = np.random.default_rng(5)
     cluster = (rng.standard_normal((8, 3)) * 0.02).astype(np.float32)
     direction = np.array([1.0, 0.3, 0.2]) / np.linalg.norm([1.0, 0.3, 0.2])
@@ -98,12 +98,12 @@ def test_local_expansion_second_order():
         # (exact), so the FMM error is the local expansion's
         ad, _ = oracle.direct(p, m, 1e-4, want_pot=False)
         errs.append(np.abs(a[:8] - ad[:8]).max())
-    # the far field is G M / D^2; the first term a second-order expansion
-    # drops is (cluster size)^3 G M / D^5, so each doubling of D divides the
-    # error by 32 -- by 16 if the second derivatives were missing or wrong,
-    # by 8 without the Jacobian
+    # the far field is G M / D^2; the first term a third-order expansion
+    # drops is (cluster size)^4 G M / D^6, so each doubling of D divides the
+    # error by 64 -- by 32 if the third derivatives were missing or wrong,
+    # 16 without the second, 8 without the Jacobian
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
-    assert 24.0 < r1 < 40.0 and 24.0 < r2 < 40.0, errs
+    assert 48.0 < r1 < 80.0 and 48.0 < r2 < 80.0, errs
 
 
 def test_error_shrinks_with_theta():
