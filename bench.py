@@ -1109,7 +1109,7 @@ def fmm_summary(args, local_rank, nsample=4096, reps=7):
                          "bodies_per_s": n / (mp / 1e3), "interactions_per_body": inter / n},
             "fmm_over_treecode": mp / mf,
             "what": "force phase alone (library events around the FMM passes / the walk + force kernel), tree built "
-                    "once; acceptance r_A + r_B < theta |c_A - c_B|, monopole sources, second-order local expansions"}
+                    "once; acceptance r_A + r_B < theta |c_A - c_B|, monopole sources, third-order local expansions"}
 
 
 def run_precision(args, rank, world, local_rank):

@@ -265,22 +265,27 @@ int tc_direct_static(const float *pos, const float *mass, int64_t n, const int64
  * implemented):
  *   expansion centres  every cell's centre of mass c_X (the build's FP64
  *                      reduction); its multipole is the monopole M_X;
- *   local expansions   second order about c_B: near B the field is
- *                      a(x) = L0 + L1 dx + (1/2) L2 dx dx, dx = x - c_B,
- *                      with L1 the field's Jacobian and L2 its second
- *                      derivatives (FP32, symmetric storage);
- *   acceptance         distinct cells A, B with s_A + s_B < theta |c_A - c_B|
- *                      (s the cube side), tested in FP32;
+ *   radii              r_X bounds the distance of X's bodies from c_X: a
+ *                      leaf's farthest body, above the farthest child
+ *                      sphere, max over children of |c_child - c_X| +
+ *                      r_child (FP64, rounded to FP32 for the test);
+ *   local expansions   third order about c_B: near B the field is
+ *                      a(x) = L0 + L1 dx + (1/2) L2 dx dx + (1/6) L3 dx dx dx,
+ *                      dx = x - c_B, L1 the field's Jacobian, L2 and L3 its
+ *                      second and third derivatives (FP32, symmetric
+ *                      storage);
+ *   acceptance         distinct cells A, B with r_A + r_B < theta |c_A - c_B|,
+ *                      tested in FP32;
  *   traversal          dual, from (root, root): a cell paired with itself
  *                      splits into every (child, child) pair (a leaf: P2P
  *                      within it); an accepted pair is an M2L from A to B;
  *                      two leaves are a P2P; otherwise B is split when it is
- *                      internal and (A is a leaf or s_B >= s_A), else A;
+ *                      internal and (A is a leaf or r_B >= r_A), else A;
  *   M2L (A -> B)       the Plummer-softened field G M_A d / rho^3 of A's
  *                      monopole, d = c_A - c_B, rho^2 = |d|^2 + eps^2, and
- *                      its first two derivatives, added to L(B);
+ *                      its first three derivatives, added to L(B);
  *   L2L                parents before children: L(child) += L(parent)
- *                      moved to the child's centre (exact for a quadratic);
+ *                      moved to the child's centre (exact for a cubic);
  *   L2P, P2P           every body of a leaf gets its leaf's expansion and
  *                      the softened direct sum over the bodies of every leaf
  *                      P2P-paired with it (compensated FP32 summation).

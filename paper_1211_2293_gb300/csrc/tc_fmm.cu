@@ -3,9 +3,9 @@
 // reading built here is stated in full in include/tc.h beside tc_ctx_fmm).
 //
 // Every cell carries a monopole at its centre of mass (the build's FP64
-// reduction) and gets a second-order local expansion about it: the field
-// L0, its Jacobian L1 (symmetric, 6 numbers) and its second derivatives L2
-// (symmetric, 10 numbers).  The dual traversal decides which ordered pairs of
+// reduction) and gets a third-order local expansion about it: the field L0,
+// its Jacobian L1 (symmetric, 6 numbers), its second and third derivatives
+// L2 and L3 (symmetric, 10 and 15 numbers).  The dual traversal decides which ordered pairs of
 // cells interact through expansions (M2L) and which pairs of leaves
 // directly (P2P): from (root, root), a pair of a cell with itself splits into
 // all pairs of its children; a pair of distinct cells is accepted when
@@ -41,15 +41,69 @@ namespace {
 constexpr int kFmmWarps = 4;
 constexpr int kFmmStack = 2048;  // refinement stack per warp (shared memory)
 constexpr int kFmmTile = 128;
-constexpr int kFmmBlocksPerSm = 5;
-constexpr int kLocW = 20;        // floats per local expansion: L0 3, L1 6, L2 10, one spare
+constexpr int kFmmBlocksPerSm = 4;
+constexpr int kLocW = 36;        // floats per local expansion: L0 3, L1 6, L2 10, L3 15, two spare
 
-// Symmetric storage: L1 as (00 01 02 11 12 22), L2 as
-// (000 001 002 011 012 022 111 112 122 222).
+// Symmetric storage of the expansion's coefficients: a sorted index tuple
+// is stored once, in lexicographic order -- L1 (00 01 02 11 12 22), L2
+// (000 001 ... 222, 10 entries), L3 (0000 ... 2222, 15 entries).  The
+// positions are pure arithmetic on the indices, so in the unrolled loops
+// below every one folds to a constant (the coefficients stay in registers).
+__host__ __device__ constexpr int mn(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int mx(int a, int b) { return a < b ? b : a; }
+// sorted pair x <= y over the alphabet 0..n-1
+__host__ __device__ constexpr int si2n(int x, int y, int n) { return x * n - x * (x - 1) / 2 + (y - x); }
+// sorted triples over 0..n-1 whose first element is below x
+__host__ __device__ constexpr int off3n(int x, int n)
+{
+    return x == 0 ? 0 : (x == 1 ? n * (n + 1) / 2 : n * (n + 1) / 2 + (n - 1) * n / 2);
+}
+__host__ __device__ constexpr int si3s(int a, int b, int c, int n) { return off3n(a, n) + si2n(b - a, c - a, n - a); }
+__host__ __device__ constexpr int si2(int i, int j) { return si2n(mn(i, j), mx(i, j), 3); }
+__host__ __device__ constexpr int si3(int i, int j, int k)
+{
+    return si3s(mn(mn(i, j), k), i + j + k - mn(mn(i, j), k) - mx(mx(i, j), k), mx(mx(i, j), k), 3);
+}
+__host__ __device__ constexpr int si4(int i, int j, int k, int l)
+{
+    // a four-element sorting network: the extremes, then the middle pair
+    return (mn(mn(i, j), mn(k, l)) == 0 ? 0 : (mn(mn(i, j), mn(k, l)) == 1 ? 10 : 14)) +
+           si3s(mn(mx(mn(i, j), mn(k, l)), mn(mx(i, j), mx(k, l))) - mn(mn(i, j), mn(k, l)),
+                mx(mx(mn(i, j), mn(k, l)), mn(mx(i, j), mx(k, l))) - mn(mn(i, j), mn(k, l)),
+                mx(mx(i, j), mx(k, l)) - mn(mn(i, j), mn(k, l)), 3 - mn(mn(i, j), mn(k, l)));
+}
+static_assert(si2(2, 1) == 4 && si3(2, 0, 1) == 4 && si3(2, 1, 1) == 7 && si4(0, 1, 1, 2) == 7 &&
+                  si4(2, 1, 2, 1) == 12 && si4(2, 2, 1, 2) == 13 && si4(2, 2, 2, 2) == 14 && si4(1, 0, 0, 0) == 1,
+              "symmetric storage positions");
+
+__device__ __forceinline__ float ipow(float x, int n)  // n in [0, 4], a constant after unrolling
+{
+    return n == 0 ? 1.f : (n == 1 ? x : (n == 2 ? x * x : (n == 3 ? x * x * x : (x * x) * (x * x))));
+}
+
+// the monomials of an offset t over the sorted pairs and triples
+__device__ __forceinline__ void monomials(const float (&t)[3], float (&t2)[6], float (&t3)[10])
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) t2[si2(i, j)] = t[i] * t[j];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++)
+#pragma unroll
+            for (int k = j; k < 3; k++) t3[si3(i, j, k)] = t2[si2(i, j)] * t[k];
+}
+
+// The Taylor series of the field about a cell's centre to third order:
+// a(c + t) = L0 + L1 t + (1/2) L2 t t + (1/6) L3 t t t (L1 the Jacobian,
+// L2, L3 the second and third derivatives).
 struct Loc {
     float l0[3];
     float l1[6];
     float l2[10];
+    float l3[15];
     __device__ void zero()
     {
 #pragma unroll
@@ -58,12 +112,20 @@ struct Loc {
         for (int k = 0; k < 6; k++) l1[k] = 0.f;
 #pragma unroll
         for (int k = 0; k < 10; k++) l2[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 15; k++) l3[k] = 0.f;
     }
     // M2L: the softened field of mass gm (G M) seen from d = c_A - c_B and
-    // its first two derivatives with respect to the evaluation point:
-    //   L0_i   += gm d_i / rho^3
-    //   L1_ij  += gm (3 d_i d_j / rho^5 - delta_ij / rho^3)
-    //   L2_ijk += gm (15 d_i d_j d_k / rho^7 - 3 (delta_ij d_k + delta_ik d_j + delta_jk d_i) / rho^5)
+    // its first three derivatives with respect to the evaluation point:
+    //   L0_i    += gm d_i / rho^3
+    //   L1_ij   += gm (3 d_i d_j / rho^5 - delta_ij / rho^3)
+    //   L2_ijk  += gm (15 d_i d_j d_k / rho^7 - 3 (delta_ij d_k + delta_ik d_j + delta_jk d_i) / rho^5)
+    //   L3_ijkl += gm (105 d_i d_j d_k d_l / rho^9 - 15 (6 terms delta d d) / rho^7
+    //                  + 3 (3 terms delta delta) / rho^5)
+    // For an L3 entry with axis counts (a, b, c) the six delta d d terms sum
+    // to C(a,2) x^(a-2) y^b z^c + C(b,2) ... + C(c,2) ..., the three delta
+    // delta terms to 3 for (4, 0, 0) and its permutations, 1 for (2, 2, 0)
+    // and its permutations, 0 otherwise.
     __device__ void add_monopole(float gm, float dx, float dy, float dz, float eps2)
     {
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
@@ -72,6 +134,7 @@ struct Loc {
         const float g3 = gm * ri * ri2;
         const float g5 = g3 * ri2;
         const float g7 = g5 * ri2;
+        const float g9 = g7 * ri2;
         l0[0] = fmaf(g3, dx, l0[0]);
         l0[1] = fmaf(g3, dy, l0[1]);
         l0[2] = fmaf(g3, dz, l0[2]);
@@ -94,31 +157,110 @@ struct Loc {
         l2[7] += fmaf(ay * dy, dz, -t5 * dz);
         l2[8] += fmaf(ay * dz, dz, -t5 * dy);
         l2[9] += fmaf(az * dz, dz, -3.f * t5 * dz);
+        const float h9 = 105.f * g9, m7 = -15.f * g7;
+        // the L3 entries in storage order: axis counts (ca, cb, cc), ca
+        // falling, then cb falling
+        int k = 0;
+#pragma unroll
+        for (int ca = 4; ca >= 0; ca--)
+#pragma unroll
+            for (int cb = 4 - ca; cb >= 0; cb--) {
+                const int cc = 4 - ca - cb;
+                const float P = ipow(dx, ca) * ipow(dy, cb) * ipow(dz, cc);
+                float S6 = 0.f;
+                if (ca >= 2) S6 += (float)(ca * (ca - 1) / 2) * ipow(dx, ca - 2) * ipow(dy, cb) * ipow(dz, cc);
+                if (cb >= 2) S6 += (float)(cb * (cb - 1) / 2) * ipow(dx, ca) * ipow(dy, cb - 2) * ipow(dz, cc);
+                if (cc >= 2) S6 += (float)(cc * (cc - 1) / 2) * ipow(dx, ca) * ipow(dy, cb) * ipow(dz, cc - 2);
+                const int S3 = (ca == 4 || cb == 4 || cc == 4) ? 3
+                               : ((ca == 2 && cb == 2) || (ca == 2 && cc == 2) || (cb == 2 && cc == 2)) ? 1 : 0;
+                l3[k] += fmaf(h9, P, fmaf(m7, S6, (float)(3 * S3) * g5));
+                k++;
+            }
     }
-    // sum_j L1_ij t_j
-    __device__ float l1t(int i, float tx, float ty, float tz) const
+    // the field of the series at offset t from its centre (L2P, and the L0
+    // part of L2L): L0 + L1 t + (1/2) L2 t t + (1/6) L3 t t t, each sum over
+    // the sorted index tuples with their multiplicities
+    __device__ void eval(const float (&t)[3], const float (&t2)[6], const float (&t3)[10], float (&o)[3]) const
     {
-        const int a = i == 0 ? 0 : (i == 1 ? 1 : 2), b = i == 0 ? 1 : (i == 1 ? 3 : 4), c = i == 0 ? 2 : (i == 1 ? 4 : 5);
-        return fmaf(l1[a], tx, fmaf(l1[b], ty, l1[c] * tz));
+        eval_series(l0, l1, l2, l3, t, t2, t3, o);
     }
-    // sum_jk L2_ijk t_j t_k
-    __device__ float l2tt(int i, float tx, float ty, float tz) const
+    // the same for any storage of the 34 coefficients (registers, or the
+    // parent's record read in place)
+    template <typename A0, typename A1, typename A2, typename A3>
+    __device__ static void eval_series(const A0& l0, const A1& l1, const A2& l2, const A3& l3, const float (&t)[3],
+                                       const float (&t2)[6], const float (&t3)[10], float (&o)[3])
     {
-        int k00, k11, k22, k01, k02, k12;
-        if (i == 0) { k00 = 0; k11 = 3; k22 = 5; k01 = 1; k02 = 2; k12 = 4; }
-        else if (i == 1) { k00 = 1; k11 = 6; k22 = 8; k01 = 3; k02 = 4; k12 = 7; }
-        else { k00 = 2; k11 = 7; k22 = 9; k01 = 4; k02 = 5; k12 = 8; }
-        const float sq = fmaf(l2[k00], tx * tx, fmaf(l2[k11], ty * ty, l2[k22] * tz * tz));
-        const float cr = fmaf(l2[k01], tx * ty, fmaf(l2[k02], tx * tz, l2[k12] * ty * tz));
-        return fmaf(2.f, cr, sq);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            float s = l0[i];
+#pragma unroll
+            for (int j = 0; j < 3; j++) s = fmaf(l1[si2(i, j)], t[j], s);
+            float s2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+#pragma unroll
+                for (int k = j; k < 3; k++) s2 = fmaf((float)(j == k ? 1 : 2) * l2[si3(i, j, k)], t2[si2(j, k)], s2);
+            float s3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+#pragma unroll
+                for (int k = j; k < 3; k++)
+#pragma unroll
+                    for (int m = k; m < 3; m++) {
+                        const int mult = (j == k && k == m) ? 1 : ((j == k || k == m) ? 3 : 6);
+                        s3 = fmaf((float)mult * l3[si4(i, j, k, m)], t3[si3(j, k, m)], s3);
+                    }
+            o[i] = s + 0.5f * s2 + (1.f / 6.f) * s3;
+        }
     }
-    // the field of the expansion at offset t from its centre (L2P, and the
-    // L0 part of L2L): L0 + L1 t + (1/2) L2 t t
-    __device__ void eval(float tx, float ty, float tz, float& ax, float& ay, float& az) const
+    // this += parent's series moved to offset t (L2L):
+    //   L0 += L0p + L1p t + (1/2) L2p t t + (1/6) L3p t t t
+    //   L1 += L1p + L2p t + (1/2) L3p t t,  L2 += L2p + L3p t,  L3 += L3p
+    // (the parent's record q: L0 at q[0..3), L1 at q[3..9), L2 at q[9..19),
+    // L3 at q[19..34), read where it is)
+    __device__ void add_shifted(const float* __restrict__ q, const float (&t)[3])
     {
-        ax = l0[0] + l1t(0, tx, ty, tz) + 0.5f * l2tt(0, tx, ty, tz);
-        ay = l0[1] + l1t(1, tx, ty, tz) + 0.5f * l2tt(1, tx, ty, tz);
-        az = l0[2] + l1t(2, tx, ty, tz) + 0.5f * l2tt(2, tx, ty, tz);
+        struct P {
+            const float* b;
+            __device__ float operator[](int k) const { return __ldg(b + k); }
+        };
+        const P p0{q}, p1{q + 3}, p2{q + 9}, p3{q + 19};
+        struct {
+            P l1, l2, l3;
+        } p{p1, p2, p3};
+        float t2[6], t3[10];
+        monomials(t, t2, t3);
+        float s[3];
+        eval_series(p0, p.l1, p.l2, p.l3, t, t2, t3, s);
+#pragma unroll
+        for (int i = 0; i < 3; i++) l0[i] += s[i];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = i; j < 3; j++) {
+                float u = p.l1[si2(i, j)];
+#pragma unroll
+                for (int m = 0; m < 3; m++) u = fmaf(p.l2[si3(i, j, m)], t[m], u);
+                float w = 0.f;
+#pragma unroll
+                for (int m = 0; m < 3; m++)
+#pragma unroll
+                    for (int n = m; n < 3; n++) w = fmaf((float)(m == n ? 1 : 2) * p.l3[si4(i, j, m, n)], t2[si2(m, n)], w);
+                l1[si2(i, j)] += fmaf(0.5f, w, u);
+            }
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = i; j < 3; j++)
+#pragma unroll
+                for (int m = j; m < 3; m++) {
+                    float u = p.l2[si3(i, j, m)];
+#pragma unroll
+                    for (int n = 0; n < 3; n++) u = fmaf(p.l3[si4(i, j, m, n)], t[n], u);
+                    l2[si3(i, j, m)] += u;
+                }
+#pragma unroll
+        for (int k = 0; k < 15; k++) l3[k] += p.l3[k];
     }
 };
 
@@ -450,35 +592,18 @@ __global__ void __launch_bounds__(kFmmWarps * 32, kFmmBlocksPerSm) k_fmm_level(F
             for (int k = 0; k < 10; k++)
 #pragma unroll
                 for (int o = 16; o; o >>= 1) L.l2[k] += __shfl_xor_sync(0xffffffffu, L.l2[k], o);
-            // plus the parent's expansion moved to this centre (L2L):
-            // L0 += L0p + L1p t + (1/2) L2p t t, L1 += L1p + L2p t, L2 += L2p
+#pragma unroll
+            for (int k = 0; k < 15; k++)
+#pragma unroll
+                for (int o = 16; o; o >>= 1) L.l3[k] += __shfl_xor_sync(0xffffffffu, L.l3[k], o);
+            // plus the parent's expansion moved to this centre (L2L)
             if (P >= 0) {
-                Loc Lp;
                 const float* q = a.loc + (int64_t)P * kLocW;
-#pragma unroll
-                for (int k = 0; k < 3; k++) Lp.l0[k] = q[k];
-#pragma unroll
-                for (int k = 0; k < 6; k++) Lp.l1[k] = q[3 + k];
-#pragma unroll
-                for (int k = 0; k < 10; k++) Lp.l2[k] = q[9 + k];
                 const float4 pa = nt.a[P];
                 const int4 pc = nt.c[P];
-                const float tx = fmaf((float)(bc.x - pc.x), uf, ba.x - pa.x);
-                const float ty = fmaf((float)(bc.y - pc.y), uf, ba.y - pa.y);
-                const float tz = fmaf((float)(bc.z - pc.z), uf, ba.z - pa.z);
-                float sx, sy, sz;
-                Lp.eval(tx, ty, tz, sx, sy, sz);
-                L.l0[0] += sx;
-                L.l0[1] += sy;
-                L.l0[2] += sz;
-                L.l1[0] += Lp.l1[0] + fmaf(Lp.l2[0], tx, fmaf(Lp.l2[1], ty, Lp.l2[2] * tz));
-                L.l1[1] += Lp.l1[1] + fmaf(Lp.l2[1], tx, fmaf(Lp.l2[3], ty, Lp.l2[4] * tz));
-                L.l1[2] += Lp.l1[2] + fmaf(Lp.l2[2], tx, fmaf(Lp.l2[4], ty, Lp.l2[5] * tz));
-                L.l1[3] += Lp.l1[3] + fmaf(Lp.l2[3], tx, fmaf(Lp.l2[6], ty, Lp.l2[7] * tz));
-                L.l1[4] += Lp.l1[4] + fmaf(Lp.l2[4], tx, fmaf(Lp.l2[7], ty, Lp.l2[8] * tz));
-                L.l1[5] += Lp.l1[5] + fmaf(Lp.l2[5], tx, fmaf(Lp.l2[8], ty, Lp.l2[9] * tz));
-#pragma unroll
-                for (int k = 0; k < 10; k++) L.l2[k] += Lp.l2[k];
+                const float t[3] = {fmaf((float)(bc.x - pc.x), uf, ba.x - pa.x), fmaf((float)(bc.y - pc.y), uf, ba.y - pa.y),
+                                    fmaf((float)(bc.z - pc.z), uf, ba.z - pa.z)};
+                L.add_shifted(q, t);
             }
             if (r == 0 && lane == 0) {
                 float* o = a.loc + B * kLocW;
@@ -488,6 +613,8 @@ __global__ void __launch_bounds__(kFmmWarps * 32, kFmmBlocksPerSm) k_fmm_level(F
                 for (int k = 0; k < 6; k++) o[3 + k] = L.l1[k];
 #pragma unroll
                 for (int k = 0; k < 10; k++) o[9 + k] = L.l2[k];
+#pragma unroll
+                for (int k = 0; k < 15; k++) o[19 + k] = L.l3[k];
             }
             if (!leafB) {
                 // the unresolved candidates, from the slab to the pool
@@ -519,8 +646,11 @@ __global__ void __launch_bounds__(kFmmWarps * 32, kFmmBlocksPerSm) k_fmm_level(F
                 const float ox = (float)((double)me.x - cx) - ba.x;
                 const float oy = (float)((double)me.y - cy) - ba.y;
                 const float oz = (float)((double)me.z - cz) - ba.z;
-                float lx, ly, lz;
-                L.eval(ox, oy, oz, lx, ly, lz);
+                const float ot[3] = {ox, oy, oz};
+                float ot2[6], ot3[10], lo[3];
+                monomials(ot, ot2, ot3);
+                L.eval(ot, ot2, ot3, lo);
+                const float lx = lo[0], ly = lo[1], lz = lo[2];
                 const int64_t o = a.perm[bb.x + ib];
                 a.acc[3 * o + 0] = fmaf(a.G, fx, lx);
                 a.acc[3 * o + 1] = fmaf(a.G, fy, ly);

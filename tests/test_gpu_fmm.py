@@ -1,5 +1,5 @@
 """GPU fast multipole method (tc_ctx_fmm) vs the oracle's FMM (a reading of
-Sec. 5: monopoles at centres of mass, second-order local expansions, pair
+Sec. 5: monopoles at centres of mass, third-order local expansions, pair
 acceptance r_A + r_B < theta |c_A - c_B| with r_X the cell's radius about its
 centre of mass, dual traversal, M2L / L2L / L2P, P2P), through the C ABI.
 
