@@ -139,8 +139,8 @@ struct tc_ctx {
     int64_t* fmm_off = nullptr;
     int32_t* fmm_cnt = nullptr;
     unsigned long long* fmm_rec = nullptr;  // 4 per node
-    double* fmm_rad = nullptr;               // acceptance radii (FP64, FP32)
-    float* fmm_radf = nullptr;
+    double* fmm_rad = nullptr;               // acceptance radii (FP64)
+    int4* fmm_fnode = nullptr;               // 3 per node: the FMM's gathered cell records
     int64_t fmm_cap_m = 0;
     int32_t* fmm_pool[2] = {nullptr, nullptr};
     int64_t fmm_pool_cap = 0;
@@ -1080,7 +1080,7 @@ int tc_ctx_fmm(tc_ctx* c, float theta, float eps, float G)
         TC_GROW(c, c->fmm_cnt, c->cap_m);
         TC_GROW(c, c->fmm_rec, 4 * c->cap_m);
         TC_GROW(c, c->fmm_rad, c->cap_m);
-        TC_GROW(c, c->fmm_radf, c->cap_m);
+        TC_GROW(c, c->fmm_fnode, 3 * c->cap_m);
         c->fmm_cap_m = c->cap_m;
     }
     if (!c->fmm_ctr) TC_GROW(c, c->fmm_ctr, 8);
@@ -1139,7 +1139,7 @@ int tc_ctx_fmm(tc_ctx* c, float theta, float eps, float G)
         p.ctr = c->fmm_ctr;
         p.rec = c->fmm_rec;
         p.rad = c->fmm_rad;
-        p.radf = c->fmm_radf;
+        p.fnode = c->fmm_fnode;
         p.records = c->cfg.verify;
         p.acc = c->acc;
         p.theta = theta;

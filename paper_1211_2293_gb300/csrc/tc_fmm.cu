@@ -28,7 +28,10 @@
 // force loop, and the slices are added at the end.
 //
 // Radii are FP64 (a bottom-up pass per level, leaves from their bodies,
-// cells from their children's spheres), rounded to FP32 for the test.  The
+// cells from their children's spheres), rounded to FP32 for the test; the
+// same pass gathers each cell's walk record (centre of mass, cube centre,
+// radius, body and child ranges) into one 48-byte run, one gather per
+// candidate.  The
 // acceptance test runs in FP32 on cell-relative values (integer cube centres
 // in units of h/2 plus the float offset of each centre of mass from its cube
 // centre), as the treecode walk does.
@@ -284,7 +287,7 @@ struct FmmArgs {
     int32_t* near_cnt;
     float* acc;              // n x 3, original order
     unsigned long long* rec; // per node: M2L pairs, P2P pairs, their hashes (target = the node)
-    const float* radf;       // per node: r_X rounded to FP32
+    const int4* fnode;       // per node, 3 entries: {com offset, mass}, {cube centre, r_X (FP32 bits)}, b
     int records;             // keep the pair-set hashes and the per-node records
     float theta2, eps2, G;
 };
@@ -328,7 +331,7 @@ struct P2PSum {
 // r_X for the cells [start, end) of one level (FP64): a leaf's farthest
 // body from its centre of mass, above, the farthest child sphere
 __global__ void k_fmm_radius(const float4* __restrict__ body, NodeTables nt, double* __restrict__ rad,
-                             float* __restrict__ radf, int64_t start, int64_t end)
+                             int4* __restrict__ fnode, int64_t start, int64_t end)
 {
     for (int64_t v = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < end;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -350,7 +353,12 @@ __global__ void k_fmm_radius(const float4* __restrict__ body, NodeTables nt, dou
             }
         }
         rad[v] = r;
-        radf[v] = (float)r;
+        // the walk's record of the cell, gathered into one place
+        const float4 na = nt.a[v];
+        const int4 nc = nt.c[v];
+        fnode[3 * v] = make_int4(__float_as_int(na.x), __float_as_int(na.y), __float_as_int(na.z), __float_as_int(na.w));
+        fnode[3 * v + 1] = make_int4(nc.x, nc.y, nc.z, __float_as_int((float)r));
+        fnode[3 * v + 2] = b;
     }
 }
 
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(kFmmWarps * 32, kFmmBlocksPerSm) k_fmm_level(F
         const SysParams& SP = a.sysp[bc.w];
         const float uf = SP.uf;
         const bool leafB = (bb.w >> 8) == 0;
-        const float rB = a.radf[B];
+        const float rB = __int_as_float(a.fnode[3 * B + 1].w);
         const int P = a.parent[B];
         // candidates: the parent's unresolved sources, then its children; a
         // root has none, or itself when it is a leaf
@@ -453,17 +461,20 @@ __global__ void __launch_bounds__(kFmmWarps * 32, kFmmBlocksPerSm) k_fmm_level(F
                 bool m2l = false, p2p = false, keep = false, split = false;
                 int4 ab = make_int4(0, 0, 0, 0);
                 if (A >= 0) {
-                    ab = __ldg(&nt.b[A]);
+                    // the candidate's record: one 48-byte run
+                    const int4* fr = a.fnode + 3 * (int64_t)A;
+                    const int4 a0 = __ldg(fr), ac = __ldg(fr + 1);
+                    ab = __ldg(fr + 2);
                     const bool leafA = (ab.w >> 8) == 0;
                     if (A == (int)B) {
                         p2p = leafB;  // an internal cell's self pair is its children's pairs
                     } else {
-                        const float4 aa = __ldg(&nt.a[A]);
-                        const int4 ac = __ldg(&nt.c[A]);
+                        const float4 aa = make_float4(__int_as_float(a0.x), __int_as_float(a0.y), __int_as_float(a0.z),
+                                                      __int_as_float(a0.w));
                         const float dx = fmaf((float)(ac.x - bc.x), uf, aa.x - ba.x);
                         const float dy = fmaf((float)(ac.y - bc.y), uf, aa.y - ba.y);
                         const float dz = fmaf((float)(ac.z - bc.z), uf, aa.z - ba.z);
-                        const float rA = __ldg(&a.radf[A]);
+                        const float rA = __int_as_float(ac.w);
                         const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                         const float rr = rA + rB;
                         if (rr * rr < a.theta2 * d2) {
@@ -693,7 +704,7 @@ cudaError_t launch_fmm(const FmmLaunch& p, const int64_t* lstart_h, int depth, c
         if (end <= start) continue;
         int64_t gb = (end - start + 127) / 128;
         if (gb > 8 * sm_count()) gb = 8 * sm_count();
-        k_fmm_radius<<<(unsigned)gb, 128, 0, s>>>(p.body, p.nt, p.rad, p.radf, start, end);
+        k_fmm_radius<<<(unsigned)gb, 128, 0, s>>>(p.body, p.nt, p.rad, p.fnode, start, end);
         count_launches(1);
     }
     FmmArgs a;
@@ -713,7 +724,7 @@ cudaError_t launch_fmm(const FmmLaunch& p, const int64_t* lstart_h, int depth, c
     a.near_cnt = p.near_cnt;
     a.acc = p.acc;
     a.rec = p.rec;
-    a.radf = p.radf;
+    a.fnode = p.fnode;
     a.records = p.records;
     a.theta2 = p.theta * p.theta;
     a.eps2 = p.eps * p.eps;

@@ -328,8 +328,8 @@ struct FmmLaunch {
     int32_t* near_cnt;
     unsigned long long* ctr;
     unsigned long long* rec;  // 4 per node (M2L pairs, P2P pairs, their hashes), 32-byte aligned
-    double* rad;              // per node: r_X (FP64), and rounded to FP32
-    float* radf;
+    double* rad;              // per node: r_X (FP64)
+    int4* fnode;              // per node, 3 entries: the walk's record with r_X in FP32
     int records;              // pair-set hashes and per-node records (else counts only)
     float* acc;
     float theta, eps, G;
