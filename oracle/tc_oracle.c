@@ -1160,9 +1160,10 @@ static void feature_radius(const double *f, double s, double sref, double r, int
     fr[5] = 4.0 * (4.0 * u * (1.0 + f[5]));
     fr[6] = 4.0 * (4.0 * u * f[6]);
     /* the moment ratios also carry the FP32 second moments' error:
-     * (leaf_max + 96) 2^-26 in units of M s^2, taken twice */
+     * (leaf_max + 122) 2^-26 in units of M s^2 (taken as leaf_max + 128),
+     * twice */
     for (int k = 7; k < 13; k++)
-        fr[k] = 4.0 * (4.0 * u * fabs(f[k])) + (double)(leaf_max + 96) * u / 4.0;
+        fr[k] = 4.0 * (4.0 * u * fabs(f[k])) + (double)(leaf_max + 128) * u / 4.0;
 }
 
 /* Learned correction of the group walk.  For each group: the accepted cells

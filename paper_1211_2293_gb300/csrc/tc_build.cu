@@ -481,8 +481,11 @@ __device__ void store_node(NodeTables& nt, int64_t v, double M, const double* co
 // (their error stays a few hundred FP32 ulps of M s^2); the FP64 pipe, a
 // small fraction of the FP32 rate on GB300, is left to the mass and the
 // centre of mass.  Per leaf: Q about the cube centre C from the bodies'
-// offsets x - C (formed in FP64, rounded once), then moved to the centre of
-// mass by the parallel-axis rule Q_com = Q_C - M (com - C)(com - C)^T.
+// offsets x - C, then moved to the centre of mass by the parallel-axis rule
+// Q_com = Q_C - M (com - C)(com - C)^T.  The offsets are formed in FP32
+// against C split into C_hi = fl(C) and C_lo = fl(C - C_hi): (x - C_hi) -
+// C_lo, within 2 FP32 roundings of x - C (the first subtraction is exact
+// unless |C| < 2 s, where its rounding is one of a number below 2 s).
 template <bool QUAD>
 __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams* __restrict__ sysp,
                                const Info* info, NodeTables nt)
@@ -495,6 +498,12 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
         const int4 c = nt.c[v];
         double C[3];
         cube_centre(sysp[c.w], c, C);
+        float Chi[3] = {0.f, 0.f, 0.f}, Clo[3] = {0.f, 0.f, 0.f};
+        if (QUAD)
+            for (int a = 0; a < 3; a++) {
+                Chi[a] = (float)C[a];
+                Clo[a] = (float)(C[a] - (double)Chi[a]);
+            }
         // m and sum m x in absolute coordinates (the product of two floats is
         // exact in FP64, so each term is one fused multiply-add); Q about C
         // in FP32 alongside
@@ -509,7 +518,7 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
             S[1] = fma(w, y, S[1]);
             S[2] = fma(w, z, S[2]);
             if (QUAD) {
-                const float dx = (float)(x - C[0]), dy = (float)(y - C[1]), dz = (float)(z - C[2]);
+                const float dx = (q.x - Chi[0]) - Clo[0], dy = (q.y - Chi[1]) - Clo[1], dz = (q.z - Chi[2]) - Clo[2];
                 const float wx = q.w * dx, wy = q.w * dy, wz = q.w * dz;
                 QC[0] = fmaf(wx, dx, QC[0]);
                 QC[1] = fmaf(wx, dy, QC[1]);
@@ -539,6 +548,9 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
 // one internal cell v from its children (a leaf returns at once): mass and
 // centre of mass in FP64, second moments in FP32 by the parallel-axis rule
 // from the children's, Q_v = sum_c Q_c + m_c d_c d_c^T, d_c = com_c - com_v
+// formed in FP32 from the stored offsets of the centres of mass from their
+// cube centres, d_c = (a_c - a_v) + (k_c - k_v) u (k the integer cube
+// centres in units u = h/2, their difference exact)
 template <bool QUAD>
 __device__ __forceinline__ void level_node(int64_t v, const SysParams* __restrict__ sysp, NodeTables& nt)
 {
@@ -554,12 +566,19 @@ __device__ __forceinline__ void level_node(int64_t v, const SysParams* __restric
     }
     const double inv = 1.0 / m;
     const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
+    const int4 cc = nt.c[v];
+    double C[3];
+    cube_centre(sysp[cc.w], cc, C);
     float Q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float av[3] = {(float)(com[0] - C[0]), (float)(com[1] - C[1]), (float)(com[2] - C[2])};
+    const float uf = sysp[cc.w].uf;
     for (int k = 0; QUAD && k < nch; k++) {
         const int64_t c = pb.z + k;
-        const float mc = (float)nt.mass64[c];
-        float d[3];
-        for (int a = 0; a < 3; a++) d[a] = (float)(nt.com64[3 * c + a] - com[a]);
+        const float4 ac = nt.a[c];
+        const int4 kc = nt.c[c];
+        const float mc = ac.w;
+        const float d[3] = {fmaf((float)(kc.x - cc.x), uf, ac.x - av[0]), fmaf((float)(kc.y - cc.y), uf, ac.y - av[1]),
+                            fmaf((float)(kc.z - cc.z), uf, ac.z - av[2])};
         const float* qc = nt.quad + 6 * c;
         Q[0] += fmaf(mc * d[0], d[0], qc[0]);
         Q[1] += fmaf(mc * d[0], d[1], qc[1]);
@@ -568,9 +587,6 @@ __device__ __forceinline__ void level_node(int64_t v, const SysParams* __restric
         Q[4] += fmaf(mc * d[1], d[2], qc[4]);
         Q[5] += fmaf(mc * d[2], d[2], qc[5]);
     }
-    const int4 cc = nt.c[v];
-    double C[3];
-    cube_centre(sysp[cc.w], cc, C);
     store_node<QUAD>(nt, v, m, com, Q, C);
 }
 

@@ -71,15 +71,20 @@ def _compare_tree(ctx, t, gmax):
     scale = np.abs(t.com).max(1) + side
     assert np.all(np.abs(tr["com"] - t.com).max(1) <= 1e-12 * scale)
     if tr["quad"] is not None:
-        # second moments are FP32.  A leaf of c bodies: offsets, products and
-        # c running-sum roundings, each at most u = 2^-24 of a term of size
-        # <= M s^2 / 4, plus the parallel-axis shift: (c + 8) u M s^2 / 4.
-        # A cell above: 12 roundings of its children's terms (<= 1.25 M s^2)
-        # plus the children's errors, a quarter of theirs in units of the
-        # parent's M s^2, so at most 20 u M s^2 in all.  Together
-        # (leaf_max + 96) 2^-26 M s^2, taken with a factor 2 of margin.
+        # second moments are FP32.  A leaf of c bodies: offsets within two
+        # roundings (formed against the cube centre split in two floats),
+        # products and c running-sum roundings, each at most u = 2^-24 of a
+        # term of size <= M s^2 / 4, plus the parallel-axis shift:
+        # (c + 10) u M s^2 / 4.  A cell above: its children's offsets d
+        # from its centre of mass are formed in FP32 from the stored
+        # centre-of-mass offsets (three roundings of numbers <= s, one of d:
+        # 3.5 u s), so 6 u m_c s^2 per child term, plus 12 roundings of terms
+        # <= 1.25 M s^2, plus the children's errors, a quarter of theirs in
+        # units of the parent's M s^2: at most 28 u M s^2 in all.  Together
+        # (leaf_max + 122) 2^-26 M s^2, taken as leaf_max + 128 and with a
+        # factor 2 of margin.
         qs = t.node_mass * side ** 2
-        assert np.all(np.abs(tr["quad"] - t.quad).max(1) <= (t.leaf_max + 96) * 2.0 ** -25 * qs)
+        assert np.all(np.abs(tr["quad"] - t.quad).max(1) <= (t.leaf_max + 128) * 2.0 ** -25 * qs)
     t.make_groups(gmax)
     assert G == t.G
     assert np.array_equal(tr["gfirst"], t.gfirst)
