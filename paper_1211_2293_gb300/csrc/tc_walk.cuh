@@ -103,6 +103,28 @@ __device__ __forceinline__ void put_entry(float* tile, int k, float4 q)
     t[6] = q.w;
 }
 
+// entry k from global memory by cp.async: four 4-byte copies into the
+// pair-interleaved tile, global -> shared without passing through
+// registers; the copier waits for its copies (cp_async_wait_all, or an
+// mbarrier that tracks them) before the tile is read
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void put_entry_async(float* tile, int k, const float4* src)
+{
+    float* t = tile + 8 * (k >> 1) + (k & 1);
+    const float* q = reinterpret_cast<const float*>(src);
+    cp_async4(t, q);
+    cp_async4(t + 2, q + 1);
+    cp_async4(t + 4, q + 2);
+    cp_async4(t + 6, q + 3);
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 {
     z += 0x9E3779B97F4A7C15ull;
@@ -500,6 +522,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
     }
 
     for (;;) {
+        cp_async_wait_all();  // a group that stopped early (list export, stack overflow) may have copies in flight
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&a.info->work[a.work_slot], 1u) + g_shift;
         g = __shfl_sync(0xffffffffu, g, 0);
@@ -741,9 +764,10 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
                     }
                     const int f = __shfl_sync(0xffffffffu, nb.x, pos);
                     const int e0 = __shfl_sync(0xffffffffu, excl_c, pos);
-                    if (o + lane < T) put_entry(btile, bn + lane, __ldg(&a.body[f + (t - e0)]));
+                    if (o + lane < T) put_entry_async(btile, bn + lane, &a.body[f + (t - e0)]);
                     bn += min(32, T - o);
                     if (bn >= kTile) {
+                        cp_async_wait_all();
                         fsum.flush(btile, bn, XA, YA, ZA, E2);
                         bn = 0;
                     }
@@ -765,6 +789,7 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
         if (QUADW) fsum.flush_quad(ctile, qtile, cn, XR, YR, ZR, E2);
         else if (PRECISE) fsum.flush(ctile, cn, XR, YR, ZR, E2);
         else fsum.flush(ctile, cn, XA, YA, ZA, E2);
+        cp_async_wait_all();
         fsum.flush(btile, bn, XA, YA, ZA, E2);
         if (LEARNED) {
             if (qn > 0) {

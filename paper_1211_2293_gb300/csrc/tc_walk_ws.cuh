@@ -68,33 +68,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b)
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_addr(b)) : "memory");
 }
 
-// the opened leaves' bodies reach a slot by cp.async (4-byte copies into the
-// pair-interleaved tile, global -> shared without passing through registers);
+// the opened leaves' bodies reach a slot by cp.async (put_entry_async);
 // before its arrival on the slot's full barrier every producer lane makes the
 // barrier track its copies (cp.async.mbarrier.arrive without .noinc: the
 // pending count rises now and falls when the lane's copies have landed), so
 // the phase completes only once the bodies are in the tile
-__device__ __forceinline__ void cp_async4(void* dst, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void put_entry_async(float* tile, int k, const float4* src)
-{
-    float* t = tile + 8 * (k >> 1) + (k & 1);
-    const float* s = reinterpret_cast<const float*>(src);
-    cp_async4(t, s);
-    cp_async4(t + 2, s + 1);
-    cp_async4(t + 4, s + 2);
-    cp_async4(t + 6, s + 3);
-}
-
 __device__ __forceinline__ void mbar_track_copies(uint64_t* b)
 {
     asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
 }
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
 {
