@@ -685,11 +685,13 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
     p_tr, _, m_tr = inputs.plummer(N_TRAIN, seed=SEED_TRAIN + 1000 * rank)
     ctx_tr = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
     ctx_tr.build(torch.from_numpy(p_tr).to(dev), torch.from_numpy(m_tr).to(dev), LEAF)
+    # the pairs' count is kept below the cap (the cap would make the kept set
+    # depend on the walk's schedule; below it the pairs repeat exactly)
     target = 2_000_000
-    n_all = len(ctx_tr.mlp_pairs(THETA_TRAIN, EPS, BAND_TRAIN, 0.05, 1, target)[0])
+    n_all = len(ctx_tr.mlp_pairs(THETA_TRAIN, EPS, BAND_TRAIN, 0.05, 1, 2 * target)[0])
     prob = min(1.0, 0.05 * target / max(1, n_all))
     t0 = time.perf_counter()
-    X, T, F, _, _ = ctx_tr.mlp_pairs(THETA_TRAIN, EPS, BAND_TRAIN, prob, 2, target)
+    X, T, F, _, _ = ctx_tr.mlp_pairs(THETA_TRAIN, EPS, BAND_TRAIN, prob, 2, 2 * target)
     pairs_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     losses = ctx_tr.mlp_train(X, T, F, epochs=args.epochs, batch=1024, lr=2e-3, seed=3, band=BAND_TRAIN,
@@ -1249,7 +1251,7 @@ def run_profile_case(args):
     build: a uniform cube built twice (eager builds; capture the second);
     learned: one learned walk (seeded random network, band 0.5, theta 0.9)
     on a 2^20-body Plummer sphere; quadrupole: one quadrupole walk (theta
-    0.7) on the same sphere; fmm: two FMM passes (theta 0.4) on a Plummer
+    0.7) on the same sphere; fmm: two FMM passes (theta 0.55) on a Plummer
     sphere of --n bodies (default 2^20); band: two learned force phases with
     the network after the walk (split 2: k_band_eval, the same random network,
     band 0.55, theta 0.667) on a 2^21-body sphere; walk_plummer: two plain
@@ -1308,9 +1310,9 @@ def run_profile_case(args):
     if case == "fmm":
         ctx = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
         ctx.build(P, M, 16)
-        ctx.fmm(0.4, 1e-3)
-        ctx.fmm(0.4, 1e-3)
-        print(f"fmm: Plummer N={n}, theta 0.4, {ctx.fmm_stats()}")
+        ctx.fmm(0.55, 1e-3)
+        ctx.fmm(0.55, 1e-3)
+        print(f"fmm: Plummer N={n}, theta 0.55, {ctx.fmm_stats()}")
         ctx.close()
         return 0
     if case == "learned":

@@ -375,8 +375,12 @@ int tc_mlp_train(tc_ctx *ctx, const float *X, const float *T, const float *W, in
  * group; features at that body, the exact label and the factor F (G = 1).
  * Outputs (any nullable except npairs): X (max_pairs x 13), T (max_pairs x
  * 3), F (max_pairs), body (original index), node (breadth-first index);
- * *npairs = pairs written (at most max_pairs).  Needs quad = 1; overwrites
- * the context's accelerations. */
+ * *npairs = pairs written (at most max_pairs).  The pairs come in one order
+ * (by body position in the tree, then node), whatever the order the walk
+ * emitted them in, so the same bodies, theta, band, prob and seed give the
+ * same pairs in the same order -- as long as no more than max_pairs are
+ * emitted (past the cap, which pairs are kept depends on the walk's
+ * schedule).  Needs quad = 1; overwrites the context's accelerations. */
 int tc_mlp_pairs(tc_ctx *ctx, float theta, float eps, float band, float prob, uint64_t seed, int64_t max_pairs,
                  float *X, float *T, float *F, int64_t *body, int64_t *node, int64_t *npairs);
 /* corrections evaluated by learned walks since the last call */

@@ -101,6 +101,8 @@ struct tc_ctx {
     float* mlp_m = nullptr;       // Adam moments
     float* mlp_v = nullptr;
     float* mlp_grad = nullptr;
+    float* mlp_part = nullptr;    // per-warp partial gradients of a training step
+    int64_t mlp_part_cap = 0;
     float* mlp_loss = nullptr;
     unsigned long long* mlp_evals = nullptr;
     float* mlp_x = nullptr;       // scratch: features / normalised rows / outputs
@@ -129,6 +131,11 @@ struct tc_ctx {
     int32_t* pair_v = nullptr;
     unsigned long long* pair_n = nullptr;
     int64_t pair_cap = 0;
+    // the pairs' sort: keys, values and the radix sort's scratch
+    uint64_t* pair_key = nullptr;
+    uint32_t* pair_val = nullptr;
+    SortBufs pair_sb{};
+    int64_t pair_sort_cap = 0;
 
     // fast multipole method: parent table, local expansions, unresolved
     // source lists (per node: offset and count into the pool of its level's
@@ -1404,6 +1411,17 @@ int tc_mlp_forward(tc_ctx* c, const float* X, int64_t n, float* Y)
     return check_device(c);
 }
 
+// scratch of a training step's per-warp partial gradients
+static int mlp_part(tc_ctx* c, int blocks)
+{
+    const int64_t want = mlp_train_part_floats(blocks);
+    if (want > c->mlp_part_cap) {
+        TC_GROW(c, c->mlp_part, want);
+        c->mlp_part_cap = want;
+    }
+    return TC_OK;
+}
+
 int tc_mlp_loss_grad(tc_ctx* c, const float* X, const float* T, const float* W, int64_t n, float* grad, float* loss)
 {
     if (!c || !X || !T) return fail(c, TC_EINVAL, "tc_mlp_loss_grad: null argument");
@@ -1415,12 +1433,12 @@ int tc_mlp_loss_grad(tc_ctx* c, const float* X, const float* T, const float* W, 
     launch_mlp_shuffle(n, 0, c->mlp_idx, c->stream);  // key 0: the rows in order
     const float* wdev = nullptr;
     if ((r = mlp_weights(c, W, 0, n, &wdev))) return r;
-    TC_CUDA(c, cudaMemsetAsync(c->mlp_grad, 0, kMlpNParamHost * sizeof(float), c->stream));
     TC_CUDA(c, cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), c->stream));
     int64_t blocks = (n + 63) / 64;
     if (blocks > 2 * c->num_sms) blocks = 2 * c->num_sms;
+    if ((r = mlp_part(c, (int)blocks))) return r;
     cudaError_t e = launch_mlp_train(c->mlp_x, c->mlp_t, wdev, c->mlp_idx, (int)n, c->mlp_dev, c->mlp_grad,
-                                     c->mlp_loss, (int)blocks, c->stream);
+                                     c->mlp_loss, c->mlp_part, (int)blocks, c->stream);
     if (e != cudaSuccess) return fail(c, TC_ECUDA, "mlp training kernel: %s", cudaGetErrorString(e));
     if (grad) TC_CUDA(c, cudaMemcpyAsync(grad, c->mlp_grad, kMlpNParamHost * sizeof(float), cudaMemcpyDefault, c->stream));
     if (loss) TC_CUDA(c, cudaMemcpyAsync(loss, c->mlp_loss, sizeof(float), cudaMemcpyDefault, c->stream));
@@ -1484,11 +1502,11 @@ int tc_mlp_train(tc_ctx* c, const float* X, const float* T, const float* W, int3
         int nb = 0;
         for (int64_t b0 = 0; b0 < n; b0 += batch) {
             const int B = (int)std::min<int64_t>(batch, n - b0);
-            TC_CUDA(c, cudaMemsetAsync(c->mlp_grad, 0, kMlpNParamHost * sizeof(float), c->stream));
             int64_t blocks = (B + 63) / 64;
             if (blocks > 2 * c->num_sms) blocks = 2 * c->num_sms;
+            if ((r = mlp_part(c, (int)blocks))) return r;
             cudaError_t e = launch_mlp_train(c->mlp_x, c->mlp_t, wdev, c->mlp_idx + b0, B, c->mlp_dev,
-                                             c->mlp_grad, c->mlp_loss, (int)blocks, c->stream);
+                                             c->mlp_grad, c->mlp_loss, c->mlp_part, (int)blocks, c->stream);
             if (e != cudaSuccess) return fail(c, TC_ECUDA, "mlp training kernel: %s", cudaGetErrorString(e));
             // cosine decay of the learning rate over all steps
             const float lr_t = (float)(0.5 * lr * (1.0 + std::cos(3.141592653589793 * step / (double)total_steps)));
@@ -1519,6 +1537,19 @@ int tc_mlp_pairs(tc_ctx* c, float theta, float eps, float band, float prob, uint
         TC_GROW(c, c->pair_v, max_pairs);
         TC_GROW(c, c->pair_n, 1);
         c->pair_cap = max_pairs;
+    }
+    if (max_pairs > c->pair_sort_cap) {
+        const int64_t cap = max_pairs;
+        TC_GROW(c, c->pair_key, cap);
+        TC_GROW(c, c->pair_val, cap);
+        TC_GROW(c, c->pair_sb.keys_alt, cap);
+        TC_GROW(c, c->pair_sb.vals_alt, cap);
+        TC_GROW(c, c->pair_sb.ghist, kSortMaxPasses * 256);
+        TC_GROW(c, c->pair_sb.status, (int64_t)kSortMaxPasses * radix_tiles(cap) * 256);
+        TC_GROW(c, c->pair_sb.tiles, kSortMaxPasses);
+        TC_GROW(c, c->pair_sb.blocksum, scan_blocksum_size(cap));
+        c->pair_sb.err = &c->info->err;
+        c->pair_sort_cap = cap;
     }
     int r = mlp_scratch(c, max_pairs);
     if (r) return r;
@@ -1565,6 +1596,8 @@ int tc_mlp_pairs(tc_ctx* c, float theta, float eps, float band, float prob, uint
     const int64_t np = (int64_t)std::min<unsigned long long>(cnt, (unsigned long long)max_pairs);
     *npairs = np;
     if (np == 0) return TC_OK;
+    // one order whatever the order the walk's warps emitted them in
+    launch_pair_order(c->pair_b, c->pair_v, np, c->pair_key, c->pair_val, c->pair_sb, c->stream);
     launch_pair_labels(c->pair_b, c->pair_v, np, c->body, c->sys_of, c->sysp, c->nt, eps, 1.f, c->mlp_x, c->mlp_t,
                        c->mlp_w, c->stream);
     TC_CUDA(c, cudaGetLastError());

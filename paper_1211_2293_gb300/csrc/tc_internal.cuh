@@ -251,8 +251,12 @@ double launch_force_probe(int blocks, int reps, float* out, cudaStream_t s);
 size_t mlp_dev_size();
 size_t mlp_frag_size();  // the inference part at the front of a device model
 size_t mlp_train_smem();
+// training step on B rows: per-warp partial gradients in part (at least
+// mlp_train_part_floats(blocks) floats), added in warp order into grad (the
+// packed gradient, overwritten) and the loss added to *loss
+int64_t mlp_train_part_floats(int blocks);
 cudaError_t launch_mlp_train(const float* X, const float* T, const float* W, const int32_t* idx, int B,
-                             const void* model, float* grad, float* loss, int blocks, cudaStream_t s);
+                             const void* model, float* grad, float* loss, float* part, int blocks, cudaStream_t s);
 void launch_mlp_pack(const float* params, const float* maps, void* model, cudaStream_t s);
 void launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, int t, cudaStream_t s);
 void launch_mlp_infer(const float* X, int64_t n, const void* model, float* Y, cudaStream_t s);
@@ -268,6 +272,10 @@ void launch_band_apply(const Info* info, int64_t cap_g, const int32_t* gfirst, c
 // eps under the model (run before a learned walk)
 void launch_node_features(const Info* info, int64_t cap_m, const SysParams* sysp, NodeTables nt, float eps,
                           const void* model, cudaStream_t s);
+// the emitted (body, node) pairs sorted by (body, node): the walk emits them
+// in whatever order its warps finish, the training wants one order
+void launch_pair_order(int32_t* pb, int32_t* pv, int64_t np, uint64_t* keys, uint32_t* vals, SortBufs& b,
+                       cudaStream_t s);
 void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const float4* body, const uint32_t* sys_of,
                         const SysParams* sysp, NodeTables nt, float eps, float G, float* feat, float* lab,
                         float* fac, cudaStream_t s);

@@ -86,14 +86,16 @@ __device__ __forceinline__ void load_bt(uint32_t (&b)[2], const __nv_bfloat16* W
     b[1] = pack_raw(W[n * ldk + k + 8], W[n * ldk + k + 9]);
 }
 
+// G is the warp's own partial gradient: each element always belongs to the
+// same lane, so the sums are plain additions in the warp's order of tiles
 __device__ __forceinline__ void add_c(float* G, int ld, int mt, int nb, const float (&c)[4], int lane)
 {
     const int g = lane >> 2, q = lane & 3;
     const int r = mt * 16 + g, col = nb * 8 + 2 * q;
-    atomicAdd(&G[r * ld + col], c[0]);
-    atomicAdd(&G[r * ld + col + 1], c[1]);
-    atomicAdd(&G[(r + 8) * ld + col], c[2]);
-    atomicAdd(&G[(r + 8) * ld + col + 1], c[3]);
+    G[r * ld + col] += c[0];
+    G[r * ld + col + 1] += c[1];
+    G[(r + 8) * ld + col] += c[2];
+    G[(r + 8) * ld + col + 1] += c[3];
 }
 
 // column sums of a C tile over its 16 rows into G[col]
@@ -106,29 +108,32 @@ __device__ __forceinline__ void colsum_c(float* G, int nb, const float (&c)[4], 
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
     if (lane < 4) {
-        atomicAdd(&G[nb * 8 + 2 * lane], s0);
-        atomicAdd(&G[nb * 8 + 2 * lane + 1], s1);
+        G[nb * 8 + 2 * lane] += s0;
+        G[nb * 8 + 2 * lane + 1] += s1;
     }
 }
 
 // X: n x 16 normalised features (FP32, padding zero); T: n x 3 scaled
-// targets; W: n weights (nullable); idx: the batch's row indices (B of them)
+// targets; W: n weights (nullable); idx: the batch's row indices (B of
+// them).  Every warp sums its tiles' gradient into its own partial (part,
+// kGPad floats per warp of the grid) and its loss into lpart; k_grad_reduce
+// adds the partials in warp order, so a training run repeats bit for bit.
 __global__ void __launch_bounds__(kTrainWarps * 32) k_mlp_train(const float* __restrict__ X,
                                                                  const float* __restrict__ T,
                                                                  const float* __restrict__ W,
                                                                  const int32_t* __restrict__ idx, int B,
                                                                  const MlpDev* __restrict__ model,
-                                                                 float* __restrict__ grad, float* __restrict__ loss)
+                                                                 float* __restrict__ part, float* __restrict__ lpart)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     MlpDev& m = *reinterpret_cast<MlpDev*>(smem);
-    float* gs = reinterpret_cast<float*>(smem + sizeof(MlpDev));
-    __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(gs + kGPad);
+    __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem + sizeof(MlpDev));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __nv_bfloat16* st = stage + w * kStSize;
+    float* gs = part + ((int64_t)blockIdx.x * kTrainWarps + w) * kGPad;  // this warp's partial
     for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t*>(&m)[i] = reinterpret_cast<const uint32_t*>(model)[i];
-    for (int i = threadIdx.x; i < kGPad; i += blockDim.x) gs[i] = 0.f;
+    for (int i = lane; i < kGPad; i += 32) gs[i] = 0.f;
     __syncthreads();
     const int g = lane >> 2, q = lane & 3;
     const float inv_b = 1.0f / (float)B;
@@ -256,23 +261,47 @@ __global__ void __launch_bounds__(kTrainWarps * 32) k_mlp_train(const float* __r
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if (lane == 0) atomicAdd(loss, lsum * inv_b);
+    if (lane == 0) lpart[(int64_t)blockIdx.x * kTrainWarps + w] = lsum * inv_b;
+}
+
+// the partials of nw warps, added in one fixed order, into the packed
+// gradient (W1[13][64], b1, W2, b2, W3[64][3], b3) and the loss (element
+// kMlpNParam, added to *loss).  A block takes 32 elements; its 8 warps sum
+// the warps k = y, y + 8, ... in turn, and warp 0 adds the 8 sums in order.
+constexpr int kReduceSlices = 8;
+__global__ void __launch_bounds__(32 * kReduceSlices) k_grad_reduce(const float* __restrict__ part,
+                                                                    const float* __restrict__ lpart, int nw,
+                                                                    float* __restrict__ grad, float* __restrict__ loss)
+{
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + tx;
+    // packed index -> the padded index of a warp's partial (stride kGPad),
+    // or the loss partials (stride 1)
+    const float* src = nullptr;
+    int64_t stride = kGPad;
+    constexpr int kB1 = kMlpIn * kMlpHid, kW2 = kB1 + kMlpHid, kB2 = kW2 + kMlpHid * kMlpHid;
+    constexpr int kW3 = kB2 + kMlpHid, kB3 = kW3 + kMlpHid * kMlpOut;
+    static_assert(kB3 + kMlpOut == kMlpNParam, "packed gradient layout");
+    if (e < kB1) src = part + kGW1 + e;
+    else if (e < kW2) src = part + kGB1 + (e - kB1);
+    else if (e < kB2) src = part + kGW2 + (e - kW2);
+    else if (e < kW3) src = part + kGB2 + (e - kB2);
+    else if (e < kB3) src = part + kGW3 + ((e - kW3) / kMlpOut) * kMlpOutPad + ((e - kW3) % kMlpOut);
+    else if (e < kMlpNParam) src = part + kGB3 + (e - kB3);
+    else if (e == kMlpNParam) { src = lpart; stride = 1; }
+    float s = 0.f;
+    if (src)
+        for (int k = ty; k < nw; k += kReduceSlices) s += src[(int64_t)k * stride];
+    __shared__ float red[kReduceSlices][33];
+    red[ty][tx] = s;
     __syncthreads();
-    // padded block sums -> packed global gradient (W1[13][64], b1, W2, b2, W3[64][3], b3)
-    for (int i = threadIdx.x; i < kMlpIn * kMlpHid; i += blockDim.x) atomicAdd(&grad[i], gs[kGW1 + i]);
-    float* gb1 = grad + kMlpIn * kMlpHid;
-    float* gw2 = gb1 + kMlpHid;
-    float* gb2 = gw2 + kMlpHid * kMlpHid;
-    float* gw3 = gb2 + kMlpHid;
-    float* gb3 = gw3 + kMlpHid * kMlpOut;
-    for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) {
-        atomicAdd(&gb1[i], gs[kGB1 + i]);
-        atomicAdd(&gb2[i], gs[kGB2 + i]);
+    if (ty == 0 && src) {
+        float t = red[0][tx];
+#pragma unroll
+        for (int j = 1; j < kReduceSlices; j++) t += red[j][tx];
+        if (e < kMlpNParam) grad[e] = t;
+        else *loss += t;
     }
-    for (int i = threadIdx.x; i < kMlpHid * kMlpHid; i += blockDim.x) atomicAdd(&gw2[i], gs[kGW2 + i]);
-    for (int i = threadIdx.x; i < kMlpHid * kMlpOut; i += blockDim.x)
-        atomicAdd(&gw3[i], gs[kGW3 + (i / kMlpOut) * kMlpOutPad + (i % kMlpOut)]);
-    if (threadIdx.x < kMlpOut) atomicAdd(&gb3[threadIdx.x], gs[kGB3 + threadIdx.x]);
 }
 
 // packed FP32 parameters + feature/output maps -> device BF16 model: the
@@ -609,16 +638,20 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-size_t mlp_train_smem() { return sizeof(MlpDev) + kGPad * sizeof(float) + (size_t)kTrainWarps * kStSize * 2; }
+size_t mlp_train_smem() { return sizeof(MlpDev) + (size_t)kTrainWarps * kStSize * 2; }
+int64_t mlp_train_part_floats(int blocks) { return (int64_t)blocks * kTrainWarps * (kGPad + 1); }
 
 cudaError_t launch_mlp_train(const float* X, const float* T, const float* W, const int32_t* idx, int B,
-                             const void* model, float* grad, float* loss, int blocks, cudaStream_t s)
+                             const void* model, float* grad, float* loss, float* part, int blocks, cudaStream_t s)
 {
     const size_t smem = mlp_train_smem();
     cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_mlp_train<<<blocks, kTrainWarps * 32, smem, s>>>(X, T, W, idx, B, (const MlpDev*)model, grad, loss);
-    count_launches(1);
+    const int nw = blocks * kTrainWarps;
+    float* lpart = part + (int64_t)nw * kGPad;
+    k_mlp_train<<<blocks, kTrainWarps * 32, smem, s>>>(X, T, W, idx, B, (const MlpDev*)model, part, lpart);
+    k_grad_reduce<<<(kMlpNParam + 1 + 31) / 32, 32 * kReduceSlices, 0, s>>>(part, lpart, nw, grad, loss);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -644,6 +677,39 @@ void launch_mlp_infer(const float* X, int64_t n, const void* model, float* Y, cu
     count_launches(1);
 }
 
+namespace {
+// (body, node) pairs as sort keys (body position in the high half) and back
+__global__ void k_pair_keys(const int32_t* __restrict__ pb, const int32_t* __restrict__ pv, int64_t np,
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
+        keys[k] = ((uint64_t)(uint32_t)pb[k] << 32) | (uint32_t)pv[k];
+        vals[k] = (uint32_t)k;
+    }
+}
+
+__global__ void k_pair_unkey(const uint64_t* __restrict__ keys, int64_t np, int32_t* __restrict__ pb,
+                             int32_t* __restrict__ pv)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
+        pb[k] = (int32_t)(keys[k] >> 32);
+        pv[k] = (int32_t)(keys[k] & 0xffffffffu);
+    }
+}
+}  // namespace
+
+void launch_pair_order(int32_t* pb, int32_t* pv, int64_t np, uint64_t* keys, uint32_t* vals, SortBufs& b,
+                       cudaStream_t s)
+{
+    int64_t g = nblk(np, 256);
+    if (g > 8 * sm_count()) g = 8 * sm_count();
+    k_pair_keys<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(pb, pv, np, keys, vals);
+    count_launches(1);
+    radix_sort_u64(keys, vals, np, 63, nullptr, 0, b, s);
+    k_pair_unkey<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(keys, np, pb, pv);
+    count_launches(1);
+}
+
 void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const float4* body, const uint32_t* sys_of,
                         const SysParams* sysp, NodeTables nt, float eps, float G, float* feat, float* lab,
                         float* fac, cudaStream_t s)
@@ -654,10 +720,10 @@ void launch_pair_labels(const int32_t* pb, const int32_t* pv, int64_t np, const 
 
 void launch_mlp_sums(const float* X, const float* T, const float* F, int64_t n, double* sums, cudaStream_t s)
 {
+    // one block per column: each sum is taken in one fixed order, so the
+    // maps (and the training that follows) repeat bit for bit
     cudaMemsetAsync(sums, 0, kMlpSums * sizeof(double), s);
-    int64_t g = (n + 255) / 256;
-    if (g > 2 * sm_count()) g = 2 * sm_count();
-    k_mlp_sums<<<dim3((unsigned)(g < 1 ? 1 : g), kMlpSums), 256, 0, s>>>(X, T, F, n, sums);
+    k_mlp_sums<<<dim3(1, kMlpSums), 1024, 0, s>>>(X, T, F, n, sums);
     count_launches(1);
 }
 

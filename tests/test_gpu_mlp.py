@@ -265,9 +265,11 @@ def test_training_pairs_match_oracle(tc):
         assert t.count[v] >= 2
     # sampling: about prob x (number of band cells), reproducible by seed
     X2, T2, F2, b2, v2 = ctx.mlp_pairs(theta, eps, band, 0.05, 13, 100000)
-    key1 = np.sort(body * (1 << 32) + node)
-    key2 = np.sort(b2 * (1 << 32) + v2)
-    assert np.array_equal(key1, key2)
+    # one order: by the body's position in the tree (the oracle's tree has
+    # the same permutation), then node
+    assert np.all(np.diff(inv[body] * (1 << 32) + node) > 0)
+    assert np.array_equal(body, b2) and np.array_equal(node, v2)
+    assert np.array_equal(X, X2) and np.array_equal(T, T2) and np.array_equal(F, F2)
     Xa, _, _, _, _ = ctx.mlp_pairs(theta, eps, band, 1.0, 13, 2000000)
     assert abs(len(X) / len(Xa) - 0.05) < 0.01
     # the cap truncates
@@ -305,6 +307,26 @@ def test_training_reduces_loss_and_error(tc):
     print(f"theta {theta}: plain rms {e_plain:.3e}, learned rms {e_learn:.3e}, losses {losses[0]:.3g} -> "
           f"{losses[-1]:.3g}")
     assert e_learn < 0.85 * e_plain
+
+
+def test_training_repeats_bit_for_bit(tc):
+    """Pairs, feature maps and training are deterministic: two contexts on
+    the same bodies with the same seeds end with the same model and losses,
+    bit for bit (gradients are summed per warp and then in warp order, the
+    pairs sorted by (body, node), the maps' sums taken in one order)."""
+    theta, eps, band = 0.9, 1e-3, 0.5
+    out = []
+    for _ in range(2):
+        ctx, _, _ = _built(tc, 32768, 31)
+        X, T, F, _, _ = ctx.mlp_pairs(theta, eps, band, 0.5, 7, 1_000_000)
+        losses = ctx.mlp_train(X, T, F, epochs=3, batch=1024, lr=2e-3, seed=3, band=band, factors=True)
+        model, b = ctx.mlp_get()
+        out.append((X, losses, model, b))
+        ctx.close()
+    assert len(out[0][0]) > 10000
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2]) and out[0][3] == out[1][3]
 
 
 def test_learned_step_and_config_errors(tc):
