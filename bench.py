@@ -683,7 +683,8 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
     n_ev = args.n if args.n != N_DEFAULT else N_EVAL
     # ---- training: pairs generated by the walk itself, trained on the GPU
     p_tr, _, m_tr = inputs.plummer(N_TRAIN, seed=SEED_TRAIN + 1000 * rank)
-    ctx_tr = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
+    lsplit = {} if args.learned_split is None else {"split": args.learned_split}
+    ctx_tr = tc.Context(precise=1, quad=1, want_pot=0, verify=0, **lsplit)
     ctx_tr.build(torch.from_numpy(p_tr).to(dev), torch.from_numpy(m_tr).to(dev), LEAF)
     # the pairs' count is kept below the cap (the cap would make the kept set
     # depend on the walk's schedule; below it the pairs repeat exactly)
@@ -722,7 +723,7 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
     p, v, m = inputs.plummer(n_ev, seed=SEED_EVAL + 1000 * rank)
     P, M, V = (torch.from_numpy(a).to(dev) for a in (p, m, v))
     ctxP = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
-    ctxL = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
+    ctxL = tc.Context(precise=1, quad=1, want_pot=0, verify=0, **lsplit)
     ctxP.build(P, M, LEAF)
     ctxL.build(P, M, LEAF)
     ctxL.mlp_set(model, band)
@@ -806,7 +807,7 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
     hp = torch.from_numpy(p).pin_memory()
     hm = torch.from_numpy(m).pin_memory()
     hacc = torch.empty((n_ev, 3), dtype=torch.float32).pin_memory()
-    ctxE = tc.Context(precise=1, quad=1, want_pot=0, verify=0)
+    ctxE = tc.Context(precise=1, quad=1, want_pot=0, verify=0, **lsplit)
     ctxE.build(hp, hm, LEAF)
     ctxE.mlp_set(model, band)
     ctxE.set_config(learned=1)
@@ -1356,6 +1357,8 @@ def main():
                          "Plummer spheres; learned: the learned correction's sweep (bands, quadrupole, fixed theta)")
     ap.add_argument("--headline-only", action="store_true", help="default workload without the sub-keys")
     ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--learned-split", type=int, default=None, choices=[0, 1, 2],
+                    help="tc_config.split of the learned path's contexts (default: the library's)")
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")
     ap.add_argument("--band-train", type=float, default=0.4, help="learned: band of the training pairs")
     ap.add_argument("--nsys", type=int, default=512)
