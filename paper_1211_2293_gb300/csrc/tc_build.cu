@@ -463,6 +463,19 @@ __device__ __forceinline__ double widen(float f)
     return __longlong_as_double((long long)d);
 }
 
+// (hi, lo) += p + e for a normalised pair (|lo| <= ulp(hi) / 2): hi + p by
+// Knuth's TwoSum (s + t = hi + p exactly), the error t, lo and e added in
+// FP32, then renormalised by Dekker's FastTwoSum (exact: |t| is a few ulps
+// of s at most, or s = 0).  One call errs by at most about 2^-46 |s|.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p, float e)
+{
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float t = ((hi - (s - bp)) + (p - bp)) + (lo + e);
+    hi = s + t;
+    lo = t - (hi - s);
+}
+
 template <bool QUAD>
 __device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const float* Q, const double* C)
 {
@@ -504,19 +517,26 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
                 Chi[a] = (float)C[a];
                 Clo[a] = (float)(C[a] - (double)Chi[a]);
             }
-        // m and sum m x in absolute coordinates (the product of two floats is
-        // exact in FP64, so each term is one fused multiply-add); Q about C
-        // in FP32 alongside
-        double m = 0.0, S[3] = {0, 0, 0};
+        // m and sum m x in absolute coordinates as unevaluated sums of two
+        // floats (hi + lo): each product m x split exactly into p + e by
+        // one FMA and added by two_sum_acc.  Over a leaf's c bodies the error
+        // stays below about c 2^-46 of the largest partial sum of |terms|
+        // (2.3e-13 of it for c = 16): FP64-class accuracy on the FP32 pipe,
+        // which GB300 runs 64 times faster than its FP64 pipe; hi + lo is
+        // then taken exactly into FP64 for the centre of mass and the levels
+        // above.  Q about C in FP32 alongside.
+        float mh = 0.f, ml = 0.f, Sh[3] = {0.f, 0.f, 0.f}, Sl[3] = {0.f, 0.f, 0.f};
         float QC[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int j = b.x; j < b.x + b.y; j++) {
             const float4 q = body[j];
-            const double w = widen(q.w);
-            const double x = widen(q.x), y = widen(q.y), z = widen(q.z);
-            m += w;
-            S[0] = fma(w, x, S[0]);
-            S[1] = fma(w, y, S[1]);
-            S[2] = fma(w, z, S[2]);
+            two_sum_acc(mh, ml, q.w, 0.f);
+            const float xs[3] = {q.x, q.y, q.z};
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float p = q.w * xs[a];
+                const float e = fmaf(q.w, xs[a], -p);  // q.w x = p + e exactly
+                two_sum_acc(Sh[a], Sl[a], p, e);
+            }
             if (QUAD) {
                 const float dx = (q.x - Chi[0]) - Clo[0], dy = (q.y - Chi[1]) - Clo[1], dz = (q.z - Chi[2]) - Clo[2];
                 const float wx = q.w * dx, wy = q.w * dy, wz = q.w * dz;
@@ -528,6 +548,8 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
                 QC[5] = fmaf(wz, dz, QC[5]);
             }
         }
+        const double m = widen(mh) + widen(ml);
+        const double S[3] = {widen(Sh[0]) + widen(Sl[0]), widen(Sh[1]) + widen(Sl[1]), widen(Sh[2]) + widen(Sl[2])};
         const double inv = 1.0 / m;
         const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
         float Q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
