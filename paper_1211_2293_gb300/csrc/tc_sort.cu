@@ -189,6 +189,13 @@ __global__ void __launch_bounds__(256) k_sort_offsets(uint32_t* __restrict__ ghi
     }
 }
 
+__device__ __forceinline__ void sort_cp16(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void sort_cp_wait() { asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory"); }
+
 // Dynamic shared memory of one onesweep tile: the tile's items in their
 // locally sorted order (keys, then values), staged so that the write to the
 // output is one contiguous run per digit instead of a scatter per item.
@@ -227,10 +234,31 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K* __restric
     if ((int64_t)tile * kSortTile >= n) return;  // a tile past the device-side count: nothing to do
     const int tile_n = (int)min((int64_t)kSortTile, n - (int64_t)tile * kSortTile);
 
+    // the tile's items into the staging buffer in their input order: a full
+    // tile by cp.async, every 16-byte chunk in flight at once, instead of
+    // one dependent round of loads per ranking round
+    const int64_t tbase = (int64_t)tile * kSortTile;
+    if (tile_n == kSortTile && ((reinterpret_cast<uintptr_t>(kin + tbase) | reinterpret_cast<uintptr_t>(vin + tbase)) & 15u) == 0) {
+        const unsigned char* gk = reinterpret_cast<const unsigned char*>(kin + tbase);
+        const unsigned char* gv = reinterpret_cast<const unsigned char*>(vin + tbase);
+        unsigned char* sk = reinterpret_cast<unsigned char*>(skey);
+        unsigned char* sv = reinterpret_cast<unsigned char*>(sval);
+        for (int i = threadIdx.x; i < (int)(kSortTile * sizeof(K) / 16); i += kSortThreads) sort_cp16(sk + 16 * i, gk + 16 * i);
+        for (int i = threadIdx.x; i < (int)(kSortTile * sizeof(uint32_t) / 16); i += kSortThreads)
+            sort_cp16(sv + 16 * i, gv + 16 * i);
+        sort_cp_wait();
+    } else {
+        for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
+            skey[i] = kin[tbase + i];
+            sval[i] = vin[tbase + i];
+        }
+    }
+    __syncthreads();
+
     // stable ranks within the tile (warp w owns items [tile*T + w*512, +512),
     // in 16 rounds of 32; equal digits of a round find each other with
     // __match_any_sync and the lowest lane reserves their slots)
-    const int64_t wbase = (int64_t)tile * kSortTile + (int64_t)w * kWarpItems;
+    const int64_t wbase = tbase + (int64_t)w * kWarpItems;
     const uint32_t lt = (1u << lane) - 1u;
     K key[kSortItems];
     uint32_t val[kSortItems];
@@ -239,8 +267,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K* __restric
     for (int r = 0; r < kSortItems; r++) {
         const int64_t k = wbase + r * 32 + lane;
         const bool ok = k < n;
-        key[r] = ok ? kin[k] : K(0);
-        val[r] = ok ? vin[k] : 0u;
+        const int li = w * kWarpItems + r * 32 + lane;
+        key[r] = ok ? skey[li] : K(0);
+        val[r] = ok ? sval[li] : 0u;
         const uint32_t dig = SYS ? (ok ? sys_of[val[r]] >> shift : 0u) : (uint32_t)(key[r] >> shift);
         const uint32_t d = ok ? (dig & 255u) : 256u + lane;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -314,7 +343,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K* __restric
             }
         }
     }
-    __syncthreads();
+    __syncthreads();  // every item is in registers: the buffer takes the sorted order now
     // stage the tile in its sorted order (positions are inside [0, tile_n))
 #pragma unroll
     for (int r = 0; r < kSortItems; r++) {
