@@ -476,13 +476,18 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p, float
     lo = t - (hi - s);
 }
 
+// comf / Mf (leaves): the float roundings of com and M when the caller has
+// them (the same values, without the FP64 pipe's conversions)
 template <bool QUAD>
-__device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const float* Q, const double* C)
+__device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const float* Q, const double* C,
+                           const float* comf = nullptr, float Mf = 0.f)
 {
     nt.mass64[v] = M;
     for (int a = 0; a < 3; a++) nt.com64[3 * v + a] = com[a];
-    nt.a[v] = make_float4((float)(com[0] - C[0]), (float)(com[1] - C[1]), (float)(com[2] - C[2]), (float)M);
-    nt.d[v] = make_float4((float)com[0], (float)com[1], (float)com[2], (float)M);
+    const float mf = comf ? Mf : (float)M;
+    nt.a[v] = make_float4((float)(com[0] - C[0]), (float)(com[1] - C[1]), (float)(com[2] - C[2]), mf);
+    if (comf) nt.d[v] = make_float4(comf[0], comf[1], comf[2], mf);
+    else nt.d[v] = make_float4((float)com[0], (float)com[1], (float)com[2], mf);
     if (QUAD) {
         for (int a = 0; a < 6; a++) nt.quad[6 * v + a] = Q[a];
     }
@@ -548,10 +553,22 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
                 QC[5] = fmaf(wz, dz, QC[5]);
             }
         }
+        // the centre of mass S / m as a pair of floats too: q1 = Sh / mh, the
+        // remainder S - q1 m (Sh - q1 mh exact by one FMA: the residual of
+        // a correctly rounded quotient is a float), q2 = remainder / mh;
+        // q1 + q2 is S / m within about 2^-44 of it, and the FP64 pipe is
+        // spared the division
         const double m = widen(mh) + widen(ml);
-        const double S[3] = {widen(Sh[0]) + widen(Sl[0]), widen(Sh[1]) + widen(Sl[1]), widen(Sh[2]) + widen(Sl[2])};
-        const double inv = 1.0 / m;
-        const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
+        double com[3];
+        float comf[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const float q1 = Sh[a] / mh;
+            const float r = fmaf(-q1, mh, Sh[a]) + fmaf(-q1, ml, Sl[a]);
+            const float q2 = r / mh;
+            com[a] = widen(q1) + widen(q2);
+            comf[a] = q1 + q2;
+        }
         float Q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (QUAD) {
             const float ex = (float)(com[0] - C[0]), ey = (float)(com[1] - C[1]), ez = (float)(com[2] - C[2]);
@@ -563,7 +580,7 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
             Q[4] = fmaf(-mf * ey, ez, QC[4]);
             Q[5] = fmaf(-mf * ez, ez, QC[5]);
         }
-        store_node<QUAD>(nt, v, m, com, Q, C);
+        store_node<QUAD>(nt, v, m, com, Q, C, comf, mh + ml);
     }
 }
 
