@@ -1257,7 +1257,10 @@ def run_profile_case(args):
     the network after the walk (split 2: k_band_eval, the same random network,
     band 0.55, theta 0.667) on a 2^21-body sphere; walk_plummer: two plain
     force phases of the default line's plain path (2^22, theta 0.62);
-    walk_uniform: two force phases on the uniform cube (2^20, theta 0.5)."""
+    walk_uniform: two force phases on the uniform cube (2^20, theta 0.5);
+    step_plummer: three captured steps of each path of the default line
+    (plain at theta 0.62, learned with a seeded random network at 0.667,
+    band 0.55) on its 2^22 sphere, for the launch list of a step."""
     import torch
 
     from paper_1211_2293_gb300 import inputs, tc
@@ -1307,6 +1310,28 @@ def run_profile_case(args):
         ctx.sync()
         print(f"band: Plummer N={n}, evaluations {ctx.mlp_evals()}")
         ctx.close()
+        return 0
+    if case == "step_plummer":
+        # three steps of each path of the default line on its sphere: plain
+        # at theta 0.62, learned (seeded random network, band 0.55) at 0.667
+        p, v, m = inputs.plummer(N_EVAL, seed=101)
+        P, M, V = (torch.from_numpy(a).cuda() for a in (p, m, v))
+        rng = np.random.default_rng(0)
+        params = (rng.standard_normal(tc.MLP_NPARAM) * 0.1).astype(np.float32)
+        model = np.concatenate([params, np.zeros(13), np.ones(13), np.full(3, 1e-3)]).astype(np.float32)
+        for name, th in (("plain", 0.62), ("learned", 0.667)):
+            ctx = tc.Context(precise=1, quad=int(name == "learned"), want_pot=0, verify=0)
+            ctx.build(P, M, LEAF)
+            if name == "learned":
+                ctx.mlp_set(model, 0.55)
+                ctx.set_config(learned=1)
+            ctx.set_velocity(V)
+            ctx.forces(th, EPS)
+            for _ in range(3):
+                ctx.step(DT)
+            ctx.sync()
+            print(f"step_plummer: {name} path, N={N_EVAL}, theta {th}, three steps")
+            ctx.close()
         return 0
     if case == "fmm":
         ctx = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
@@ -1362,7 +1387,7 @@ def main():
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")
     ap.add_argument("--band-train", type=float, default=0.4, help="learned: band of the training pairs")
     ap.add_argument("--nsys", type=int, default=512)
-    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole", "fmm", "band", "walk_plummer",
+    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole", "fmm", "band", "walk_plummer", "step_plummer",
                                                "walk_uniform"], default=None,
                     help="run one small case of a kernel family for an ncu capture and exit")
     args = ap.parse_args()

@@ -15,22 +15,56 @@ namespace {
 // (the error is reported at the next synchronisation).
 __device__ __forceinline__ bool failed(const Info* info) { return *(volatile const int32_t*)&info->err != 0; }
 
+// The update is elementwise over the 3 n floats of the state: x += (v +=
+// a hk) dt.  Each thread takes float4 runs (grid-stride) when the arrays are
+// 16-byte aligned, else single floats; the error word is read once per warp.
+__device__ __forceinline__ bool warp_failed(const Info* info)
+{
+    bool f = false;
+    if ((threadIdx.x & 31) == 0) f = failed(info);
+    return __shfl_sync(0xffffffffu, f, 0);
+}
+
+__device__ __forceinline__ float kick1(float v, float a, float hk) { return __fadd_rn(v, __fmul_rn(a, hk)); }
+__device__ __forceinline__ float drift1(float x, float v, float dt) { return __fadd_rn(x, __fmul_rn(v, dt)); }
+
+template <bool DRIFT, bool VEC>
 __global__ void k_kick_drift(float* __restrict__ pos, float* __restrict__ vel, const float* __restrict__ acc,
                              int64_t n3, float hk, float dt, const Info* info)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n3 || failed(info)) return;
-    float v = __fadd_rn(vel[i], __fmul_rn(acc[i], hk));
-    vel[i] = v;
-    pos[i] = __fadd_rn(pos[i], __fmul_rn(v, dt));
-}
-
-__global__ void k_kick(float* __restrict__ vel, const float* __restrict__ acc, int64_t n3, float hk,
-                       const Info* info)
-{
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n3 || failed(info)) return;
-    vel[i] = __fadd_rn(vel[i], __fmul_rn(acc[i], hk));
+    if (warp_failed(info)) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (VEC) {
+        const int64_t n4 = n3 >> 2;
+        float4* v4 = reinterpret_cast<float4*>(vel);
+        float4* p4 = reinterpret_cast<float4*>(pos);
+        const float4* a4 = reinterpret_cast<const float4*>(acc);
+        for (int64_t i = i0; i < n4; i += stride) {
+            const float4 a = a4[i];
+            float4 v = v4[i];
+            v.x = kick1(v.x, a.x, hk);
+            v.y = kick1(v.y, a.y, hk);
+            v.z = kick1(v.z, a.z, hk);
+            v.w = kick1(v.w, a.w, hk);
+            v4[i] = v;
+            if (DRIFT) {
+                float4 x = p4[i];
+                x.x = drift1(x.x, v.x, dt);
+                x.y = drift1(x.y, v.y, dt);
+                x.z = drift1(x.z, v.z, dt);
+                x.w = drift1(x.w, v.w, dt);
+                p4[i] = x;
+            }
+        }
+        done = n4 << 2;
+    }
+    for (int64_t i = done + i0; i < n3; i += stride) {
+        const float v = kick1(vel[i], acc[i], hk);
+        vel[i] = v;
+        if (DRIFT) pos[i] = drift1(pos[i], v, dt);
+    }
 }
 
 // KE, PE = 1/2 sum m pot, P, L in FP64; block sums, then FP64 atomics
@@ -139,17 +173,31 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+namespace {
+template <bool DRIFT>
+void launch_update(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt, const Info* info,
+                   cudaStream_t s)
+{
+    const bool vec = ((reinterpret_cast<uintptr_t>(vel) | reinterpret_cast<uintptr_t>(acc) |
+                       (DRIFT ? reinterpret_cast<uintptr_t>(pos) : 0)) & 15u) == 0;
+    int64_t g = nblk(vec ? (3 * n + 3) / 4 : 3 * n, 256);
+    if (g > 8 * sm_count()) g = 8 * sm_count();
+    if (g < 1) g = 1;
+    if (vec) k_kick_drift<DRIFT, true><<<(unsigned)g, 256, 0, s>>>(pos, vel, acc, 3 * n, hkick, dt, info);
+    else k_kick_drift<DRIFT, false><<<(unsigned)g, 256, 0, s>>>(pos, vel, acc, 3 * n, hkick, dt, info);
+    count_launches(1);
+}
+}  // namespace
+
 void launch_kick_drift(float* pos, float* vel, const float* acc, int64_t n, float hkick, float dt, const Info* info,
                        cudaStream_t s)
 {
-    k_kick_drift<<<nblk(3 * n, 256), 256, 0, s>>>(pos, vel, acc, 3 * n, hkick, dt, info);
-    count_launches(1);
+    launch_update<true>(pos, vel, acc, n, hkick, dt, info, s);
 }
 
 void launch_kick(float* vel, const float* acc, int64_t n, float hkick, const Info* info, cudaStream_t s)
 {
-    k_kick<<<nblk(3 * n, 256), 256, 0, s>>>(vel, acc, 3 * n, hkick, info);
-    count_launches(1);
+    launch_update<false>(nullptr, vel, acc, n, hkick, 0.f, info, s);
 }
 
 // FP32 throughput probe: every thread runs 8 independent chains of `iters`
