@@ -345,6 +345,7 @@ int ensure_nodes(tc_ctx* c, int64_t M)
     TC_GROW(c, c->nt.quad, 6 * cap);
     TC_GROW(c, c->nt.feat, 2 * cap);
     TC_GROW(c, c->nt.mass64, cap);
+    TC_GROW(c, c->nt.dsum, 2 * cap);
     TC_GROW(c, c->nt.com64, 3 * cap);
     // the level sort reuses the body sort's value ping-pong buffer and status words
     if (cap > c->cap_n) TC_GROW(c, c->sb.vals_alt, cap);

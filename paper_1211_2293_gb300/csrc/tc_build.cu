@@ -20,7 +20,8 @@
 //   7. one stable radix pass by level  -> breadth-first order
 //   8. k_node_finalize  counts, children, integer centres
 //   9. k_leaf_moments, then k_level_moments level by level from the deepest
-//                  FP64 mass / centre of mass / second moments, bottom-up
+//                  mass / centre of mass (float-pair sums, FP64-class, stored
+//                  in FP64) / second moments (FP32), bottom-up
 //  10. k_group_marks + scan + k_group_table   body groups for the walk
 //
 // Which cubes exist.  Let cd(a, b) be the number of leading octal digits two
@@ -434,8 +435,11 @@ __global__ void k_node_finalize(const uint64_t* __restrict__ keys, const int8_t*
 }
 
 // ------------------------------------------------------------------ moments
-// Mass, centre of mass and second moments about the centre of mass, FP64.
-// Leaves sum their bodies (positions taken relative to the cube centre);
+// Mass, centre of mass and second moments about the centre of mass.  The
+// sums of m and m x are kept as unevaluated pairs of floats (hi + lo, about
+// 48 significant bits) on the FP32 pipe and stored in FP64 as well; GB300's
+// FP64 pipe, a small fraction of its FP32 rate, bound these kernels when
+// they summed in FP64.  Leaves sum their bodies;
 // an internal cell combines its children: M = sum M_c,
 // com = sum M_c com_c / M, Q = sum Q_c + M_c dc dc^T with dc = com_c - com.
 // Leaves are done in one launch; internal cells level by level from the
@@ -476,7 +480,25 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p, float
     lo = t - (hi - s);
 }
 
-// comf / Mf (leaves): the float roundings of com and M when the caller has
+// the centre of mass S / m of float pairs as a pair of floats: q1 = Sh / mh,
+// the remainder S - q1 m (Sh - q1 mh exact by one FMA: the residual of a
+// correctly rounded quotient is a float), q2 = remainder / mh; q1 + q2 is
+// S / m within about 2^-44 of it, taken exactly into FP64 (com) and rounded
+// once to float (comf); the FP64 pipe is spared the division
+__device__ __forceinline__ void pair_quotient(const float (&Sh)[3], const float (&Sl)[3], float mh, float ml,
+                                              double (&com)[3], float (&comf)[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float q1 = Sh[a] / mh;
+        const float r = fmaf(-q1, mh, Sh[a]) + fmaf(-q1, ml, Sl[a]);
+        const float q2 = r / mh;
+        com[a] = widen(q1) + widen(q2);
+        comf[a] = q1 + q2;
+    }
+}
+
+// comf / Mf: the float roundings of com and M when the caller has
 // them (the same values, without the FP64 pipe's conversions)
 template <bool QUAD>
 __device__ void store_node(NodeTables& nt, int64_t v, double M, const double* com, const float* Q, const double* C,
@@ -493,12 +515,11 @@ __device__ void store_node(NodeTables& nt, int64_t v, double M, const double* co
     }
 }
 
-// Mass and centre of mass in FP64; second moments in FP32.  The second
-// moments only feed the learned correction's BF16 features and the
-// quadrupole terms, small corrections to the monopole, so FP32 serves them
-// (their error stays a few hundred FP32 ulps of M s^2); the FP64 pipe, a
-// small fraction of the FP32 rate on GB300, is left to the mass and the
-// centre of mass.  Per leaf: Q about the cube centre C from the bodies'
+// Mass and centre of mass as float pairs (FP64-class); second moments in
+// FP32.  The second moments only feed the learned correction's BF16
+// features and the quadrupole terms, small corrections to the monopole, so
+// FP32 serves them (their error stays a few hundred FP32 ulps of M s^2).
+// Per leaf: Q about the cube centre C from the bodies'
 // offsets x - C, then moved to the centre of mass by the parallel-axis rule
 // Q_com = Q_C - M (com - C)(com - C)^T.  The offsets are formed in FP32
 // against C split into C_hi = fl(C) and C_lo = fl(C - C_hi): (x - C_hi) -
@@ -527,9 +548,9 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
         // one FMA and added by two_sum_acc.  Over a leaf's c bodies the error
         // stays below about c 2^-46 of the largest partial sum of |terms|
         // (2.3e-13 of it for c = 16): FP64-class accuracy on the FP32 pipe,
-        // which GB300 runs 64 times faster than its FP64 pipe; hi + lo is
-        // then taken exactly into FP64 for the centre of mass and the levels
-        // above.  Q about C in FP32 alongside.
+        // which GB300 runs 64 times faster than its FP64 pipe; the pair goes
+        // to the levels above, and hi + lo exactly into FP64.  Q about C in
+        // FP32 alongside.
         float mh = 0.f, ml = 0.f, Sh[3] = {0.f, 0.f, 0.f}, Sl[3] = {0.f, 0.f, 0.f};
         float QC[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int j = b.x; j < b.x + b.y; j++) {
@@ -553,22 +574,10 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
                 QC[5] = fmaf(wz, dz, QC[5]);
             }
         }
-        // the centre of mass S / m as a pair of floats too: q1 = Sh / mh, the
-        // remainder S - q1 m (Sh - q1 mh exact by one FMA: the residual of
-        // a correctly rounded quotient is a float), q2 = remainder / mh;
-        // q1 + q2 is S / m within about 2^-44 of it, and the FP64 pipe is
-        // spared the division
         const double m = widen(mh) + widen(ml);
         double com[3];
         float comf[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const float q1 = Sh[a] / mh;
-            const float r = fmaf(-q1, mh, Sh[a]) + fmaf(-q1, ml, Sl[a]);
-            const float q2 = r / mh;
-            com[a] = widen(q1) + widen(q2);
-            comf[a] = q1 + q2;
-        }
+        pair_quotient(Sh, Sl, mh, ml, com, comf);
         float Q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (QUAD) {
             const float ex = (float)(com[0] - C[0]), ey = (float)(com[1] - C[1]), ez = (float)(com[2] - C[2]);
@@ -581,11 +590,17 @@ __global__ void k_leaf_moments(const float4* __restrict__ body, const SysParams*
             Q[5] = fmaf(-mf * ez, ez, QC[5]);
         }
         store_node<QUAD>(nt, v, m, com, Q, C, comf, mh + ml);
+        nt.dsum[2 * v] = make_float4(mh, Sh[0], Sh[1], Sh[2]);
+        nt.dsum[2 * v + 1] = make_float4(ml, Sl[0], Sl[1], Sl[2]);
     }
 }
 
 // one internal cell v from its children (a leaf returns at once): mass and
-// centre of mass in FP64, second moments in FP32 by the parallel-axis rule
+// the sum of m x as float pairs, the children's pairs added by two_sum_acc
+// (each addition errs by at most about 2^-47 of the magnitudes added, so a
+// body's term collects at most depth x 2^-47 of relative error on its way
+// to the root: 1.5e-13 at depth 21), the centre of mass as their float-pair
+// quotient, both stored in FP64 too; second moments in FP32 by the parallel-axis rule
 // from the children's, Q_v = sum_c Q_c + m_c d_c d_c^T, d_c = com_c - com_v
 // formed in FP32 from the stored offsets of the centres of mass from their
 // cube centres, d_c = (a_c - a_v) + (k_c - k_v) u (k the integer cube
@@ -596,15 +611,21 @@ __device__ __forceinline__ void level_node(int64_t v, const SysParams* __restric
     const int4 pb = nt.b[v];
     const int nch = pb.w >> 8;
     if (nch == 0) return;  // leaf: done by k_leaf_moments
-    double m = 0.0, S[3] = {0, 0, 0};
+    float mh = 0.f, ml = 0.f, Sh[3] = {0.f, 0.f, 0.f}, Sl[3] = {0.f, 0.f, 0.f};
     for (int k = 0; k < nch; k++) {
         const int64_t c = pb.z + k;
-        const double mc = nt.mass64[c];
-        m += mc;
-        for (int a = 0; a < 3; a++) S[a] += mc * nt.com64[3 * c + a];
+        const float4 h = nt.dsum[2 * c], l = nt.dsum[2 * c + 1];
+        two_sum_acc(mh, ml, h.x, l.x);
+        two_sum_acc(Sh[0], Sl[0], h.y, l.y);
+        two_sum_acc(Sh[1], Sl[1], h.z, l.z);
+        two_sum_acc(Sh[2], Sl[2], h.w, l.w);
     }
-    const double inv = 1.0 / m;
-    const double com[3] = {S[0] * inv, S[1] * inv, S[2] * inv};
+    const double m = widen(mh) + widen(ml);
+    double com[3];
+    float comf[3];
+    pair_quotient(Sh, Sl, mh, ml, com, comf);
+    nt.dsum[2 * v] = make_float4(mh, Sh[0], Sh[1], Sh[2]);
+    nt.dsum[2 * v + 1] = make_float4(ml, Sl[0], Sl[1], Sl[2]);
     const int4 cc = nt.c[v];
     double C[3];
     cube_centre(sysp[cc.w], cc, C);
@@ -626,7 +647,7 @@ __device__ __forceinline__ void level_node(int64_t v, const SysParams* __restric
         Q[4] += fmaf(mc * d[1], d[2], qc[4]);
         Q[5] += fmaf(mc * d[2], d[2], qc[5]);
     }
-    store_node<QUAD>(nt, v, m, com, Q, C);
+    store_node<QUAD>(nt, v, m, com, Q, C, comf, mh + ml);
 }
 
 // internal cells of level `lev`: [level_start[lev], level_start[lev + 1])

@@ -76,6 +76,7 @@ struct NodeTables {
                      // M / M_sys, 6 moment ratios), normalised, as BF16 pairs (words 2..7 of a row)
     double* mass64;  // FP64 bottom-up reduction results
     double* com64;   // 3 per node
+    float4* dsum;    // 2 per node: the bottom-up sums {m, m x} as float pairs, hi parts then lo parts
 };
 
 // scratch of the radix sort / scans
