@@ -1260,7 +1260,9 @@ def run_profile_case(args):
     walk_uniform: two force phases on the uniform cube (2^20, theta 0.5);
     step_plummer: three captured steps of each path of the default line
     (plain at theta 0.62, learned with a seeded random network at 0.667,
-    band 0.55) on its 2^22 sphere, for the launch list of a step."""
+    band 0.55) on its 2^22 sphere, for the launch list of a step;
+    step_uniform: three captured steps of the uniform-cube workload (2^20,
+    theta 0.5)."""
     import torch
 
     from paper_1211_2293_gb300 import inputs, tc
@@ -1309,6 +1311,18 @@ def run_profile_case(args):
             ctx.forces(0.667, EPS)
         ctx.sync()
         print(f"band: Plummer N={n}, evaluations {ctx.mlp_evals()}")
+        ctx.close()
+        return 0
+    if case == "step_uniform":
+        # three captured steps of the uniform-cube workload (2^20, theta 0.5)
+        p, _, m = inputs.uniform_cube(1 << 20, SEED)
+        ctx = tc.Context(want_pot=0, verify=0)
+        ctx.build(torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda(), LEAF)
+        ctx.forces(THETA, EPS)
+        for _ in range(3):
+            ctx.step(DT)
+        ctx.sync()
+        print(f"step_uniform: N={1 << 20}, theta {THETA}, three steps")
         ctx.close()
         return 0
     if case == "step_plummer":
@@ -1387,7 +1401,7 @@ def main():
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")
     ap.add_argument("--band-train", type=float, default=0.4, help="learned: band of the training pairs")
     ap.add_argument("--nsys", type=int, default=512)
-    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole", "fmm", "band", "walk_plummer", "step_plummer",
+    ap.add_argument("--profile-case", choices=["build", "learned", "quadrupole", "fmm", "band", "walk_plummer", "step_plummer", "step_uniform",
                                                "walk_uniform"], default=None,
                     help="run one small case of a kernel family for an ncu capture and exit")
     args = ap.parse_args()

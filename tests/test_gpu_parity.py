@@ -39,6 +39,18 @@ def _bodies(kind, n, seed):
         p = rng.standard_normal((n, 3)).astype(np.float32)
         v = np.zeros((n, 3), np.float32)
         m = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    elif kind == "masses":
+        # masses over twelve decades: the float-pair moment sums against FP64
+        rng = np.random.default_rng(seed)
+        p = rng.standard_normal((n, 3)).astype(np.float32)
+        v = np.zeros((n, 3), np.float32)
+        m = (10.0 ** rng.uniform(-6, 6, n)).astype(np.float32)
+    elif kind == "offset":
+        # a tight cluster far from the origin: m x sums of large terms
+        rng = np.random.default_rng(seed)
+        p = (1000.0 + 0.01 * rng.standard_normal((n, 3))).astype(np.float32)
+        v = np.zeros((n, 3), np.float32)
+        m = (10.0 ** rng.uniform(-3, 3, n)).astype(np.float32)
     elif kind == "coincident":
         p = np.zeros((n, 3), np.float32)
         p[: n // 2] = [0.5, 0.5, 0.5]
@@ -96,7 +108,7 @@ def _compare_tree(ctx, t, gmax):
     ("plummer", 4096, 8, 64), ("random", 1, 1, 32), ("random", 2, 1, 32), ("random", 9, 8, 32),
     ("random", 17, 4, 64), ("random", 100, 3, 128), ("uniform", 5000, 16, 64), ("coincident", 40, 4, 32),
     ("random", 3000, 1, 32), ("plummer", 20000, 64, 128), ("plummer", 30000, 256, 128),
-    ("uniform", 30000, 300, 64)])
+    ("uniform", 30000, 300, 64), ("masses", 20000, 16, 64), ("offset", 20000, 16, 64)])
 def test_tree_bit_exact(tc, kind, n, leaf, gmax):
     p, _, m = _bodies(kind, n, 7)
     ctx = _ctx(tc, gmax=gmax)
