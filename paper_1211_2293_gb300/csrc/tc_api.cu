@@ -294,6 +294,9 @@ int ensure_bodies(tc_ctx* c, int64_t n)
     TC_GROW(c, c->sb.tiles, kSortMaxPasses);
     c->sb.err = &c->info->err;
     TC_GROW(c, c->sb.blocksum, scan_blocksum_size(cap));
+    TC_GROW(c, c->sb.runs, cap / 32 + 16);  // runs of more than 32 items
+    c->sb.run_cap = cap / 32 + 16;
+    TC_GROW(c, c->sb.nruns, 1);
     TC_GROW(c, c->w, cap);
     TC_GROW(c, c->delta, cap);
     TC_GROW(c, c->top, cap);
@@ -367,6 +370,12 @@ int check_device(tc_ctx* c)
         TC_CUDA(c, cudaStreamSynchronize(c->stream));
         if (e & kErrNonFinite)
             return fail(c, TC_EINVAL, "input holds a non-finite coordinate or a non-positive/non-finite mass");
+        if (e & kErrSortRun)
+            return fail(c, TC_EDEVICE,
+                        "a rebuild inside a step found a tree far deeper than the last synchronised build's "
+                        "(a run of more than %lld bodies sharing the sorted key digits); the state holds that "
+                        "step's drift -- call tc_ctx_build or tc_set_state to rebuild",
+                        (long long)kSortRunMax);
         if (e & kErrCapacity)
             return fail(c, TC_EDEVICE,
                         "node table capacity exceeded by a rebuild inside a step; the state holds that step's "
@@ -461,7 +470,19 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
     if (synced) TC_CUDA(c, cudaMemsetAsync(&c->info->err, 0, sizeof(int32_t), s));
     launch_bbox(c->pos, c->chunks, c->nchunks, c->sysp, c->nsys, &c->info->err, s);
     launch_keys(c->pos, c->mass, n, c->sys_of, c->sysp, c->keys, c->perm, &c->info->err, s);
-    radix_sort_u64(c->keys, c->perm, n, 63, c->sys_of, c->nsys > 1 ? sys_bits(c->nsys) : 0, c->sb, s);
+    // Inside a step the passes sort only the key digits of the levels down
+    // to the last synchronised build's depth + kSortMarginLevels (rounded
+    // to whole bytes); runs of equal top digits, a leaf's bodies as long as
+    // the tree is no deeper than that, are then completed one by one, which
+    // gives the full sort's order (a deeper tree gives longer runs, which
+    // the completion still orders, up to kSortRunMax bodies a run).  A
+    // synchronised build sorts every digit.
+    int low_bit = 0;
+    if (!synced && c->depth_hint >= 0) {
+        const int levels = std::min(kMaxLevel, c->depth_hint + kSortMarginLevels);
+        low_bit = (63 - 3 * levels) / 8 * 8;
+    }
+    radix_sort_u64(c->keys, c->perm, n, 63, c->sys_of, c->nsys > 1 ? sys_bits(c->nsys) : 0, c->sb, s, low_bit);
     launch_gather(c->pos, c->mass, c->perm, n, c->body, s);
     TC_CUDA(c, cudaMemsetAsync(&c->info->depth, 0, sizeof(int32_t), s));
     launch_node_counts(c->keys, c->sys_of, n, c->leaf_max, c->w, c->delta, c->top, c->nstart, &c->info->depth, s);

@@ -27,6 +27,7 @@ enum : int32_t {
     kErrFmmPool = 32,     // the FMM's unresolved-source pool outgrew its allocation (regrown, rerun)
     kErrFmmSlab = 64,     // one cell's unresolved-source list outgrew its slab (regrown, rerun)
     kErrFmmStack = 128,   // the FMM's refinement stack overflowed
+    kErrSortRun = 256,    // a rebuild inside a step met a run of equal top key bits too long to complete
 };
 
 // Per-system root cube (written by the bounding-box kernels).
@@ -88,6 +89,11 @@ struct SortBufs {
     uint32_t* tiles;                 // tile counters, one per pass
     int32_t* err;                    // device error word (bounded look-back)
     uint32_t* blocksum;              // scan partials
+    // a sort of the keys' top bits only: the starts of runs of equal top bits
+    // longer than the per-thread completion takes (capacity run_cap), their count
+    int64_t* runs = nullptr;
+    unsigned long long* nruns = nullptr;
+    int64_t run_cap = 0;
 };
 constexpr int kSortMaxPasses = 10;   // 8 key passes + up to 2 system passes
 
@@ -112,8 +118,16 @@ int64_t scan_blocksum_size(int64_t n);
 // sys_bits > 0) by the system of each value's body, sys_of[val], so the
 // result is ordered by (system, key).  Afterwards b.ghist[p * 256 + d] is
 // the number of items whose pass-p digit is below d.
+// low_bit > 0 (a multiple of 8; needs b.runs): the passes sort bits
+// [low_bit, nbits) only, then every run of items with equal top bits (and
+// system) is put in (key, val) order by a per-run completion, so the
+// result is the same as the full sort's whenever the values are distinct
+// (the bodies' indices); a run longer than kSortRunMax raises kErrSortRun
+// and kErrCapacity instead.
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of,
-                    int sys_bits, SortBufs& b, cudaStream_t s);
+                    int sys_bits, SortBufs& b, cudaStream_t s, int low_bit = 0);
+constexpr int64_t kSortRunMax = 16384;
+constexpr int kSortMarginLevels = 2;  // levels below the last synchronised depth a step's sort orders
 // The same for 32-bit keys when the item count is only known on the device:
 // n_cap bounds it, *n_dev (device) holds it.
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n_cap, const int64_t* n_dev, int nbits,

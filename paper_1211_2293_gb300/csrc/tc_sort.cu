@@ -142,7 +142,7 @@ constexpr unsigned kLookbackMaxPolls = 1u << 22;  // about a second of polling
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(const K* __restrict__ keys, int64_t n_host,
                                                                 const int64_t* __restrict__ n_dev, int npass,
-                                                                uint32_t* __restrict__ ghist)
+                                                                int shift0, uint32_t* __restrict__ ghist)
 {
     __shared__ uint32_t h[8][256];
     const int64_t n = n_dev ? min(*n_dev, n_host) : n_host;  // never past the buffers
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(const K* __restr
     __syncthreads();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const K key = keys[k];
-        for (int p = 0; p < npass; p++) atomicAdd(&h[p][(uint32_t)(key >> (8 * p)) & 255u], 1u);
+        for (int p = 0; p < npass; p++) atomicAdd(&h[p][(uint32_t)(key >> (shift0 + 8 * p)) & 255u], 1u);
     }
     __syncthreads();
     for (int p = 0; p < npass; p++) {
@@ -390,13 +390,114 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
     count_launches(3);
 }
 
+// ---------------------------------------------------- per-run completion
+// After passes over bits [low_bit, 63) only, items with equal top bits (and
+// equal system) sit together in value order; each such run is put in
+// (key, val) order -- which, the values being distinct, is the order of
+// the full sort.  A run of at most kShortRun items is ranked by its own
+// threads (one item each, rank = the items of the run that precede it);
+// a longer run is listed and ranked by a block of its own.
+constexpr int kShortRun = 32;
+
+__device__ __forceinline__ bool same_run(const uint64_t* __restrict__ k, const uint32_t* __restrict__ v,
+                                         const uint32_t* __restrict__ sys_of, int low_bit, int64_t i, int64_t j)
+{
+    if ((k[i] >> low_bit) != (k[j] >> low_bit)) return false;
+    return !sys_of || sys_of[v[i]] == sys_of[v[j]];
+}
+
+__device__ __forceinline__ bool before(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb)
+{
+    return ka < kb || (ka == kb && va < vb);
+}
+
+__global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                   uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                   int64_t n, int low_bit, const uint32_t* __restrict__ sys_of,
+                                                   int64_t* __restrict__ runs, unsigned long long* __restrict__ nruns,
+                                                   int64_t run_cap, int32_t* __restrict__ err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t st = i;
+        while (st > 0 && i - st < kShortRun && same_run(kin, vin, sys_of, low_bit, st - 1, i)) st--;
+        int64_t en = i + 1;
+        while (en < n && en - st <= kShortRun && same_run(kin, vin, sys_of, low_bit, en, i)) en++;
+        if (en - st > kShortRun || (st > 0 && i - st >= kShortRun && same_run(kin, vin, sys_of, low_bit, st - 1, i))) {
+            // part of a long run: its first item lists it
+            if (i == 0 || !same_run(kin, vin, sys_of, low_bit, i - 1, i)) {
+                const unsigned long long at = atomicAdd(nruns, 1ull);
+                if ((int64_t)at < run_cap) runs[at] = i;
+                else atomicOr(err, kErrSortRun | kErrCapacity);
+            }
+            continue;
+        }
+        const uint64_t k = kin[i];
+        const uint32_t v = vin[i];
+        int64_t r = 0;
+        for (int64_t j = st; j < en; j++) r += before(kin[j], vin[j], k, v) ? 1 : 0;
+        kout[st + r] = k;
+        vout[st + r] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sort_long_runs(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                        uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                        int64_t n, int low_bit, const uint32_t* __restrict__ sys_of,
+                                                        const int64_t* __restrict__ runs,
+                                                        const unsigned long long* __restrict__ nruns, int64_t run_cap,
+                                                        int32_t* __restrict__ err)
+{
+    __shared__ long long en_sh;
+    const int64_t nr = (int64_t)min(*nruns, (unsigned long long)run_cap);
+    for (int64_t q = blockIdx.x; q < nr; q += gridDim.x) {
+        const int64_t st = runs[q];
+        // the run's end: the first item past st of another run (or n), or
+        // past kSortRunMax items
+        if (threadIdx.x == 0) en_sh = min(n, st + kSortRunMax + 1);
+        __syncthreads();
+        for (int64_t j = st + 1 + threadIdx.x; j < min(n, st + kSortRunMax + 1); j += blockDim.x) {
+            if (j >= en_sh) break;
+            if (!same_run(kin, vin, sys_of, low_bit, j, st)) atomicMin(&en_sh, (long long)j);
+        }
+        __syncthreads();
+        const int64_t en = en_sh;
+        __syncthreads();
+        if (en - st > kSortRunMax) {
+            if (threadIdx.x == 0) atomicOr(err, kErrSortRun | kErrCapacity);
+            continue;
+        }
+        for (int64_t i = st + threadIdx.x; i < en; i += blockDim.x) {
+            const uint64_t k = kin[i];
+            const uint32_t v = vin[i];
+            int64_t r = 0;
+            for (int64_t j = st; j < en; j++) r += before(kin[j], vin[j], k, v) ? 1 : 0;
+            kout[st + r] = k;
+            vout[st + r] = v;
+        }
+    }
+}
+
+void launch_sort_runs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
+                      int low_bit, const uint32_t* sys_of, SortBufs& b, cudaStream_t s)
+{
+    cudaMemsetAsync(b.nruns, 0, sizeof(unsigned long long), s);
+    int64_t g = (n + 255) / 256;
+    if (g > 16 * sm_count()) g = 16 * sm_count();
+    k_sort_runs<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(kin, vin, kout, vout, n, low_bit, sys_of, b.runs, b.nruns,
+                                                          b.run_cap, b.err);
+    k_sort_long_runs<<<(unsigned)(2 * sm_count()), 256, 0, s>>>(kin, vin, kout, vout, n, low_bit, sys_of, b.runs,
+                                                                b.nruns, b.run_cap, b.err);
+    count_launches(2);
+}
+
 int64_t radix_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 
 template <typename K>
 static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n_dev, int nbits,
-                            const uint32_t* sys_of, int sys_bits, SortBufs& b, K* keys_alt, cudaStream_t s)
+                            const uint32_t* sys_of, int sys_bits, SortBufs& b, K* keys_alt, cudaStream_t s,
+                            int low_bit = 0)
 {
-    const int nkey = (nbits + 7) / 8;
+    const int nkey = (nbits + 7) / 8 - low_bit / 8;
     const int nsys = (sys_bits + 7) / 8;
     const int npass = nkey + nsys;
     cudaMemsetAsync(b.ghist, 0, kSortMaxPasses * 256 * sizeof(uint32_t), s);
@@ -407,7 +508,7 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
     cudaMemsetAsync(b.tiles, 0, kSortMaxPasses * sizeof(uint32_t), s);
     int hb = (int)((n + kSortThreads * 16 - 1) / (kSortThreads * 16));
     if (hb > 4 * sm_count()) hb = 4 * sm_count();
-    k_sort_hist_all<K><<<hb, kSortThreads, 0, s>>>(keys, n, n_dev, nkey, b.ghist);
+    k_sort_hist_all<K><<<hb, kSortThreads, 0, s>>>(keys, n, n_dev, nkey, low_bit, b.ghist);
     count_launches(1);
     if (nsys) {
         k_sort_hist_sys<<<hb, kSortThreads, 0, s>>>(sys_of, n, nsys, b.ghist + 256 * nkey);
@@ -440,7 +541,7 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
     const size_t dsm = onesweep_smem<K>();
     for (int p = 0; p < npass; p++) {
         const bool sysp = p >= nkey;
-        const int shift = sysp ? 8 * (p - nkey) : 8 * p;
+        const int shift = sysp ? 8 * (p - nkey) : low_bit + 8 * p;
         if (sysp)
             k_onesweep<K, true><<<(unsigned)nt, kSortThreads, dsm, s>>>(ka, va, kb, vb, n, n_dev, shift, b.ghist + 256 * p,
                                                                       b.status + (size_t)p * nt * 256, b.tiles + p,
@@ -454,7 +555,16 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
-    if (npass & 1) {
+    if constexpr (sizeof(K) == 8) {
+        if (low_bit > 0) {
+            // the runs of equal top bits into (key, val) order, from the
+            // passes' result into the other buffer pair
+            launch_sort_runs(ka, va, kb, vb, n, low_bit, sys_bits > 0 ? sys_of : nullptr, b, s);
+            ka = kb;
+            va = vb;
+        }
+    }
+    if (ka != keys) {
         cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     }
@@ -485,9 +595,10 @@ cudaError_t sort_wait_selftest(uint64_t* keys, uint32_t* vals, uint64_t* kout, u
 int64_t sort_selftest_items() { return 2 * (int64_t)kSortTile; }
 
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of, int sys_bits,
-                    SortBufs& b, cudaStream_t s)
+                    SortBufs& b, cudaStream_t s, int low_bit)
 {
-    radix_sort_impl<uint64_t>(keys, vals, n, nullptr, nbits, sys_of, sys_bits, b, b.keys_alt, s);
+    if (low_bit < 0 || low_bit % 8 != 0 || low_bit >= nbits || (low_bit > 0 && (!b.runs || !b.nruns))) low_bit = 0;
+    radix_sort_impl<uint64_t>(keys, vals, n, nullptr, nbits, sys_of, sys_bits, b, b.keys_alt, s, low_bit);
 }
 
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n_cap, const int64_t* n_dev, int nbits, SortBufs& b,

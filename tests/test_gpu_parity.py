@@ -534,13 +534,34 @@ def test_size_class_modes_agree(tc, gmax):
     assert np.array_equal(accs[0][0], accs[1][0]) and np.array_equal(accs[0][1], accs[1][1])
 
 
+@pytest.mark.parametrize("kind,n,leaf", [("uniform", 1 << 18, 16), ("plummer", 1 << 18, 16), ("plummer", 50000, 4)])
+def test_step_sort_of_top_digits_gives_the_full_order(tc, kind, n, leaf):
+    """Inside a step the radix passes sort only the key digits down to the
+    last synchronised depth + 2 levels and complete every run of equal top
+    digits by itself: Morton order, keys and tree equal the oracle's full
+    sort on the stepped positions."""
+    p, v, m = _bodies(kind, n, 41)
+    ctx = _ctx(tc, gmax=64)
+    ctx.build(_dev(p), _dev(m), leaf)
+    ctx.forces(0.6, 0.01)
+    ctx.sizes()  # synchronise: the depth hint
+    rng = np.random.default_rng(42)
+    ctx.set_velocity(_dev((0.1 * rng.standard_normal((n, 3))).astype(np.float32)))
+    ctx.step(1e-3)
+    pos, _ = ctx.get_state()
+    t = oracle.Tree(pos, m, leaf, 64)
+    _compare_tree(ctx, t, 64)
+
+
 def test_step_builds_a_deeper_tree_than_the_last_synchronised_one(tc):
     """A captured step knows the tree depth only from an earlier build; its
     moment reduction gives each level down to that depth + 2 a launch and
-    any deeper level one block.  The drift of one step moves 40 bodies into
-    a cube of side 1e-6, so the step's tree is 15+ levels deeper than the
-    last synchronised one: its moments and structure still equal the
-    oracle's on the new positions."""
+    any deeper level one block; its sort orders the key digits down to that
+    depth + 2 and completes longer runs of equal digits one block each.  The
+    drift of one step moves 40 bodies into a cube of side 1e-6, so the
+    step's tree is 15+ levels deeper than the last synchronised one: its
+    order, moments and structure still equal the oracle's on the new
+    positions."""
     p, _, m = _bodies("uniform", 4096, 31)
     ctx = _ctx(tc, gmax=64)
     ctx.build(_dev(p), _dev(m), 8)
