@@ -471,8 +471,8 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
     launch_bbox(c->pos, c->chunks, c->nchunks, c->sysp, c->nsys, &c->info->err, s);
     launch_keys(c->pos, c->mass, n, c->sys_of, c->sysp, c->keys, c->perm, &c->info->err, s);
     // Inside a step the passes sort only the key digits of the levels down
-    // to the last synchronised build's depth + kSortMarginLevels (rounded
-    // to whole bytes); runs of equal top digits, a leaf's bodies as long as
+    // to the last synchronised build's depth + kSortMarginLevels; runs of
+    // equal top digits, a leaf's bodies as long as
     // the tree is no deeper than that, are then completed one by one, which
     // gives the full sort's order (a deeper tree gives longer runs, which
     // the completion still orders, up to kSortRunMax bodies a run).  A
@@ -480,7 +480,7 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
     int low_bit = 0;
     if (!synced && c->depth_hint >= 0) {
         const int levels = std::min(kMaxLevel, c->depth_hint + kSortMarginLevels);
-        low_bit = (63 - 3 * levels) / 8 * 8;
+        low_bit = 63 - 3 * levels;
     }
     radix_sort_u64(c->keys, c->perm, n, 63, c->sys_of, c->nsys > 1 ? sys_bits(c->nsys) : 0, c->sb, s, low_bit);
     launch_gather(c->pos, c->mass, c->perm, n, c->body, s);

@@ -118,8 +118,8 @@ int64_t scan_blocksum_size(int64_t n);
 // sys_bits > 0) by the system of each value's body, sys_of[val], so the
 // result is ordered by (system, key).  Afterwards b.ghist[p * 256 + d] is
 // the number of items whose pass-p digit is below d.
-// low_bit > 0 (a multiple of 8; needs b.runs): the passes sort bits
-// [low_bit, nbits) only, then every run of items with equal top bits (and
+// low_bit > 0 (needs b.runs): the passes sort bits [low_bit, nbits) only
+// (8-bit digits from low_bit up), then every run of items with equal top bits (and
 // system) is put in (key, val) order by a per-run completion, so the
 // result is the same as the full sort's whenever the values are distinct
 // (the bodies' indices); a run longer than kSortRunMax raises kErrSortRun

@@ -497,7 +497,7 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
                             const uint32_t* sys_of, int sys_bits, SortBufs& b, K* keys_alt, cudaStream_t s,
                             int low_bit = 0)
 {
-    const int nkey = (nbits + 7) / 8 - low_bit / 8;
+    const int nkey = (nbits - low_bit + 7) / 8;  // 8-bit digits from bit low_bit up
     const int nsys = (sys_bits + 7) / 8;
     const int npass = nkey + nsys;
     cudaMemsetAsync(b.ghist, 0, kSortMaxPasses * 256 * sizeof(uint32_t), s);
@@ -597,7 +597,7 @@ int64_t sort_selftest_items() { return 2 * (int64_t)kSortTile; }
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of, int sys_bits,
                     SortBufs& b, cudaStream_t s, int low_bit)
 {
-    if (low_bit < 0 || low_bit % 8 != 0 || low_bit >= nbits || (low_bit > 0 && (!b.runs || !b.nruns))) low_bit = 0;
+    if (low_bit < 0 || low_bit >= nbits || (low_bit > 0 && (!b.runs || !b.nruns))) low_bit = 0;
     radix_sort_impl<uint64_t>(keys, vals, n, nullptr, nbits, sys_of, sys_bits, b, b.keys_alt, s, low_bit);
 }
 
