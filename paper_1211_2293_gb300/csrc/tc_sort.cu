@@ -89,7 +89,7 @@ __global__ void k_scan_top(uint32_t* __restrict__ bsum, int64_t nb, uint32_t* __
 // PREFIX: the block's offset is the sum of the raw partials of the blocks
 // before it (no k_scan_top; the last block writes the total) -- for up to
 // kScanFusedBlocks blocks, where that sum is cheaper than another launch
-constexpr int64_t kScanFusedBlocks = 1024;
+constexpr int64_t kScanFusedBlocks = 256;
 
 template <bool PREFIX>
 __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
