@@ -72,7 +72,9 @@ typedef struct tc_ctx tc_ctx;
  *             monopole (second-order expansion of the softened potential
  *             about the centre of mass; needs precise = 1, quad = 1)
  *   classes   1: with gmax 64 or 128 the walk runs one launch per group
- *             size class, largest first: a group of at most 32 bodies is
+ *             size class (the largest on the calling stream, the others
+ *             beside it on a stream of the context's, joined back before the
+ *             call returns its work to the stream): a group of at most 32 bodies is
  *             summed one body per lane, one of at most 64 two per lane, a
  *             larger one four (the default); 0: one launch, gmax / 32
  *             bodies per lane for every group.  Lists and forces are the

@@ -27,6 +27,10 @@ constexpr int kMlpNParamHost = 13 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3;
 struct tc_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // a stream of our own to capture step graphs on
+    // the walk's smaller size classes run beside the largest on a stream of
+    // their own (forked from and joined to the launching stream by events)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     int num_sms = 0;
     tc_config cfg{};
@@ -632,13 +636,25 @@ int run_forces(tc_ctx* c, float theta, float eps, float G, cudaStream_t s)
     if (c->walk_ncls == 0) {
         e = launch_walk(a, c->walk_cfg, c->walk_grid, c->walk_smem, s);
     } else {
+        // the largest class on s, the others after it on the side stream:
+        // their blocks take the SMs that the largest class's blocks leave
+        // when its groups run out, instead of waiting for its last block
+        if (!c->side_stream) TC_CUDA(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        if (!c->ev_fork) TC_CUDA(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        if (!c->ev_join) TC_CUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        // the work counters and the totals behind them, before either stream starts
+        TC_CUDA(c, cudaMemsetAsync(&c->info->work[0], 0, sizeof(c->info->work) + 3 * sizeof(unsigned long long), s));
+        TC_CUDA(c, cudaEventRecord(c->ev_fork, s));
+        TC_CUDA(c, cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
         for (int k = c->walk_ncls - 1; k >= 0 && e == cudaSuccess; k--) {
             a.glist = c->glists + (int64_t)k * c->cap_n;
             a.glist_n = c->glist_n + k;
             a.work_slot = k;
-            e = launch_walk(a, c->walk_cls[k], c->walk_cls_grid[k], c->walk_cls_smem[k], s,
-                            k == c->walk_ncls - 1);
+            e = launch_walk(a, c->walk_cls[k], c->walk_cls_grid[k], c->walk_cls_smem[k],
+                            k == c->walk_ncls - 1 ? s : c->side_stream, false);
         }
+        TC_CUDA(c, cudaEventRecord(c->ev_join, c->side_stream));
+        TC_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
     }
     if (e == cudaSuccess && deferred) {
         launch_band_eval(a, c->mlp_dev, c->gcorr, c->mlp_evals, s);
@@ -799,6 +815,9 @@ void tc_destroy(tc_ctx* c)
     if (c->info_h) cudaFreeHost(c->info_h);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 

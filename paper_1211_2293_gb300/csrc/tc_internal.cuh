@@ -245,7 +245,7 @@ struct WalkConfig {
     int tile;         // list tile entries: 64, 128 or 256
     int learned;      // 1: learned far-field correction (precise mode, no potential)
     int quadw;        // 1: accepted cells add their quadrupole term (precise mode)
-    int classes;      // 1: one launch per group size class, largest first; 0: one launch
+    int classes;      // 1: one launch per group size class (the smaller beside the largest); 0: one launch
     int split;        // 1: monopole walks on producer/consumer warp pairs (k_walk_ws)
 };
 // host-side preparation of the walk kernel's launch (attributes, occupancy);
