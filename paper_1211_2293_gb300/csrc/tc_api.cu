@@ -86,6 +86,7 @@ struct tc_ctx {
     int32_t* glist_n = nullptr;  // 3 counts, then the split's scratch
     int walk_ncls = 0;
     int depth_hint = -1;  // tree depth of the last build the host saw (-1: none)
+    int64_t depth_hint_n = -1;  // its body count
     WalkConfig walk_cls[3]{};
     int walk_cls_grid[3] = {0, 0, 0};
     size_t walk_cls_smem[3] = {0, 0, 0};
@@ -467,26 +468,28 @@ int setup_systems(tc_ctx* c, const int64_t* off, int nsys)
 // synced: validate the input and size the node table (one synchronisation);
 // otherwise no host interaction at all (the form captured in a step graph),
 // with the node count checked against the capacity on the device.
-int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
+int build_tree(tc_ctx* c, bool synced, cudaStream_t s, bool all_digits = false)
 {
     const int64_t n = c->n;
     cudaEvent_t t0 = phase_begin(c, s, 0);
     if (synced) TC_CUDA(c, cudaMemsetAsync(&c->info->err, 0, sizeof(int32_t), s));
     launch_bbox(c->pos, c->chunks, c->nchunks, c->sysp, c->nsys, &c->info->err, s);
     launch_keys(c->pos, c->mass, n, c->sys_of, c->sysp, c->keys, c->perm, &c->info->err, s);
-    // Inside a step the passes sort only the key digits of the levels down
-    // to the last synchronised build's depth + kSortMarginLevels; runs of
-    // equal top digits, a leaf's bodies as long as
-    // the tree is no deeper than that, are then completed one by one, which
-    // gives the full sort's order (a deeper tree gives longer runs, which
-    // the completion still orders, up to kSortRunMax bodies a run).  A
-    // synchronised build sorts every digit.
+    // The passes sort only the key digits of the levels down to the last
+    // synchronised build's depth + kSortMarginLevels; runs of equal top
+    // digits, a leaf's bodies as long as the tree is no deeper than that,
+    // are then completed one by one, which gives the full sort's order (a
+    // deeper tree gives longer runs, which the completion still orders: up
+    // to kSortRunMax bodies a run inside a step; in a synchronised build up
+    // to kSortRunMaxSynced, past which the build is redone sorting every
+    // digit).  With no earlier depth every digit is sorted.
     int low_bit = 0;
-    if (!synced && c->depth_hint >= 0) {
+    if (!all_digits && c->depth_hint >= 0 && (!synced || n == c->depth_hint_n)) {
         const int levels = std::min(kMaxLevel, c->depth_hint + kSortMarginLevels);
         low_bit = 63 - 3 * levels;
     }
-    radix_sort_u64(c->keys, c->perm, n, 63, c->sys_of, c->nsys > 1 ? sys_bits(c->nsys) : 0, c->sb, s, low_bit);
+    radix_sort_u64(c->keys, c->perm, n, 63, c->sys_of, c->nsys > 1 ? sys_bits(c->nsys) : 0, c->sb, s, low_bit,
+                   synced ? kSortRunMaxSynced : kSortRunMax);
     launch_gather(c->pos, c->mass, c->perm, n, c->body, s);
     TC_CUDA(c, cudaMemsetAsync(&c->info->depth, 0, sizeof(int32_t), s));
     launch_node_counts(c->keys, c->sys_of, n, c->leaf_max, c->w, c->delta, c->top, c->nstart, &c->info->depth, s);
@@ -494,6 +497,17 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
     int depth = -1;
     if (synced) {
         TC_CUDA(c, cudaGetLastError());
+        if (low_bit > 0) {
+            // a run too long for the completion: build again, sorting every digit
+            TC_CUDA(c, cudaStreamSynchronize(s));
+            int32_t err = 0;
+            TC_CUDA(c, cudaMemcpy(&err, &c->info->err, sizeof(err), cudaMemcpyDeviceToHost));
+            if (err & kErrSortRun) {
+                TC_CUDA(c, cudaMemsetAsync(&c->info->err, 0, sizeof(int32_t), s));
+                phase_end(c, 0, t0, s);
+                return build_tree(c, true, s, true);
+            }
+        }
         int r = check_device(c);  // synchronises; reports invalid input
         if (r) return r;
         uint32_t M32 = 0;
@@ -506,6 +520,7 @@ int build_tree(tc_ctx* c, bool synced, cudaStream_t s)
         TC_CUDA(c, cudaMemcpyAsync(&c->info->cap_m, &c->cap_m_h, sizeof(int64_t), cudaMemcpyHostToDevice, s));
         depth = c->info_h->depth;
         c->depth_hint = depth;
+        c->depth_hint_n = n;
     }
     launch_check_capacity(&c->totals[0], c->info, s);
     launch_emit_preorder(c->delta, c->nstart, c->prepos, n, c->info, c->pre_level, c->pre_first, c->iota, s);

@@ -122,11 +122,12 @@ int64_t scan_blocksum_size(int64_t n);
 // (8-bit digits from low_bit up), then every run of items with equal top bits (and
 // system) is put in (key, val) order by a per-run completion, so the
 // result is the same as the full sort's whenever the values are distinct
-// (the bodies' indices); a run longer than kSortRunMax raises kErrSortRun
-// and kErrCapacity instead.
-void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of,
-                    int sys_bits, SortBufs& b, cudaStream_t s, int low_bit = 0);
+// (the bodies' indices); a run longer than run_max (at most kSortRunMax)
+// raises kErrSortRun and kErrCapacity instead.
 constexpr int64_t kSortRunMax = 16384;
+void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of,
+                    int sys_bits, SortBufs& b, cudaStream_t s, int low_bit = 0, int64_t run_max = kSortRunMax);
+constexpr int64_t kSortRunMaxSynced = 1024;  // a synchronised build re-sorts every digit past this
 constexpr int kSortMarginLevels = 2;  // levels below the last synchronised depth a step's sort orders
 // The same for 32-bit keys when the item count is only known on the device:
 // n_cap bounds it, *n_dev (device) holds it.

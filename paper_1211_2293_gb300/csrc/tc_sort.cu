@@ -445,24 +445,24 @@ __global__ void __launch_bounds__(256) k_sort_long_runs(const uint64_t* __restri
                                                         int64_t n, int low_bit, const uint32_t* __restrict__ sys_of,
                                                         const int64_t* __restrict__ runs,
                                                         const unsigned long long* __restrict__ nruns, int64_t run_cap,
-                                                        int32_t* __restrict__ err)
+                                                        int64_t run_max, int32_t* __restrict__ err)
 {
     __shared__ long long en_sh;
     const int64_t nr = (int64_t)min(*nruns, (unsigned long long)run_cap);
     for (int64_t q = blockIdx.x; q < nr; q += gridDim.x) {
         const int64_t st = runs[q];
         // the run's end: the first item past st of another run (or n), or
-        // past kSortRunMax items
-        if (threadIdx.x == 0) en_sh = min(n, st + kSortRunMax + 1);
+        // past run_max items
+        if (threadIdx.x == 0) en_sh = min(n, st + run_max + 1);
         __syncthreads();
-        for (int64_t j = st + 1 + threadIdx.x; j < min(n, st + kSortRunMax + 1); j += blockDim.x) {
+        for (int64_t j = st + 1 + threadIdx.x; j < min(n, st + run_max + 1); j += blockDim.x) {
             if (j >= en_sh) break;
             if (!same_run(kin, vin, sys_of, low_bit, j, st)) atomicMin(&en_sh, (long long)j);
         }
         __syncthreads();
         const int64_t en = en_sh;
         __syncthreads();
-        if (en - st > kSortRunMax) {
+        if (en - st > run_max) {
             if (threadIdx.x == 0) atomicOr(err, kErrSortRun | kErrCapacity);
             continue;
         }
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256) k_sort_long_runs(const uint64_t* __restri
 }
 
 void launch_sort_runs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
-                      int low_bit, const uint32_t* sys_of, SortBufs& b, cudaStream_t s)
+                      int low_bit, const uint32_t* sys_of, SortBufs& b, cudaStream_t s, int64_t run_max)
 {
     cudaMemsetAsync(b.nruns, 0, sizeof(unsigned long long), s);
     int64_t g = (n + 255) / 256;
@@ -486,7 +486,7 @@ void launch_sort_runs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, 
     k_sort_runs<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(kin, vin, kout, vout, n, low_bit, sys_of, b.runs, b.nruns,
                                                           b.run_cap, b.err);
     k_sort_long_runs<<<(unsigned)(2 * sm_count()), 256, 0, s>>>(kin, vin, kout, vout, n, low_bit, sys_of, b.runs,
-                                                                b.nruns, b.run_cap, b.err);
+                                                                b.nruns, b.run_cap, run_max, b.err);
     count_launches(2);
 }
 
@@ -495,7 +495,7 @@ int64_t radix_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 template <typename K>
 static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n_dev, int nbits,
                             const uint32_t* sys_of, int sys_bits, SortBufs& b, K* keys_alt, cudaStream_t s,
-                            int low_bit = 0)
+                            int low_bit = 0, int64_t run_max = kSortRunMax)
 {
     const int nkey = (nbits - low_bit + 7) / 8;  // 8-bit digits from bit low_bit up
     const int nsys = (sys_bits + 7) / 8;
@@ -559,7 +559,7 @@ static void radix_sort_impl(K* keys, uint32_t* vals, int64_t n, const int64_t* n
         if (low_bit > 0) {
             // the runs of equal top bits into (key, val) order, from the
             // passes' result into the other buffer pair
-            launch_sort_runs(ka, va, kb, vb, n, low_bit, sys_bits > 0 ? sys_of : nullptr, b, s);
+            launch_sort_runs(ka, va, kb, vb, n, low_bit, sys_bits > 0 ? sys_of : nullptr, b, s, run_max);
             ka = kb;
             va = vb;
         }
@@ -595,10 +595,11 @@ cudaError_t sort_wait_selftest(uint64_t* keys, uint32_t* vals, uint64_t* kout, u
 int64_t sort_selftest_items() { return 2 * (int64_t)kSortTile; }
 
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int nbits, const uint32_t* sys_of, int sys_bits,
-                    SortBufs& b, cudaStream_t s, int low_bit)
+                    SortBufs& b, cudaStream_t s, int low_bit, int64_t run_max)
 {
     if (low_bit < 0 || low_bit >= nbits || (low_bit > 0 && (!b.runs || !b.nruns))) low_bit = 0;
-    radix_sort_impl<uint64_t>(keys, vals, n, nullptr, nbits, sys_of, sys_bits, b, b.keys_alt, s, low_bit);
+    if (run_max < 1 || run_max > kSortRunMax) run_max = kSortRunMax;
+    radix_sort_impl<uint64_t>(keys, vals, n, nullptr, nbits, sys_of, sys_bits, b, b.keys_alt, s, low_bit, run_max);
 }
 
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n_cap, const int64_t* n_dev, int nbits, SortBufs& b,

@@ -553,6 +553,25 @@ def test_step_sort_of_top_digits_gives_the_full_order(tc, kind, n, leaf):
     _compare_tree(ctx, t, 64)
 
 
+@pytest.mark.parametrize("cluster", [600, 5000])
+def test_synchronised_build_with_a_stale_depth_hint(tc, cluster):
+    """A synchronised build of a system of the same size as the last one
+    sorts the digits down to that one's depth + 2 and completes the runs;
+    a new system with a tight cluster gives long runs: completed in place up
+    to 1024 bodies (600), else the build is redone sorting every digit
+    (5000).  Either way the tree equals the oracle's full sort."""
+    n = 20000
+    p, _, m = _bodies("uniform", n, 51)
+    ctx = _ctx(tc, gmax=64)
+    ctx.build(_dev(p), _dev(m), 16)
+    ctx.sizes()
+    q = p.copy()
+    q[:cluster] = (0.3 + 1e-5 * np.random.default_rng(52).random((cluster, 3))).astype(np.float32)
+    ctx.build(_dev(q), _dev(m), 16)
+    t = oracle.Tree(q, m, 16)
+    _compare_tree(ctx, t, 64)
+
+
 def test_step_builds_a_deeper_tree_than_the_last_synchronised_one(tc):
     """A captured step knows the tree depth only from an earlier build; its
     moment reduction gives each level down to that depth + 2 a launch and
