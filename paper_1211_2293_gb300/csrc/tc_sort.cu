@@ -104,13 +104,23 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restric
     } else {
         off = bsum[blockIdx.x];
     }
-    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    // the tile through shared memory: coalesced loads and stores, each
+    // thread scanning kScanItems consecutive items (padded every 32 words,
+    // so the threads' strided reads hit distinct banks)
+    __shared__ uint32_t tile[kScanTile + kScanTile / 32];
+    auto pad = [](int p) { return p + (p >> 5); };
+    const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        const int p = i * kScanThreads + threadIdx.x;
+        tile[pad(p)] = t0 + p < n ? in[t0 + p] : 0u;
+    }
+    __syncthreads();
     uint32_t v[kScanItems];
     uint32_t s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
-        int64_t k = base + i;
-        v[i] = k < n ? in[k] : 0;
+        v[i] = tile[pad(threadIdx.x * kScanItems + i)];
         s += v[i];
     }
     uint32_t tot;
@@ -118,9 +128,14 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restric
     if (PREFIX && total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = off + tot;
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
-        int64_t k = base + i;
-        if (k < n) out[k] = e;
+        tile[pad(threadIdx.x * kScanItems + i)] = e;
         e += v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        const int p = i * kScanThreads + threadIdx.x;
+        if (t0 + p < n) out[t0 + p] = tile[pad(p)];
     }
 }
 
