@@ -1257,7 +1257,7 @@ def run_profile_case(args):
     the network after the walk (split 2: k_band_eval, the same random network,
     band 0.55, theta 0.667) on a 2^21-body sphere; walk_plummer: two plain
     force phases of the default line's plain path (2^22, theta 0.62);
-    walk_uniform: two force phases on the uniform cube (2^20, theta 0.5);
+    walk_uniform: two force phases on the uniform cube (2^20, or --n, theta 0.5);
     step_plummer: three captured steps of each path of the default line
     (plain at theta 0.62, learned with a seeded random network at 0.667,
     band 0.55) on its 2^22 sphere, for the launch list of a step;
@@ -1284,7 +1284,7 @@ def run_profile_case(args):
     P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
     if case in ("walk_plummer", "walk_uniform", "band") or (case == "fmm" and args.n != N_DEFAULT):
         if case == "walk_uniform":
-            p, _, m = inputs.uniform_cube(1 << 20, SEED)
+            p, _, m = inputs.uniform_cube(args.n if args.n != N_DEFAULT else 1 << 20, SEED)
         else:
             p, _, m = inputs.plummer({"fmm": args.n, "band": 1 << 21}.get(case, N_EVAL), seed=101)
         P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
