@@ -118,8 +118,9 @@ int tc_set_stream(tc_ctx *ctx, void *cuda_stream);
 /* Tree construction (Sec. 3.1): copies pos (n x 3) and mass (n), builds the
  * root cube, Morton keys (stable sort), the oct-tree with leaf threshold
  * leaf_max (a cube is divided while it holds more than leaf_max bodies,
- * down to level 21), the cells' masses and centres of mass (FP64 reduction)
- * and the body groups.  1 <= n < 2^31, 1 <= leaf_max <= 4096, masses > 0.
+ * down to level 21), the cells' masses and centres of mass (bottom-up sums
+ * as pairs of floats, FP64-class: within 1e-12 of the exact sums; results
+ * stored in FP64) and the body groups.  1 <= n < 2^31, 1 <= leaf_max <= 4096, masses > 0.
  * Velocities are reset to zero when n changes.  Synchronises with the
  * device part-way (to report invalid input and size the node table); the
  * rest is enqueued. */

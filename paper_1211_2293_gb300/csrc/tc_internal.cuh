@@ -75,7 +75,7 @@ struct NodeTables {
     float* quad;     // 6 per node, second moments about the COM (FP32)
     uint4* feat;     // 2 per node: the learned correction's cell-only features (eps/s, log2 count,
                      // M / M_sys, 6 moment ratios), normalised, as BF16 pairs (words 2..7 of a row)
-    double* mass64;  // FP64 bottom-up reduction results
+    double* mass64;  // the bottom-up reduction's results in FP64
     double* com64;   // 3 per node
     float4* dsum;    // 2 per node: the bottom-up sums {m, m x} as float pairs, hi parts then lo parts
 };
