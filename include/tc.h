@@ -56,7 +56,8 @@ typedef struct tc_ctx tc_ctx;
  *   stack     walk stack entries per warp (shared memory), 64..8192
  *   blocks_per_sm  0 = as many as fit, else a cap
  *   quad      1: also reduce the cells' second moments about the centre of
- *             mass (FP64; the learned correction's features, tc_get_nodes'
+ *             mass (FP32, within (leaf_max + 128) 2^-25 M s^2; the learned
+ *             correction's features and the quadrupole walk, tc_get_nodes'
  *             quad); 0: mass and centre of mass only
  *   tile      interaction-list entries summed per shared-memory tile: 64,
  *             128 or 256
