@@ -62,7 +62,8 @@ MLP_FLOPS_PER_EVAL = 2 * (16 * 64 + 64 * 64 + 64 * 8)  # one network row on the 
 FP32_LANES, SM_MAX_MHZ = 128, 2070.0
 # learned workload: training sphere, evaluation sphere, accuracy goal
 N_TRAIN, N_EVAL, SEED_TRAIN, SEED_EVAL = 1 << 20, 1 << 22, 100, 101
-THETA_TRAIN, BAND_TRAIN, BANDS, GOAL = 0.7, 0.4, (0.5, 0.55, 0.6, 0.65), 1e-3
+THETA_TRAIN, BAND_TRAIN, BANDS, GOAL = 0.7, 0.4, (0.5, 0.525, 0.55, 0.575, 0.6, 0.65), 1e-3
+TRAIN_SEEDS = (3, 4, 5)  # networks trained from these seeds; the training sphere picks one
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "walk_uniform_1m.txt")
 PROFILE_TRAFFIC_PLUMMER = os.path.join(ROOT, "profiles", "walk_plummer_4m.txt")
 WALK_SRC = [os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", f) for f in ("tc_walk.cuh", "tc_walk_ws.cuh")]
@@ -694,28 +695,45 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
     t0 = time.perf_counter()
     X, T, F, _, _ = ctx_tr.mlp_pairs(THETA_TRAIN, EPS, BAND_TRAIN, prob, 2, 2 * target)
     pairs_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    losses = ctx_tr.mlp_train(X, T, F, epochs=args.epochs, batch=1024, lr=2e-3, seed=3, band=BAND_TRAIN,
-                              factors=True)
-    train_s = time.perf_counter() - t0
-    model, _ = ctx_tr.mlp_get()
     npairs = int(len(X))
-    # ---- the band (the correction's one free parameter) chosen on the
-    # training sphere: each candidate at its own theta of RMS error 1e-3
-    # there, the fastest walk kept
+    # ---- the network and the band (the correction's one free parameter)
+    # chosen on the training sphere: a network trained from each of
+    # TRAIN_SEEDS, each band candidate at its own theta of RMS error 1e-3
+    # there, the (network, band) with the fastest walk kept.  The evaluation
+    # sphere never takes part in the choice.
     idx_tr = inputs.sample_indices(N_TRAIN, 4096, seed=1)
     ad_tr, _ = ctx_tr.direct(idx_tr, EPS)
-    ctx_tr.set_config(learned=1)
-    bands = []
-    for b in BANDS:
-        ctx_tr.mlp_set(model, b)
-        th, e = _iso_theta(ctx_tr, idx_tr, ad_tr, 0.4, 1.2)
-        if th is not None:
-            bands.append({"band": b, "theta": th, "rms_err": e, "walk_ms": _walk_median(ctx_tr, th)})
-    ctx_tr.set_config(learned=0)
+    trials = []
+    best = None
+    for tseed in TRAIN_SEEDS:
+        t0 = time.perf_counter()
+        losses_k = ctx_tr.mlp_train(X, T, F, epochs=args.epochs, batch=1024, lr=2e-3, seed=tseed, band=BAND_TRAIN,
+                                    factors=True)
+        train_k = time.perf_counter() - t0
+        model_k, _ = ctx_tr.mlp_get()
+        ctx_tr.set_config(learned=1)
+        bands_k = []
+        for b in BANDS:
+            ctx_tr.mlp_set(model_k, b)
+            th, e = _iso_theta(ctx_tr, idx_tr, ad_tr, 0.4, 1.2)
+            if th is not None:
+                bands_k.append({"band": b, "theta": th, "rms_err": e, "walk_ms": _walk_median(ctx_tr, th)})
+        ctx_tr.set_config(learned=0)
+        fast = min(bands_k, key=lambda r: r["walk_ms"]) if bands_k else None
+        trials.append({"seed": tseed, "loss_first": float(losses_k[0]), "loss_last": float(losses_k[-1]),
+                       "train_s": train_k, "bands": bands_k})
+        if fast is not None and (best is None or fast["walk_ms"] < best[0]["walk_ms"]):
+            best = (fast, tseed, model_k, losses_k, train_k, bands_k)
     th_tr_plain, e_tr_plain = _iso_theta(ctx_tr, idx_tr, ad_tr, 0.4, 1.0)
     plain_tr_ms = _walk_median(ctx_tr, th_tr_plain) if th_tr_plain is not None else None
-    band = min(bands, key=lambda r: r["walk_ms"])["band"] if bands else BANDS[0]
+    if best is None:  # no band reaches the goal: the first network at the first band
+        ctx_tr.mlp_train(X, T, F, epochs=args.epochs, batch=1024, lr=2e-3, seed=TRAIN_SEEDS[0], band=BAND_TRAIN,
+                         factors=True)
+        model, _ = ctx_tr.mlp_get()
+        band, train_seed, losses, train_s, bands = BANDS[0], TRAIN_SEEDS[0], np.zeros(1), 0.0, []
+    else:
+        band = best[0]["band"]
+        train_seed, model, losses, train_s, bands = best[1], best[2], best[3], best[4], best[5]
     ctx_tr.close()
     del X, T, F
 
@@ -885,9 +903,12 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
                     "vs_fp64_oracle": errL},
         "learned_over_plain": {"step": medP / medL, "step_per_rep_ratio": _spread(ratios),
                                "walk": statistics.median(wP) / statistics.median(wL)},
-        "band_selection_on_training_sphere": {"candidates": bands, "chosen": band,
+        "band_selection_on_training_sphere": {"candidates": bands, "chosen": band, "network_seed": train_seed,
                                               "plain": {"theta": th_tr_plain, "rms_err": e_tr_plain,
-                                                        "walk_ms": plain_tr_ms}},
+                                                        "walk_ms": plain_tr_ms},
+                                              "networks": [{k: v for k, v in t.items() if k != "bands"} |
+                                                           {"fastest": min((r["walk_ms"] for r in t["bands"]),
+                                                                           default=None)} for t in trials]},
         "training": {"pairs": npairs, "pair_prob": prob, "pairs_s": pairs_s,
                      "epochs": args.epochs, "batch": 1024, "lr": "2e-3, cosine decay",
                      "loss_weights": "F^2 / mean F^2 (acceleration error), formed in the library", "train_s": train_s,
