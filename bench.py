@@ -66,6 +66,7 @@ THETA_TRAIN, BAND_TRAIN, BANDS, GOAL = 0.7, 0.4, (0.5, 0.525, 0.55, 0.575, 0.6, 
 TRAIN_SEEDS = (3, 4, 5)  # networks trained from these seeds; the training sphere picks one
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "walk_uniform_1m.txt")
 PROFILE_TRAFFIC_PLUMMER = os.path.join(ROOT, "profiles", "walk_plummer_4m.txt")
+PROFILE_TRAFFIC_PLUMMER_ONEWARP = os.path.join(ROOT, "profiles", "walk_plummer_4m_onewarp.txt")
 WALK_SRC = [os.path.join(ROOT, "paper_1211_2293_gb300", "csrc", f) for f in ("tc_walk.cuh", "tc_walk_ws.cuh")]
 
 
@@ -173,10 +174,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile(shape=None, path=None):
+def _traffic_from_profile(shape=None, path=None, split=None):
     """dram bytes of one force phase (every launch of the walk) from the
     committed ncu summary, or None if the walk kernel's source changed since
-    it was captured or the summary's walk shape is not the one measured."""
+    it was captured or the summary's walk shape or walk variant (split) is
+    not the one measured."""
     try:
         txt = open(path or PROFILE_TRAFFIC).read()
         cur = walk_source_hash()
@@ -188,6 +190,8 @@ def _traffic_from_profile(shape=None, path=None):
         if kv.get("walk_source_sha256_16") != cur:
             return None
         if shape is not None and kv.get("walk_shape") != "%d,%d,%d" % (shape["gmax"], shape["tile"], shape["warps"]):
+            return None
+        if split is not None and kv.get("walk_split", "1") != str(split):
             return None
         return float(kv["dram_bytes_per_phase"])
     except Exception:
@@ -749,6 +753,15 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
     idx = inputs.sample_indices(n_ev, 4096, seed=1)
     ad, _ = ctxP.direct(idx, EPS)
     thP, eP = _iso_theta(ctxP, idx, ad, 0.4, 1.0)
+    # the plain path gets its faster walk on this sphere at its theta: the
+    # one-warp walk (split 0) or the producer/consumer walk (split 1); the
+    # lists are the same, the sums differ at rounding level
+    plain_walks = {}
+    for sp in (0, 1):
+        ctxP.set_config(split=sp)
+        plain_walks[sp] = _walk_median(ctxP, thP)
+    plain_split = min(plain_walks, key=plain_walks.get)
+    ctxP.set_config(split=plain_split)
     thL, eL = _iso_theta(ctxL, idx, ad, 0.4, 1.2)
     if thL is None:  # the correction cannot reach the goal at any theta >= 0.4: time it at the plain theta
         thL = thP
@@ -903,6 +916,8 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
                     "vs_fp64_oracle": errL},
         "learned_over_plain": {"step": medP / medL, "step_per_rep_ratio": _spread(ratios),
                                "walk": statistics.median(wP) / statistics.median(wL)},
+        "plain_walk_choice": {"walk_ms_split0_one_warp": plain_walks[0], "walk_ms_split1_producer_consumer":
+                              plain_walks[1], "chosen_split": plain_split},
         "band_selection_on_training_sphere": {"candidates": bands, "chosen": band, "network_seed": train_seed,
                                               "plain": {"theta": th_tr_plain, "rms_err": e_tr_plain,
                                                         "walk_ms": plain_tr_ms},
@@ -914,8 +929,11 @@ def run_learned_default(args, rank, world, local_rank, dist=None):
                      "loss_weights": "F^2 / mean F^2 (acceleration error), formed in the library", "train_s": train_s,
                      "loss_first": float(losses[0]), "loss_last": float(losses[-1])},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": _traffic_from_profile(shape, PROFILE_TRAFFIC_PLUMMER),
-                     "kernel": "k_walk, plain precise walk of the evaluation sphere at its 1e-3 theta (one force "
+                     "traffic": _traffic_from_profile(shape, PROFILE_TRAFFIC_PLUMMER if plain_split else
+                                                      PROFILE_TRAFFIC_PLUMMER_ONEWARP, split=plain_split),
+                     "kernel": ("k_walk_ws (producer/consumer warps)" if plain_split else
+                                "k_walk (one warp per group)") +
+                               ", plain precise walk of the evaluation sphere at its 1e-3 theta (one force "
                                "phase = one launch per group-size class)",
                      "peak_basis": f"2 flops x 128 FP32 lanes x {device_sms()} SMs x 2070 MHz (max SM clock); "
                                    "MEASURED_PEAKS.json has no FP32 figure",
@@ -1311,7 +1329,8 @@ def run_profile_case(args):
         P, M = torch.from_numpy(p).cuda(), torch.from_numpy(m).cuda()
         n = p.shape[0]
     if case in ("walk_plummer", "walk_uniform"):
-        ctx = tc.Context(precise=1, quad=0, want_pot=0, verify=0)
+        ctx = tc.Context(precise=1, quad=0, want_pot=0, verify=0,
+                         **({} if args.plain_split is None else {"split": args.plain_split}))
         ctx.build(P, M, LEAF)
         th = 0.62 if case == "walk_plummer" else THETA
         for _ in range(2):
@@ -1417,6 +1436,8 @@ def main():
                          "Plummer spheres; learned: the learned correction's sweep (bands, quadrupole, fixed theta)")
     ap.add_argument("--headline-only", action="store_true", help="default workload without the sub-keys")
     ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--plain-split", type=int, default=None, choices=[0, 1],
+                    help="tc_config.split of the walk_plummer / walk_uniform profile cases (default: the library's)")
     ap.add_argument("--learned-split", type=int, default=None, choices=[0, 1, 2],
                     help="tc_config.split of the learned path's contexts (default: the library's)")
     ap.add_argument("--theta-train", type=float, default=0.7, help="learned: theta of the walk generating the pairs")

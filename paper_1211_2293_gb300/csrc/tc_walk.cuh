@@ -706,11 +706,12 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             // band cells (s / d at or above the band, two bodies or more):
             // training pairs and learned corrections
             bool band = false;
-            if (acc && nb.y >= 2) {
+            const bool pairs_on = !LEARNED && a.pair_body != nullptr;  // pair emission runs a plain walk
+            if ((LEARNED || pairs_on) && acc && nb.y >= 2) {
                 const float sz = pow2_down(Lf, nb.w & 255, fast_side);
                 band = sz * sz >= a.band2 * band_e2;
             }
-            if (a.pair_body && band) {
+            if (pairs_on && band) {
                 const unsigned long long hh = mix64(a.pair_seed ^ (((unsigned long long)g << 32) | (unsigned)v));
                 if ((float)(hh >> 40) * (1.0f / 16777216.0f) < a.pair_prob) {
                     const unsigned long long k = atomicAdd(a.pair_count, 1ull);
@@ -722,20 +723,23 @@ __global__ void __launch_bounds__(128, LEARNED ? kLearnedMinBlocks : (B >= 4 ? 3
             }
             if (LEARNED) {
                 const unsigned bm = __ballot_sync(0xffffffffu, band);
-                if (band) pend[qn + __popc(bm & lt)] = (uint32_t)v;
-                qn += __popc(bm);
-                if (qn >= 32) {
+                if (bm) {
+                    if (band) pend[qn + __popc(bm & lt)] = (uint32_t)v;
+                    qn += __popc(bm);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        learned_rows(*mlp, pend, 32, rows, nt, rc, uf, Lf, inv_L, xgc, a.eps, inv_msys, a.G, corr,
+                                     lane);
+                        nevals += 32;
+                        // move the cells past the first 32 to the front (read all, then write)
+                        const int rest = qn - 32;
+                        const uint32_t t = lane < rest ? pend[32 + lane] : 0u;
+                        __syncwarp();
+                        if (lane < rest) pend[lane] = t;
+                        qn = rest;
+                    }
                     __syncwarp();
-                    learned_rows(*mlp, pend, 32, rows, nt, rc, uf, Lf, inv_L, xgc, a.eps, inv_msys, a.G, corr, lane);
-                    nevals += 32;
-                    // move the cells past the first 32 to the front (read all, then write)
-                    const int rest = qn - 32;
-                    const uint32_t t = lane < rest ? pend[32 + lane] : 0u;
-                    __syncwarp();
-                    if (lane < rest) pend[lane] = t;
-                    qn = rest;
                 }
-                __syncwarp();
             }
             // opened leaves -> body tile.  The bodies of all leaves opened in
             // this step are gathered 32 at a time: lane j takes body t of the
